@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: Cartesian FMM particles/s on one GB300 (and N replicas).
+
+Default workload: 1,000,000 point dipoles uniform in the unit cube, field only,
+p = 6, theta = 0.5, at most 128 particles per leaf, FP64.  One step is the
+whole path: Morton keys, radix sort, cells, dual-tree lists, derivative
+tables, P2M, M2M, M2L, L2L, L2P, P2P and the un-permute.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
+oracle on the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_12351_gb300 import synth  # noqa: E402
+
+METRIC = "FMM particles/sec at p=6 & rel err vs FP64 direct sum; served p50/p99 latency"
+UNIT = "particles/s"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+
+
+def flops_per_pair(s: int, want_phi: bool, want_field: bool) -> int:
+    """Algorithmic FP64 flops of one P2P pair (rsqrt counted as one op)."""
+    base = 3 + 5 + 1 + 2               # R, r^2, rsqrt, 1/r^2 and 1/r^3
+    if s == 0:
+        return base + (2 if want_phi else 0) + (7 if want_field else 0)
+    if s == 1:
+        return base + 5 + (2 if want_phi else 0) + (15 if want_field else 0)
+    return base + 1 + 15 + 5 + (4 if want_phi else 0) + (19 if want_field else 0)
+
+
+def m2l_macs_per_pair(s: int, p: int, want_phi: bool) -> int:
+    """Terms of L_n += D_{n+m} M_m kept by |n| + |m| <= p + s (n from 0 or 1)."""
+    tri = lambda k: (k + 1) * (k + 2) // 2
+    lo = 0 if want_phi else 1
+    return sum(tri(a) * sum(tri(b) for b in range(s, p + s - a + 1)) for a in range(lo, p + 1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w: dict, n_sample: int, seed_shift: int = 0):
+    """Time the oracle FMM on a bounded sample: the full tree and lists of the
+    workload, then the FMM result for n_sample particles (upward pass on all
+    cells, downward pass on their ancestor chains, L2P and P2P for them)."""
+    import oracle
+    pos, S = synth.make_system(w["n"], w["s"], w["dist"], w["seed"] + seed_shift)
+    tg = synth.sample_indices(w["n"], n_sample, 17)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, w["ncrit"])
+    tree.lists(w["theta"])
+    t1 = time.perf_counter()
+    tree.fmm(S, w["s"], w["p"], targets=tg)
+    t2 = time.perf_counter()
+    # tree and lists serve all N particles: charge the sample its share; the
+    # upward pass and the ancestors' M2L stay fully charged (a conservative CPU figure)
+    dt = (t2 - t1) + (t1 - t0) * len(tg) / w["n"]
+    return dt, len(tg), oracle.num_threads()
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    n_sample = args.oracle_sample
+    dt_w = []
+    for _ in range(args.warmup):
+        dt_w.append(oracle_sample(w, n_sample)[0])
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, k, cores = oracle_sample(w, n_sample)
+        times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = n_sample / (ms / 1e3)
+    sample = ("oracle FMM (C, FP64, OpenMP) on the full %d-particle tree and lists; FMM result for "
+              "%d sampled particles per step (full upward pass, downward pass on their ancestor "
+              "chains, L2P + P2P); value = sampled particles / step time" % (w["n"], n_sample))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, args),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, args):
+    return {"workload": args.workload, "n": w["n"], "source_order": w["s"], "p": w["p"],
+            "theta": w["theta"], "max_leaf": w["ncrit"], "distribution": w["dist"],
+            "outputs": "field" if not w.get("phi", False) else "potential+field",
+            "precision": "fp64", "l2": "flushed (256 MB write) between timed steps",
+            "replicas": args.gpus}
+
+
+def run_ours(args, w):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2005_12351_gb300 import fmm
+    s, p, theta, n = w["s"], w["p"], w["theta"], w["n"]
+    want_phi, want_field = bool(w.get("phi", False)), True
+    pos_np, S_np = synth.make_system(n, s, w["dist"], w["seed"] + 1000 * rank)
+    pos_h = torch.from_numpy(pos_np).pin_memory()
+    S_h = torch.from_numpy(S_np).pin_memory()
+    pos_d, S_d = pos_h.to(dev), S_h.to(dev)
+    E_d = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    phi_d = torch.empty(n, dtype=torch.float64, device=dev) if want_phi else None
+    E_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"])
+    tree.set_profiling(True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        tree.set_sources(pos_d, S_d, s)
+        tree.evaluate(p, theta, want_phi, want_field, potential=phi_d, field=E_d)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed steps (inputs resident in HBM)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phases = []
+    clk = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clk.start()
+    time.sleep(0.3)
+    launches0 = tree.launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phases.append(tree.phase_times())
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    launches = tree.launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
+    value = n * world / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pos_d.copy_(pos_h, non_blocking=True)
+        S_d.copy_(S_h, non_blocking=True)
+        step()
+        E_h.copy_(E_d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), world, dev)
+    h2d = pos_h.numel() * 8 + S_h.numel() * 8
+    d2h = E_h.numel() * 8
+
+    # ---- accuracy against the FP64 direct sum (GPU), sampled targets
+    tg = synth.sample_indices(n, args.err_samples, 23)
+    tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
+    _, E_ref = fmm.direct_sum(pos_d, S_d, s, targets=tg_d, want_potential=False)
+    Ef = E_d[tg_d.long()]
+    num = ((Ef - E_ref) ** 2).sum().item()
+    den = (E_ref ** 2).sum().item()
+    per = (torch.linalg.norm(Ef - E_ref, dim=1) / torch.linalg.norm(E_ref, dim=1)).cpu().numpy()
+    rel_err = {"field_rel_rms": math.sqrt(num / den), "field_rel_median": float(np.median(per)),
+               "field_rel_p99": float(np.quantile(per, 0.99)), "field_rel_max": float(per.max()),
+               "targets": int(len(tg)), "reference": "GPU FP64 direct sum (parity-tested vs oracle)"}
+
+    # ---- roofline of the dominant kernel (per-phase CUDA events on this stream)
+    info = tree.info()
+    ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
+    pair_flops = flops_per_pair(s, want_phi, want_field) * info["n_p2p_interactions"]
+    m2l_flops = 2 * m2l_macs_per_pair(s, p, want_phi) * info["n_m2l"]
+    fp64_peak = args.fp64_peak_tflops
+    cand = {"p2p": pair_flops, "m2l": m2l_flops}
+    dom = max(cand, key=lambda k: ph[k])
+    achieved = cand[dom] / (ph[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "algorithmic_flops": cand[dom], "peak_source": args.fp64_peak_source}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; %s)" % w["dist"],
+            "config": config_of(w, args), "rel_err": rel_err,
+            "e2e": {"value": n * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            "roofline": roofline, "phase_ms": ph, "clocks": clocks, "gpu_launches": launches,
+            "wall_s_timed": t_wall,
+            "tree": {k: info[k] for k in ("ncells", "nleaves", "nlevels", "n_m2l", "n_p2p",
+                                          "n_p2p_interactions", "n_doffsets")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, k, cores = oracle_sample(w, args.oracle_sample)
+        line["cpu_baseline"] = {
+            "value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle FMM on the full tree and lists, FMM result for %d sampled particles "
+                      "(full upward pass, ancestor-chain downward pass, L2P + P2P); %.1f s" % (k, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="dipole_1m_p6", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--err-samples", type=int, default=4096)
+    ap.add_argument("--oracle-sample", type=int, default=65536)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.259)
+    ap.add_argument("--fp64-peak-source", default="152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                    "(nominal 1.25 TFLOP/s FP64 of the part)")
+    args = ap.parse_args(argv)
+    w = dict(synth.WORKLOADS[args.workload])
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * fmm_gb300.h -- C ABI of the GB300 (sm_103a) Cartesian-Taylor fast multipole
+ * method for point sources of arbitrary order (Pepper & Fangohr, "fmmgen:
+ * Automatic Code Generation of Operators for Cartesian Fast Multipole and
+ * Barnes-Hut Methods", arXiv:2005.12351).
+ *
+ * What is computed (paper §2 and §3.2):
+ *   N point sources at positions x_j carry source moments S_{j,n}, |n| = s
+ *   (s = 0 charge, 1 dipole, 2 quadrupole; §2, the "source multipole"
+ *   before Eq. (5)).  Every source is also a target.  For each target i the
+ *   library returns
+ *       phi_i = sum_{j != i} sum_{|n|=s} S_{j,n} D_n(x_i - x_j),
+ *       E_i   = -grad phi_i,
+ *   where D_n(R) = grad^n (1/|R|) (kernel of §2, Eq. (1); no 4 pi eps0),
+ *   approximated by the Cartesian FMM of §3.2: octree with at most n_crit
+ *   particles per leaf, P2M/M2M upward, M2L over the dual-tree interaction
+ *   lists accepted by the MAC (r_A + r_B)/R < theta (§3.2, Eq. (13), r =
+ *   half the cell side), L2L downward, L2P and the P2P near field.
+ *
+ * Truncation: multipoles keep s <= |m| <= p+s, locals keep |n| <= p, and
+ * M2L keeps the terms with |n| + |m| <= p+s, so the derivative tensors of
+ * 1/r are needed up to order p+s.
+ *
+ * Moment layout and sign convention: moments are S_n exactly as in the
+ * paper, in graded-lexicographic order within |n| = s:
+ *   s = 0: q                      (phi = q / r)
+ *   s = 1: S_100, S_010, S_001    (phi = -S.R / r^3; a physical dipole mu
+ *                                  with phi = mu.R / r^3 is passed as S = -mu)
+ *   s = 2: S_200, S_110, S_101, S_020, S_011, S_002
+ *                                 (a quadrupole tensor Q is S_n = Q_n / n!,
+ *                                  i.e. Qxx/2, Qxy, Qxz, Qyy/2, Qyz, Qzz/2)
+ *
+ * Threading and streams: a tree handle is not thread-safe; use one handle
+ * per host thread.  All device work of a handle is issued on the stream
+ * given at creation, in order.  Calls return once the work is enqueued and
+ * the few host-visible sizes (cell and list counts) have been read, so a
+ * call may synchronise the stream internally; outputs are complete when the
+ * stream is synchronised.
+ *
+ * Errors: every call returns an fmm_status; nothing aborts and no kernel
+ * traps.  fmm_last_error() gives a message for the last failing call.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_tree fmm_tree;   /* opaque: owns all device state of one system */
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_EINVAL = -1,    /* bad argument (NULL, size, order, theta, non-finite input) */
+    FMM_ENOMEM = -2,    /* device allocation failed                                   */
+    FMM_EORDER = -3,    /* p or s outside the supported range                         */
+    FMM_ECUDA = -4,     /* a CUDA runtime call failed                                 */
+    FMM_ETIMEOUT = -5,  /* a bounded device wait gave up                              */
+    FMM_EBUDGET = -6,   /* the handle's device-memory budget would be exceeded        */
+    FMM_ESTATE = -7     /* call out of order (e.g. evaluate before set_sources)       */
+} fmm_status;
+
+typedef enum {
+    FMM_FP64 = 0,       /* every step in FP64                                         */
+    FMM_FP32 = 1,       /* mixed: FP32 pair and contraction arithmetic, FP64 elsewhere */
+    FMM_3XTF32 = 2      /* mixed: split-precision contraction, FP32 pair arithmetic   */
+} fmm_precision;
+
+/* Largest supported total order p + s (derivative tensors up to this order). */
+#define FMM_MAX_TOTAL_ORDER 12
+/* Largest supported source order s. */
+#define FMM_MAX_SOURCE_ORDER 2
+
+/*
+ * Create an empty system on CUDA device `device`.
+ *   cuda_stream : a cudaStream_t (NULL = the legacy default stream); the
+ *                 caller keeps it alive for the handle's lifetime.
+ *   max_leaf    : n_crit of §3.2: a cell is split while it holds more than
+ *                 max_leaf particles (and its level is below 21).  >= 1.
+ *   prec        : arithmetic of the P2P and M2L bulk work (fmm_precision).
+ *   mem_budget_bytes : upper bound on the device memory the handle may hold
+ *                 (0 = unlimited); exceeding it returns FMM_EBUDGET.
+ * On success *out owns the handle; release it with fmm_destroy.
+ */
+fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int max_leaf,
+                           fmm_precision prec, size_t mem_budget_bytes);
+
+/*
+ * Load N sources and build the octree (§3.2): Morton keys at depth 21,
+ * a stable radix sort by (key, original index), and the cells (level,
+ * range, integer coordinates, geometric centre, half side).
+ *   positions : DEVICE pointer, n x 3 doubles, row-major (x, y, z).
+ *   moments   : DEVICE pointer, n x T(s) doubles, T(s) = (s+1)(s+2)/2, row-
+ *               major, the S_n layout described above.  May be NULL iff n == 0.
+ *   n         : number of particles, 0 <= n < 2^31.
+ *   source_order : s in {0, 1, 2}.
+ * The library copies (and permutes) both arrays into its own buffers, so the
+ * caller may free or overwrite them once the stream has passed this call.
+ * Non-finite positions give FMM_EINVAL.  Invalidates cached lists.
+ */
+fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *moments,
+                           int64_t n, int source_order);
+
+/*
+ * Evaluate the FMM (§3.2 FMM traversal) at order p with opening angle theta.
+ *   p      : local expansion order, 0 <= p and p + s <= FMM_MAX_TOTAL_ORDER;
+ *            p >= 1 when want_field.
+ *   theta  : MAC parameter of Eq. (13), 0 < theta < 1 (checked: it must also
+ *            keep accepted offsets within +-2^18 finer half-cells).
+ *   potential : DEVICE pointer to n doubles, or NULL when !want_potential.
+ *   field     : DEVICE pointer to n x 3 doubles (E = -grad phi), or NULL when
+ *               !want_field.
+ * Outputs are in the caller's original particle order.  The interaction
+ * lists are rebuilt when theta differs from the cached value; the
+ * derivative tables when theta or p change.
+ */
+fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, int want_field,
+                        double *potential, double *field);
+
+/* Release all device memory of the handle.  NULL is accepted. */
+fmm_status fmm_destroy(fmm_tree *t);
+
+/* Static string for a status code. */
+const char *fmm_status_string(fmm_status s);
+
+/* Message of the last failing call on this handle ("" if none).  The pointer
+ * stays valid until the next call on the handle.  NULL handle: the message of
+ * the last failing fmm_create_tree on this host thread. */
+const char *fmm_last_error(const fmm_tree *t);
+
+/* ------------------------------------------------------------------------ */
+/* Introspection (tests, benchmarks).                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;              /* particles                                         */
+    int64_t ncells;         /* cells, breadth-first (level, Morton prefix) order */
+    int64_t nleaves;
+    int32_t nlevels;        /* deepest level + 1                                 */
+    int32_t source_order;
+    int64_t n_m2l;          /* M2L pairs in the cached lists (0 if none)          */
+    int64_t n_p2p;          /* P2P leaf pairs in the cached lists                 */
+    int64_t n_p2p_interactions; /* sum over P2P pairs of n_target * n_source      */
+    int64_t n_doffsets;     /* distinct M2L offsets (rows of the D table)         */
+    double theta;           /* theta of the cached lists (0 if none)             */
+    double lo[3];           /* root box corner                                   */
+    double side;            /* root box side (a power of two)                    */
+    int64_t device_bytes;   /* device memory held by the handle                  */
+} fmm_tree_info;
+
+fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
+
+/* Identifiers for fmm_copy_array.  Element types and counts:
+ *   FMM_ARR_KEYS        uint64 [n]   Morton keys in sorted order
+ *   FMM_ARR_PERM        int32  [n]   perm[k] = original index of sorted slot k
+ *   FMM_ARR_CELL_LEVEL  int32  [ncells]
+ *   FMM_ARR_CELL_COORD  int32  [ncells x 3] integer cell coordinates
+ *   FMM_ARR_CELL_RANGE  int32  [ncells x 2] sorted-particle range [begin, end)
+ *   FMM_ARR_CELL_PARENT int32  [ncells] (-1 for the root)
+ *   FMM_ARR_CELL_CHILD  int32  [ncells x 2] (first child or -1, child count)
+ *   FMM_ARR_CELL_CENTRE double [ncells x 3]
+ *   FMM_ARR_CELL_HALF   double [ncells]   half side
+ *   FMM_ARR_M2L         int32  [n_m2l x 2] (target, source), sorted
+ *   FMM_ARR_P2P         int32  [n_p2p x 2] (target, source), sorted
+ *   FMM_ARR_MULTIPOLE   double [ncells x n_M] M of the last evaluate
+ *   FMM_ARR_LOCAL       double [ncells x n_L] L of the last evaluate
+ */
+typedef enum {
+    FMM_ARR_KEYS = 0, FMM_ARR_PERM, FMM_ARR_CELL_LEVEL, FMM_ARR_CELL_COORD,
+    FMM_ARR_CELL_RANGE, FMM_ARR_CELL_PARENT, FMM_ARR_CELL_CHILD, FMM_ARR_CELL_CENTRE,
+    FMM_ARR_CELL_HALF, FMM_ARR_M2L, FMM_ARR_P2P, FMM_ARR_MULTIPOLE, FMM_ARR_LOCAL
+} fmm_array;
+
+/* Copy one internal array into a HOST buffer of `bytes` bytes (synchronous).
+ * FMM_EINVAL if the buffer is too small; *written receives the byte count. */
+fmm_status fmm_copy_array(const fmm_tree *t, fmm_array which, void *host_dst, size_t bytes,
+                          size_t *written);
+
+/* Per-phase device times of the last evaluate (milliseconds, CUDA events on
+ * the handle's stream) when profiling is on.  Phases, in order:
+ *   0 keys+bbox, 1 sort, 2 cells, 3 lists, 4 D tables, 5 P2M, 6 M2M,
+ *   7 M2L, 8 L2L, 9 L2P, 10 P2P (incl. un-permute)
+ * Phases 0-2 belong to fmm_set_sources, 3-10 to fmm_evaluate. */
+#define FMM_NUM_PHASES 11
+fmm_status fmm_set_profiling(fmm_tree *t, int enable);
+fmm_status fmm_get_phase_times(const fmm_tree *t, float *ms_out /* FMM_NUM_PHASES */);
+
+/* Number of kernels this handle has launched since creation. */
+int64_t fmm_launch_count(const fmm_tree *t);
+
+/* ------------------------------------------------------------------------ */
+/* Reference evaluation on the GPU.                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * FP64 direct sum (the plain definition above, no tree) at selected targets:
+ *   positions/moments : DEVICE, as for fmm_set_sources;
+ *   targets   : DEVICE int32 [n_targets] original indices, or NULL for all n;
+ *   potential : DEVICE double [n_targets] or NULL; field: DEVICE [n_targets x 3]
+ *               or NULL.
+ * Enqueued on cuda_stream; no allocation.
+ */
+fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const double *moments,
+                          int64_t n, int source_order, const int32_t *targets, int64_t n_targets,
+                          double *potential, double *field);
+
+/*
+ * Morton order of a point set (the first two steps of fmm_set_sources as a
+ * standalone call): the root box of fmm_set_sources, 63-bit keys at depth 21,
+ * and a stable sort by (key, original index).
+ *   positions : DEVICE n x 3 doubles.
+ *   keys_out  : DEVICE uint64 [n], keys in sorted order.
+ *   perm_out  : DEVICE int32 [n], perm_out[k] = original index of slot k.
+ * Allocates its scratch (about 24 bytes per point) with cudaMalloc and frees
+ * it before returning; synchronises cuda_stream.
+ */
+fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
+                            uint64_t *keys_out, int32_t *perm_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

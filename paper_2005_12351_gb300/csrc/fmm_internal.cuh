@@ -1,0 +1,169 @@
+// fmm_internal.cuh -- shared declarations of the sm_103a FMM library.
+//
+// Layout in device memory (one system):
+//   particles, Morton-sorted: px/py/pz [n] f64 (SoA), S [n x nS] f64, perm [n] i32
+//   cells, breadth-first:     level/parent/child_first/nchild/begin/end/cx,cy,cz (i32)
+//                             centre [ncells x 3] f64, half [ncells] f64
+//   expansions:               M [ncells x nM] f64, L [ncells x nL] f64 (row per cell)
+//   lists (CSR by target):    m2l_src/m2l_didx [n_m2l], m2l_off [ncells+1]
+//                             p2p_src [n_p2p], p2p_off [ncells+1]
+//   derivative tables:        D [n_doffsets x ntot(p+s)] f64
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmm_gb300.h"
+
+namespace fmm {
+
+constexpr int kLevels = 21;            // key depth: 3 x 21 = 63 bits
+constexpr int kMaxOrder = 16;          // multi-index tables cover |n| <= 16
+constexpr int kMaxTot = 969;           // ntot(16)
+constexpr int kKeyBias = 1 << 18;      // D-table key: offsets in [-2^18, 2^18)
+
+// device error word bits
+constexpr int kErrNonFinite = 1;
+constexpr int kErrKeyRange = 2;
+constexpr int kErrHashFull = 4;
+
+inline int ntot(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
+inline int nshell(int k) { return (k + 1) * (k + 2) / 2; }
+
+// Multi-index enumeration of the library (graded lexicographic, §3.1 of the
+// paper): shell by shell; inside a shell, by increasing ny + nz, then by
+// increasing nz.  Built once by enumeration into a lookup cube.
+struct MultiIndex {
+    int nx[kMaxTot], ny[kMaxTot], nz[kMaxTot];
+    int16_t lut[kMaxOrder + 1][kMaxOrder + 1][kMaxOrder + 1];
+    MultiIndex();
+    int operator()(int x, int y, int z) const { return lut[x][y][z]; }
+};
+const MultiIndex &multi_index();
+
+// Host-built operator tables for one (s, p) pair, uploaded once per change.
+struct OpTables {
+    int s = -1, p = -1, n_lo = -1;
+    int nS = 0, nM = 0, nL = 0, nD = 0, m0 = 0;
+    // P2M: for each m (0..nM), up to nS terms (a, mono index of m - a); -1 = none
+    std::vector<int> p2m_terms;          // [nM x nS] mono index or -1
+    // monomial recurrences: mono[k] = mono[par[k]] * d[axis[k]] / k_axis
+    std::vector<int> mono_par, mono_axis, mono_pow;   // [ntot(P)]
+    // M2M: CSR over outputs n (M storage), terms (mono k, M index q)
+    std::vector<int> m2m_off, m2m_k, m2m_q;
+    // L2L: CSR over outputs n (L storage), terms (mono k, L index n+k)
+    std::vector<int> l2l_off, l2l_k, l2l_q;
+    // L2P gradient: for |k| <= p-1, L index of k + e_d (3 per k)
+    std::vector<int> l2p_grad;
+    // M2L: per-thread term lists (slot-major) and the partial-sum reduction map
+    int m2l_threads = 0, m2l_T = 0, m2l_slots = 0;
+    std::vector<uint32_t> m2l_desc;      // [T x threads]
+    std::vector<int> m2l_red_off, m2l_red_src;   // CSR over n: partial slot ids
+};
+void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads);
+
+}  // namespace fmm
+
+// ---------------------------------------------------------------------------
+// The handle.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct fmm_tree {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int max_leaf = 64;
+    fmm_precision prec = FMM_FP64;
+    size_t budget = 0;
+    size_t held = 0;
+    std::string err;
+    int64_t launches = 0;
+
+    // system
+    int64_t n = 0;
+    int s = -1, nS = 0;
+    bool have_sources = false;
+    int64_t ncells = 0, nleaves = 0;
+    int nlevels = 0;
+    std::vector<int> level_begin;          // host copy, nlevels + 1
+    double lo[3] = {0, 0, 0}, side = 1.0;
+
+    // lists
+    double theta = 0.0;
+    bool have_lists = false;
+    int64_t n_m2l = 0, n_p2p = 0, n_p2p_inter = 0, n_doff = 0;
+    size_t m2l_cap_hint = 0;
+    // D tables / operator tables
+    int d_p = -1;                          // p the D table was built for
+    fmm::OpTables tab;
+    int tab_key_s = -1, tab_key_p = -1, tab_key_nlo = -1;
+    int64_t m_cells = 0;                   // rows of the M/L buffers as sized
+
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[fmm::kLevels + 16];
+    bool ev_made = false;
+    float phase_ms[FMM_NUM_PHASES];
+
+    // device buffers (all owned)
+    DevBuf b_err, b_box;
+    DevBuf b_keys, b_keys2, b_idx, b_idx2, b_hist;
+    DevBuf b_px, b_py, b_pz, b_S, b_perm;
+    DevBuf b_level, b_parent, b_child, b_nchild, b_begin, b_end, b_cx, b_cy, b_cz;
+    DevBuf b_centre, b_half, b_leaves;
+    DevBuf b_flags, b_scan, b_scan_tmp;
+    DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;
+    DevBuf b_m2l_src, b_m2l_off, b_m2l_didx, b_p2p_src, b_p2p_off, b_lkeys, b_lkeys2, b_lval, b_lval2;
+    DevBuf b_hash, b_dkeys, b_D;
+    DevBuf b_M, b_L, b_phi, b_E;
+    DevBuf b_tab_i32, b_tab_u32;
+};
+
+// ---------------------------------------------------------------------------
+// Internal host API (implemented in the .cu files; all enqueue on `st`).
+// ---------------------------------------------------------------------------
+namespace fmm {
+
+fmm_status ensure(fmm_tree *t, DevBuf &b, size_t bytes);
+void release(fmm_tree *t, DevBuf &b);
+fmm_status cuda_check(fmm_tree *t, cudaError_t e, const char *what);
+
+// primitives.cu
+size_t scan_scratch_bytes(int64_t n);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
+                        cudaStream_t st, int64_t *launches);
+size_t radix_hist_bytes(int64_t n);
+// Stable LSD radix sort of (key, value) pairs on bits [0, end_bit).  The
+// result ends in (keys, vals); (keys2, vals2) are scratch of the same size.
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
+                      int end_bit, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t st,
+                      int64_t *launches);
+
+// tree.cu
+fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom);
+fmm_status build_lists(fmm_tree *t, double theta);
+fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
+                            uint32_t *idx, uint64_t *keys2, uint32_t *idx2, uint32_t *hist,
+                            uint32_t *scan_scratch, unsigned long long *box_scratch,
+                            double *box_out, int *err, int64_t *launches);
+
+// operators.cu
+fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field);
+// p2p.cu
+fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
+void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
+                   const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches);
+
+}  // namespace fmm
+
+#define FMM_TRY(expr)                         \
+    do {                                      \
+        fmm_status _st = (expr);              \
+        if (_st != FMM_OK) return _st;        \
+    } while (0)

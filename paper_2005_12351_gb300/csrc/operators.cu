@@ -1,0 +1,597 @@
+// operators.cu -- derivative tables and the expansion operators (FP64).
+//
+// Conventions (paper §2, read as stated in the header):
+//   P2M  M_m(z)   = sum_j sum_{|a|=s, a<=m} (z - x_j)^(m-a)/(m-a)! S_{j,a}   (Eq. (5))
+//   M2M  M_n(z')  = sum_{k<=n} (z' - z)^k/k! M_{n-k}(z)                        (Eq. (4))
+//   M2L  L_n(zt)  = sum_{m, |n|+|m|<=p+s} D_{n+m}(zt - zs) M_m(zs)            (Eq. (8))
+//   L2L  L_n(z')  = sum_{|n+k|<=p} (z' - z)^k/k! L_{n+k}(z)
+//   L2P  phi = sum_n (x-z)^n/n! L_n,  d_k phi = sum_{n>=e_k} (x-z)^(n-e_k)/(n-e_k)! L_n
+//                                                                             (Eqs. (9), (10))
+// D_n(R) = grad^n (1/|R|) is generated once per distinct M2L offset.
+#include <algorithm>
+#include <cstring>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+MultiIndex::MultiIndex()
+{
+    std::memset(lut, 0xff, sizeof(lut));
+    int i = 0;
+    for (int k = 0; k <= kMaxOrder; ++k)
+        for (int a = 0; a <= k; ++a)          // a = ny + nz
+            for (int z = 0; z <= a; ++z) {
+                nx[i] = k - a; ny[i] = a - z; nz[i] = z;
+                lut[k - a][a - z][z] = (int16_t)i;
+                ++i;
+            }
+}
+
+const MultiIndex &multi_index()
+{
+    static MultiIndex mi;
+    return mi;
+}
+
+void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads)
+{
+    const MultiIndex &I = multi_index();
+    T.s = s; T.p = p; T.n_lo = n_lo;
+    T.nS = nshell(s); T.m0 = ntot(s - 1); T.nM = ntot(p + s) - T.m0; T.nL = ntot(p);
+    T.nD = ntot(p + s);
+    const int nK = ntot(p);                   // shift / particle monomials |k| <= p
+
+    T.p2m_terms.assign((size_t)T.nM * T.nS, -1);
+    for (int mi = 0; mi < T.nM; ++mi) {
+        const int m = mi + T.m0;
+        for (int ai = 0; ai < T.nS; ++ai) {
+            const int a = ai + T.m0;
+            int kx = I.nx[m] - I.nx[a], ky = I.ny[m] - I.ny[a], kz = I.nz[m] - I.nz[a];
+            if (kx >= 0 && ky >= 0 && kz >= 0) T.p2m_terms[(size_t)mi * T.nS + ai] = I(kx, ky, kz);
+        }
+    }
+    T.mono_par.assign(nK, 0); T.mono_axis.assign(nK, 0); T.mono_pow.assign(nK, 0);
+
+    T.m2m_off.assign(1, 0); T.m2m_k.clear(); T.m2m_q.clear();
+    for (int ni = 0; ni < T.nM; ++ni) {
+        const int n = ni + T.m0;
+        for (int qi = 0; qi < T.nM; ++qi) {
+            const int q = qi + T.m0;
+            int kx = I.nx[n] - I.nx[q], ky = I.ny[n] - I.ny[q], kz = I.nz[n] - I.nz[q];
+            if (kx < 0 || ky < 0 || kz < 0) continue;
+            T.m2m_k.push_back(I(kx, ky, kz));
+            T.m2m_q.push_back(qi);
+        }
+        T.m2m_off.push_back((int)T.m2m_k.size());
+    }
+    T.l2l_off.assign(1, 0); T.l2l_k.clear(); T.l2l_q.clear();
+    for (int n = 0; n < T.nL; ++n) {
+        for (int k = 0; k < nK; ++k) {
+            int qx = I.nx[n] + I.nx[k], qy = I.ny[n] + I.ny[k], qz = I.nz[n] + I.nz[k];
+            if (qx + qy + qz > p) continue;
+            T.l2l_k.push_back(k);
+            T.l2l_q.push_back(I(qx, qy, qz));
+        }
+        T.l2l_off.push_back((int)T.l2l_k.size());
+    }
+    const int nG = ntot(p - 1);
+    T.l2p_grad.assign((size_t)3 * std::max(nG, 0), 0);
+    for (int k = 0; k < nG; ++k) {
+        T.l2p_grad[3 * k + 0] = I(I.nx[k] + 1, I.ny[k], I.nz[k]);
+        T.l2p_grad[3 * k + 1] = I(I.nx[k], I.ny[k] + 1, I.nz[k]);
+        T.l2p_grad[3 * k + 2] = I(I.nx[k], I.ny[k], I.nz[k] + 1);
+    }
+
+    // ---- M2L: flat (n, m) term list in n order, cut into equal per-thread
+    // chunks; each maximal same-n run inside a chunk owns one partial slot.
+    struct Term { int n, m, d; };
+    std::vector<Term> terms;
+    for (int n = 0; n < T.nL; ++n) {
+        const int kn = I.nx[n] + I.ny[n] + I.nz[n];
+        if (kn < n_lo) continue;
+        for (int mi = 0; mi < T.nM; ++mi) {
+            const int m = mi + T.m0;
+            if (kn + I.nx[m] + I.ny[m] + I.nz[m] > p + s) continue;
+            terms.push_back({n, mi, I(I.nx[n] + I.nx[m], I.ny[n] + I.ny[m], I.nz[n] + I.nz[m])});
+        }
+    }
+    const int W = (int)terms.size(), Tn = m2l_threads;
+    const int cap = std::max(1, (W + Tn - 1) / Tn);
+    T.m2l_threads = Tn; T.m2l_T = cap;
+    T.m2l_desc.assign((size_t)cap * Tn, 0xffffffffu);
+    std::vector<std::vector<int>> red(T.nL);
+    int max_slots = 0;
+    for (int j = 0; j < Tn; ++j) {
+        const int b = j * cap, e = std::min(W, b + cap);
+        int slot = -1;
+        for (int i = b; i < e; ++i) {
+            if (i == b || terms[i].n != terms[i - 1].n) {
+                ++slot;
+                red[terms[i].n].push_back(slot * Tn + j);
+            }
+            const bool flush = (i + 1 == e) || terms[i + 1].n != terms[i].n;
+            T.m2l_desc[(size_t)(i - b) * Tn + j] =
+                (uint32_t)terms[i].m | ((uint32_t)terms[i].d << 9) | ((uint32_t)flush << 18) |
+                ((uint32_t)slot << 19);
+        }
+        max_slots = std::max(max_slots, slot + 1);
+    }
+    T.m2l_slots = max_slots;
+    T.m2l_red_off.assign(1, 0); T.m2l_red_src.clear();
+    for (int n = 0; n < T.nL; ++n) {
+        for (int v : red[n]) T.m2l_red_src.push_back(v);
+        T.m2l_red_off.push_back((int)T.m2l_red_src.size());
+    }
+}
+
+namespace {
+
+constexpr int kM2LThreads = 128;
+constexpr int kM2LBatch = 16;
+
+__constant__ int8_t c_nx[kMaxTot], c_ny[kMaxTot], c_nz[kMaxTot];
+
+// Device views of the uploaded tables.
+struct DevTables {
+    int s, p, n_lo, nS, nM, nL, nD, m0, nK, nG;
+    const int *p2m_terms;
+    const int *m2m_off, *m2m_k, *m2m_q;
+    const int *l2l_off, *l2l_k, *l2l_q;
+    const int *l2p_grad;
+    const int *m2l_red_off, *m2l_red_src;
+    const uint32_t *m2l_desc;
+    int m2l_T, m2l_slots;
+};
+
+// ---------------------------------------------------- derivative tables
+// r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
+//           - sum_{j != i} [ 2 n_j R_j D_{n-e_j} + n_j (n_j - 1) D_{n-2e_j} ],
+// i = first axis with n_i >= 1 (Leibniz' rule on r^2 d_i(1/r) = -R_i / r).
+__global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, double side, int nD,
+                          const int32_t *lut, double *D)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= ndoff) return;
+    const uint64_t key = dkeys[r];
+    const int lf = (int)(key >> 57);
+    const double unit = ldexp(side, -(lf + 1));
+    double R[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        R[i] = (double)((long long)((key >> (38 - 19 * i)) & 0x7ffffull) - kKeyBias) * unit;
+    double *Dr = D + r * nD;
+    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    const double inv_r2 = 1.0 / r2;
+    Dr[0] = rsqrt(r2);
+    const int L = kMaxOrder + 1;
+    for (int idx = 1; idx < nD; ++idx) {
+        const int n[3] = {c_nx[idx], c_ny[idx], c_nz[idx]};
+        const int i = n[0] ? 0 : (n[1] ? 1 : 2);
+        int m[3] = {n[0], n[1], n[2]};
+        m[i] -= 1;
+        double acc = -(2.0 * n[i] - 1.0) * R[i] * Dr[lut[(m[0] * L + m[1]) * L + m[2]]];
+        if (n[i] >= 2) {
+            int q[3] = {m[0], m[1], m[2]};
+            q[i] -= 1;
+            acc -= (double)((n[i] - 1) * (n[i] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j == i || n[j] == 0) continue;
+            int q[3] = {n[0], n[1], n[2]};
+            q[j] -= 1;
+            acc -= 2.0 * n[j] * R[j] * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+            if (n[j] >= 2) {
+                q[j] -= 1;
+                acc -= (double)(n[j] * (n[j] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+            }
+        }
+        Dr[idx] = acc * inv_r2;
+    }
+}
+
+// per-axis scaled powers d^j / j!, j <= P, then monomials d^k / k! = ax[kx] ay[ky] az[kz]
+__device__ __forceinline__ void axis_powers(double d, int P, double *out)
+{
+    double v = 1.0;
+    out[0] = 1.0;
+    for (int j = 1; j <= P; ++j) {
+        v = v * d / (double)j;
+        out[j] = v;
+    }
+}
+
+// ------------------------------------------------------------------ P2M
+constexpr int kP2MThreads = 128;
+constexpr int kP2MChunk = 16;
+constexpr int kP2MPer = 4;                // up to 4 * 128 = 512 M components
+
+__global__ void __launch_bounds__(kP2MThreads)
+k_p2m(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
+      const double *px, const double *py, const double *pz, const double *S, DevTables tb,
+      double *M)
+{
+    extern __shared__ double sm[];
+    const int P = tb.p, nK = tb.nK;
+    double *apow = sm;                                  // [chunk][3][P+1]
+    double *mono = apow + kP2MChunk * 3 * (P + 1);      // [chunk][nK]
+    double *Ssm = mono + kP2MChunk * nK;                // [chunk][nS]
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c];
+    const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
+    double acc[kP2MPer];
+#pragma unroll
+    for (int u = 0; u < kP2MPer; ++u) acc[u] = 0.0;
+    for (int j0 = b; j0 < e; j0 += kP2MChunk) {
+        const int nj = min(kP2MChunk, e - j0);
+        for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
+            const int j = t / 3, ax = t % 3;
+            const double x = ax == 0 ? px[j0 + j] : (ax == 1 ? py[j0 + j] : pz[j0 + j]);
+            const double zc = ax == 0 ? z0 : (ax == 1 ? z1 : z2);
+            axis_powers(zc - x, P, apow + (j * 3 + ax) * (P + 1));
+        }
+        for (int t = threadIdx.x; t < nj * tb.nS; t += blockDim.x)
+            Ssm[t] = S[(int64_t)j0 * tb.nS + t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < nj * nK; t += blockDim.x) {
+            const int j = t / nK, k = t % nK;
+            const double *a = apow + j * 3 * (P + 1);
+            mono[t] = a[c_nx[k]] * a[(P + 1) + c_ny[k]] * a[2 * (P + 1) + c_nz[k]];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kP2MPer; ++u) {
+            const int mi = threadIdx.x + u * kP2MThreads;
+            if (mi >= tb.nM) break;
+            for (int j = 0; j < nj; ++j)
+                for (int a = 0; a < tb.nS; ++a) {
+                    const int k = tb.p2m_terms[mi * tb.nS + a];
+                    if (k >= 0) acc[u] = fma(mono[j * nK + k], Ssm[j * tb.nS + a], acc[u]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kP2MPer; ++u) {
+        const int mi = threadIdx.x + u * kP2MThreads;
+        if (mi < tb.nM) M[(int64_t)c * tb.nM + mi] = acc[u];
+    }
+}
+
+// ------------------------------------------------------------------ M2M
+// One block per parent cell of one level.
+__global__ void __launch_bounds__(128)
+k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre, DevTables tb,
+      double *M)
+{
+    extern __shared__ double sm[];
+    const int P = tb.p, nK = tb.nK;
+    double *apow = sm;                  // [3][P+1]
+    double *mono = apow + 3 * (P + 1);  // [nK]
+    double *Mc = mono + nK;             // [nM]
+    const int c = lb + blockIdx.x;
+    const int nch = nchild[c];
+    if (nch == 0) return;
+    double acc[kP2MPer];
+#pragma unroll
+    for (int u = 0; u < kP2MPer; ++u) acc[u] = 0.0;
+    for (int i = 0; i < nch; ++i) {
+        const int ch = child[c] + i;
+        if (threadIdx.x < 3)
+            axis_powers(centre[3 * c + threadIdx.x] - centre[3 * ch + threadIdx.x], P,
+                        apow + threadIdx.x * (P + 1));
+        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * tb.nM + t];
+        __syncthreads();
+        for (int k = threadIdx.x; k < nK; k += blockDim.x)
+            mono[k] = apow[c_nx[k]] * apow[(P + 1) + c_ny[k]] * apow[2 * (P + 1) + c_nz[k]];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kP2MPer; ++u) {
+            const int ni = threadIdx.x + u * 128;
+            if (ni >= tb.nM) break;
+            for (int q = tb.m2m_off[ni]; q < tb.m2m_off[ni + 1]; ++q)
+                acc[u] = fma(mono[tb.m2m_k[q]], Mc[tb.m2m_q[q]], acc[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kP2MPer; ++u) {
+        const int ni = threadIdx.x + u * 128;
+        if (ni < tb.nM) M[(int64_t)c * tb.nM + ni] = acc[u];
+    }
+}
+
+// ------------------------------------------------------------------ M2L
+// One block per target cell.  Sources are taken kM2LBatch at a time: their
+// multipoles and derivative-table rows are staged in shared memory, then
+// each thread walks its fixed chunk of (n, m) terms, accumulating
+// D_{n+m} M_m over the staged sources, and flushes each finished n-run to its
+// partial slot.  Partials are summed per n in a fixed order at the end.
+__global__ void __launch_bounds__(kM2LThreads)
+k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const double *M,
+      const double *D, DevTables tb, double *L)
+{
+    extern __shared__ double sm[];
+    const int c = blockIdx.x;
+    const int b = off[c], e = off[c + 1];
+    if (b == e) return;
+    const int nM = tb.nM, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
+    const int ldM = nM | 1, ldD = nD | 1;              // odd strides spread banks
+    double *Msm = sm;                                  // [batch][ldM]
+    double *Dsm = Msm + kM2LBatch * ldM;               // [batch][ldD]
+    double *part = Dsm + kM2LBatch * ldD;              // [slots][Tn]
+    uint32_t *desc = (uint32_t *)(part + tb.m2l_slots * Tn);   // [T][Tn]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < T * Tn; i += Tn) desc[i] = tb.m2l_desc[i];
+    for (int i = tid; i < tb.m2l_slots * Tn; i += Tn) part[i] = 0.0;
+    for (int k0 = b; k0 < e; k0 += kM2LBatch) {
+        const int kb = min(kM2LBatch, e - k0);
+        __syncthreads();
+        for (int i = tid; i < kb * nM; i += Tn) {
+            const int k = i / nM, m = i % nM;
+            Msm[k * ldM + m] = M[(int64_t)src[k0 + k] * nM + m];
+        }
+        for (int i = tid; i < kb * nD; i += Tn) {
+            const int k = i / nD, d = i % nD;
+            Dsm[k * ldD + d] = D[(int64_t)didx[k0 + k] * nD + d];
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const uint32_t u = desc[t * Tn + tid];
+            if (u == 0xffffffffu) break;
+            const double *Mp = Msm + (u & 511u);
+            const double *Dp = Dsm + ((u >> 9) & 511u);
+            int k = 0;
+            for (; k + 4 <= kb; k += 4) {
+                acc = fma(Dp[k * ldD], Mp[k * ldM], acc);
+                acc = fma(Dp[(k + 1) * ldD], Mp[(k + 1) * ldM], acc);
+                acc = fma(Dp[(k + 2) * ldD], Mp[(k + 2) * ldM], acc);
+                acc = fma(Dp[(k + 3) * ldD], Mp[(k + 3) * ldM], acc);
+            }
+            for (; k < kb; ++k) acc = fma(Dp[k * ldD], Mp[k * ldM], acc);
+            if (u & (1u << 18)) {
+                part[(u >> 19) * Tn + tid] += acc;
+                acc = 0.0;
+            }
+        }
+    }
+    __syncthreads();
+    for (int n = tid; n < tb.nL; n += Tn) {
+        double v = 0.0;
+        for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
+        L[(int64_t)c * tb.nL + n] = v;
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+__global__ void __launch_bounds__(128)
+k_l2l(int lb, const int32_t *parent, const double *centre, DevTables tb, double *L)
+{
+    extern __shared__ double sm[];
+    const int P = tb.p, nK = tb.nK;
+    double *apow = sm;
+    double *mono = apow + 3 * (P + 1);
+    double *Lp = mono + nK;
+    const int c = lb + blockIdx.x;
+    const int pa = parent[c];
+    if (threadIdx.x < 3)
+        axis_powers(centre[3 * c + threadIdx.x] - centre[3 * pa + threadIdx.x], P,
+                    apow + threadIdx.x * (P + 1));
+    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lp[t] = L[(int64_t)pa * tb.nL + t];
+    __syncthreads();
+    for (int k = threadIdx.x; k < nK; k += blockDim.x)
+        mono[k] = apow[c_nx[k]] * apow[(P + 1) + c_ny[k]] * apow[2 * (P + 1) + c_nz[k]];
+    __syncthreads();
+    for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
+        const int kn = c_nx[n] + c_ny[n] + c_nz[n];
+        if (kn < tb.n_lo) continue;
+        double acc = 0.0;
+        for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
+            acc = fma(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
+        L[(int64_t)c * tb.nL + n] += acc;
+    }
+}
+
+// ------------------------------------------------------------------ L2P
+constexpr int kL2PThreads = 128;
+
+// One block per leaf; one thread per particle.  Writes the far-field part
+// of phi and E = -grad phi in sorted particle order.
+__global__ void __launch_bounds__(kL2PThreads)
+k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
+      const double *px, const double *py, const double *pz, const double *L, DevTables tb,
+      int want_phi, int want_field, double *phi, double *E)
+{
+    extern __shared__ double sm[];
+    const int P = tb.p, P1 = tb.p + 1;
+    double *Lsm = sm;                                       // [nL]
+    double *a = Lsm + tb.nL + threadIdx.x * 3 * P1;         // this thread's [3][P+1]
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c];
+    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lsm[t] = L[(int64_t)c * tb.nL + t];
+    __syncthreads();
+    const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
+    for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
+        axis_powers(px[j] - z0, P, a);
+        axis_powers(py[j] - z1, P, a + P1);
+        axis_powers(pz[j] - z2, P, a + 2 * P1);
+        if (want_phi) {
+            double f = 0.0;
+            for (int k = 0; k < tb.nL; ++k)
+                f = fma(a[c_nx[k]] * a[P1 + c_ny[k]] * a[2 * P1 + c_nz[k]], Lsm[k], f);
+            phi[j] = f;
+        }
+        if (want_field) {
+            double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+            for (int k = 0; k < tb.nG; ++k) {
+                const double m = a[c_nx[k]] * a[P1 + c_ny[k]] * a[2 * P1 + c_nz[k]];
+                g0 = fma(m, Lsm[tb.l2p_grad[3 * k]], g0);
+                g1 = fma(m, Lsm[tb.l2p_grad[3 * k + 1]], g1);
+                g2 = fma(m, Lsm[tb.l2p_grad[3 * k + 2]], g2);
+            }
+            E[3 * (int64_t)j] = -g0;
+            E[3 * (int64_t)j + 1] = -g1;
+            E[3 * (int64_t)j + 2] = -g2;
+        }
+    }
+}
+
+inline unsigned grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Table buffer layout (int32): lut | p2m | m2m_off | m2m_k | m2m_q | l2l_off |
+// l2l_k | l2l_q | l2p_grad | red_off | red_src
+fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut)
+{
+    static int consts_ready[64] = {0};
+    if (t->device < 64 && !consts_ready[t->device]) {
+        const MultiIndex &I = multi_index();
+        int8_t x[kMaxTot], y[kMaxTot], z[kMaxTot];
+        for (int i = 0; i < kMaxTot; ++i) { x[i] = (int8_t)I.nx[i]; y[i] = (int8_t)I.ny[i]; z[i] = (int8_t)I.nz[i]; }
+        FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_nx, x, sizeof(x)), "constants"));
+        FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_ny, y, sizeof(y)), "constants"));
+        FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_nz, z, sizeof(z)), "constants"));
+        consts_ready[t->device] = 1;
+    }
+    OpTables &T = t->tab;
+    std::vector<int32_t> buf;
+    size_t o_lut, o_p2m, o_m2m_off, o_m2m_k, o_m2m_q, o_l2l_off, o_l2l_k, o_l2l_q, o_grad, o_roff, o_rsrc;
+    auto put = [&](const std::vector<int> &v) {
+        size_t o = buf.size();
+        buf.insert(buf.end(), v.begin(), v.end());
+        buf.push_back(0);
+        return o;
+    };
+    const bool rebuild = !(t->tab_key_s == s && t->tab_key_p == p && t->tab_key_nlo == n_lo);
+    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreads);
+    {
+        const MultiIndex &I = multi_index();
+        std::vector<int> lutv((kMaxOrder + 1) * (kMaxOrder + 1) * (kMaxOrder + 1));
+        for (int i = 0; i < (int)lutv.size(); ++i) lutv[i] = ((const int16_t *)I.lut)[i];
+        o_lut = put(lutv);
+    }
+    o_p2m = put(T.p2m_terms); o_m2m_off = put(T.m2m_off); o_m2m_k = put(T.m2m_k);
+    o_m2m_q = put(T.m2m_q); o_l2l_off = put(T.l2l_off); o_l2l_k = put(T.l2l_k);
+    o_l2l_q = put(T.l2l_q); o_grad = put(T.l2p_grad); o_roff = put(T.m2l_red_off);
+    o_rsrc = put(T.m2l_red_src);
+    FMM_TRY(ensure(t, t->b_tab_i32, 4 * buf.size()));
+    FMM_TRY(ensure(t, t->b_tab_u32, 4 * T.m2l_desc.size()));
+    if (rebuild) {
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_i32.ptr, buf.data(), 4 * buf.size(),
+                                              cudaMemcpyHostToDevice, t->stream), "tables"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_u32.ptr, T.m2l_desc.data(),
+                                              4 * T.m2l_desc.size(), cudaMemcpyHostToDevice,
+                                              t->stream), "tables"));
+        t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo;
+    }
+    const int32_t *B = (const int32_t *)t->b_tab_i32.ptr;
+    dt->s = s; dt->p = p; dt->n_lo = n_lo; dt->nS = T.nS; dt->nM = T.nM; dt->nL = T.nL;
+    dt->nD = T.nD; dt->m0 = T.m0; dt->nK = ntot(p); dt->nG = ntot(p - 1);
+    dt->p2m_terms = B + o_p2m; dt->m2m_off = B + o_m2m_off; dt->m2m_k = B + o_m2m_k;
+    dt->m2m_q = B + o_m2m_q; dt->l2l_off = B + o_l2l_off; dt->l2l_k = B + o_l2l_k;
+    dt->l2l_q = B + o_l2l_q; dt->l2p_grad = B + o_grad; dt->m2l_red_off = B + o_roff;
+    dt->m2l_red_src = B + o_rsrc;
+    dt->m2l_desc = (const uint32_t *)t->b_tab_u32.ptr;
+    dt->m2l_T = T.m2l_T; dt->m2l_slots = T.m2l_slots;
+    *lut = B + o_lut;
+    return FMM_OK;
+}
+
+void record(fmm_tree *t, int i)
+{
+    if (t->profiling) cudaEventRecord(t->ev[i], t->stream);
+}
+
+}  // namespace
+
+fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
+{
+    cudaStream_t st = t->stream;
+    const int s = t->s;
+    const int n_lo = want_phi ? 0 : 1;
+    DevTables tb;
+    const int32_t *lut;
+    FMM_TRY(upload_tables(t, s, p, n_lo, &tb, &lut));
+    const int64_t nc = t->ncells, n = t->n;
+    const int P1 = p + 1;
+
+    // derivative tables, one row per distinct M2L offset
+    if (t->d_p != p && t->n_doff > 0) {
+        FMM_TRY(ensure(t, t->b_D, 8 * (size_t)t->n_doff * tb.nD));
+        k_dtables<<<grid(t->n_doff, 128), 128, 0, st>>>((const uint64_t *)t->b_dkeys.ptr, t->n_doff,
+                                                         t->side, tb.nD, lut, (double *)t->b_D.ptr);
+        ++t->launches;
+        t->d_p = p;
+    }
+    record(t, 6);
+    FMM_TRY(ensure(t, t->b_M, 8 * (size_t)nc * tb.nM));
+    FMM_TRY(ensure(t, t->b_L, 8 * (size_t)nc * tb.nL));
+    FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
+    FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
+    t->m_cells = nc;
+    double *M = (double *)t->b_M.ptr, *L = (double *)t->b_L.ptr;
+    const int32_t *leaves = (const int32_t *)t->b_leaves.ptr;
+    const int32_t *begin = (const int32_t *)t->b_begin.ptr, *end = (const int32_t *)t->b_end.ptr;
+    const double *centre = (const double *)t->b_centre.ptr;
+    const double *px = (const double *)t->b_px.ptr, *py = (const double *)t->b_py.ptr,
+                 *pz = (const double *)t->b_pz.ptr;
+
+    // P2M at the leaves
+    {
+        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * tb.nK + kP2MChunk * tb.nS);
+        cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
+                                                               (const double *)t->b_S.ptr, tb, M);
+        ++t->launches;
+    }
+    record(t, 7);
+    // M2M upward, level by level
+    {
+        size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nM);
+        for (int l = t->nlevels - 2; l >= 0; --l) {
+            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
+            k_m2m<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
+                                          (const int32_t *)t->b_nchild.ptr, centre, tb, M);
+            ++t->launches;
+        }
+    }
+    record(t, 8);
+    // M2L over the stored lists
+    cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nL, st);
+    if (t->n_m2l > 0) {
+        const int ldM = tb.nM | 1, ldD = tb.nD | 1;
+        size_t fixed = 8 * (size_t)tb.m2l_slots * kM2LThreads + 4 * (size_t)tb.m2l_T * kM2LThreads;
+        size_t smem = fixed + 8 * (size_t)kM2LBatch * (ldM + ldD);
+        cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2l<<<(unsigned)nc, kM2LThreads, smem, st>>>(
+            (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
+            (const int32_t *)t->b_m2l_didx.ptr, M, (const double *)t->b_D.ptr, tb, L);
+        ++t->launches;
+    }
+    record(t, 9);
+    // L2L downward
+    {
+        size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nL);
+        for (int l = 1; l < t->nlevels; ++l) {
+            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
+            k_l2l<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_parent.ptr, centre, tb, L);
+            ++t->launches;
+        }
+    }
+    record(t, 10);
+    // L2P
+    {
+        size_t smem = 8 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
+        cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_l2p<<<(unsigned)t->nleaves, kL2PThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
+                                                               L, tb, want_phi, want_field,
+                                                               (double *)t->b_phi.ptr,
+                                                               (double *)t->b_E.ptr);
+        ++t->launches;
+    }
+    record(t, 11);
+    return cuda_check(t, cudaGetLastError(), "expansion kernels");
+}
+
+}  // namespace fmm

@@ -1,0 +1,715 @@
+// tree.cu -- octree and interaction lists on the GPU (paper §3.2).
+//
+// Root box: lo = per-axis minimum; side = the smallest power of two not below
+// the largest extent.  Integer coordinates q = min(floor((x - lo) * 2^21 /
+// side), 2^21 - 1) are interleaved (x highest) into 63-bit Morton keys and
+// sorted stably.  Cells are built breadth-first: a cell splits while it holds
+// more than n_crit particles and its level is below 21; empty octants are
+// not created, so cells come out in (level, Morton prefix) order.
+//
+// Lists come from the dual-tree traversal of §3.2 run as a breadth-first
+// frontier of cell pairs.  MAC (Eq. (13)) with r = half the cell side,
+// evaluated exactly in integer units of the finest half-cell; when it fails:
+// two leaves -> P2P, one leaf -> open the other, else open the larger cell
+// (the target on a tie); a self pair opens into all ordered child pairs.
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long ordered_bits(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered_bits(unsigned long long b)
+{
+    b = (b >> 63) ? (b & 0x7fffffffffffffffull) : ~b;
+    return __longlong_as_double((long long)b);
+}
+
+__global__ void k_box_init(unsigned long long *box)
+{
+    int i = threadIdx.x;
+    if (i < 3) box[i] = ~0ull;            // running minimum
+    else if (i < 6) box[i] = 0ull;        // running maximum
+}
+
+__global__ void k_bbox(const double *pos, int64_t n, unsigned long long *box, int *err)
+{
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * i + d];
+            if (!isfinite(x)) bad = true;
+            unsigned long long b = ordered_bits(x);
+            mn[d] = b < mn[d] ? b : mn[d];
+            mx[d] = b > mx[d] ? b : mx[d];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+            unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], o);
+            mn[d] = a < mn[d] ? a : mn[d];
+            mx[d] = b > mx[d] ? b : mx[d];
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&box[d], mn[d]);
+            atomicMax(&box[3 + d], mx[d]);
+        }
+    }
+    if (bad) atomicOr(err, kErrNonFinite);
+}
+
+// box_out = (lo_x, lo_y, lo_z, side)
+__global__ void k_box_final(const unsigned long long *box, double *box_out)
+{
+    double lo[3], ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = from_ordered_bits(box[d]);
+        double e = __dsub_rn(from_ordered_bits(box[3 + d]), lo[d]);
+        ext = e > ext ? e : ext;
+    }
+    double side = 1.0;
+    if (ext > 0.0 && isfinite(ext)) {
+        int e2;
+        double m = frexp(ext, &e2);        // ext = m 2^e2, m in [0.5, 1)
+        side = ldexp(1.0, m == 0.5 ? e2 - 1 : e2);
+    }
+    box_out[0] = lo[0]; box_out[1] = lo[1]; box_out[2] = lo[2]; box_out[3] = side;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t x)
+{
+    x &= 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_keys(const double *pos, int64_t n, const double *box, uint64_t *keys,
+                       uint32_t *idx)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double scale = ldexp(1.0, kLevels) / box[3];      // a power of two
+    uint64_t q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double u = floor(__dmul_rn(__dsub_rn(pos[3 * i + d], box[d]), scale));
+        uint64_t v = (uint64_t)u;
+        q[d] = v > (uint64_t)((1 << kLevels) - 1) ? (uint64_t)((1 << kLevels) - 1) : v;
+    }
+    keys[i] = spread3(q[0]) << 2 | spread3(q[1]) << 1 | spread3(q[2]);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_gather(const double *pos, const double *mom, int nS, const uint32_t *perm,
+                         int64_t n, double *px, double *py, double *pz, double *S, int32_t *perm_out)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = perm[k];
+    px[k] = pos[3 * o];
+    py[k] = pos[3 * o + 1];
+    pz[k] = pos[3 * o + 2];
+    for (int a = 0; a < nS; ++a) S[k * nS + a] = mom[o * nS + a];
+    perm_out[k] = (int32_t)o;
+}
+
+struct CellArrays {
+    int32_t *level, *parent, *child, *nchild, *begin, *end, *cx, *cy, *cz;
+};
+
+__global__ void k_root(CellArrays c, int32_t n)
+{
+    c.level[0] = 0; c.parent[0] = -1; c.begin[0] = 0; c.end[0] = n;
+    c.cx[0] = c.cy[0] = c.cz[0] = 0;
+}
+
+__device__ __forceinline__ int digit_at(uint64_t key, int level)
+{
+    return (int)((key >> (3 * (kLevels - level))) & 7ull);
+}
+
+// For each (cell of this level, octant): the child's particle range.
+__global__ void k_child_ranges(CellArrays c, int lb, int ncl, int level, int ncrit,
+                               const uint64_t *keys, uint32_t *flags, int32_t *cb, int32_t *ce)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncl * 8) return;
+    const int cell = lb + t / 8, o = t % 8;
+    const int b = c.begin[cell], e = c.end[cell];
+    uint32_t flag = 0;
+    int lo_i = b, hi_i = b;
+    if (e - b > ncrit && level < kLevels) {
+        // first index in [b, e) whose child digit is >= o (resp. >= o + 1)
+        int L = b, R = e;
+        while (L < R) {
+            int mid = (L + R) >> 1;
+            if (digit_at(keys[mid], level + 1) < o) L = mid + 1; else R = mid;
+        }
+        lo_i = L;
+        R = e;
+        while (L < R) {
+            int mid = (L + R) >> 1;
+            if (digit_at(keys[mid], level + 1) <= o) L = mid + 1; else R = mid;
+        }
+        hi_i = L;
+        flag = hi_i > lo_i;
+    }
+    flags[t] = flag;
+    cb[t] = lo_i;
+    ce[t] = hi_i;
+}
+
+__global__ void k_write_children(CellArrays c, int lb, int le, int ncl, int level,
+                                 const uint32_t *flags, const uint32_t *pos, const int32_t *cb,
+                                 const int32_t *ce)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncl * 8) return;
+    const int i = t / 8, o = t % 8, cell = lb + i;
+    if (o == 0) {
+        const int nch = (int)(pos[8 * i + 8] - pos[8 * i]);
+        c.nchild[cell] = nch;
+        c.child[cell] = nch ? le + (int)pos[8 * i] : -1;
+    }
+    if (!flags[t]) return;
+    const int ch = le + (int)pos[t];
+    c.level[ch] = level + 1;
+    c.parent[ch] = cell;
+    c.begin[ch] = cb[t];
+    c.end[ch] = ce[t];
+    c.cx[ch] = 2 * c.cx[cell] + ((o >> 2) & 1);
+    c.cy[ch] = 2 * c.cy[cell] + ((o >> 1) & 1);
+    c.cz[ch] = 2 * c.cz[cell] + (o & 1);
+}
+
+__global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box, double *centre,
+                                double *half, uint32_t *leaf_flag)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ncells) return;
+    const double h = ldexp(box[3], -(c.level[i] + 1));
+    half[i] = h;
+    centre[3 * i] = __dadd_rn(box[0], __dmul_rn((double)(2 * c.cx[i] + 1), h));
+    centre[3 * i + 1] = __dadd_rn(box[1], __dmul_rn((double)(2 * c.cy[i] + 1), h));
+    centre[3 * i + 2] = __dadd_rn(box[2], __dmul_rn((double)(2 * c.cz[i] + 1), h));
+    leaf_flag[i] = c.nchild[i] == 0;
+}
+
+__global__ void k_compact_leaves(const uint32_t *flag, const uint32_t *pos, int64_t ncells,
+                                 int32_t *leaves)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < ncells && flag[i]) leaves[pos[i]] = (int32_t)i;
+}
+
+// ----------------------------------------------------------- traversal
+// MAC of Eq. (13), exact: centres (2c+1) 2^(21-l) and radii 2^(21-l) in units
+// of the finest half-cell; (rA + rB)^2 < (theta*theta) |dc|^2.
+__device__ __forceinline__ bool mac_accept(const CellArrays &c, int a, int b, double theta2)
+{
+    const int la = c.level[a], lb = c.level[b];
+    const long long ra = 1ll << (kLevels - la), rb = 1ll << (kLevels - lb);
+    const long long dx = (2ll * c.cx[a] + 1) * ra - (2ll * c.cx[b] + 1) * rb;
+    const long long dy = (2ll * c.cy[a] + 1) * ra - (2ll * c.cy[b] + 1) * rb;
+    const long long dz = (2ll * c.cz[a] + 1) * ra - (2ll * c.cz[b] + 1) * rb;
+    const long long d2 = dx * dx + dy * dy + dz * dz;
+    const double lhs = (double)((ra + rb) * (ra + rb));
+    return lhs < __dmul_rn(theta2, (double)d2);
+}
+
+__device__ __forceinline__ void push(int2 *buf, unsigned *count, unsigned cap, int a, int b)
+{
+    unsigned k = atomicAdd(count, 1u);
+    if (k < cap) buf[k] = make_int2(a, b);
+}
+
+// counters: 0 = m2l, 1 = p2p, 2 = next frontier
+__global__ void k_traverse(CellArrays c, const int2 *front, int nf, double theta2, int2 *m2l,
+                           unsigned m2l_cap, int2 *p2p, unsigned p2p_cap, int2 *next,
+                           unsigned next_cap, unsigned *counters)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    const int a = front[t].x, b = front[t].y;
+    const int na = c.nchild[a], nb = c.nchild[b];
+    if (a == b) {
+        if (na == 0) { push(p2p, &counters[1], p2p_cap, a, a); return; }
+        const int f = c.child[a];
+        for (int i = 0; i < na; ++i)
+            for (int j = 0; j < na; ++j) push(next, &counters[2], next_cap, f + i, f + j);
+        return;
+    }
+    if (mac_accept(c, a, b, theta2)) { push(m2l, &counters[0], m2l_cap, a, b); return; }
+    if (na == 0 && nb == 0) { push(p2p, &counters[1], p2p_cap, a, b); return; }
+    bool open_a;
+    if (na == 0) open_a = false;
+    else if (nb == 0) open_a = true;
+    else open_a = c.level[a] <= c.level[b];
+    if (open_a) {
+        const int f = c.child[a];
+        for (int i = 0; i < na; ++i) push(next, &counters[2], next_cap, f + i, b);
+    } else {
+        const int f = c.child[b];
+        for (int j = 0; j < nb; ++j) push(next, &counters[2], next_cap, a, f + j);
+    }
+}
+
+__global__ void k_pack_pairs(const int2 *pairs, int64_t np, int cbits, uint64_t *keys,
+                             uint32_t *vals)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    keys[k] = ((uint64_t)(uint32_t)pairs[k].x << cbits) | (uint32_t)pairs[k].y;
+    vals[k] = (uint32_t)k;
+}
+
+// CSR offsets: off[c] = first sorted pair whose target is >= c.
+__global__ void k_row_offsets(const uint64_t *keys, int64_t np, int cbits, int64_t ncells,
+                              int32_t *off)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c > ncells) return;
+    int64_t L = 0, R = np;
+    while (L < R) {
+        int64_t mid = (L + R) >> 1;
+        if ((int64_t)(keys[mid] >> cbits) < c) L = mid + 1; else R = mid;
+    }
+    off[c] = (int32_t)L;
+}
+
+__global__ void k_unpack_src(const uint64_t *keys, int64_t np, int cbits, int32_t *src)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < np) src[k] = (int32_t)(keys[k] & ((1ull << cbits) - 1ull));
+}
+
+__global__ void k_p2p_interactions(const uint64_t *keys, int64_t np, int cbits, CellArrays c,
+                                   unsigned long long *total)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (k < np) {
+        const int a = (int)(keys[k] >> cbits), b = (int)(keys[k] & ((1ull << cbits) - 1ull));
+        v = (unsigned long long)(c.end[a] - c.begin[a]) * (unsigned long long)(c.end[b] - c.begin[b]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+// --------------------------------------------------- D-table offset keys
+// key = finer level (5 bits) | three 19-bit biased offsets in units of the
+// finer cell's half side.  The real offset is exactly offset * side / 2^(lf+1).
+__device__ __forceinline__ uint64_t hash64(uint64_t x)
+{
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+__global__ void k_offset_keys(CellArrays c, const uint64_t *pair_keys, int64_t np, int cbits,
+                              unsigned long long *table, uint32_t hmask, uint32_t *slot_of,
+                              int *err)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int a = (int)(pair_keys[k] >> cbits), b = (int)(pair_keys[k] & ((1ull << cbits) - 1ull));
+    const int la = c.level[a], lb = c.level[b], lf = la > lb ? la : lb;
+    const long long sa = 1ll << (lf - la), sb = 1ll << (lf - lb);
+    long long d[3] = {(2ll * c.cx[a] + 1) * sa - (2ll * c.cx[b] + 1) * sb,
+                      (2ll * c.cy[a] + 1) * sa - (2ll * c.cy[b] + 1) * sb,
+                      (2ll * c.cz[a] + 1) * sa - (2ll * c.cz[b] + 1) * sb};
+    uint64_t key = (uint64_t)lf << 57;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] < -kKeyBias || d[i] >= kKeyBias) { atomicOr(err, kErrKeyRange); slot_of[k] = 0; return; }
+        key |= (uint64_t)(d[i] + kKeyBias) << (38 - 19 * i);
+    }
+    uint32_t h = (uint32_t)hash64(key) & hmask;
+    for (uint32_t probe = 0; probe <= hmask; ++probe) {
+        unsigned long long cur = table[h];
+        if (cur == key) { slot_of[k] = h; return; }
+        if (cur == ~0ull) {
+            unsigned long long prev = atomicCAS(&table[h], ~0ull, (unsigned long long)key);
+            if (prev == ~0ull || prev == key) { slot_of[k] = h; return; }
+        }
+        h = (h + 1) & hmask;
+    }
+    atomicOr(err, kErrHashFull);
+    slot_of[k] = 0;
+}
+
+__global__ void k_slot_flags(const unsigned long long *table, uint32_t H, uint32_t *flag)
+{
+    uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < H) flag[h] = table[h] != ~0ull;
+}
+
+__global__ void k_slot_compact(const unsigned long long *table, uint32_t H, const uint32_t *dense,
+                               uint64_t *dkeys)
+{
+    uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < H && table[h] != ~0ull) dkeys[dense[h]] = table[h];
+}
+
+__global__ void k_slot_to_dense(int32_t *didx, int64_t np, const uint32_t *dense)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < np) didx[k] = (int32_t)dense[(uint32_t)didx[k]];
+}
+
+inline unsigned grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+CellArrays cells_of(fmm_tree *t)
+{
+    CellArrays c;
+    c.level = (int32_t *)t->b_level.ptr; c.parent = (int32_t *)t->b_parent.ptr;
+    c.child = (int32_t *)t->b_child.ptr; c.nchild = (int32_t *)t->b_nchild.ptr;
+    c.begin = (int32_t *)t->b_begin.ptr; c.end = (int32_t *)t->b_end.ptr;
+    c.cx = (int32_t *)t->b_cx.ptr; c.cy = (int32_t *)t->b_cy.ptr; c.cz = (int32_t *)t->b_cz.ptr;
+    return c;
+}
+
+// Grow a buffer, keeping its first keep_bytes.
+fmm_status grow_keep(fmm_tree *t, DevBuf &b, size_t bytes, size_t keep_bytes)
+{
+    if (b.bytes >= bytes) return FMM_OK;
+    DevBuf nb;
+    size_t want = std::max(bytes, b.bytes + b.bytes / 2);
+    FMM_TRY(ensure(t, nb, want));
+    if (keep_bytes && b.ptr)
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(nb.ptr, b.ptr, keep_bytes, cudaMemcpyDeviceToDevice,
+                                              t->stream), "grow copy"));
+    release(t, b);
+    b = nb;
+    return FMM_OK;
+}
+
+fmm_status read_err(fmm_tree *t)
+{
+    int e = 0;
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&e, t->b_err.ptr, sizeof(int), cudaMemcpyDeviceToHost,
+                                          t->stream), "read error word"));
+    FMM_TRY(cuda_check(t, cudaStreamSynchronize(t->stream), "sync"));
+    if (e & kErrNonFinite) { t->err = "non-finite particle position"; return FMM_EINVAL; }
+    if (e & kErrKeyRange) {
+        t->err = "an accepted M2L offset exceeds 2^18 finer half-cells (theta too small for the tree)";
+        return FMM_EINVAL;
+    }
+    return FMM_OK;
+}
+
+void record(fmm_tree *t, int i)
+{
+    if (t->profiling) cudaEventRecord(t->ev[i], t->stream);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+static void morton_keys(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
+                        uint32_t *idx, unsigned long long *box_scratch, double *box_out, int *err,
+                        int64_t *launches)
+{
+    k_box_init<<<1, 32, 0, st>>>(box_scratch);
+    k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 152 * 8), 256, 0, st>>>(pos, n, box_scratch, err);
+    k_box_final<<<1, 1, 0, st>>>(box_scratch, box_out);
+    k_keys<<<grid(n, 256), 256, 0, st>>>(pos, n, box_out, keys, idx);
+    *launches += 4;
+}
+
+fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
+                            uint32_t *idx, uint64_t *keys2, uint32_t *idx2, uint32_t *hist,
+                            uint32_t *scan_scratch, unsigned long long *box_scratch,
+                            double *box_out, int *err, int64_t *launches)
+{
+    morton_keys(st, pos, n, keys, idx, box_scratch, box_out, err, launches);
+    radix_sort_pairs(keys, idx, keys2, idx2, n, 3 * kLevels, hist, scan_scratch, st, launches);
+    return FMM_OK;
+}
+
+fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
+{
+    const int64_t n = t->n;
+    cudaStream_t st = t->stream;
+    t->have_lists = false;
+    t->ncells = t->nleaves = 0;
+    t->nlevels = 0;
+    t->level_begin.clear();
+    if (n == 0) return FMM_OK;
+
+    FMM_TRY(ensure(t, t->b_keys, 8 * n));
+    FMM_TRY(ensure(t, t->b_keys2, 8 * n));
+    FMM_TRY(ensure(t, t->b_idx, 4 * n));
+    FMM_TRY(ensure(t, t->b_idx2, 4 * n));
+    FMM_TRY(ensure(t, t->b_hist, radix_hist_bytes(n)));
+    FMM_TRY(ensure(t, t->b_scan_tmp, scan_scratch_bytes(std::max<int64_t>(n, 1 << 20) * 8)));
+    FMM_TRY(ensure(t, t->b_px, 8 * n));
+    FMM_TRY(ensure(t, t->b_py, 8 * n));
+    FMM_TRY(ensure(t, t->b_pz, 8 * n));
+    FMM_TRY(ensure(t, t->b_S, 8 * n * t->nS));
+    FMM_TRY(ensure(t, t->b_perm, 4 * n));
+    uint64_t *keys = (uint64_t *)t->b_keys.ptr;
+    uint32_t *idx = (uint32_t *)t->b_idx.ptr;
+
+    record(t, 0);
+    cudaMemsetAsync(t->b_err.ptr, 0, sizeof(int), st);
+    morton_keys(st, pos, n, keys, idx, (unsigned long long *)t->b_box.ptr,
+                (double *)t->b_box.ptr + 8, (int *)t->b_err.ptr, &t->launches);
+    record(t, 1);
+    radix_sort_pairs(keys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
+                     3 * kLevels, (uint32_t *)t->b_hist.ptr, (uint32_t *)t->b_scan_tmp.ptr, st,
+                     &t->launches);
+    k_gather<<<grid(n, 256), 256, 0, st>>>(pos, mom, t->nS, idx, n, (double *)t->b_px.ptr,
+                                           (double *)t->b_py.ptr, (double *)t->b_pz.ptr,
+                                           (double *)t->b_S.ptr, (int32_t *)t->b_perm.ptr);
+    ++t->launches;
+    record(t, 2);
+
+    // ---- cells, level by level
+    int64_t cap = std::max<int64_t>(1024, 2 * (n / std::max(1, t->max_leaf)) + 64);
+    DevBuf *cb[9] = {&t->b_level, &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin,
+                     &t->b_end, &t->b_cx, &t->b_cy, &t->b_cz};
+    for (DevBuf *b : cb) FMM_TRY(ensure(t, *b, 4 * cap));
+    CellArrays c = cells_of(t);
+    k_root<<<1, 1, 0, st>>>(c, (int32_t)n);
+    ++t->launches;
+    t->level_begin.push_back(0);
+    int64_t lb = 0, le = 1;
+    int level = 0;
+    uint32_t total = 0;
+    while (le > lb) {
+        const int64_t ncl = le - lb;
+        FMM_TRY(ensure(t, t->b_flags, 4 * (8 * ncl + 1)));
+        FMM_TRY(ensure(t, t->b_scan, 4 * (8 * ncl + 1)));
+        FMM_TRY(grow_keep(t, t->b_front, 8 * 8 * ncl, 0));    // child begin/end scratch
+        uint32_t *flags = (uint32_t *)t->b_flags.ptr, *pos8 = (uint32_t *)t->b_scan.ptr;
+        int32_t *cbeg = (int32_t *)t->b_front.ptr, *cend = cbeg + 8 * ncl;
+        cudaMemsetAsync(flags + 8 * ncl, 0, 4, st);
+        k_child_ranges<<<grid(8 * ncl, 256), 256, 0, st>>>(c, (int)lb, (int)ncl, level,
+                                                            t->max_leaf, keys, flags, cbeg, cend);
+        exclusive_scan_u32(flags, pos8, 8 * ncl + 1, (uint32_t *)t->b_scan_tmp.ptr, st,
+                           &t->launches);
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&total, pos8 + 8 * ncl, 4, cudaMemcpyDeviceToHost, st),
+                           "child count"));
+        FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+        if (le + (int64_t)total > cap) {
+            int64_t ncap = std::max<int64_t>(2 * cap, le + total);
+            for (DevBuf *b : cb) FMM_TRY(grow_keep(t, *b, 4 * ncap, 4 * le));
+            cap = ncap;
+            c = cells_of(t);
+        }
+        k_write_children<<<grid(8 * ncl, 256), 256, 0, st>>>(c, (int)lb, (int)le, (int)ncl, level,
+                                                              flags, pos8, cbeg, cend);
+        t->launches += 2;
+        lb = le;
+        le += total;
+        ++level;
+        t->level_begin.push_back((int)lb);
+    }
+    t->ncells = le;
+    t->nlevels = level;       // levels 0 .. level-1 hold cells
+    // level_begin has nlevels + 1 entries: the last one equals ncells
+    const int64_t nc = t->ncells;
+    FMM_TRY(ensure(t, t->b_centre, 8 * 3 * nc));
+    FMM_TRY(ensure(t, t->b_half, 8 * nc));
+    FMM_TRY(ensure(t, t->b_flags, 4 * (nc + 1)));
+    FMM_TRY(ensure(t, t->b_scan, 4 * (nc + 1)));
+    uint32_t *flags = (uint32_t *)t->b_flags.ptr, *posc = (uint32_t *)t->b_scan.ptr;
+    cudaMemsetAsync(flags + nc, 0, 4, st);
+    k_cell_geometry<<<grid(nc, 256), 256, 0, st>>>(c, nc, (double *)t->b_box.ptr + 8,
+                                                    (double *)t->b_centre.ptr,
+                                                    (double *)t->b_half.ptr, flags);
+    exclusive_scan_u32(flags, posc, nc + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+    uint32_t nleaves = 0;
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nleaves, posc + nc, 4, cudaMemcpyDeviceToHost, st),
+                       "leaf count"));
+    FMM_TRY(ensure(t, t->b_leaves, 4 * (size_t)nc));
+    k_compact_leaves<<<grid(nc, 256), 256, 0, st>>>(flags, posc, nc, (int32_t *)t->b_leaves.ptr);
+    t->launches += 2;
+    double box[4];
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(box, (double *)t->b_box.ptr + 8, sizeof(box),
+                                          cudaMemcpyDeviceToHost, st), "box"));
+    record(t, 3);
+    FMM_TRY(read_err(t));
+    t->nleaves = nleaves;
+    t->lo[0] = box[0]; t->lo[1] = box[1]; t->lo[2] = box[2]; t->side = box[3];
+    return FMM_OK;
+}
+
+fmm_status build_lists(fmm_tree *t, double theta)
+{
+    cudaStream_t st = t->stream;
+    t->have_lists = false;
+    t->n_m2l = t->n_p2p = t->n_p2p_inter = t->n_doff = 0;
+    t->d_p = -1;
+    if (t->n == 0) { t->theta = theta; t->have_lists = true; return FMM_OK; }
+    const int64_t nc = t->ncells;
+    CellArrays c = cells_of(t);
+    const double theta2 = theta * theta;
+
+    // ---- breadth-first dual traversal
+    FMM_TRY(ensure(t, t->b_counters, 64));
+    unsigned *cnt = (unsigned *)t->b_counters.ptr;
+    size_t m2l_cap = std::max<size_t>(4096, t->m2l_cap_hint), p2p_cap = std::max<size_t>(4096, 40 * (size_t)t->nleaves);
+    FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * m2l_cap, 0));
+    FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * p2p_cap, 0));
+    m2l_cap = t->b_m2l_raw.bytes / 8;
+    p2p_cap = t->b_p2p_raw.bytes / 8;
+    FMM_TRY(grow_keep(t, t->b_front, 8 * 4096, 0));
+    FMM_TRY(grow_keep(t, t->b_front2, 8 * 4096, 0));
+    int2 root = make_int2(0, 0);
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_front.ptr, &root, 8, cudaMemcpyHostToDevice, st),
+                       "frontier"));
+    unsigned host_cnt[3] = {0, 0, 0};
+    int64_t nf = 1;
+    while (nf > 0) {
+        const unsigned base[3] = {host_cnt[0], host_cnt[1], 0};
+        size_t next_cap = t->b_front2.bytes / 8;
+        for (;;) {
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(cnt, base, sizeof(base), cudaMemcpyHostToDevice, st),
+                               "counters"));
+            k_traverse<<<grid(nf, 256), 256, 0, st>>>(c, (const int2 *)t->b_front.ptr, (int)nf,
+                                                      theta2, (int2 *)t->b_m2l_raw.ptr,
+                                                      (unsigned)m2l_cap, (int2 *)t->b_p2p_raw.ptr,
+                                                      (unsigned)p2p_cap, (int2 *)t->b_front2.ptr,
+                                                      (unsigned)next_cap, cnt);
+            ++t->launches;
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(host_cnt, cnt, sizeof(host_cnt),
+                                                  cudaMemcpyDeviceToHost, st), "counters"));
+            FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+            bool retry = false;
+            if (host_cnt[0] > m2l_cap) {
+                FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * (size_t)host_cnt[0] * 2, 8 * (size_t)base[0]));
+                m2l_cap = t->b_m2l_raw.bytes / 8;
+                retry = true;
+            }
+            if (host_cnt[1] > p2p_cap) {
+                FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * (size_t)host_cnt[1] * 2, 8 * (size_t)base[1]));
+                p2p_cap = t->b_p2p_raw.bytes / 8;
+                retry = true;
+            }
+            if (host_cnt[2] > next_cap) {
+                FMM_TRY(grow_keep(t, t->b_front2, 8 * (size_t)host_cnt[2] * 2, 0));
+                next_cap = t->b_front2.bytes / 8;
+                retry = true;
+            }
+            if (!retry) break;
+        }
+        nf = host_cnt[2];
+        std::swap(t->b_front, t->b_front2);
+    }
+    const int64_t nm2l = host_cnt[0], np2p = host_cnt[1];
+    t->m2l_cap_hint = (size_t)nm2l + nm2l / 8;
+
+    // ---- sort both lists by (target, source) and build CSR offsets
+    int cbits = 1;
+    while ((1ll << cbits) < nc) ++cbits;
+    const int64_t nmax = std::max(nm2l, np2p);
+    FMM_TRY(ensure(t, t->b_lkeys, 8 * std::max<int64_t>(nmax, 1)));
+    FMM_TRY(ensure(t, t->b_lkeys2, 8 * std::max<int64_t>(nmax, 1)));
+    FMM_TRY(ensure(t, t->b_lval, 4 * std::max<int64_t>(nmax, 1)));
+    FMM_TRY(ensure(t, t->b_lval2, 4 * std::max<int64_t>(nmax, 1)));
+    FMM_TRY(ensure(t, t->b_hist, radix_hist_bytes(nmax)));
+    FMM_TRY(ensure(t, t->b_scan_tmp, scan_scratch_bytes(std::max<int64_t>(nmax, 1 << 20) * 8)));
+    FMM_TRY(ensure(t, t->b_m2l_src, 4 * std::max<int64_t>(nm2l, 1)));
+    FMM_TRY(ensure(t, t->b_m2l_didx, 4 * std::max<int64_t>(nm2l, 1)));
+    FMM_TRY(ensure(t, t->b_m2l_off, 4 * (nc + 1)));
+    FMM_TRY(ensure(t, t->b_p2p_src, 4 * std::max<int64_t>(np2p, 1)));
+    FMM_TRY(ensure(t, t->b_p2p_off, 4 * (nc + 1)));
+    uint64_t *lk = (uint64_t *)t->b_lkeys.ptr, *lk2 = (uint64_t *)t->b_lkeys2.ptr;
+    uint32_t *lv = (uint32_t *)t->b_lval.ptr, *lv2 = (uint32_t *)t->b_lval2.ptr;
+
+    // P2P first (its keys are not needed afterwards except for the count)
+    k_pack_pairs<<<grid(np2p, 256), 256, 0, st>>>((const int2 *)t->b_p2p_raw.ptr, np2p, cbits, lk, lv);
+    radix_sort_pairs(lk, lv, lk2, lv2, np2p, 2 * cbits, (uint32_t *)t->b_hist.ptr,
+                     (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+    k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, np2p, cbits, nc, (int32_t *)t->b_p2p_off.ptr);
+    k_unpack_src<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, (int32_t *)t->b_p2p_src.ptr);
+    cudaMemsetAsync(cnt + 8, 0, 8, st);
+    k_p2p_interactions<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, c,
+                                                        (unsigned long long *)(cnt + 8));
+    t->launches += 4;
+    unsigned long long inter = 0;
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&inter, cnt + 8, 8, cudaMemcpyDeviceToHost, st), "p2p count"));
+
+    // M2L
+    if (nm2l > 0) {
+        k_pack_pairs<<<grid(nm2l, 256), 256, 0, st>>>((const int2 *)t->b_m2l_raw.ptr, nm2l, cbits, lk, lv);
+        radix_sort_pairs(lk, lv, lk2, lv2, nm2l, 2 * cbits, (uint32_t *)t->b_hist.ptr,
+                         (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+        k_unpack_src<<<grid(nm2l, 256), 256, 0, st>>>(lk, nm2l, cbits, (int32_t *)t->b_m2l_src.ptr);
+        t->launches += 2;
+    }
+    k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, nm2l, cbits, nc, (int32_t *)t->b_m2l_off.ptr);
+    ++t->launches;
+
+    // ---- distinct M2L offsets (rows of the derivative table)
+    int64_t ndoff = 0;
+    if (nm2l > 0) {
+        uint32_t H = 1u << 16;
+        while (H < 4 * (uint32_t)std::min<int64_t>(nm2l, 1 << 22) && H < (1u << 20)) H <<= 1;
+        for (;;) {
+            FMM_TRY(ensure(t, t->b_hash, 8 * (size_t)H));
+            FMM_TRY(ensure(t, t->b_flags, 4 * ((size_t)H + 1)));
+            FMM_TRY(ensure(t, t->b_scan, 4 * ((size_t)H + 1)));
+            cudaMemsetAsync(t->b_hash.ptr, 0xff, 8 * (size_t)H, st);
+            cudaMemsetAsync(t->b_err.ptr, 0, sizeof(int), st);
+            k_offset_keys<<<grid(nm2l, 256), 256, 0, st>>>(c, lk, nm2l, cbits,
+                                                            (unsigned long long *)t->b_hash.ptr,
+                                                            H - 1, (uint32_t *)t->b_m2l_didx.ptr,
+                                                            (int *)t->b_err.ptr);
+            ++t->launches;
+            int e = 0;
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&e, t->b_err.ptr, 4, cudaMemcpyDeviceToHost, st), "err"));
+            FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+            if (e & kErrKeyRange) {
+                t->err = "an accepted M2L offset exceeds 2^18 finer half-cells (theta too small for the tree)";
+                return FMM_EINVAL;
+            }
+            if (!(e & kErrHashFull)) break;
+            H <<= 1;
+        }
+        uint32_t *flag = (uint32_t *)t->b_flags.ptr, *dense = (uint32_t *)t->b_scan.ptr;
+        cudaMemsetAsync(flag + H, 0, 4, st);
+        k_slot_flags<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, flag);
+        exclusive_scan_u32(flag, dense, (int64_t)H + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+        uint32_t nd = 0;
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nd, dense + H, 4, cudaMemcpyDeviceToHost, st), "ndoff"));
+        FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+        ndoff = nd;
+        FMM_TRY(ensure(t, t->b_dkeys, 8 * std::max<int64_t>(ndoff, 1)));
+        k_slot_compact<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, dense,
+                                                       (uint64_t *)t->b_dkeys.ptr);
+        k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense);
+        t->launches += 3;
+    }
+    FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+    t->n_m2l = nm2l;
+    t->n_p2p = np2p;
+    t->n_p2p_inter = (int64_t)inter;
+    t->n_doff = ndoff;
+    t->theta = theta;
+    t->have_lists = true;
+    return FMM_OK;
+}
+
+}  // namespace fmm

@@ -1,0 +1,232 @@
+"""Python binding of the GB300 Cartesian FMM C ABI (include/fmm_gb300.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libfmm_gb300.so``; PyTorch provides device memory and streams.
+The names mirror the C entry points (fmm_create_tree -> create_tree, ...).
+There is no CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
+
+FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_EORDER, FMM_ECUDA, FMM_ETIMEOUT, FMM_EBUDGET, FMM_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PRECISIONS = {"fp64": 0, "fp32": 1, "3xtf32": 2}
+PHASES = ["keys", "sort", "cells", "lists", "dtables", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+ARRAYS = {"keys": (0, torch.int64, 1), "perm": (1, torch.int32, 1), "level": (2, torch.int32, 1),
+          "coord": (3, torch.int32, 3), "range": (4, torch.int32, 2), "parent": (5, torch.int32, 1),
+          "child": (6, torch.int32, 2), "centre": (7, torch.float64, 3),
+          "half": (8, torch.float64, 1), "m2l": (9, torch.int32, 2), "p2p": (10, torch.int32, 2),
+          "multipole": (11, torch.float64, 0), "local": (12, torch.float64, 0)}
+
+
+class FMMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ncells", C.c_int64), ("nleaves", C.c_int64),
+                ("nlevels", C.c_int32), ("source_order", C.c_int32), ("n_m2l", C.c_int64),
+                ("n_p2p", C.c_int64), ("n_p2p_interactions", C.c_int64),
+                ("n_doffsets", C.c_int64), ("theta", C.c_double), ("lo", C.c_double * 3),
+                ("side", C.c_double), ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["lo"] = list(self.lo)
+        return d
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libfmm_gb300.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libfmm_gb300.so is not built (%s); run __graft_entry__.build()"
+                                  % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+            L.fmm_create_tree.argtypes = [C.POINTER(vp), i32, vp, i32, i32, C.c_size_t]
+            L.fmm_set_sources.argtypes = [vp, vp, vp, i64, i32]
+            L.fmm_evaluate.argtypes = [vp, i32, dbl, i32, i32, vp, vp]
+            L.fmm_destroy.argtypes = [vp]
+            L.fmm_status_string.argtypes = [i32]
+            L.fmm_status_string.restype = C.c_char_p
+            L.fmm_last_error.argtypes = [vp]
+            L.fmm_last_error.restype = C.c_char_p
+            L.fmm_get_info.argtypes = [vp, C.POINTER(TreeInfo)]
+            L.fmm_copy_array.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+            L.fmm_set_profiling.argtypes = [vp, i32]
+            L.fmm_get_phase_times.argtypes = [vp, C.POINTER(C.c_float)]
+            L.fmm_launch_count.argtypes = [vp]
+            L.fmm_launch_count.restype = i64
+            L.fmm_direct_sum.argtypes = [vp, vp, vp, i64, i32, vp, i64, vp, vp]
+            L.fmm_morton_order.argtypes = [vp, vp, i64, vp, vp]
+            for f in ("fmm_create_tree", "fmm_set_sources", "fmm_evaluate", "fmm_destroy",
+                      "fmm_get_info", "fmm_copy_array", "fmm_set_profiling", "fmm_get_phase_times",
+                      "fmm_direct_sum", "fmm_morton_order"):
+                getattr(L, f).restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(status, handle=None, what=""):
+    if status != FMM_OK:
+        msg = lib().fmm_last_error(handle).decode() if handle is not None else ""
+        base = lib().fmm_status_string(status).decode()
+        raise FMMError(status, "%s: %s%s" % (what, base, (" -- " + msg) if msg else ""))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(x, name, shape1=None):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64):
+        raise TypeError("%s must be a CUDA float64 tensor" % name)
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape1 is not None and (x.dim() != 2 or x.shape[1] != shape1):
+        raise ValueError("%s must have shape (n, %d)" % (name, shape1))
+    return x
+
+
+def source_terms(s: int) -> int:
+    return (s + 1) * (s + 2) // 2
+
+
+class FMMTree:
+    """One system: fmm_create_tree / fmm_set_sources / fmm_evaluate."""
+
+    def __init__(self, device=0, stream=None, max_leaf=64, precision="fp64", mem_budget_bytes=0):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().fmm_create_tree(C.byref(h), self.device.index or 0, _stream_ptr(stream),
+                                   int(max_leaf), PRECISIONS[precision], int(mem_budget_bytes))
+        if st != FMM_OK:
+            raise FMMError(st, "create_tree: %s -- %s" % (lib().fmm_status_string(st).decode(),
+                                                          lib().fmm_last_error(None).decode()))
+        self._h = h
+        self.n = 0
+        self.s = None
+        self._keep = None
+
+    def set_sources(self, positions, moments, source_order: int):
+        _dev_f64(positions, "positions", 3)
+        if moments is not None:
+            _dev_f64(moments, "moments", source_terms(source_order))
+        n = positions.shape[0]
+        st = lib().fmm_set_sources(self._h, _ptr(positions), _ptr(moments), n, int(source_order))
+        _check(st, self._h, "set_sources")
+        self.n, self.s = n, source_order
+
+    def evaluate(self, p: int, theta: float, want_potential=True, want_field=True,
+                 potential=None, field=None):
+        """Returns (potential or None, field or None) as CUDA float64 tensors."""
+        if want_potential and potential is None:
+            potential = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        if want_field and field is None:
+            field = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        st = lib().fmm_evaluate(self._h, int(p), float(theta), int(bool(want_potential)),
+                                int(bool(want_field)), _ptr(potential if want_potential else None),
+                                _ptr(field if want_field else None))
+        _check(st, self._h, "evaluate")
+        return (potential if want_potential else None), (field if want_field else None)
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        _check(lib().fmm_get_info(self._h, C.byref(inf)), self._h, "get_info")
+        return inf.as_dict()
+
+    def copy_array(self, name: str, width: int = None) -> torch.Tensor:
+        """Host copy of an internal array (keys, perm, cells, lists, M, L)."""
+        ident, dtype, cols = ARRAYS[name]
+        need = C.c_size_t()
+        inf = self.info()
+        rows = {"keys": inf["n"], "perm": inf["n"], "m2l": inf["n_m2l"], "p2p": inf["n_p2p"]}.get(
+            name, inf["ncells"])
+        elem = torch.empty((), dtype=dtype).element_size()
+        if cols == 0:
+            cols = width if width else 1
+        out = torch.empty((rows, cols) if cols > 1 else (rows,), dtype=dtype)
+        st = lib().fmm_copy_array(self._h, ident, C.c_void_p(out.data_ptr()),
+                                  out.numel() * elem, C.byref(need))
+        _check(st, self._h, "copy_array(%s)" % name)
+        return out
+
+    def set_profiling(self, enable=True):
+        _check(lib().fmm_set_profiling(self._h, int(bool(enable))), self._h, "set_profiling")
+
+    def phase_times(self) -> dict:
+        buf = (C.c_float * len(PHASES))()
+        _check(lib().fmm_get_phase_times(self._h, buf), self._h, "get_phase_times")
+        return {k: float(v) for k, v in zip(PHASES, buf)}
+
+    def launch_count(self) -> int:
+        return int(lib().fmm_launch_count(self._h))
+
+    def destroy(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            lib().fmm_destroy(h)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def create_tree(device=0, stream=None, max_leaf=64, precision="fp64", mem_budget_bytes=0):
+    return FMMTree(device, stream, max_leaf, precision, mem_budget_bytes)
+
+
+def direct_sum(positions, moments, source_order, targets=None, want_potential=True,
+               want_field=True, stream=None):
+    """FP64 O(N^2) sum on the GPU at ``targets`` (int32 CUDA tensor or None)."""
+    _dev_f64(positions, "positions", 3)
+    _dev_f64(moments, "moments", source_terms(source_order))
+    n = positions.shape[0]
+    if targets is not None:
+        if not (targets.is_cuda and targets.dtype == torch.int32):
+            raise TypeError("targets must be a CUDA int32 tensor")
+        nt = targets.shape[0]
+    else:
+        nt = n
+    phi = torch.empty(nt, dtype=torch.float64, device=positions.device) if want_potential else None
+    E = torch.empty((nt, 3), dtype=torch.float64, device=positions.device) if want_field else None
+    st = lib().fmm_direct_sum(_stream_ptr(stream), _ptr(positions), _ptr(moments), n,
+                              int(source_order), _ptr(targets), nt, _ptr(phi), _ptr(E))
+    _check(st, None, "direct_sum")
+    return phi, E
+
+
+def morton_order(positions, stream=None):
+    """(keys uint64-as-int64 [n], perm int32 [n]) as CUDA tensors."""
+    _dev_f64(positions, "positions", 3)
+    n = positions.shape[0]
+    keys = torch.empty(n, dtype=torch.int64, device=positions.device)
+    perm = torch.empty(n, dtype=torch.int32, device=positions.device)
+    st = lib().fmm_morton_order(_stream_ptr(stream), _ptr(positions), n, _ptr(keys), _ptr(perm))
+    _check(st, None, "morton_order")
+    return keys, perm
