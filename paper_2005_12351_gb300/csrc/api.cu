@@ -238,9 +238,9 @@ fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, in
     if (!want_potential && !want_field) return fail(t, FMM_EINVAL, "nothing requested");
     if (p < 0 || p + t->s > FMM_MAX_TOTAL_ORDER || (want_field && p < 1))
         return fail(t, FMM_EORDER, "need 0 <= p, p + s <= 12, and p >= 1 for the field");
+    if (t->n == 0) return FMM_OK;
     if ((want_potential && !potential) || (want_field && !field))
         return fail(t, FMM_EINVAL, "NULL output for a requested quantity");
-    if (t->n == 0) return FMM_OK;
     DeviceGuard g(t->device);
     record(t, 4);
     if (!t->have_lists || t->theta != theta) FMM_TRY(build_lists(t, theta));

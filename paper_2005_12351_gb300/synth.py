@@ -154,6 +154,8 @@ WORKLOADS = {
     # name: (n, source order, p, theta, n_crit, distribution, seed)
     "monopole_2k_p4": dict(n=2000, s=0, p=4, theta=0.5, ncrit=64, dist="uniform", seed=20260000),
     "dipole_1m_p6": dict(n=1_000_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260001),
+    # same leaf occupancy as the 1M workload (leaves one level higher): profiling-size case
+    "dipole_125k_p6": dict(n=125_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260011),
     "dipole_plummer_4m_p8": dict(n=4_000_000, s=1, p=8, theta=0.5, ncrit=128, dist="plummer",
                                  seed=20260002),
 }
