@@ -218,6 +218,30 @@ fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const doub
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out);
 
+/*
+ * fmm_morton_order without any device allocation.  The paper has no
+ * counterpart: this serves callers that must not allocate device memory
+ * while they call the library -- code running inside a custom allocator or
+ * memory-pool callback (an allocation would re-enter it), runtimes that give
+ * the library a fixed arena and forbid cudaMalloc/cudaFree because those
+ * calls synchronise the device, and latency-critical loops.
+ *   Arguments and results are those of fmm_morton_order (DEVICE pointers).
+ *   Scratch: a file-scope device array of about 12.3 MB holding room for
+ *   FMM_NOALLOC_MAX_POINTS points; every GPU that loads the library holds it
+ *   until the process exits.  n > FMM_NOALLOC_MAX_POINTS returns FMM_EBUDGET
+ *   and touches nothing; n < 0 or NULL pointers return FMM_EINVAL.
+ *   Device: the calling thread's current device.  The first call on each
+ *   device looks up the array's device address (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.
+ *   Sharing: all calls on a device use the same array, and each call leaves
+ *   its contents behind.  Calls that overlap on the GPU (different streams
+ *   or threads without ordering between them) race on it: serialise them.
+ *   Synchronises cuda_stream before returning; allocates nothing.
+ */
+#define FMM_NOALLOC_MAX_POINTS (1 << 20)
+fmm_status fmm_morton_order_noalloc(void *cuda_stream, const double *positions, int64_t n,
+                                    uint64_t *keys_out, int32_t *perm_out);
+
 #ifdef __cplusplus
 }
 #endif

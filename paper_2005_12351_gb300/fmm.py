@@ -230,3 +230,24 @@ def morton_order(positions, stream=None):
     st = lib().fmm_morton_order(_stream_ptr(stream), _ptr(positions), n, _ptr(keys), _ptr(perm))
     _check(st, None, "morton_order")
     return keys, perm
+
+
+NOALLOC_MAX_POINTS = 1 << 20
+
+
+def noalloc_entry():
+    """The C entry point fmm_morton_order_noalloc with its argument types."""
+    f = lib().fmm_morton_order_noalloc
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    return f
+
+
+def morton_order_noalloc(positions, keys_out, perm_out, stream=None):
+    """Morton order into caller-provided outputs with no device allocation
+    (the library's fixed scratch array; see fmm_morton_order_noalloc)."""
+    _dev_f64(positions, "positions", 3)
+    n = positions.shape[0]
+    st = noalloc_entry()(_stream_ptr(stream), _ptr(positions), n, _ptr(keys_out), _ptr(perm_out))
+    _check(st, None, "morton_order_noalloc")
+    return keys_out, perm_out
