@@ -171,33 +171,26 @@ def config_of(w, args):
     return {"workload": args.workload, "n": w["n"], "source_order": w["s"], "p": w["p"],
             "theta": w["theta"], "max_leaf": w["ncrit"], "distribution": w["dist"],
             "outputs": "field" if not w.get("phi", False) else "potential+field",
-            "precision": "fp64", "l2": "flushed (256 MB write) between timed steps",
+            "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
             "replicas": args.gpus}
 
 
-def run_ours(args, w):
+FP32_PEAK_TFLOPS = 80.5     # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+
+
+def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, flush):
+    """Time K whole steps of one precision form; returns a dict of results."""
     import torch
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
     from paper_2005_12351_gb300 import fmm
     s, p, theta, n = w["s"], w["p"], w["theta"], w["n"]
     want_phi, want_field = bool(w.get("phi", False)), True
-    pos_np, S_np = synth.make_system(n, s, w["dist"], w["seed"] + 1000 * rank)
-    pos_h = torch.from_numpy(pos_np).pin_memory()
-    S_h = torch.from_numpy(S_np).pin_memory()
-    pos_d, S_d = pos_h.to(dev), S_h.to(dev)
     E_d = torch.empty((n, 3), dtype=torch.float64, device=dev)
     phi_d = torch.empty(n, dtype=torch.float64, device=dev) if want_phi else None
     E_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"])
+    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"],
+                           precision=precision)
     tree.set_profiling(True)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step():
         tree.set_sources(pos_d, S_d, s)
@@ -269,23 +262,56 @@ def run_ours(args, w):
     ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
     pair_flops = flops_per_pair(s, want_phi, want_field) * info["n_p2p_interactions"]
     m2l_flops = 2 * m2l_macs_per_pair(s, p, want_phi) * info["n_m2l"]
-    fp64_peak = args.fp64_peak_tflops
+    if precision == "fp64":
+        peak, src = args.fp64_peak_tflops, args.fp64_peak_source
+    else:
+        peak, src = FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"
     cand = {"p2p": pair_flops, "m2l": m2l_flops}
     dom = max(cand, key=lambda k: ph[k])
     achieved = cand[dom] / (ph[dom] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                "algorithmic_flops": cand[dom], "peak_source": args.fp64_peak_source}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; %s)" % w["dist"],
-            "config": config_of(w, args), "rel_err": rel_err,
-            "e2e": {"value": n * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
-            "roofline": roofline, "phase_ms": ph, "clocks": clocks, "gpu_launches": launches,
-            "wall_s_timed": t_wall,
-            "tree": {k: info[k] for k in ("ncells", "nleaves", "nlevels", "n_m2l", "n_p2p",
-                                          "n_p2p_interactions", "n_doffsets")}}
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_flops": cand[dom], "peak_source": src}
+    res = {"value": value, "ms_per_step": ms, "rel_err": rel_err,
+           "e2e": {"value": n * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+           "roofline": roofline, "phase_ms": ph, "clocks": clocks, "gpu_launches": launches,
+           "wall_s_timed": t_wall,
+           "tree": {k: info[k] for k in ("ncells", "nleaves", "nlevels", "n_m2l", "n_p2p",
+                                         "n_p2p_interactions", "n_doffsets")}}
+    tree.destroy()
+    return res
+
+
+def run_ours(args, w):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = w["n"]
+    pos_np, S_np = synth.make_system(n, w["s"], w["dist"], w["seed"] + 1000 * rank)
+    pos_h = torch.from_numpy(pos_np).pin_memory()
+    S_h = torch.from_numpy(S_np).pin_memory()
+    pos_d, S_d = pos_h.to(dev), S_h.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    main = measure_form(args, w, args.precision, dev, world, rank, pos_h, S_h, pos_d, S_d, flush)
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded; %s)" % w["dist"], "config": config_of(w, args)}
+    line.update({k: main[k] for k in ("rel_err", "e2e", "roofline", "phase_ms", "clocks",
+                                      "gpu_launches", "wall_s_timed", "tree")})
+    if args.precision == "fp64" and not args.no_mixed:
+        mx = measure_form(args, w, "fp32", dev, world, rank, pos_h, S_h, pos_d, S_d, flush)
+        line["mixed_fp32"] = {k: mx[k] for k in ("value", "ms_per_step", "rel_err", "e2e",
+                                                 "roofline", "phase_ms", "gpu_launches")}
+        line["mixed_fp32"]["error_ratio_vs_fp64"] = (mx["rel_err"]["field_rel_rms"]
+                                                     / main["rel_err"]["field_rel_rms"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, k, cores = oracle_sample(w, args.oracle_sample)
         line["cpu_baseline"] = {
@@ -294,7 +320,6 @@ def run_ours(args, w):
                       "(full upward pass, ancestor-chain downward pass, L2P + P2P); %.1f s" % (k, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tree.destroy()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -310,6 +335,9 @@ def main(argv=None):
     ap.add_argument("--err-samples", type=int, default=4096)
     ap.add_argument("--oracle-sample", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the extra FP32-form measurement in the same run")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.259)
     ap.add_argument("--fp64-peak-source", default="152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                     "(nominal 1.25 TFLOP/s FP64 of the part)")

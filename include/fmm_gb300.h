@@ -109,7 +109,7 @@ fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *m
  *   p      : local expansion order, 0 <= p and p + s <= FMM_MAX_TOTAL_ORDER;
  *            p >= 1 when want_field.
  *   theta  : MAC parameter of Eq. (13), 0 < theta < 1 (checked: it must also
- *            keep accepted offsets within +-2^18 finer half-cells).
+ *            keep accepted offsets within +-2^16 finer half-cells).
  *   potential : DEVICE pointer to n doubles, or NULL when !want_potential.
  *   field     : DEVICE pointer to n x 3 doubles (E = -grad phi), or NULL when
  *               !want_field.
@@ -217,6 +217,16 @@ fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const doub
  */
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out);
+
+/*
+ * Self-check of the library's own FP64 reciprocal square root used by the
+ * P2P near field (an FP32 rsqrtf seed refined by one third-order
+ * Householder step in FP64): writes own[i] = the library's 1/sqrt(x[i]) and
+ * ref[i] = CUDA's rsqrt(x[i]) for comparison.  x > 0, normal doubles.
+ * All pointers DEVICE, n entries; enqueued on cuda_stream, no allocation.
+ */
+fmm_status fmm_check_rsqrt(void *cuda_stream, const double *x, int64_t n, double *own,
+                           double *ref);
 
 /*
  * fmm_morton_order without any device allocation.  The paper has no

@@ -80,7 +80,7 @@ void record(fmm_tree *t, int i)
 
 void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
 {
-    DevBuf *b[] = {&t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
+    DevBuf *b[] = {&t->b_o32, &t->b_S32, &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
                    &t->b_hist, &t->b_px, &t->b_py, &t->b_pz, &t->b_S, &t->b_perm, &t->b_level,
                    &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,
                    &t->b_cy, &t->b_cz, &t->b_centre, &t->b_half, &t->b_leaves, &t->b_flags,
@@ -140,8 +140,8 @@ fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int ma
         g_create_err = "no CUDA device " + std::to_string(device);
         return FMM_EINVAL;
     }
-    if (prec != FMM_FP64) {
-        g_create_err = "only FMM_FP64 is available in this build";
+    if (prec == FMM_3XTF32) {
+        g_create_err = "FMM_3XTF32 is not available in this build (use FMM_FP64 or FMM_FP32)";
         return FMM_EINVAL;
     }
     DeviceGuard g(device);
@@ -245,8 +245,12 @@ fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, in
     record(t, 4);
     if (!t->have_lists || t->theta != theta) FMM_TRY(build_lists(t, theta));
     record(t, 5);
-    FMM_TRY(run_expansions(t, p, want_potential, want_field));
-    FMM_TRY(run_p2p(t, want_potential, want_field, potential, field));
+    if (t->prec == FMM_FP32) {
+        FMM_TRY(run_mixed(t, p, want_potential, want_field, potential, field));
+    } else {
+        FMM_TRY(run_expansions(t, p, want_potential, want_field));
+        FMM_TRY(run_p2p(t, want_potential, want_field, potential, field));
+    }
     record(t, 12);
     if (t->profiling) {
         FMM_TRY(cuda_check(t, cudaEventSynchronize(t->ev[12]), "event sync"));
@@ -355,6 +359,14 @@ fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const doub
                   potential, field, &launches);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : FMM_ECUDA;
+}
+
+fmm_status fmm_check_rsqrt(void *cuda_stream, const double *x, int64_t n, double *own,
+                           double *ref)
+{
+    if (n < 0 || (n > 0 && (!x || !own || !ref))) return FMM_EINVAL;
+    launch_check_rsqrt((cudaStream_t)cuda_stream, x, n, own, ref);
+    return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ECUDA;
 }
 
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,

@@ -23,7 +23,7 @@ namespace fmm {
 constexpr int kLevels = 21;            // key depth: 3 x 21 = 63 bits
 constexpr int kMaxOrder = 16;          // multi-index tables cover |n| <= 16
 constexpr int kMaxTot = 969;           // ntot(16)
-constexpr int kKeyBias = 1 << 18;      // D-table key: offsets in [-2^18, 2^18)
+constexpr int kKeyBias = 1 << 16;      // D-table key: offsets in [-2^16, 2^16)
 
 // device error word bits
 constexpr int kErrNonFinite = 1;
@@ -65,6 +65,21 @@ struct OpTables {
 };
 void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads);
 
+// threads of the M2L blocks (the per-thread term lists are built for it)
+constexpr int kM2LThreadsShared = 128;
+
+// Device views of the uploaded tables (passed to kernels by value).
+struct DevTables {
+    int s, p, n_lo, nS, nM, nL, nD, m0, nK, nG;
+    const int *p2m_terms;
+    const int *m2m_off, *m2m_k, *m2m_q;
+    const int *l2l_off, *l2l_k, *l2l_q;
+    const int *l2p_grad;
+    const int *m2l_red_off, *m2l_red_src;
+    const uint32_t *m2l_desc;
+    int m2l_T, m2l_slots;
+};
+
 }  // namespace fmm
 
 // ---------------------------------------------------------------------------
@@ -99,6 +114,7 @@ struct fmm_tree {
     bool have_lists = false;
     int64_t n_m2l = 0, n_p2p = 0, n_p2p_inter = 0, n_doff = 0;
     size_t m2l_cap_hint = 0;
+    int max_gap = 0;                       // largest level gap of an M2L pair
     // D tables / operator tables
     int d_p = -1;                          // p the D table was built for
     fmm::OpTables tab;
@@ -123,6 +139,9 @@ struct fmm_tree {
     DevBuf b_hash, b_dkeys, b_D;
     DevBuf b_M, b_L, b_phi, b_E;
     DevBuf b_tab_i32, b_tab_u32;
+    // mixed-precision state
+    DevBuf b_o32, b_S32, b_M32, b_L32, b_D32;
+    int d32_p = -1;                        // p the FP32 D table was built for
 };
 
 // ---------------------------------------------------------------------------
@@ -154,9 +173,15 @@ fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint6
                             double *box_out, int *err, int64_t *launches);
 
 // operators.cu
+fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut);
+fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t *lut);
 fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field);
+// mixed.cu (FMM_FP32): scaled FP32 expansions, FP32 pair arithmetic, FP64 outputs
+fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *phi_out,
+                     double *E_out);
 // p2p.cu
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
+void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref);
 void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
                    const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches);
 

@@ -1,0 +1,669 @@
+// mixed.cu -- the mixed-precision form (FMM_FP32).
+//
+// FP64 stays where it decides accuracy: the derivative tensors of 1/r are
+// generated in FP64 (one row per distinct M2L offset, shared with the FP64
+// form), box-centre offsets are exact dyadic numbers, particle offsets are
+// formed in FP64 before rounding, and each particle's potential and field
+// are accumulated and returned in FP64.  The bulk arithmetic -- P2M, M2M,
+// M2L, L2L, L2P sums and the P2P pair terms -- runs in FP32 on scaled
+// expansions so that every stored value is O(1) at any tree depth.
+//
+// Scaling (h = half side of the cell, all factors exact powers of two):
+//   M~_m = M_m / h^(|m|-s),                   L~_n = L_n h^(|n|+s+1)
+//   P2M  M~_m = sum_j sum_a (-d_j)^(m-a)/(m-a)! S_{j,a},  d_j = (x_j - z)/h
+//   M2M  M~p_n = 2^-(|n|-s) sum_k sig^k/k! M~c_{n-k},     sig = (z_p - z_c)/h_c
+//   M2L  L~t_n += sum_m Dh_{n+m} Mh_m,  Dh_k = h_t^(|k|+1) D_k(z_t - z_s),
+//        Mh_m = (h_s/h_t)^(|m|-s) M~s_m                   (Eq. (8) rescaled)
+//   L2L  L~c_n += sum_k sig^k/k! 2^-(|n+k|+s+1) L~p_{n+k}, sig = (z_c - z_p)/h_c
+//   L2P  phi = h^-(s+1) sum_n d^n/n! L~_n,  d_k phi = h^-(s+2) sum d^(n-e_k)/(n-e_k)! L~_n
+#include <algorithm>
+#include <cmath>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+__constant__ int8_t x_nx[kMaxTot], x_ny[kMaxTot], x_nz[kMaxTot];
+__constant__ float x_invint[kMaxOrder + 2];     // 1/q
+__constant__ float x_invfact[kMaxOrder + 1];    // 1/q!
+
+inline unsigned gridm(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+__device__ __forceinline__ int shell(int idx) { return x_nx[idx] + x_ny[idx] + x_nz[idx]; }
+
+// per-axis scaled powers w^q / q!, q <= P
+__device__ __forceinline__ void axis_powers32(float w, int P, float *out)
+{
+    float v = 1.0f;
+    out[0] = 1.0f;
+    for (int q = 1; q <= P; ++q) {
+        v = v * w * x_invint[q];
+        out[q] = v;
+    }
+}
+
+// ------------------------------------------------------------------ prep
+// o_j = x_j - z_leaf formed in FP64 and kept as an unevaluated float pair
+// hi + lo (hi = o rounded, lo = the remainder rounded): together they carry
+// ~48 bits, so pair separations can later be formed accurately relative to
+// their own size.  S32 = (float)S.
+__global__ void k_prep32(const int32_t *leaves, const int32_t *begin, const int32_t *end,
+                         const double *centre, const double *px, const double *py,
+                         const double *pz, const double *S, int nS, float4 *o, float4 *olo,
+                         float *S32)
+{
+    const int c = leaves[blockIdx.x];
+    const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
+    for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
+        const double dx = px[j] - z0, dy = py[j] - z1, dz = pz[j] - z2;
+        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+        o[j] = make_float4(hx, hy, hz, 0.0f);
+        olo[j] = make_float4((float)(dx - hx), (float)(dy - hy), (float)(dz - hz), 0.0f);
+        for (int a = 0; a < nS; ++a) S32[(int64_t)j * nS + a] = (float)S[(int64_t)j * nS + a];
+    }
+}
+
+// a + b = s + e exactly (Knuth's TwoSum), then e absorbs the low part c
+__device__ __forceinline__ void two_sum_lo(float a, float b, float c, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)), c);
+}
+
+// ------------------------------------------------------------------ P2M
+constexpr int kChunk = 32;
+constexpr int kPer = 4;                   // up to 4 * 128 = 512 components per thread block
+
+__global__ void __launch_bounds__(128)
+k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
+        const float4 *o, const float *S32, DevTables tb, float *M)
+{
+    extern __shared__ float sf[];
+    const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nS = tb.nS;
+    float *apow = sf;                              // [chunk][3][P1]
+    float *mono = apow + kChunk * 3 * P1;          // [chunk][nK]
+    float *Ssm = mono + kChunk * nK;               // [chunk][nS]
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c];
+    const float inv_h = (float)(1.0 / half[c]);    // a power of two
+    double acc[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+    for (int j0 = b; j0 < e; j0 += kChunk) {
+        const int nj = min(kChunk, e - j0);
+        for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
+            const int j = t / 3, ax = t % 3;
+            const float4 v = o[j0 + j];
+            const float d = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
+            axis_powers32(-d * inv_h, P, apow + (j * 3 + ax) * P1);
+        }
+        for (int t = threadIdx.x; t < nj * nS; t += blockDim.x) Ssm[t] = S32[(int64_t)j0 * nS + t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < nj * nK; t += blockDim.x) {
+            const int j = t / nK, k = t % nK;
+            const float *a = apow + j * 3 * P1;
+            mono[t] = a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int mi = threadIdx.x + u * 128;
+            if (mi >= tb.nM) break;
+            // FP32 over groups of 8 particles, FP64 across groups (cancellation
+            // between randomly oriented sources is absorbed in FP64)
+            for (int j8 = 0; j8 < nj; j8 += 8) {
+                float sum = 0.0f;
+                for (int j = j8; j < min(j8 + 8, nj); ++j)
+                    for (int a = 0; a < nS; ++a) {
+                        const int k = tb.p2m_terms[mi * nS + a];
+                        if (k >= 0) sum = fmaf(mono[j * nK + k], Ssm[j * nS + a], sum);
+                    }
+                acc[u] += (double)sum;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int mi = threadIdx.x + u * 128;
+        if (mi < tb.nM) M[(int64_t)c * tb.nM + mi] = (float)acc[u];
+    }
+}
+
+// sig^k / k! with sig_d = +1 or -1 given by neg_d (1 means -1)
+__device__ __forceinline__ float sign_mono(int k, int nx_neg, int ny_neg, int nz_neg)
+{
+    const int kx = x_nx[k], ky = x_ny[k], kz = x_nz[k];
+    const int odd = (nx_neg & kx) ^ (ny_neg & ky) ^ (nz_neg & kz);
+    const float m = x_invfact[kx] * x_invfact[ky] * x_invfact[kz];
+    return (odd & 1) ? -m : m;
+}
+
+// ------------------------------------------------------------------ M2M
+__global__ void __launch_bounds__(128)
+k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, const int32_t *cy,
+        const int32_t *cz, DevTables tb, float *M)
+{
+    extern __shared__ float sf[];
+    float *mono = sf;               // [nK]
+    float *Mc = mono + tb.nK;       // [nM]
+    const int c = lb + blockIdx.x;
+    const int nch = nchild[c];
+    if (nch == 0) return;
+    double acc[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+    for (int i = 0; i < nch; ++i) {
+        const int ch = child[c] + i;
+        // z_p - z_c = (1 - 2 bit) h_c per axis: negative where the child's low bit is 1
+        const int bx = cx[ch] & 1, by = cy[ch] & 1, bz = cz[ch] & 1;
+        for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(k, bx, by, bz);
+        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * tb.nM + t];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int ni = threadIdx.x + u * 128;
+            if (ni >= tb.nM) break;
+            float sum = 0.0f;
+            for (int q = tb.m2m_off[ni]; q < tb.m2m_off[ni + 1]; ++q)
+                sum = fmaf(mono[tb.m2m_k[q]], Mc[tb.m2m_q[q]], sum);
+            acc[u] += (double)sum;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int ni = threadIdx.x + u * 128;
+        if (ni < tb.nM) M[(int64_t)c * tb.nM + ni] = (float)ldexp(acc[u], -(shell(ni + tb.m0) - tb.s));
+    }
+}
+
+// ------------------------------------------------------------ D rows, FP32
+// Dh_k = h_t^(|k|+1) D_k: the FP64 row scaled by the target's half side
+// (exactly, by the exponent) and rounded once.
+__global__ void k_dtables32(const uint64_t *dkeys, int64_t ndoff, int e_side, int nD,
+                            const double *D, float *D32)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ndoff * nD) return;
+    const int64_t r = i / nD;
+    const int k = (int)(i % nD);
+    const uint64_t key = dkeys[r];
+    const int lf = (int)(key >> 57), gap = (int)((key >> 52) & 31), tfiner = (int)((key >> 51) & 1);
+    const int lt = tfiner ? lf : lf - gap;
+    const int e_t = e_side - lt - 1;                 // h_t = 2^e_t
+    D32[i] = (float)ldexp(D[i], (shell(k) + 1) * e_t);
+}
+
+// ------------------------------------------------------------------ M2L
+constexpr int kM2LThreads = 128;
+constexpr int kBatch = 16;
+
+__global__ void __launch_bounds__(kM2LThreads)
+k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t *level,
+        const float *M, const float *D32, DevTables tb, float *L)
+{
+    extern __shared__ float sf[];
+    const int c = blockIdx.x;
+    const int b = off[c], e = off[c + 1];
+    if (b == e) return;
+    const int nM = tb.nM, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
+    const int ldM = nM | 1, ldD = nD | 1;
+    double *part = (double *)sf;                   // [slots][Tn], FP64 across batches
+    float *Msm = (float *)(part + tb.m2l_slots * Tn);   // [batch][ldM]
+    float *Dsm = Msm + kBatch * ldM;               // [batch][ldD]
+    uint32_t *desc = (uint32_t *)(Dsm + kBatch * ldD);  // [T][Tn]
+    const int tid = threadIdx.x;
+    const int lt = level[c];
+    for (int i = tid; i < T * Tn; i += Tn) desc[i] = tb.m2l_desc[i];
+    for (int i = tid; i < tb.m2l_slots * Tn; i += Tn) part[i] = 0.0;
+    for (int k0 = b; k0 < e; k0 += kBatch) {
+        const int kb = min(kBatch, e - k0);
+        __syncthreads();
+        for (int i = tid; i < kb * nM; i += Tn) {
+            const int k = i / nM, m = i % nM;
+            const int s = src[k0 + k];
+            float v = M[(int64_t)s * nM + m];
+            const int ls = level[s];
+            if (ls != lt) v = ldexpf(v, (lt - ls) * (shell(m + tb.m0) - tb.s));
+            Msm[k * ldM + m] = v;
+        }
+        for (int i = tid; i < kb * nD; i += Tn) {
+            const int k = i / nD, d = i % nD;
+            Dsm[k * ldD + d] = D32[(int64_t)didx[k0 + k] * nD + d];
+        }
+        __syncthreads();
+        float acc = 0.0f;
+        for (int t = 0; t < T; ++t) {
+            const uint32_t u = desc[t * Tn + tid];
+            if (u == 0xffffffffu) break;
+            const float *Mp = Msm + (u & 511u);
+            const float *Dp = Dsm + ((u >> 9) & 511u);
+            int k = 0;
+            for (; k + 4 <= kb; k += 4) {
+                acc = fmaf(Dp[k * ldD], Mp[k * ldM], acc);
+                acc = fmaf(Dp[(k + 1) * ldD], Mp[(k + 1) * ldM], acc);
+                acc = fmaf(Dp[(k + 2) * ldD], Mp[(k + 2) * ldM], acc);
+                acc = fmaf(Dp[(k + 3) * ldD], Mp[(k + 3) * ldM], acc);
+            }
+            for (; k < kb; ++k) acc = fmaf(Dp[k * ldD], Mp[k * ldM], acc);
+            if (u & (1u << 18)) {
+                part[(u >> 19) * Tn + tid] += (double)acc;
+                acc = 0.0f;
+            }
+        }
+    }
+    __syncthreads();
+    for (int n = tid; n < tb.nL; n += Tn) {
+        double v = 0.0;
+        for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
+        L[(int64_t)c * tb.nL + n] = (float)v;
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+__global__ void __launch_bounds__(128)
+k_l2l32(int lb, const int32_t *parent, const int32_t *cx, const int32_t *cy, const int32_t *cz,
+        DevTables tb, float *L)
+{
+    extern __shared__ float sf[];
+    float *mono = sf;               // [nK]
+    float *Lp = mono + tb.nK;       // [nL], pre-scaled by 2^-(|q|+s+1)
+    const int c = lb + blockIdx.x;
+    const int pa = parent[c];
+    // z_c - z_p = (2 bit - 1) h_c: negative where the child's low bit is 0
+    const int bx = 1 - (cx[c] & 1), by = 1 - (cy[c] & 1), bz = 1 - (cz[c] & 1);
+    for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(k, bx, by, bz);
+    for (int q = threadIdx.x; q < tb.nL; q += blockDim.x)
+        Lp[q] = ldexpf(L[(int64_t)pa * tb.nL + q], -(shell(q) + tb.s + 1));
+    __syncthreads();
+    for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
+        if (shell(n) < tb.n_lo) continue;
+        float acc = 0.0f;
+        for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
+            acc = fmaf(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
+        L[(int64_t)c * tb.nL + n] += acc;
+    }
+}
+
+// ------------------------------------------------------------------ L2P
+constexpr int kL2PThreads = 128;
+
+__global__ void __launch_bounds__(kL2PThreads)
+k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
+        const float4 *o, const float *L, DevTables tb, int want_phi, int want_field,
+        double *phi, double *E)
+{
+    extern __shared__ float sf[];
+    const int P = tb.p, P1 = tb.p + 1;
+    float *Lsm = sf;                                       // [nL]
+    float *a = Lsm + tb.nL + threadIdx.x * 3 * P1;         // this thread's [3][P1]
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c];
+    const double h = half[c];
+    const float inv_h = (float)(1.0 / h);
+    const int eh = ilogb(h);
+    const double sphi = ldexp(1.0, -(tb.s + 1) * eh), sfield = ldexp(1.0, -(tb.s + 2) * eh);
+    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lsm[t] = L[(int64_t)c * tb.nL + t];
+    __syncthreads();
+    for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const float4 v = o[j];
+        axis_powers32(v.x * inv_h, P, a);
+        axis_powers32(v.y * inv_h, P, a + P1);
+        axis_powers32(v.z * inv_h, P, a + 2 * P1);
+        if (want_phi) {
+            float f = 0.0f;
+            for (int k = 0; k < tb.nL; ++k)
+                f = fmaf(a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]], Lsm[k], f);
+            phi[j] = (double)f * sphi;
+        }
+        if (want_field) {
+            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+            for (int k = 0; k < tb.nG; ++k) {
+                const float m = a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]];
+                g0 = fmaf(m, Lsm[tb.l2p_grad[3 * k]], g0);
+                g1 = fmaf(m, Lsm[tb.l2p_grad[3 * k + 1]], g1);
+                g2 = fmaf(m, Lsm[tb.l2p_grad[3 * k + 2]], g2);
+            }
+            E[3 * (int64_t)j] = -(double)g0 * sfield;
+            E[3 * (int64_t)j + 1] = -(double)g1 * sfield;
+            E[3 * (int64_t)j + 2] = -(double)g2 * sfield;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ P2P
+// FP32 pair terms on coordinates relative to the target leaf's centre:
+// target o_i, source o_j + (z_B - z_A), the centre offset formed exactly from
+// the integer cell coordinates.  Each thread sums a staged round in FP32 and
+// adds it to FP64 totals; the far field is added in FP64.
+template <int S, bool PHI, bool FIELD>
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, const float *Sj, float &f,
+                                       float &e0, float &e1, float &e2)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    y = y * fmaf(-0.5f * r2 * y, y, 1.5f);          // one Newton step: ~1 ulp
+    const float y2 = y * y;
+    if (S == 0) {
+        if (PHI) f = fmaf(Sj[0], y, f);
+        if (FIELD) {
+            const float w = Sj[0] * (y * y2);
+            e0 = fmaf(w, dx, e0); e1 = fmaf(w, dy, e1); e2 = fmaf(w, dz, e2);
+        }
+    } else if (S == 1) {
+        const float y3 = y * y2;
+        const float sr = fmaf(Sj[0], dx, fmaf(Sj[1], dy, Sj[2] * dz));
+        if (PHI) f = fmaf(-sr, y3, f);
+        if (FIELD) {
+            const float w = 3.0f * sr * (y3 * y2);
+            e0 = fmaf(Sj[0], y3, fmaf(-w, dx, e0));
+            e1 = fmaf(Sj[1], y3, fmaf(-w, dy, e1));
+            e2 = fmaf(Sj[2], y3, fmaf(-w, dz, e2));
+        }
+    } else {
+        const float y3 = y * y2, y5 = y3 * y2;
+        const float gq0 = fmaf(2.0f * Sj[0], dx, fmaf(Sj[1], dy, Sj[2] * dz));
+        const float gq1 = fmaf(Sj[1], dx, fmaf(2.0f * Sj[3], dy, Sj[4] * dz));
+        const float gq2 = fmaf(Sj[2], dx, fmaf(Sj[4], dy, 2.0f * Sj[5] * dz));
+        const float q = 0.5f * fmaf(gq0, dx, fmaf(gq1, dy, gq2 * dz));
+        const float tr = Sj[0] + Sj[3] + Sj[5];
+        if (PHI) f += 3.0f * q * y5 - tr * y3;
+        if (FIELD) {
+            const float a = 3.0f * y5;
+            const float w = fmaf(15.0f * q, y5 * y2, -3.0f * tr * y5);
+            e0 = fmaf(w, dx, fmaf(-a, gq0, e0));
+            e1 = fmaf(w, dy, fmaf(-a, gq1, e1));
+            e2 = fmaf(w, dz, fmaf(-a, gq2, e2));
+        }
+    }
+}
+
+constexpr int kP2PThreads = 128;
+constexpr int kP2PChunk = 768;
+constexpr int kGroups = 64;
+
+template <int S, bool PHI, bool FIELD>
+__global__ void __launch_bounds__(kP2PThreads)
+k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
+        const int32_t *src, const int32_t *level, const int32_t *cx, const int32_t *cy,
+        const int32_t *cz, double side, const float4 *o, const float4 *olo, const float *S32,
+        const double *phi_far, const double *E_far, const int32_t *perm, double *phi_out,
+        double *E_out)
+{
+    constexpr int nS = (S + 1) * (S + 2) / 2;
+    __shared__ float sx[kP2PChunk], sy[kP2PChunk], sz[kP2PChunk], sS[kP2PChunk * nS];
+    __shared__ float lx[kP2PChunk], ly[kP2PChunk], lz[kP2PChunk];
+    __shared__ double red[8][kP2PThreads];
+    __shared__ int gbeg[kGroups], gpre[kGroups + 1];
+    __shared__ float gdx[kGroups], gdy[kGroups], gdz[kGroups];
+    __shared__ int s_next_q, s_next_j, s_ngroups;
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c], nt = e - b;
+    const int q0 = off[c], q1 = off[c + 1];
+    const int tid = threadIdx.x;
+    const int lc = level[c];
+    const long long rc = 1ll << (kLevels - lc);
+    const long long ccx = (2ll * cx[c] + 1) * rc, ccy = (2ll * cy[c] + 1) * rc,
+                    ccz = (2ll * cz[c] + 1) * rc;
+    const double unit = ldexp(side, -(kLevels + 1));        // finest half-cell
+    for (int t0 = 0; t0 < nt; t0 += 2 * kP2PThreads) {
+        const int cnt = min(2 * kP2PThreads, nt - t0);
+        const int h = (cnt + 1) / 2;
+        const int k = max(1, kP2PThreads / h);
+        const int ti = tid % h, sp = tid / h;
+        const bool act = sp < k;
+        const bool two = act && (ti + h < cnt);
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 oi = act ? o[b + t0 + ti] : zero4, li = act ? olo[b + t0 + ti] : zero4;
+        const float4 oj = two ? o[b + t0 + ti + h] : zero4, lj = two ? olo[b + t0 + ti + h] : zero4;
+        double F[2] = {0.0, 0.0}, A[2] = {0.0, 0.0}, B[2] = {0.0, 0.0}, C[2] = {0.0, 0.0};
+        int q = q0, j_in = 0;
+        while (q < q1) {
+            __syncthreads();
+            if (tid == 0) {
+                int used = 0, g = 0;
+                while (q < q1 && used < kP2PChunk && g < kGroups) {
+                    const int sl = src[q];
+                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
+                    const long long rs = 1ll << (kLevels - level[sl]);
+                    gbeg[g] = lb;
+                    gpre[g] = used;
+                    gdx[g] = (float)((double)((2ll * cx[sl] + 1) * rs - ccx) * unit);
+                    gdy[g] = (float)((double)((2ll * cy[sl] + 1) * rs - ccy) * unit);
+                    gdz[g] = (float)((double)((2ll * cz[sl] + 1) * rs - ccz) * unit);
+                    ++g;
+                    used += take;
+                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
+                }
+                gpre[g] = used;
+                s_ngroups = g;
+                s_next_q = q;
+                s_next_j = j_in;
+            }
+            __syncthreads();
+            const int ng = s_ngroups, used = gpre[ng];
+            for (int d = tid; d < used; d += kP2PThreads) {
+                int lo = 0, hi = ng - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+                }
+                const int j = gbeg[lo] + (d - gpre[lo]);
+                const float4 v = o[j], vl = olo[j];
+                // source position in the target leaf's frame, as an exact hi + lo pair
+                two_sum_lo(v.x, gdx[lo], vl.x, sx[d], lx[d]);
+                two_sum_lo(v.y, gdy[lo], vl.y, sy[d], ly[d]);
+                two_sum_lo(v.z, gdz[lo], vl.z, sz[d], lz[d]);
+#pragma unroll
+                for (int a = 0; a < nS; ++a) sS[d * nS + a] = S32[(int64_t)j * nS + a];
+            }
+            __syncthreads();
+            if (act) {
+                float f = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, g = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                for (int j = sp; j < used; j += k) {
+                    const float ax = sx[j], ay = sy[j], az = sz[j];
+                    const float bx = lx[j], by = ly[j], bz = lz[j];
+                    const float *Sj = sS + j * nS;
+                    // hi parts of nearby points subtract exactly; the lo parts restore
+                    // the bits lost when the positions were rounded
+                    pair32<S, PHI, FIELD>((oi.x - ax) + (li.x - bx), (oi.y - ay) + (li.y - by),
+                                          (oi.z - az) + (li.z - bz), Sj, f, e0, e1, e2);
+                    if (two)
+                        pair32<S, PHI, FIELD>((oj.x - ax) + (lj.x - bx), (oj.y - ay) + (lj.y - by),
+                                              (oj.z - az) + (lj.z - bz), Sj, g, g0, g1, g2);
+                }
+                F[0] += f; A[0] += e0; B[0] += e1; C[0] += e2;
+                F[1] += g; A[1] += g0; B[1] += g1; C[1] += g2;
+            }
+            q = s_next_q;
+            j_in = s_next_j;
+        }
+        __syncthreads();
+        red[0][tid] = F[0]; red[1][tid] = A[0]; red[2][tid] = B[0]; red[3][tid] = C[0];
+        red[4][tid] = F[1]; red[5][tid] = A[1]; red[6][tid] = B[1]; red[7][tid] = C[1];
+        __syncthreads();
+        if (tid < h) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && tid + h >= cnt) break;
+                const int r = 4 * half;
+                double Fv = red[r][tid], Av = red[r + 1][tid], Bv = red[r + 2][tid], Cv = red[r + 3][tid];
+                for (int u = 1; u < k; ++u) {
+                    Fv += red[r][u * h + tid];
+                    Av += red[r + 1][u * h + tid];
+                    Bv += red[r + 2][u * h + tid];
+                    Cv += red[r + 3][u * h + tid];
+                }
+                const int ii = b + t0 + tid + half * h;
+                const int64_t oo = perm[ii];
+                if (PHI) phi_out[oo] = phi_far[ii] + Fv;
+                if (FIELD) {
+                    E_out[3 * oo] = E_far[3 * (int64_t)ii] + Av;
+                    E_out[3 * oo + 1] = E_far[3 * (int64_t)ii + 1] + Bv;
+                    E_out[3 * oo + 2] = E_far[3 * (int64_t)ii + 2] + Cv;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int S>
+void launch_p2p32(fmm_tree *t, int want_phi, int want_field, double *phi, double *E)
+{
+    auto go = [&](auto kern) {
+        kern<<<(unsigned)t->nleaves, kP2PThreads, 0, t->stream>>>(
+            (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
+            (const int32_t *)t->b_end.ptr, (const int32_t *)t->b_p2p_off.ptr,
+            (const int32_t *)t->b_p2p_src.ptr, (const int32_t *)t->b_level.ptr,
+            (const int32_t *)t->b_cx.ptr, (const int32_t *)t->b_cy.ptr, (const int32_t *)t->b_cz.ptr,
+            t->side, (const float4 *)t->b_o32.ptr, (const float4 *)t->b_o32.ptr + t->n,
+            (const float *)t->b_S32.ptr,
+            (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr, (const int32_t *)t->b_perm.ptr,
+            phi, E);
+    };
+    if (want_phi && want_field) go(k_p2p32<S, true, true>);
+    else if (want_phi) go(k_p2p32<S, true, false>);
+    else go(k_p2p32<S, false, true>);
+}
+
+void record(fmm_tree *t, int i)
+{
+    if (t->profiling) cudaEventRecord(t->ev[i], t->stream);
+}
+
+fmm_status upload_consts32(fmm_tree *t)
+{
+    static int ready[64] = {0};
+    if (t->device < 64 && ready[t->device]) return FMM_OK;
+    const MultiIndex &I = multi_index();
+    int8_t x[kMaxTot], y[kMaxTot], z[kMaxTot];
+    for (int i = 0; i < kMaxTot; ++i) { x[i] = (int8_t)I.nx[i]; y[i] = (int8_t)I.ny[i]; z[i] = (int8_t)I.nz[i]; }
+    float inv[kMaxOrder + 2], invf[kMaxOrder + 1];
+    inv[0] = 0.0f;
+    for (int q = 1; q < kMaxOrder + 2; ++q) inv[q] = (float)(1.0 / q);
+    double fct = 1.0;
+    for (int q = 0; q <= kMaxOrder; ++q) { if (q) fct *= q; invf[q] = (float)(1.0 / fct); }
+    FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(x_nx, x, sizeof(x)), "constants"));
+    FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(x_ny, y, sizeof(y)), "constants"));
+    FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(x_nz, z, sizeof(z)), "constants"));
+    FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(x_invint, inv, sizeof(inv)), "constants"));
+    FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(x_invfact, invf, sizeof(invf)), "constants"));
+    if (t->device < 64) ready[t->device] = 1;
+    return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *phi_out,
+                     double *E_out)
+{
+    cudaStream_t st = t->stream;
+    const int s = t->s;
+    FMM_TRY(upload_consts32(t));
+    DevTables tb;
+    const int32_t *lut;
+    FMM_TRY(upload_tables(t, s, p, want_phi ? 0 : 1, &tb, &lut));
+    const int64_t nc = t->ncells, n = t->n;
+    const int P1 = p + 1;
+    int e_side = 0;
+    std::frexp(t->side, &e_side);
+    e_side -= 1;                                   // side = 2^e_side
+    // cross-level M2L pairs scale FP32 values by 2^(gap * order): keep them in range
+    if (t->max_gap * (p + s + 1) > 96) {
+        t->err = "mixed precision: level gap " + std::to_string(t->max_gap) +
+                 " of an M2L pair is too large for FP32 scaled expansions at this order";
+        return FMM_EORDER;
+    }
+    FMM_TRY(build_dtables(t, p, tb, lut));
+    if (t->d32_p != p && t->n_doff > 0) {
+        FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * tb.nD));
+        k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
+            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, e_side, tb.nD, (const double *)t->b_D.ptr,
+            (float *)t->b_D32.ptr);
+        ++t->launches;
+        t->d32_p = p;
+    }
+    record(t, 6);
+    FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
+    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * t->nS));
+    FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * tb.nM));
+    FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
+    FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
+    FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
+    const int32_t *leaves = (const int32_t *)t->b_leaves.ptr;
+    const int32_t *begin = (const int32_t *)t->b_begin.ptr, *end = (const int32_t *)t->b_end.ptr;
+    const int32_t *cx = (const int32_t *)t->b_cx.ptr, *cy = (const int32_t *)t->b_cy.ptr,
+                  *cz = (const int32_t *)t->b_cz.ptr;
+    const double *half = (const double *)t->b_half.ptr;
+    float4 *o = (float4 *)t->b_o32.ptr;
+    float *S32 = (float *)t->b_S32.ptr, *M = (float *)t->b_M32.ptr, *L = (float *)t->b_L32.ptr;
+
+    k_prep32<<<(unsigned)t->nleaves, 128, 0, st>>>(leaves, begin, end, (const double *)t->b_centre.ptr,
+                                                   (const double *)t->b_px.ptr,
+                                                   (const double *)t->b_py.ptr,
+                                                   (const double *)t->b_pz.ptr,
+                                                   (const double *)t->b_S.ptr, t->nS, o, o + n,
+                                                   S32);
+    {
+        size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * tb.nK + kChunk * tb.nS);
+        cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_p2m32<<<(unsigned)t->nleaves, 128, smem, st>>>(leaves, begin, end, half, o, S32, tb, M);
+    }
+    t->launches += 2;
+    record(t, 7);
+    {
+        size_t smem = 4 * (size_t)(tb.nK + tb.nM);
+        for (int l = t->nlevels - 2; l >= 0; --l) {
+            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
+            k_m2m32<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
+                                            (const int32_t *)t->b_nchild.ptr, cx, cy, cz, tb, M);
+            ++t->launches;
+        }
+    }
+    record(t, 8);
+    cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nL, st);
+    if (t->n_m2l > 0) {
+        const int ldM = tb.nM | 1, ldD = tb.nD | 1;
+        size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +
+                      4 * ((size_t)kBatch * (ldM + ldD) + (size_t)tb.m2l_T * kM2LThreads);
+        cudaFuncSetAttribute(k_m2l32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2l32<<<(unsigned)nc, kM2LThreads, smem, st>>>(
+            (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
+            (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr, M,
+            (const float *)t->b_D32.ptr, tb, L);
+        ++t->launches;
+    }
+    record(t, 9);
+    {
+        size_t smem = 4 * (size_t)(tb.nK + tb.nL);
+        for (int l = 1; l < t->nlevels; ++l) {
+            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
+            k_l2l32<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_parent.ptr, cx, cy, cz, tb, L);
+            ++t->launches;
+        }
+    }
+    record(t, 10);
+    {
+        size_t smem = 4 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
+        cudaFuncSetAttribute(k_l2p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_l2p32<<<(unsigned)t->nleaves, kL2PThreads, smem, st>>>(
+            leaves, begin, end, half, o, L, tb, want_phi, want_field, (double *)t->b_phi.ptr,
+            (double *)t->b_E.ptr);
+        ++t->launches;
+    }
+    record(t, 11);
+    switch (s) {
+    case 0: launch_p2p32<0>(t, want_phi, want_field, phi_out, E_out); break;
+    case 1: launch_p2p32<1>(t, want_phi, want_field, phi_out, E_out); break;
+    default: launch_p2p32<2>(t, want_phi, want_field, phi_out, E_out); break;
+    }
+    ++t->launches;
+    return cuda_check(t, cudaGetLastError(), "mixed-precision kernels");
+}
+
+}  // namespace fmm

@@ -132,17 +132,6 @@ constexpr int kM2LBatch = 16;
 
 __constant__ int8_t c_nx[kMaxTot], c_ny[kMaxTot], c_nz[kMaxTot];
 
-// Device views of the uploaded tables.
-struct DevTables {
-    int s, p, n_lo, nS, nM, nL, nD, m0, nK, nG;
-    const int *p2m_terms;
-    const int *m2m_off, *m2m_k, *m2m_q;
-    const int *l2l_off, *l2l_k, *l2l_q;
-    const int *l2p_grad;
-    const int *m2l_red_off, *m2l_red_src;
-    const uint32_t *m2l_desc;
-    int m2l_T, m2l_slots;
-};
 
 // ---------------------------------------------------- derivative tables
 // r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
@@ -159,7 +148,7 @@ __global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, double side, int
     double R[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        R[i] = (double)((long long)((key >> (38 - 19 * i)) & 0x7ffffull) - kKeyBias) * unit;
+        R[i] = (double)((long long)((key >> (34 - 17 * i)) & 0x1ffffull) - kKeyBias) * unit;
     double *Dr = D + r * nD;
     const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
     const double inv_r2 = 1.0 / r2;
@@ -438,6 +427,8 @@ k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const dou
     }
 }
 
+}  // namespace
+
 inline unsigned grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // Table buffer layout (int32): lut | p2m | m2m_off | m2m_k | m2m_q | l2l_off |
@@ -464,7 +455,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         return o;
     };
     const bool rebuild = !(t->tab_key_s == s && t->tab_key_p == p && t->tab_key_nlo == n_lo);
-    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreads);
+    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreadsShared);
     {
         const MultiIndex &I = multi_index();
         std::vector<int> lutv((kMaxOrder + 1) * (kMaxOrder + 1) * (kMaxOrder + 1));
@@ -498,12 +489,29 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     return FMM_OK;
 }
 
+namespace {
+
 void record(fmm_tree *t, int i)
 {
     if (t->profiling) cudaEventRecord(t->ev[i], t->stream);
 }
 
 }  // namespace
+
+// derivative tables, one FP64 row per distinct M2L offset key
+fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t *lut)
+{
+    if (t->d_p != p && t->n_doff > 0) {
+        FMM_TRY(ensure(t, t->b_D, 8 * (size_t)t->n_doff * tb.nD));
+        k_dtables<<<grid(t->n_doff, 128), 128, 0, t->stream>>>((const uint64_t *)t->b_dkeys.ptr,
+                                                                t->n_doff, t->side, tb.nD, lut,
+                                                                (double *)t->b_D.ptr);
+        ++t->launches;
+        t->d_p = p;
+        t->d32_p = -1;
+    }
+    return FMM_OK;
+}
 
 fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
 {
@@ -516,14 +524,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
     const int64_t nc = t->ncells, n = t->n;
     const int P1 = p + 1;
 
-    // derivative tables, one row per distinct M2L offset
-    if (t->d_p != p && t->n_doff > 0) {
-        FMM_TRY(ensure(t, t->b_D, 8 * (size_t)t->n_doff * tb.nD));
-        k_dtables<<<grid(t->n_doff, 128), 128, 0, st>>>((const uint64_t *)t->b_dkeys.ptr, t->n_doff,
-                                                         t->side, tb.nD, lut, (double *)t->b_D.ptr);
-        ++t->launches;
-        t->d_p = p;
-    }
+    FMM_TRY(build_dtables(t, p, tb, lut));
     record(t, 6);
     FMM_TRY(ensure(t, t->b_M, 8 * (size_t)nc * tb.nM));
     FMM_TRY(ensure(t, t->b_L, 8 * (size_t)nc * tb.nL));

@@ -9,12 +9,50 @@
 //           with q(R) = sum_{|a|=2} S_a R^a and tr = S_200 + S_020 + S_002.
 // Pairs with r = 0 (the target itself, coincident points) contribute nothing.
 #include <algorithm>
+#include <cstdlib>
 
 #include "fmm_internal.cuh"
 
 namespace fmm {
 
 namespace {
+
+// 1/sqrt(x) for x > 0 in FP64 without the double-precision MUFU path:
+//  1. x = m 4^k with m in [1, 4), by integer operations on the exponent;
+//  2. an FP32 seed y_m = rsqrtf(m) (m rounded toward zero to float);
+//  3. y0 = y_m 2^-k, assembled from the float's bits;
+//  4. one third-order Householder step for f(y) = y^-2 - x:
+//        e = 1 - x y0^2,   y = y0 + y0 e (1/2 + 3/8 e),
+//     which leaves a relative error of about (5/16) e^3 ~ 2^-67 before the
+//     final roundings (e ~ 2^-22 from the seed).  Five FP64 operations.
+// x = 0 returns +inf (the caller masks it); subnormal x is not supported
+// (pairs closer than ~1e-154 do not occur in a dyadic octree of doubles).
+__device__ __forceinline__ double rsqrt_hh(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int ex = ((hi >> 20) & 0x7ff) - 1023;                 // unbiased exponent
+    const int k = ex >> 1;                                      // floor(ex / 2)
+    const int mhi = (hi & 0x000fffff) | ((1023 + (ex - 2 * k)) << 20);   // m in [1, 4)
+    // float with m's exponent and the top 23 mantissa bits
+    const int fbits = ((mhi - (896 << 20)) << 3) | ((unsigned)lo >> 29);
+    const float ym = rsqrtf(__int_as_float(fbits));
+    const int yb = __float_as_int(ym);
+    const int yhi = ((yb >> 3) + (896 << 20)) - (k << 20);
+    const double y0 = __hiloint2double(yhi, yb << 29);
+    const double t = x * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double c = fma(e, 0.375, 0.5);
+    const double u = y0 * e;
+    return fma(u, c, y0);
+}
+
+__global__ void k_check_rsqrt(const double *x, int64_t n, double *own, double *ref)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    own[i] = rsqrt_hh(x[i]);
+    ref[i] = rsqrt(x[i]);
+}
 
 template <int S, bool PHI, bool FIELD>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, const double *Sj,
@@ -61,11 +99,48 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, const
 }
 
 constexpr int kP2PThreads = 128;
+constexpr int kP2PChunk = 512;            // source particles staged per round
 
-// One block per target leaf.  A leaf of nt <= 128 targets is covered
-// floor(128/nt) times; each copy takes every k-th particle of every source
-// leaf, and the copies are summed in a fixed order.  The block then adds the
-// far field from L2P and writes phi, E at the caller's original index.
+// One source seen from one target, FP64, with S3 = 3 S pre-scaled in shared memory.
+template <int S, bool PHI, bool FIELD>
+__device__ __forceinline__ void pair_p2p(double dx, double dy, double dz, const double *Sj,
+                                         const double *S3j, double &f, double &e0, double &e1,
+                                         double &e2)
+{
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    // r2 >= 0, so "r2 > 0" is "its bit pattern is nonzero": an integer test
+    const double y = __double_as_longlong(r2) != 0 ? rsqrt_hh(r2) : 0.0;
+    const double y2 = y * y;
+    if (S == 0) {
+        if (PHI) f = fma(Sj[0], y, f);
+        if (FIELD) {
+            const double w = Sj[0] * (y * y2);
+            e0 = fma(w, dx, e0); e1 = fma(w, dy, e1); e2 = fma(w, dz, e2);
+        }
+    } else if (S == 1) {
+        const double y3 = y * y2;
+        if (PHI) f = fma(-fma(Sj[0], dx, fma(Sj[1], dy, Sj[2] * dz)), y3, f);
+        if (FIELD) {
+            // E = S/r^3 - 3 (S.R) R / r^5
+            const double w3 = fma(S3j[0], dx, fma(S3j[1], dy, S3j[2] * dz)) * (y3 * y2);
+            e0 = fma(Sj[0], y3, fma(-w3, dx, e0));
+            e1 = fma(Sj[1], y3, fma(-w3, dy, e1));
+            e2 = fma(Sj[2], y3, fma(-w3, dz, e2));
+        }
+    } else {
+        pair_fp64<2, PHI, FIELD>(dx, dy, dz, Sj, f, e0, e1, e2);
+    }
+}
+
+// One block per target leaf.  The flattened source list of the leaf (all
+// particles of its P2P partner leaves, in list order) is staged in shared
+// memory in rounds of up to kP2PChunk particles from at most kP2PGroups
+// leaves.  A leaf of nt <= 128 targets is covered k = floor(128/nt) times and
+// copy c takes the staged sources c, c+k, c+2k, ..., so all threads run the
+// same trip count.  Copies are combined in a fixed order, the L2P far field
+// is added and the result is written at the caller's original index.
+constexpr int kP2PGroups = 64;
+
 template <int S, bool PHI, bool FIELD>
 __global__ void __launch_bounds__(kP2PThreads)
 k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
@@ -74,7 +149,11 @@ k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int
       double *E_out)
 {
     constexpr int nS = (S + 1) * (S + 2) / 2;
+    __shared__ double sx[kP2PChunk], sy[kP2PChunk], sz[kP2PChunk];
+    __shared__ double sS[kP2PChunk * nS], sS3[S == 1 ? kP2PChunk * 3 : 1];
     __shared__ double red[4][kP2PThreads];
+    __shared__ int gbeg[kP2PGroups], gpre[kP2PGroups + 1];
+    __shared__ int s_next_q, s_next_j, s_ngroups;
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c], nt = e - b;
     const int q0 = off[c], q1 = off[c + 1];
@@ -83,21 +162,55 @@ k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int
         const int cnt = min(kP2PThreads, nt - t0);
         const int k = max(1, kP2PThreads / cnt);
         const int ti = tid % cnt, sp = tid / cnt;
+        const bool act = sp < k;
+        const int i = b + t0 + ti;
+        const double xi = act ? px[i] : 0.0, yi = act ? py[i] : 0.0, zi = act ? pz[i] : 0.0;
         double f = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
-        if (sp < k) {
-            const int i = b + t0 + ti;
-            const double xi = px[i], yi = py[i], zi = pz[i];
-            for (int q = q0; q < q1; ++q) {
-                const int sl = src[q];
-                const int je = end[sl];
-                for (int j = begin[sl] + sp; j < je; j += k) {
-                    double Sj[nS];
+        int q = q0, j_in = 0;                 // next partner leaf and offset inside it
+        while (q < q1) {
+            __syncthreads();                  // previous round's staged data is consumed
+            if (tid == 0) {
+                int used = 0, g = 0;
+                while (q < q1 && used < kP2PChunk && g < kP2PGroups) {
+                    const int sl = src[q];
+                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
+                    gbeg[g] = lb;
+                    gpre[g] = used;
+                    ++g;
+                    used += take;
+                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
+                }
+                gpre[g] = used;
+                s_ngroups = g;
+                s_next_q = q;
+                s_next_j = j_in;
+            }
+            __syncthreads();
+            const int ng = s_ngroups, used = gpre[ng];
+            for (int d = tid; d < used; d += kP2PThreads) {
+                int lo = 0, hi = ng - 1;      // last group with gpre[g] <= d
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+                }
+                const int j = gbeg[lo] + (d - gpre[lo]);
+                sx[d] = px[j]; sy[d] = py[j]; sz[d] = pz[j];
 #pragma unroll
-                    for (int a = 0; a < nS; ++a) Sj[a] = Sm[(int64_t)j * nS + a];
-                    pair_fp64<S, PHI, FIELD>(xi - px[j], yi - py[j], zi - pz[j], Sj, f, e0, e1, e2);
+                for (int a = 0; a < nS; ++a) {
+                    const double v = Sm[(int64_t)j * nS + a];
+                    sS[d * nS + a] = v;
+                    if (S == 1) sS3[d * 3 + a] = 3.0 * v;
                 }
             }
+            __syncthreads();
+            if (act)
+                for (int j = sp; j < used; j += k)
+                    pair_p2p<S, PHI, FIELD>(xi - sx[j], yi - sy[j], zi - sz[j], sS + j * nS,
+                                            S == 1 ? sS3 + j * 3 : sS, f, e0, e1, e2);
+            q = s_next_q;
+            j_in = s_next_j;
         }
+        __syncthreads();
         red[0][tid] = f; red[1][tid] = e0; red[2][tid] = e1; red[3][tid] = e2;
         __syncthreads();
         if (tid < cnt) {
@@ -107,13 +220,124 @@ k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int
                 e1 += red[2][u * cnt + tid];
                 e2 += red[3][u * cnt + tid];
             }
-            const int i = b + t0 + tid;
-            const int64_t o = perm[i];
-            if (PHI) phi_out[o] = phi_far[i] + f;
+            const int ii = b + t0 + tid;
+            const int64_t o = perm[ii];
+            if (PHI) phi_out[o] = phi_far[ii] + f;
             if (FIELD) {
-                E_out[3 * o] = E_far[3 * (int64_t)i] + e0;
-                E_out[3 * o + 1] = E_far[3 * (int64_t)i + 1] + e1;
-                E_out[3 * o + 2] = E_far[3 * (int64_t)i + 2] + e2;
+                E_out[3 * o] = E_far[3 * (int64_t)ii] + e0;
+                E_out[3 * o + 1] = E_far[3 * (int64_t)ii + 1] + e1;
+                E_out[3 * o + 2] = E_far[3 * (int64_t)ii + 2] + e2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Variant with two targets per thread: each staged source is read once from
+// shared memory for two pair evaluations.  A chunk of up to 2*128 targets is
+// split into halves of h = ceil(cnt/2); thread (ti, copy) owns targets ti and
+// ti + h (the second one only if it exists).
+template <int S, bool PHI, bool FIELD>
+__global__ void __launch_bounds__(kP2PThreads)
+k_p2p_x2(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
+         const int32_t *src, const double *px, const double *py, const double *pz,
+         const double *Sm, const double *phi_far, const double *E_far, const int32_t *perm,
+         double *phi_out, double *E_out)
+{
+    constexpr int nS = (S + 1) * (S + 2) / 2;
+    __shared__ double sx[kP2PChunk], sy[kP2PChunk], sz[kP2PChunk];
+    __shared__ double sS[kP2PChunk * nS], sS3[S == 1 ? kP2PChunk * 3 : 1];
+    __shared__ double red[8][kP2PThreads];
+    __shared__ int gbeg[kP2PGroups], gpre[kP2PGroups + 1];
+    __shared__ int s_next_q, s_next_j, s_ngroups;
+    const int c = leaves[blockIdx.x];
+    const int b = begin[c], e = end[c], nt = e - b;
+    const int q0 = off[c], q1 = off[c + 1];
+    const int tid = threadIdx.x;
+    for (int t0 = 0; t0 < nt; t0 += 2 * kP2PThreads) {
+        const int cnt = min(2 * kP2PThreads, nt - t0);
+        const int h = (cnt + 1) / 2;
+        const int k = max(1, kP2PThreads / h);
+        const int ti = tid % h, sp = tid / h;
+        const bool act = sp < k;
+        const bool two = act && (ti + h < cnt);
+        const int i = b + t0 + ti, i2 = i + h;
+        const double xi = act ? px[i] : 0.0, yi = act ? py[i] : 0.0, zi = act ? pz[i] : 0.0;
+        const double xj = two ? px[i2] : 0.0, yj = two ? py[i2] : 0.0, zj = two ? pz[i2] : 0.0;
+        double f = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
+        double g = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        int q = q0, j_in = 0;
+        while (q < q1) {
+            __syncthreads();
+            if (tid == 0) {
+                int used = 0, gg = 0;
+                while (q < q1 && used < kP2PChunk && gg < kP2PGroups) {
+                    const int sl = src[q];
+                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
+                    gbeg[gg] = lb;
+                    gpre[gg] = used;
+                    ++gg;
+                    used += take;
+                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
+                }
+                gpre[gg] = used;
+                s_ngroups = gg;
+                s_next_q = q;
+                s_next_j = j_in;
+            }
+            __syncthreads();
+            const int ng = s_ngroups, used = gpre[ng];
+            for (int d = tid; d < used; d += kP2PThreads) {
+                int lo = 0, hi = ng - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+                }
+                const int j = gbeg[lo] + (d - gpre[lo]);
+                sx[d] = px[j]; sy[d] = py[j]; sz[d] = pz[j];
+#pragma unroll
+                for (int a = 0; a < nS; ++a) {
+                    const double v = Sm[(int64_t)j * nS + a];
+                    sS[d * nS + a] = v;
+                    if (S == 1) sS3[d * 3 + a] = 3.0 * v;
+                }
+            }
+            __syncthreads();
+            if (act) {
+                for (int j = sp; j < used; j += k) {
+                    const double ax = sx[j], ay = sy[j], az = sz[j];
+                    const double *Sj = sS + j * nS, *S3 = S == 1 ? sS3 + j * 3 : sS;
+                    pair_p2p<S, PHI, FIELD>(xi - ax, yi - ay, zi - az, Sj, S3, f, e0, e1, e2);
+                    if (two) pair_p2p<S, PHI, FIELD>(xj - ax, yj - ay, zj - az, Sj, S3, g, g0, g1, g2);
+                }
+            }
+            q = s_next_q;
+            j_in = s_next_j;
+        }
+        __syncthreads();
+        red[0][tid] = f; red[1][tid] = e0; red[2][tid] = e1; red[3][tid] = e2;
+        red[4][tid] = g; red[5][tid] = g0; red[6][tid] = g1; red[7][tid] = g2;
+        __syncthreads();
+        if (tid < h) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && tid + h >= cnt) break;
+                const int r = 4 * half;
+                double F = red[r][tid], A = red[r + 1][tid], B = red[r + 2][tid], C = red[r + 3][tid];
+                for (int u = 1; u < k; ++u) {
+                    F += red[r][u * h + tid];
+                    A += red[r + 1][u * h + tid];
+                    B += red[r + 2][u * h + tid];
+                    C += red[r + 3][u * h + tid];
+                }
+                const int ii = b + t0 + tid + half * h;
+                const int64_t o = perm[ii];
+                if (PHI) phi_out[o] = phi_far[ii] + F;
+                if (FIELD) {
+                    E_out[3 * o] = E_far[3 * (int64_t)ii] + A;
+                    E_out[3 * o + 1] = E_far[3 * (int64_t)ii + 1] + B;
+                    E_out[3 * o + 2] = E_far[3 * (int64_t)ii + 2] + C;
+                }
             }
         }
         __syncthreads();
@@ -172,6 +396,16 @@ void launch_p2p_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr,
             (const int32_t *)t->b_perm.ptr, phi, E);
     };
+    static const int variant = [] {
+        const char *v = getenv("FMM_P2P_VARIANT");
+        return v ? atoi(v) : 1;
+    }();
+    if (variant == 1) {
+        if (want_phi && want_field) args(k_p2p_x2<S, true, true>);
+        else if (want_phi) args(k_p2p_x2<S, true, false>);
+        else args(k_p2p_x2<S, false, true>);
+        return;
+    }
     if (want_phi && want_field) args(k_p2p<S, true, true>);
     else if (want_phi) args(k_p2p<S, true, false>);
     else args(k_p2p<S, false, true>);
@@ -199,6 +433,11 @@ fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, d
     }
     ++t->launches;
     return cuda_check(t, cudaGetLastError(), "p2p kernel");
+}
+
+void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref)
+{
+    if (n > 0) k_check_rsqrt<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, own, ref);
 }
 
 void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,

@@ -317,8 +317,10 @@ __global__ void k_p2p_interactions(const uint64_t *keys, int64_t np, int cbits, 
 }
 
 // --------------------------------------------------- D-table offset keys
-// key = finer level (5 bits) | three 19-bit biased offsets in units of the
-// finer cell's half side.  The real offset is exactly offset * side / 2^(lf+1).
+// key = finer level (5 bits) | level gap (5 bits) | target-is-finer (1 bit) |
+// three 17-bit biased offsets in units of the finer cell's half side.  The
+// real offset is exactly offset * side / 2^(lf+1); the level fields let the
+// scaled (mixed-precision) rows depend on the target's level.
 __device__ __forceinline__ uint64_t hash64(uint64_t x)
 {
     x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull;
@@ -328,7 +330,7 @@ __device__ __forceinline__ uint64_t hash64(uint64_t x)
 
 __global__ void k_offset_keys(CellArrays c, const uint64_t *pair_keys, int64_t np, int cbits,
                               unsigned long long *table, uint32_t hmask, uint32_t *slot_of,
-                              int *err)
+                              int *err, unsigned *max_gap)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= np) return;
@@ -338,10 +340,12 @@ __global__ void k_offset_keys(CellArrays c, const uint64_t *pair_keys, int64_t n
     long long d[3] = {(2ll * c.cx[a] + 1) * sa - (2ll * c.cx[b] + 1) * sb,
                       (2ll * c.cy[a] + 1) * sa - (2ll * c.cy[b] + 1) * sb,
                       (2ll * c.cz[a] + 1) * sa - (2ll * c.cz[b] + 1) * sb};
-    uint64_t key = (uint64_t)lf << 57;
+    const int gap = la > lb ? la - lb : lb - la;
+    if (gap) atomicMax(max_gap, (unsigned)gap);
+    uint64_t key = (uint64_t)lf << 57 | (uint64_t)gap << 52 | (uint64_t)(la > lb) << 51;
     for (int i = 0; i < 3; ++i) {
         if (d[i] < -kKeyBias || d[i] >= kKeyBias) { atomicOr(err, kErrKeyRange); slot_of[k] = 0; return; }
-        key |= (uint64_t)(d[i] + kKeyBias) << (38 - 19 * i);
+        key |= (uint64_t)(d[i] + kKeyBias) << (34 - 17 * i);
     }
     uint32_t h = (uint32_t)hash64(key) & hmask;
     for (uint32_t probe = 0; probe <= hmask; ++probe) {
@@ -411,7 +415,7 @@ fmm_status read_err(fmm_tree *t)
     FMM_TRY(cuda_check(t, cudaStreamSynchronize(t->stream), "sync"));
     if (e & kErrNonFinite) { t->err = "non-finite particle position"; return FMM_EINVAL; }
     if (e & kErrKeyRange) {
-        t->err = "an accepted M2L offset exceeds 2^18 finer half-cells (theta too small for the tree)";
+        t->err = "an accepted M2L offset exceeds 2^16 finer half-cells (theta too small for the tree)";
         return FMM_EINVAL;
     }
     return FMM_OK;
@@ -667,6 +671,7 @@ fmm_status build_lists(fmm_tree *t, double theta)
     if (nm2l > 0) {
         uint32_t H = 1u << 16;
         while (H < 4 * (uint32_t)std::min<int64_t>(nm2l, 1 << 22) && H < (1u << 20)) H <<= 1;
+        cudaMemsetAsync(cnt + 12, 0, 4, st);
         for (;;) {
             FMM_TRY(ensure(t, t->b_hash, 8 * (size_t)H));
             FMM_TRY(ensure(t, t->b_flags, 4 * ((size_t)H + 1)));
@@ -676,13 +681,13 @@ fmm_status build_lists(fmm_tree *t, double theta)
             k_offset_keys<<<grid(nm2l, 256), 256, 0, st>>>(c, lk, nm2l, cbits,
                                                             (unsigned long long *)t->b_hash.ptr,
                                                             H - 1, (uint32_t *)t->b_m2l_didx.ptr,
-                                                            (int *)t->b_err.ptr);
+                                                            (int *)t->b_err.ptr, cnt + 12);
             ++t->launches;
             int e = 0;
             FMM_TRY(cuda_check(t, cudaMemcpyAsync(&e, t->b_err.ptr, 4, cudaMemcpyDeviceToHost, st), "err"));
             FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
             if (e & kErrKeyRange) {
-                t->err = "an accepted M2L offset exceeds 2^18 finer half-cells (theta too small for the tree)";
+                t->err = "an accepted M2L offset exceeds 2^16 finer half-cells (theta too small for the tree)";
                 return FMM_EINVAL;
             }
             if (!(e & kErrHashFull)) break;
@@ -693,9 +698,12 @@ fmm_status build_lists(fmm_tree *t, double theta)
         k_slot_flags<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, flag);
         exclusive_scan_u32(flag, dense, (int64_t)H + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
         uint32_t nd = 0;
+        unsigned gmax = 0;
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&gmax, cnt + 12, 4, cudaMemcpyDeviceToHost, st), "gap"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nd, dense + H, 4, cudaMemcpyDeviceToHost, st), "ndoff"));
         FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
         ndoff = nd;
+        t->max_gap = (int)gmax;
         FMM_TRY(ensure(t, t->b_dkeys, 8 * std::max<int64_t>(ndoff, 1)));
         k_slot_compact<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, dense,
                                                        (uint64_t *)t->b_dkeys.ptr);

@@ -221,6 +221,16 @@ def direct_sum(positions, moments, source_order, targets=None, want_potential=Tr
     return phi, E
 
 
+def check_rsqrt(x, stream=None):
+    """(library 1/sqrt(x), CUDA rsqrt(x)) for a CUDA float64 tensor x > 0."""
+    fn = lib().fmm_check_rsqrt
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int
+    own, ref = torch.empty_like(x), torch.empty_like(x)
+    _check(fn(_stream_ptr(stream), _ptr(x), x.numel(), _ptr(own), _ptr(ref)), None, "check_rsqrt")
+    return own, ref
+
+
 def morton_order(positions, stream=None):
     """(keys uint64-as-int64 [n], perm int32 [n]) as CUDA tensors."""
     _dev_f64(positions, "positions", 3)

@@ -1,0 +1,102 @@
+"""Mixed-precision form (FMM_FP32): scaled FP32 expansions and pair terms, FP64 D tables and outputs.
+
+Tolerances: the FP32 form is compared with the FP64 oracle FMM on the same tree
+(difference = FP32 rounding only: ~2e-7 measured, bounded here by 1e-6 relative
+RMS = ~16 FP32 ulps), and -- the criterion that matters -- its error against the
+FP64 direct sum must stay within 1.1x the FP64 FMM truncation error at the same
+p.  Where that truncation error itself falls to the FP32 rounding floor
+(quadrupoles at p >= 5: ~4e-7), the bound is 1.1x truncation + the floor.
+"""
+FP32_FLOOR = 5e-7
+import numpy as np
+import pytest
+
+from paper_2005_12351_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True):
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    tree = fmm.create_tree(max_leaf=ncrit, precision=precision)
+    tree.set_sources(to_dev(pos), to_dev(S), s)
+    phi, E = tree.evaluate(p, theta, want_phi, want_field)
+    torch.cuda.synchronize()
+    return (phi.cpu().numpy() if phi is not None else None,
+            E.cpu().numpy() if E is not None else None), tree
+
+
+@pytest.mark.parametrize("s,p,dist,n,ncrit", [
+    (0, 4, "uniform", 2000, 64),
+    (0, 6, "plummer", 20_000, 32),
+    (1, 6, "uniform", 30_000, 128),
+    (1, 5, "plummer", 20_000, 64),
+    (2, 5, "uniform", 15_000, 128),
+    (2, 3, "plummer", 10_000, 16),
+])
+def test_fp32_close_to_fp64_oracle(orc, s, p, dist, n, ncrit):
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(n, s, dist, 700 + 10 * s + p)
+    (phi, E), _ = gpu_eval(pos, S, s, p, 0.5, ncrit, "fp32")
+    t = orc.Tree(pos, ncrit)
+    t.lists(0.5)
+    phi_o, E_o = t.fmm(S, s, p)
+    assert rel_rms(phi, phi_o) < 1e-6, rel_rms(phi, phi_o)
+    assert rel_rms(E, E_o) < 1e-6, rel_rms(E, E_o)
+
+
+@pytest.mark.parametrize("s,p,floor", [(0, 4, 0.0), (0, 8, 0.0), (1, 6, 0.0), (1, 8, 0.0),
+                                        (2, 3, 0.0), (2, 5, FP32_FLOOR)])
+def test_fp32_error_within_1p1_of_fp64_truncation(orc, s, p, floor):
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(12_000, s, "plummer", 800 + s)
+    (phi32, E32), _ = gpu_eval(pos, S, s, p, 0.5, 64, "fp32")
+    (phi64, E64), _ = gpu_eval(pos, S, s, p, 0.5, 64, "fp64")
+    phi_d, E_d = orc.direct(pos, S, s)
+    e32, e64 = rel_rms(E32, E_d), rel_rms(E64, E_d)
+    assert e32 <= 1.1 * e64 + floor, (e32, e64)
+    assert rel_rms(phi32, phi_d) <= 1.1 * rel_rms(phi64, phi_d) + floor
+
+
+def test_plummer_4m_p8_fp32_vs_fp64(orc):
+    """4M Plummer dipoles, p=8, n_crit 128: the FP32 form's field error against
+    the FP64 direct sum (4,096 sampled particles) is within 1.1x that of the
+    FP64 GPU form, and the FP64 form matches the oracle FMM on the same tree."""
+    import torch
+    from gpu_util import rel_rms, to_dev
+    from paper_2005_12351_gb300 import fmm
+    w = synth.WORKLOADS["dipole_plummer_4m_p8"]
+    pos, S = synth.make_system(w["n"], w["s"], w["dist"], w["seed"])
+    (_, E32), t32 = gpu_eval(pos, S, 1, 8, 0.5, 128, "fp32", want_phi=False)
+    (_, E64), t64 = gpu_eval(pos, S, 1, 8, 0.5, 128, "fp64", want_phi=False)
+    t32.destroy()
+    t64.destroy()
+    tg = synth.sample_indices(len(pos), 4096, 11)
+    _, E_d = fmm.direct_sum(to_dev(pos), to_dev(S), 1, targets=to_dev(tg.astype(np.int32)),
+                            want_potential=False)
+    E_d = E_d.cpu().numpy()
+    e32, e64 = rel_rms(E32[tg], E_d), rel_rms(E64[tg], E_d)
+    assert e32 <= 1.1 * e64, (e32, e64)
+    ot = orc.Tree(pos, 128)
+    ot.lists(0.5)
+    _, E_o = ot.fmm(S, 1, 8, targets=tg[:1024])
+    assert rel_rms(E64[tg[:1024]], E_o) < 1e-12
+    torch.cuda.synchronize()
+
+
+def test_fp32_edge_cases():
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    tree = fmm.create_tree(max_leaf=8, precision="fp32")
+    tree.set_sources(to_dev(np.array([[0.3, 0.4, 0.5]])), to_dev(np.array([[1.0, 0.0, 0.0]])), 1)
+    phi, E = tree.evaluate(3, 0.5)
+    assert phi.item() == 0.0 and not E.any()
+    tree.set_sources(torch.zeros((0, 3), dtype=torch.float64, device="cuda"),
+                     torch.zeros((0, 3), dtype=torch.float64, device="cuda"), 1)
+    phi, E = tree.evaluate(3, 0.5)
+    assert phi.numel() == 0
+    with pytest.raises(fmm.FMMError):
+        fmm.create_tree(precision="3xtf32")
