@@ -122,8 +122,22 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 def oracle_sample(w: dict, n_sample: int, seed_shift: int = 0):
     """Time the oracle FMM on a bounded sample: the full tree and lists of the
     workload, then the FMM result for n_sample particles (upward pass on all
-    cells, downward pass on their ancestor chains, L2P and P2P for them)."""
+    cells, downward pass on their ancestor chains, L2P and P2P for them).
+    For a batch workload the sample is whole systems (every 64th), each
+    evaluated completely."""
     import oracle
+    if "batch" in w:
+        pos, S, off = synth.make_batch(w["batch"], w["nlo"], w["nhi"], w["s"], w["seed"] + seed_shift,
+                                       w["dist"])
+        t0 = time.perf_counter()
+        k_tot = 0
+        for k in range(0, w["batch"], 64):
+            a, b = int(off[k]), int(off[k + 1])
+            tree = oracle.Tree(pos[a:b], w["ncrit"])
+            tree.lists(w["theta"])
+            tree.fmm(S[a:b], w["s"], w["p"])
+            k_tot += b - a
+        return time.perf_counter() - t0, k_tot, oracle.num_threads()
     pos, S = synth.make_system(w["n"], w["s"], w["dist"], w["seed"] + seed_shift)
     tg = synth.sample_indices(w["n"], n_sample, 17)
     t0 = time.perf_counter()
@@ -168,7 +182,11 @@ def run_reference(args, w):
 
 
 def config_of(w, args):
-    return {"workload": args.workload, "n": w["n"], "source_order": w["s"], "p": w["p"],
+    extra = {}
+    if "batch" in w:
+        extra = {"systems": w["batch"], "n_per_system": "log-uniform [%d, %d]" % (w["nlo"], w["nhi"]),
+                 "form": "forest: one octree per system, every phase one launch for all systems"}
+    return {**extra, "workload": args.workload, "n": w.get("n"), "source_order": w["s"], "p": w["p"],
             "theta": w["theta"], "max_leaf": w["ncrit"], "distribution": w["dist"],
             "outputs": "field" if not w.get("phi", False) else "potential+field",
             "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
@@ -193,7 +211,10 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     tree.set_profiling(True)
 
     def step():
-        tree.set_sources(pos_d, S_d, s)
+        if "batch" in w:
+            tree.set_sources_batch(pos_d, S_d, w["offsets"], s)
+        else:
+            tree.set_sources(pos_d, S_d, s)
         tree.evaluate(p, theta, want_phi, want_field, potential=phi_d, field=E_d)
 
     for _ in range(max(args.warmup, 0)):
@@ -246,10 +267,24 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     d2h = E_h.numel() * 8
 
     # ---- accuracy against the FP64 direct sum (GPU), sampled targets
-    tg = synth.sample_indices(n, args.err_samples, 23)
-    tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
-    _, E_ref = fmm.direct_sum(pos_d, S_d, s, targets=tg_d, want_potential=False)
-    Ef = E_d[tg_d.long()]
+    if "batch" in w:
+        # a sample of whole systems, each summed directly against itself
+        off = w["offsets"]
+        ks = synth.sample_indices(len(off) - 1, 64, 23)
+        refs, outs = [], []
+        for k in ks:
+            a, bb = int(off[k]), int(off[k + 1])
+            _, Er = fmm.direct_sum(pos_d[a:bb].contiguous(), S_d[a:bb].contiguous(), s,
+                                   want_potential=False)
+            refs.append(Er)
+            outs.append(E_d[a:bb])
+        E_ref, Ef = torch.cat(refs), torch.cat(outs)
+        tg = np.arange(E_ref.shape[0])
+    else:
+        tg = synth.sample_indices(n, args.err_samples, 23)
+        tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
+        _, E_ref = fmm.direct_sum(pos_d, S_d, s, targets=tg_d, want_potential=False)
+        Ef = E_d[tg_d.long()]
     num = ((Ef - E_ref) ** 2).sum().item()
     den = (E_ref ** 2).sum().item()
     per = (torch.linalg.norm(Ef - E_ref, dim=1) / torch.linalg.norm(E_ref, dim=1)).cpu().numpy()
@@ -292,8 +327,14 @@ def run_ours(args, w):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
-    n = w["n"]
-    pos_np, S_np = synth.make_system(n, w["s"], w["dist"], w["seed"] + 1000 * rank)
+    if "batch" in w:
+        pos_np, S_np, off = synth.make_batch(w["batch"], w["nlo"], w["nhi"], w["s"],
+                                             w["seed"] + 1000 * rank, w["dist"])
+        w["offsets"] = [int(x) for x in off]
+        w["n"] = n = int(off[-1])
+    else:
+        n = w["n"]
+        pos_np, S_np = synth.make_system(n, w["s"], w["dist"], w["seed"] + 1000 * rank)
     pos_h = torch.from_numpy(pos_np).pin_memory()
     S_h = torch.from_numpy(S_np).pin_memory()
     pos_d, S_d = pos_h.to(dev), S_h.to(dev)

@@ -105,6 +105,22 @@ fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *m
                            int64_t n, int source_order);
 
 /*
+ * Load a batch of `count` independent systems and build one octree per system
+ * (a forest): system s owns particles [offsets[s], offsets[s+1]) of the
+ * concatenated arrays, has its own root box, and never interacts with
+ * another system.  Every later phase runs as one launch over all systems.
+ *   positions, moments : DEVICE, concatenated, layouts as for fmm_set_sources.
+ *   offsets : HOST int64 [count + 1], offsets[0] = 0, non-decreasing; empty
+ *             systems are allowed.
+ *   count   : 1 .. 2^24.  All systems share source_order (and, in
+ *             fmm_evaluate, p and theta).
+ * Outputs of fmm_evaluate are in the concatenated order.  fmm_set_sources is
+ * the count = 1 case.
+ */
+fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const double *moments,
+                                 const int64_t *offsets, int count, int source_order);
+
+/*
  * Evaluate the FMM (§3.2 FMM traversal) at order p with opening angle theta.
  *   p      : local expansion order, 0 <= p and p + s <= FMM_MAX_TOTAL_ORDER;
  *            p >= 1 when want_field.
@@ -148,6 +164,7 @@ typedef struct {
     double lo[3];           /* root box corner                                   */
     double side;            /* root box side (a power of two)                    */
     int64_t device_bytes;   /* device memory held by the handle                  */
+    int64_t nsystems;       /* independent systems (1 after fmm_set_sources)      */
 } fmm_tree_info;
 
 fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
@@ -166,11 +183,14 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
  *   FMM_ARR_P2P         int32  [n_p2p x 2] (target, source), sorted
  *   FMM_ARR_MULTIPOLE   double [ncells x n_M] M of the last evaluate
  *   FMM_ARR_LOCAL       double [ncells x n_L] L of the last evaluate
+ *   FMM_ARR_CELL_SYSTEM int32  [ncells] system (batch index) of each cell
+ * In FMM_FP32 handles M and L are the scaled FP32 expansions (float).
  */
 typedef enum {
     FMM_ARR_KEYS = 0, FMM_ARR_PERM, FMM_ARR_CELL_LEVEL, FMM_ARR_CELL_COORD,
     FMM_ARR_CELL_RANGE, FMM_ARR_CELL_PARENT, FMM_ARR_CELL_CHILD, FMM_ARR_CELL_CENTRE,
-    FMM_ARR_CELL_HALF, FMM_ARR_M2L, FMM_ARR_P2P, FMM_ARR_MULTIPOLE, FMM_ARR_LOCAL
+    FMM_ARR_CELL_HALF, FMM_ARR_M2L, FMM_ARR_P2P, FMM_ARR_MULTIPOLE, FMM_ARR_LOCAL,
+    FMM_ARR_CELL_SYSTEM
 } fmm_array;
 
 /* Copy one internal array into a HOST buffer of `bytes` bytes (synchronous).

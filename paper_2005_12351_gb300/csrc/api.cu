@@ -80,7 +80,8 @@ void record(fmm_tree *t, int i)
 
 void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
 {
-    DevBuf *b[] = {&t->b_o32, &t->b_S32, &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
+    DevBuf *b[] = {&t->b_sys, &t->b_sysoff, &t->b_sysbox, &t->b_syseside, &t->b_o32, &t->b_S32,
+                   &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
                    &t->b_hist, &t->b_px, &t->b_py, &t->b_pz, &t->b_S, &t->b_perm, &t->b_level,
                    &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,
                    &t->b_cy, &t->b_cz, &t->b_centre, &t->b_half, &t->b_leaves, &t->b_flags,
@@ -202,12 +203,38 @@ fmm_status fmm_get_phase_times(const fmm_tree *t, float *ms_out)
 
 int64_t fmm_launch_count(const fmm_tree *t) { return t ? t->launches : -1; }
 
+static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const double *moments,
+                                   int64_t n, int source_order);
+
 fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *moments, int64_t n,
                            int source_order)
 {
     if (!t) return FMM_EINVAL;
     t->err.clear();
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(t, FMM_EINVAL, "n out of range");
+    t->sys_off.assign({0, n});
+    return set_sources_impl(t, positions, moments, n, source_order);
+}
+
+fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const double *moments,
+                                 const int64_t *offsets, int count, int source_order)
+{
+    if (!t) return FMM_EINVAL;
+    t->err.clear();
+    if (count < 1 || count > (1 << 24) || !offsets)
+        return fail(t, FMM_EINVAL, "count must be in [1, 2^24] with a host offsets array");
+    if (offsets[0] != 0) return fail(t, FMM_EINVAL, "offsets[0] must be 0");
+    for (int s = 0; s < count; ++s)
+        if (offsets[s + 1] < offsets[s]) return fail(t, FMM_EINVAL, "offsets must be non-decreasing");
+    const int64_t n = offsets[count];
+    if (n >= ((int64_t)1 << 31)) return fail(t, FMM_EINVAL, "total n out of range");
+    t->sys_off.assign(offsets, offsets + count + 1);
+    return set_sources_impl(t, positions, moments, n, source_order);
+}
+
+static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const double *moments,
+                                   int64_t n, int source_order)
+{
     if (source_order < 0 || source_order > FMM_MAX_SOURCE_ORDER)
         return fail(t, FMM_EORDER, "source order must be 0, 1 or 2");
     if (n > 0 && (!positions || !moments)) return fail(t, FMM_EINVAL, "NULL positions or moments");
@@ -276,6 +303,7 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *o)
     o->lo[0] = t->lo[0]; o->lo[1] = t->lo[1]; o->lo[2] = t->lo[2];
     o->side = t->side;
     o->device_bytes = (int64_t)t->held;
+    o->nsystems = t->sys_off.empty() ? 0 : (int64_t)t->sys_off.size() - 1;
     return FMM_OK;
 }
 
@@ -342,6 +370,7 @@ fmm_status fmm_copy_array(const fmm_tree *tc, fmm_array which, void *host_dst, s
     case FMM_ARR_LOCAL:
         if (t->tab_key_p < 0) return fail(t, FMM_ESTATE, "no evaluate yet");
         return plain(t->b_L, 8 * (size_t)nc * t->tab.nL);
+    case FMM_ARR_CELL_SYSTEM: return plain(t->b_sys, 4 * (size_t)nc);
     }
     return fail(t, FMM_EINVAL, "unknown array id");
 }

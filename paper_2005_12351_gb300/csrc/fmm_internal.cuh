@@ -107,7 +107,9 @@ struct fmm_tree {
     int64_t ncells = 0, nleaves = 0;
     int nlevels = 0;
     std::vector<int> level_begin;          // host copy, nlevels + 1
-    double lo[3] = {0, 0, 0}, side = 1.0;
+    double lo[3] = {0, 0, 0}, side = 1.0;  // root box of system 0
+    std::vector<int64_t> sys_off;          // host: system s owns particles [off[s], off[s+1])
+    std::vector<double> sys_box;           // host copy: (lo_x, lo_y, lo_z, side) per system
 
     // lists
     double theta = 0.0;
@@ -131,7 +133,10 @@ struct fmm_tree {
     DevBuf b_err, b_box;
     DevBuf b_keys, b_keys2, b_idx, b_idx2, b_hist;
     DevBuf b_px, b_py, b_pz, b_S, b_perm;
-    DevBuf b_level, b_parent, b_child, b_nchild, b_begin, b_end, b_cx, b_cy, b_cz;
+    DevBuf b_level, b_parent, b_child, b_nchild, b_begin, b_end, b_cx, b_cy, b_cz, b_sys;
+    DevBuf b_sysoff, b_sysbox, b_syseside;
+    // log2 of each system's root side (device int array)
+    const int *sys_eside_dev() const { return (const int *)b_syseside.ptr; }
     DevBuf b_centre, b_half, b_leaves;
     DevBuf b_flags, b_scan, b_scan_tmp;
     DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;

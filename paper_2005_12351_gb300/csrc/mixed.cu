@@ -61,7 +61,11 @@ __global__ void k_prep32(const int32_t *leaves, const int32_t *begin, const int3
         const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
         o[j] = make_float4(hx, hy, hz, 0.0f);
         olo[j] = make_float4((float)(dx - hx), (float)(dy - hy), (float)(dz - hz), 0.0f);
-        for (int a = 0; a < nS; ++a) S32[(int64_t)j * nS + a] = (float)S[(int64_t)j * nS + a];
+        const int nS32 = nS == 6 ? 7 : nS;
+        for (int a = 0; a < nS; ++a) S32[(int64_t)j * nS32 + a] = (float)S[(int64_t)j * nS + a];
+        if (nS == 6)      // quadrupole trace summed in FP64: zero stays ~zero for traceless input
+            S32[(int64_t)j * 7 + 6] = (float)(S[(int64_t)j * 6] + S[(int64_t)j * 6 + 3] +
+                                             S[(int64_t)j * 6 + 5]);
     }
 }
 
@@ -100,7 +104,9 @@ k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
             const float d = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
             axis_powers32(-d * inv_h, P, apow + (j * 3 + ax) * P1);
         }
-        for (int t = threadIdx.x; t < nj * nS; t += blockDim.x) Ssm[t] = S32[(int64_t)j0 * nS + t];
+        const int nS32 = nS == 6 ? 7 : nS;
+        for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
+            Ssm[t] = S32[(int64_t)(j0 + t / nS) * nS32 + t % nS];
         __syncthreads();
         for (int t = threadIdx.x; t < nj * nK; t += blockDim.x) {
             const int j = t / nK, k = t % nK;
@@ -182,20 +188,20 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
 }
 
 // ------------------------------------------------------------ D rows, FP32
-// Dh_k = h_t^(|k|+1) D_k: the FP64 row scaled by the target's half side
-// (exactly, by the exponent) and rounded once.
-__global__ void k_dtables32(const uint64_t *dkeys, int64_t ndoff, int e_side, int nD,
-                            const double *D, float *D32)
+// Dh_k = h_t^(|k|+1) D_k(u v) = (h_t/u)^(|k|+1) D_k(v): the unit-free FP64 row
+// shifted by the level gap when the target is the coarser cell (h_t = 2^gap u),
+// unchanged otherwise (h_t = u), and rounded once.
+__global__ void k_dtables32(const uint64_t *dkeys, int64_t ndoff, int nD, const double *D,
+                            float *D32)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ndoff * nD) return;
     const int64_t r = i / nD;
     const int k = (int)(i % nD);
     const uint64_t key = dkeys[r];
-    const int lf = (int)(key >> 57), gap = (int)((key >> 52) & 31), tfiner = (int)((key >> 51) & 1);
-    const int lt = tfiner ? lf : lf - gap;
-    const int e_t = e_side - lt - 1;                 // h_t = 2^e_t
-    D32[i] = (float)ldexp(D[i], (shell(k) + 1) * e_t);
+    const int gap = (int)((key >> 52) & 31), tfiner = (int)((key >> 51) & 1);
+    const int e = tfiner ? 0 : gap;
+    D32[i] = (float)ldexp(D[i], (shell(k) + 1) * e);
 }
 
 // ------------------------------------------------------------------ M2L
@@ -370,7 +376,7 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, const float
         const float gq1 = fmaf(Sj[1], dx, fmaf(2.0f * Sj[3], dy, Sj[4] * dz));
         const float gq2 = fmaf(Sj[2], dx, fmaf(Sj[4], dy, 2.0f * Sj[5] * dz));
         const float q = 0.5f * fmaf(gq0, dx, fmaf(gq1, dy, gq2 * dz));
-        const float tr = Sj[0] + Sj[3] + Sj[5];
+        const float tr = Sj[6];
         if (PHI) f += 3.0f * q * y5 - tr * y3;
         if (FIELD) {
             const float a = 3.0f * y5;
@@ -390,13 +396,15 @@ template <int S, bool PHI, bool FIELD>
 __global__ void __launch_bounds__(kP2PThreads)
 k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
         const int32_t *src, const int32_t *level, const int32_t *cx, const int32_t *cy,
-        const int32_t *cz, double side, const float4 *o, const float4 *olo, const float *S32,
+        const int32_t *cz, const int32_t *sys, const double *sys_box, const float4 *o,
+        const float4 *olo, const float *S32,
         const double *phi_far, const double *E_far, const int32_t *perm, double *phi_out,
         double *E_out)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
-    __shared__ float sx[kP2PChunk], sy[kP2PChunk], sz[kP2PChunk], sS[kP2PChunk * nS];
-    __shared__ float lx[kP2PChunk], ly[kP2PChunk], lz[kP2PChunk];
+    constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;     // + trace for quadrupoles
+    constexpr int CH = S == 2 ? 704 : kP2PChunk;                // static smem stays < 48 KB
+    __shared__ float sx[CH], sy[CH], sz[CH], sS[CH * nS];
+    __shared__ float lx[CH], ly[CH], lz[CH];
     __shared__ double red[8][kP2PThreads];
     __shared__ int gbeg[kGroups], gpre[kGroups + 1];
     __shared__ float gdx[kGroups], gdy[kGroups], gdz[kGroups];
@@ -409,7 +417,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     const long long rc = 1ll << (kLevels - lc);
     const long long ccx = (2ll * cx[c] + 1) * rc, ccy = (2ll * cy[c] + 1) * rc,
                     ccz = (2ll * cz[c] + 1) * rc;
-    const double unit = ldexp(side, -(kLevels + 1));        // finest half-cell
+    const double unit = ldexp(sys_box[4 * sys[c] + 3], -(kLevels + 1));   // finest half-cell
     for (int t0 = 0; t0 < nt; t0 += 2 * kP2PThreads) {
         const int cnt = min(2 * kP2PThreads, nt - t0);
         const int h = (cnt + 1) / 2;
@@ -426,9 +434,9 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             __syncthreads();
             if (tid == 0) {
                 int used = 0, g = 0;
-                while (q < q1 && used < kP2PChunk && g < kGroups) {
+                while (q < q1 && used < CH && g < kGroups) {
                     const int sl = src[q];
-                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
+                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, CH - used);
                     const long long rs = 1ll << (kLevels - level[sl]);
                     gbeg[g] = lb;
                     gpre[g] = used;
@@ -521,7 +529,8 @@ void launch_p2p32(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const int32_t *)t->b_end.ptr, (const int32_t *)t->b_p2p_off.ptr,
             (const int32_t *)t->b_p2p_src.ptr, (const int32_t *)t->b_level.ptr,
             (const int32_t *)t->b_cx.ptr, (const int32_t *)t->b_cy.ptr, (const int32_t *)t->b_cz.ptr,
-            t->side, (const float4 *)t->b_o32.ptr, (const float4 *)t->b_o32.ptr + t->n,
+            (const int32_t *)t->b_sys.ptr, (const double *)t->b_sysbox.ptr,
+            (const float4 *)t->b_o32.ptr, (const float4 *)t->b_o32.ptr + t->n,
             (const float *)t->b_S32.ptr,
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr, (const int32_t *)t->b_perm.ptr,
             phi, E);
@@ -570,9 +579,6 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     FMM_TRY(upload_tables(t, s, p, want_phi ? 0 : 1, &tb, &lut));
     const int64_t nc = t->ncells, n = t->n;
     const int P1 = p + 1;
-    int e_side = 0;
-    std::frexp(t->side, &e_side);
-    e_side -= 1;                                   // side = 2^e_side
     // cross-level M2L pairs scale FP32 values by 2^(gap * order): keep them in range
     if (t->max_gap * (p + s + 1) > 96) {
         t->err = "mixed precision: level gap " + std::to_string(t->max_gap) +
@@ -583,14 +589,14 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     if (t->d32_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * tb.nD));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
-            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, e_side, tb.nD, (const double *)t->b_D.ptr,
+            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr,
             (float *)t->b_D32.ptr);
         ++t->launches;
         t->d32_p = p;
     }
     record(t, 6);
     FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
-    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * t->nS));
+    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));
     FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * tb.nM));
     FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));

@@ -137,18 +137,18 @@ __constant__ int8_t c_nx[kMaxTot], c_ny[kMaxTot], c_nz[kMaxTot];
 // r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
 //           - sum_{j != i} [ 2 n_j R_j D_{n-e_j} + n_j (n_j - 1) D_{n-2e_j} ],
 // i = first axis with n_i >= 1 (Leibniz' rule on r^2 d_i(1/r) = -R_i / r).
-__global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, double side, int nD,
-                          const int32_t *lut, double *D)
+// Rows are unit-free: D_k(v) at the integer offset v of the key; a pair with
+// finer half-cell u uses u^-(|k|+1) D_k(v), applied exactly as an exponent shift.
+__global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, int nD, const int32_t *lut,
+                          double *D)
 {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= ndoff) return;
     const uint64_t key = dkeys[r];
-    const int lf = (int)(key >> 57);
-    const double unit = ldexp(side, -(lf + 1));
     double R[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        R[i] = (double)((long long)((key >> (34 - 17 * i)) & 0x1ffffull) - kKeyBias) * unit;
+        R[i] = (double)((long long)((key >> (34 - 17 * i)) & 0x1ffffull) - kKeyBias);
     double *Dr = D + r * nD;
     const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
     const double inv_r2 = 1.0 / r2;
@@ -297,9 +297,17 @@ k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre,
 // each thread walks its fixed chunk of (n, m) terms, accumulating
 // D_{n+m} M_m over the staged sources, and flushes each finished n-run to its
 // partial slot.  Partials are summed per n in a fixed order at the end.
+// x * 2^e for normal x (exponent field arithmetic; zeros stay zero)
+__device__ __forceinline__ double scale_pow2(double x, int e)
+{
+    const long long b = __double_as_longlong(x);
+    return (b & 0x7ff0000000000000ll) ? __longlong_as_double(b + ((long long)e << 52)) : x;
+}
+
 __global__ void __launch_bounds__(kM2LThreads)
-k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const double *M,
-      const double *D, DevTables tb, double *L)
+k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t *level,
+      const int32_t *sys, const int *e_side, const double *M, const double *D, DevTables tb,
+      double *L)
 {
     extern __shared__ double sm[];
     const int c = blockIdx.x;
@@ -312,6 +320,7 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const double 
     double *part = Dsm + kM2LBatch * ldD;              // [slots][Tn]
     uint32_t *desc = (uint32_t *)(part + tb.m2l_slots * Tn);   // [T][Tn]
     const int tid = threadIdx.x;
+    const int lt = level[c], es = e_side[sys[c]];
     for (int i = tid; i < T * Tn; i += Tn) desc[i] = tb.m2l_desc[i];
     for (int i = tid; i < tb.m2l_slots * Tn; i += Tn) part[i] = 0.0;
     for (int k0 = b; k0 < e; k0 += kM2LBatch) {
@@ -323,7 +332,11 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const double 
         }
         for (int i = tid; i < kb * nD; i += Tn) {
             const int k = i / nD, d = i % nD;
-            Dsm[k * ldD + d] = D[(int64_t)didx[k0 + k] * nD + d];
+            // u = side / 2^(lf+1): D_k(u v) = 2^(-(|k|+1) log2 u) D_k(v)
+            const int lf = max(lt, level[src[k0 + k]]);
+            const int eu = es - lf - 1;
+            Dsm[k * ldD + d] = scale_pow2(D[(int64_t)didx[k0 + k] * nD + d],
+                                          -(c_nx[d] + c_ny[d] + c_nz[d] + 1) * eu);
         }
         __syncthreads();
         double acc = 0.0;
@@ -504,7 +517,7 @@ fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t 
     if (t->d_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D, 8 * (size_t)t->n_doff * tb.nD));
         k_dtables<<<grid(t->n_doff, 128), 128, 0, t->stream>>>((const uint64_t *)t->b_dkeys.ptr,
-                                                                t->n_doff, t->side, tb.nD, lut,
+                                                                t->n_doff, tb.nD, lut,
                                                                 (double *)t->b_D.ptr);
         ++t->launches;
         t->d_p = p;
@@ -567,7 +580,8 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
         cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_m2l<<<(unsigned)nc, kM2LThreads, smem, st>>>(
             (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
-            (const int32_t *)t->b_m2l_didx.ptr, M, (const double *)t->b_D.ptr, tb, L);
+            (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr,
+            (const int32_t *)t->b_sys.ptr, t->sys_eside_dev(), M, (const double *)t->b_D.ptr, tb, L);
         ++t->launches;
     }
     record(t, 9);

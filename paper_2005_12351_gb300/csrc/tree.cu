@@ -13,6 +13,7 @@
 // two leaves -> P2P, one leaf -> open the other, else open the larger cell
 // (the target on a tie); a self pair opens into all ordered child pairs.
 #include <algorithm>
+#include <cmath>
 
 #include "fmm_internal.cuh"
 
@@ -119,6 +120,133 @@ __global__ void k_keys(const double *pos, int64_t n, const double *box, uint64_t
     idx[i] = (uint32_t)i;
 }
 
+// ---- systems (a forest of independent octrees, one root per system)
+__global__ void k_sys_of(const int64_t *off, int nsys, int64_t n, int32_t *sys_of)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsys - 1;                 // last system whose start is <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    sys_of[i] = lo;
+}
+
+__global__ void k_box_init_seg(unsigned long long *box, int nsys)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * nsys) return;
+    box[i] = (i % 6) < 3 ? ~0ull : 0ull;
+}
+
+// Per-system min/max.  A warp whose particles all belong to one system
+// reduces with shuffles first; mixed warps fall back to per-lane atomics.
+__global__ void k_bbox_seg(const double *pos, int64_t n, const int32_t *sys_of,
+                           unsigned long long *box, int *err)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const int s = valid ? sys_of[i] : -1;
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = pos[3 * i + d];
+            if (!isfinite(x)) bad = true;
+            mn[d] = mx[d] = ordered_bits(x);
+        }
+    }
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    const bool uniform = __all_sync(0xffffffffu, s == s0);
+    if (uniform) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+                unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], o);
+                mn[d] = a < mn[d] ? a : mn[d];
+                mx[d] = b > mx[d] ? b : mx[d];
+            }
+        if ((threadIdx.x & 31) == 0 && s0 >= 0)
+            for (int d = 0; d < 3; ++d) {
+                atomicMin(&box[6 * s0 + d], mn[d]);
+                atomicMax(&box[6 * s0 + 3 + d], mx[d]);
+            }
+    } else if (valid) {
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&box[6 * s + d], mn[d]);
+            atomicMax(&box[6 * s + 3 + d], mx[d]);
+        }
+    }
+    if (bad) atomicOr(err, kErrNonFinite);
+}
+
+// box_out[4 s .. 4 s + 3] = (lo_x, lo_y, lo_z, side) of system s; empty systems get side 1
+__global__ void k_box_final_seg(const unsigned long long *box, int nsys, double *box_out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const unsigned long long *b = box + 6 * s;
+    if (b[0] == ~0ull) {                       // no particles
+        box_out[4 * s] = box_out[4 * s + 1] = box_out[4 * s + 2] = 0.0;
+        box_out[4 * s + 3] = 1.0;
+        return;
+    }
+    double lo[3], ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = from_ordered_bits(b[d]);
+        const double e = __dsub_rn(from_ordered_bits(b[3 + d]), lo[d]);
+        ext = e > ext ? e : ext;
+    }
+    double side = 1.0;
+    if (ext > 0.0 && isfinite(ext)) {
+        int e2;
+        const double m = frexp(ext, &e2);
+        side = ldexp(1.0, m == 0.5 ? e2 - 1 : e2);
+    }
+    box_out[4 * s] = lo[0]; box_out[4 * s + 1] = lo[1]; box_out[4 * s + 2] = lo[2];
+    box_out[4 * s + 3] = side;
+}
+
+__global__ void k_keys_seg(const double *pos, int64_t n, const int32_t *sys_of,
+                           const double *box, uint64_t *keys, uint32_t *idx)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *bx = box + 4 * sys_of[i];
+    const double scale = ldexp(1.0, kLevels) / bx[3];
+    uint64_t q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double u = floor(__dmul_rn(__dsub_rn(pos[3 * i + d], bx[d]), scale));
+        uint64_t v = (uint64_t)u;
+        q[d] = v > (uint64_t)((1 << kLevels) - 1) ? (uint64_t)((1 << kLevels) - 1) : v;
+    }
+    keys[i] = spread3(q[0]) << 2 | spread3(q[1]) << 1 | spread3(q[2]);
+    idx[i] = (uint32_t)i;
+}
+
+// after the key sort: secondary key = system of each element, and a copy of
+// the sorted keys by original index for the final re-gather
+__global__ void k_sys_keys(const uint64_t *keys, const uint32_t *idx, const int32_t *sys_of,
+                           int64_t n, uint64_t *skeys, uint64_t *key_of)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    skeys[k] = (uint64_t)sys_of[idx[k]];
+    key_of[idx[k]] = keys[k];
+}
+
+__global__ void k_regather_keys(const uint64_t *key_of, const uint32_t *idx, int64_t n,
+                                uint64_t *keys)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) keys[k] = key_of[idx[k]];
+}
+
 __global__ void k_gather(const double *pos, const double *mom, int nS, const uint32_t *perm,
                          int64_t n, double *px, double *py, double *pz, double *S, int32_t *perm_out)
 {
@@ -133,13 +261,22 @@ __global__ void k_gather(const double *pos, const double *mom, int nS, const uin
 }
 
 struct CellArrays {
-    int32_t *level, *parent, *child, *nchild, *begin, *end, *cx, *cy, *cz;
+    int32_t *level, *parent, *child, *nchild, *begin, *end, *cx, *cy, *cz, *sys;
 };
 
-__global__ void k_root(CellArrays c, int32_t n)
+__global__ void k_roots(CellArrays c, const int64_t *off, int nsys)
 {
-    c.level[0] = 0; c.parent[0] = -1; c.begin[0] = 0; c.end[0] = n;
-    c.cx[0] = c.cy[0] = c.cz[0] = 0;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    c.level[s] = 0; c.parent[s] = -1; c.begin[s] = (int32_t)off[s]; c.end[s] = (int32_t)off[s + 1];
+    c.cx[s] = c.cy[s] = c.cz[s] = 0;
+    c.sys[s] = s;
+}
+
+__global__ void k_root_pairs(int2 *front, int nsys)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) front[s] = make_int2(s, s);
 }
 
 __device__ __forceinline__ int digit_at(uint64_t key, int level)
@@ -199,6 +336,7 @@ __global__ void k_write_children(CellArrays c, int lb, int le, int ncl, int leve
     c.cx[ch] = 2 * c.cx[cell] + ((o >> 2) & 1);
     c.cy[ch] = 2 * c.cy[cell] + ((o >> 1) & 1);
     c.cz[ch] = 2 * c.cz[cell] + (o & 1);
+    c.sys[ch] = c.sys[cell];
 }
 
 __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box, double *centre,
@@ -206,11 +344,12 @@ __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box,
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ncells) return;
-    const double h = ldexp(box[3], -(c.level[i] + 1));
+    const double *bx = box + 4 * c.sys[i];
+    const double h = ldexp(bx[3], -(c.level[i] + 1));
     half[i] = h;
-    centre[3 * i] = __dadd_rn(box[0], __dmul_rn((double)(2 * c.cx[i] + 1), h));
-    centre[3 * i + 1] = __dadd_rn(box[1], __dmul_rn((double)(2 * c.cy[i] + 1), h));
-    centre[3 * i + 2] = __dadd_rn(box[2], __dmul_rn((double)(2 * c.cz[i] + 1), h));
+    centre[3 * i] = __dadd_rn(bx[0], __dmul_rn((double)(2 * c.cx[i] + 1), h));
+    centre[3 * i + 1] = __dadd_rn(bx[1], __dmul_rn((double)(2 * c.cy[i] + 1), h));
+    centre[3 * i + 2] = __dadd_rn(bx[2], __dmul_rn((double)(2 * c.cz[i] + 1), h));
     leaf_flag[i] = c.nchild[i] == 0;
 }
 
@@ -317,10 +456,10 @@ __global__ void k_p2p_interactions(const uint64_t *keys, int64_t np, int cbits, 
 }
 
 // --------------------------------------------------- D-table offset keys
-// key = finer level (5 bits) | level gap (5 bits) | target-is-finer (1 bit) |
-// three 17-bit biased offsets in units of the finer cell's half side.  The
-// real offset is exactly offset * side / 2^(lf+1); the level fields let the
-// scaled (mixed-precision) rows depend on the target's level.
+// key = level gap (5 bits) | target-is-finer (1 bit) | three 17-bit biased
+// offsets v in units of the finer cell's half side u.  D rows are stored for
+// the unit-free offset v; a pair's real offset is u v with u = side / 2^(lf+1)
+// a power of two, so one row serves every level and every system.
 __device__ __forceinline__ uint64_t hash64(uint64_t x)
 {
     x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull;
@@ -342,7 +481,7 @@ __global__ void k_offset_keys(CellArrays c, const uint64_t *pair_keys, int64_t n
                       (2ll * c.cz[a] + 1) * sa - (2ll * c.cz[b] + 1) * sb};
     const int gap = la > lb ? la - lb : lb - la;
     if (gap) atomicMax(max_gap, (unsigned)gap);
-    uint64_t key = (uint64_t)lf << 57 | (uint64_t)gap << 52 | (uint64_t)(la > lb) << 51;
+    uint64_t key = (uint64_t)gap << 52 | (uint64_t)(la > lb) << 51;
     for (int i = 0; i < 3; ++i) {
         if (d[i] < -kKeyBias || d[i] >= kKeyBias) { atomicOr(err, kErrKeyRange); slot_of[k] = 0; return; }
         key |= (uint64_t)(d[i] + kKeyBias) << (34 - 17 * i);
@@ -389,6 +528,7 @@ CellArrays cells_of(fmm_tree *t)
     c.child = (int32_t *)t->b_child.ptr; c.nchild = (int32_t *)t->b_nchild.ptr;
     c.begin = (int32_t *)t->b_begin.ptr; c.end = (int32_t *)t->b_end.ptr;
     c.cx = (int32_t *)t->b_cx.ptr; c.cy = (int32_t *)t->b_cy.ptr; c.cz = (int32_t *)t->b_cz.ptr;
+    c.sys = (int32_t *)t->b_sys.ptr;
     return c;
 }
 
@@ -453,6 +593,7 @@ fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint6
 fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
 {
     const int64_t n = t->n;
+    const int nsys = (int)t->sys_off.size() - 1;
     cudaStream_t st = t->stream;
     t->have_lists = false;
     t->ncells = t->nleaves = 0;
@@ -471,33 +612,66 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     FMM_TRY(ensure(t, t->b_pz, 8 * n));
     FMM_TRY(ensure(t, t->b_S, 8 * n * t->nS));
     FMM_TRY(ensure(t, t->b_perm, 4 * n));
+    FMM_TRY(ensure(t, t->b_sysoff, 8 * (size_t)(nsys + 1)));
+    FMM_TRY(ensure(t, t->b_sysbox, 32 * (size_t)nsys + 48 * (size_t)nsys));
     uint64_t *keys = (uint64_t *)t->b_keys.ptr;
     uint32_t *idx = (uint32_t *)t->b_idx.ptr;
+    int64_t *off = (int64_t *)t->b_sysoff.ptr;
+    double *sbox = (double *)t->b_sysbox.ptr;                               // [nsys][4]
+    unsigned long long *sbox_raw = (unsigned long long *)(sbox + 4 * nsys); // [nsys][6]
 
     record(t, 0);
     cudaMemsetAsync(t->b_err.ptr, 0, sizeof(int), st);
-    morton_keys(st, pos, n, keys, idx, (unsigned long long *)t->b_box.ptr,
-                (double *)t->b_box.ptr + 8, (int *)t->b_err.ptr, &t->launches);
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(off, t->sys_off.data(), 8 * (size_t)(nsys + 1),
+                                          cudaMemcpyHostToDevice, st), "system offsets"));
+    if (nsys == 1) {
+        morton_keys(st, pos, n, keys, idx, sbox_raw, sbox, (int *)t->b_err.ptr, &t->launches);
+    } else {
+        // particle -> system (kept in b_idx2 until the sort needs it)
+        FMM_TRY(ensure(t, t->b_lval2, 4 * n));
+        int32_t *sys_of = (int32_t *)t->b_lval2.ptr;
+        k_sys_of<<<grid(n, 256), 256, 0, st>>>(off, nsys, n, sys_of);
+        k_box_init_seg<<<grid(6 * nsys, 256), 256, 0, st>>>(sbox_raw, nsys);
+        k_bbox_seg<<<grid(n, 256), 256, 0, st>>>(pos, n, sys_of, sbox_raw, (int *)t->b_err.ptr);
+        k_box_final_seg<<<grid(nsys, 128), 128, 0, st>>>(sbox_raw, nsys, sbox);
+        k_keys_seg<<<grid(n, 256), 256, 0, st>>>(pos, n, sys_of, sbox, keys, idx);
+        t->launches += 5;
+    }
     record(t, 1);
     radix_sort_pairs(keys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
                      3 * kLevels, (uint32_t *)t->b_hist.ptr, (uint32_t *)t->b_scan_tmp.ptr, st,
                      &t->launches);
+    if (nsys > 1) {
+        // stable second pass by system: order = (system, key, original index)
+        FMM_TRY(ensure(t, t->b_lkeys, 8 * n));
+        FMM_TRY(ensure(t, t->b_lkeys2, 8 * n));
+        uint64_t *skeys = (uint64_t *)t->b_lkeys.ptr, *key_of = (uint64_t *)t->b_lkeys2.ptr;
+        k_sys_keys<<<grid(n, 256), 256, 0, st>>>(keys, idx, (const int32_t *)t->b_lval2.ptr, n,
+                                                 skeys, key_of);
+        int sbits = 1;
+        while ((1 << sbits) < nsys) ++sbits;
+        radix_sort_pairs(skeys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
+                         sbits, (uint32_t *)t->b_hist.ptr, (uint32_t *)t->b_scan_tmp.ptr, st,
+                         &t->launches);
+        k_regather_keys<<<grid(n, 256), 256, 0, st>>>(key_of, idx, n, keys);
+        t->launches += 2;
+    }
     k_gather<<<grid(n, 256), 256, 0, st>>>(pos, mom, t->nS, idx, n, (double *)t->b_px.ptr,
                                            (double *)t->b_py.ptr, (double *)t->b_pz.ptr,
                                            (double *)t->b_S.ptr, (int32_t *)t->b_perm.ptr);
     ++t->launches;
     record(t, 2);
 
-    // ---- cells, level by level
-    int64_t cap = std::max<int64_t>(1024, 2 * (n / std::max(1, t->max_leaf)) + 64);
-    DevBuf *cb[9] = {&t->b_level, &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin,
-                     &t->b_end, &t->b_cx, &t->b_cy, &t->b_cz};
+    // ---- cells, level by level (level 0 holds one root per system)
+    int64_t cap = std::max<int64_t>(1024, 2 * (n / std::max(1, t->max_leaf)) + 64 + 2 * nsys);
+    DevBuf *cb[10] = {&t->b_level, &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin,
+                      &t->b_end, &t->b_cx, &t->b_cy, &t->b_cz, &t->b_sys};
     for (DevBuf *b : cb) FMM_TRY(ensure(t, *b, 4 * cap));
     CellArrays c = cells_of(t);
-    k_root<<<1, 1, 0, st>>>(c, (int32_t)n);
+    k_roots<<<grid(nsys, 128), 128, 0, st>>>(c, off, nsys);
     ++t->launches;
     t->level_begin.push_back(0);
-    int64_t lb = 0, le = 1;
+    int64_t lb = 0, le = nsys;
     int level = 0;
     uint32_t total = 0;
     while (le > lb) {
@@ -531,7 +705,6 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     }
     t->ncells = le;
     t->nlevels = level;       // levels 0 .. level-1 hold cells
-    // level_begin has nlevels + 1 entries: the last one equals ncells
     const int64_t nc = t->ncells;
     FMM_TRY(ensure(t, t->b_centre, 8 * 3 * nc));
     FMM_TRY(ensure(t, t->b_half, 8 * nc));
@@ -539,8 +712,7 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     FMM_TRY(ensure(t, t->b_scan, 4 * (nc + 1)));
     uint32_t *flags = (uint32_t *)t->b_flags.ptr, *posc = (uint32_t *)t->b_scan.ptr;
     cudaMemsetAsync(flags + nc, 0, 4, st);
-    k_cell_geometry<<<grid(nc, 256), 256, 0, st>>>(c, nc, (double *)t->b_box.ptr + 8,
-                                                    (double *)t->b_centre.ptr,
+    k_cell_geometry<<<grid(nc, 256), 256, 0, st>>>(c, nc, sbox, (double *)t->b_centre.ptr,
                                                     (double *)t->b_half.ptr, flags);
     exclusive_scan_u32(flags, posc, nc + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
     uint32_t nleaves = 0;
@@ -549,13 +721,20 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     FMM_TRY(ensure(t, t->b_leaves, 4 * (size_t)nc));
     k_compact_leaves<<<grid(nc, 256), 256, 0, st>>>(flags, posc, nc, (int32_t *)t->b_leaves.ptr);
     t->launches += 2;
-    double box[4];
-    FMM_TRY(cuda_check(t, cudaMemcpyAsync(box, (double *)t->b_box.ptr + 8, sizeof(box),
+    t->sys_box.assign(4 * (size_t)nsys, 0.0);
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->sys_box.data(), sbox, 32 * (size_t)nsys,
                                           cudaMemcpyDeviceToHost, st), "box"));
     record(t, 3);
     FMM_TRY(read_err(t));
     t->nleaves = nleaves;
-    t->lo[0] = box[0]; t->lo[1] = box[1]; t->lo[2] = box[2]; t->side = box[3];
+    t->lo[0] = t->sys_box[0]; t->lo[1] = t->sys_box[1]; t->lo[2] = t->sys_box[2];
+    t->side = t->sys_box[3];
+    std::vector<int> es((size_t)nsys);
+    for (int s = 0; s < nsys; ++s) es[s] = std::ilogb(t->sys_box[4 * s + 3]);
+    FMM_TRY(ensure(t, t->b_syseside, 4 * (size_t)nsys));
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_syseside.ptr, es.data(), 4 * (size_t)nsys,
+                                          cudaMemcpyHostToDevice, st), "system sides"));
+    FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
     return FMM_OK;
 }
 
@@ -580,11 +759,12 @@ fmm_status build_lists(fmm_tree *t, double theta)
     p2p_cap = t->b_p2p_raw.bytes / 8;
     FMM_TRY(grow_keep(t, t->b_front, 8 * 4096, 0));
     FMM_TRY(grow_keep(t, t->b_front2, 8 * 4096, 0));
-    int2 root = make_int2(0, 0);
-    FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_front.ptr, &root, 8, cudaMemcpyHostToDevice, st),
-                       "frontier"));
+    const int nsys = (int)t->sys_off.size() - 1;
+    FMM_TRY(grow_keep(t, t->b_front, 8 * (size_t)nsys, 0));
+    k_root_pairs<<<grid(nsys, 128), 128, 0, st>>>((int2 *)t->b_front.ptr, nsys);
+    ++t->launches;
     unsigned host_cnt[3] = {0, 0, 0};
-    int64_t nf = 1;
+    int64_t nf = nsys;
     while (nf > 0) {
         const unsigned base[3] = {host_cnt[0], host_cnt[1], 0};
         size_t next_cap = t->b_front2.bytes / 8;

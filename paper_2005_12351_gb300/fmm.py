@@ -24,7 +24,8 @@ ARRAYS = {"keys": (0, torch.int64, 1), "perm": (1, torch.int32, 1), "level": (2,
           "coord": (3, torch.int32, 3), "range": (4, torch.int32, 2), "parent": (5, torch.int32, 1),
           "child": (6, torch.int32, 2), "centre": (7, torch.float64, 3),
           "half": (8, torch.float64, 1), "m2l": (9, torch.int32, 2), "p2p": (10, torch.int32, 2),
-          "multipole": (11, torch.float64, 0), "local": (12, torch.float64, 0)}
+          "multipole": (11, torch.float64, 0), "local": (12, torch.float64, 0),
+          "system": (13, torch.int32, 1)}
 
 
 class FMMError(RuntimeError):
@@ -38,7 +39,7 @@ class TreeInfo(C.Structure):
                 ("nlevels", C.c_int32), ("source_order", C.c_int32), ("n_m2l", C.c_int64),
                 ("n_p2p", C.c_int64), ("n_p2p_interactions", C.c_int64),
                 ("n_doffsets", C.c_int64), ("theta", C.c_double), ("lo", C.c_double * 3),
-                ("side", C.c_double), ("device_bytes", C.c_int64)]
+                ("side", C.c_double), ("device_bytes", C.c_int64), ("nsystems", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -139,6 +140,18 @@ class FMMTree:
         st = lib().fmm_set_sources(self._h, _ptr(positions), _ptr(moments), n, int(source_order))
         _check(st, self._h, "set_sources")
         self.n, self.s = n, source_order
+
+    def set_sources_batch(self, positions, moments, offsets, source_order: int):
+        """A forest of independent systems; ``offsets`` is a host int sequence of count+1."""
+        _dev_f64(positions, "positions", 3)
+        _dev_f64(moments, "moments", source_terms(source_order))
+        off = (C.c_int64 * len(offsets))(*[int(x) for x in offsets])
+        fn = lib().fmm_set_sources_batch
+        fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_int, C.c_int]
+        fn.restype = C.c_int
+        st = fn(self._h, _ptr(positions), _ptr(moments), off, len(offsets) - 1, int(source_order))
+        _check(st, self._h, "set_sources_batch")
+        self.n, self.s = int(offsets[-1]), source_order
 
     def evaluate(self, p: int, theta: float, want_potential=True, want_field=True,
                  potential=None, field=None):

@@ -158,7 +158,28 @@ WORKLOADS = {
     "dipole_125k_p6": dict(n=125_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260011),
     "dipole_plummer_4m_p8": dict(n=4_000_000, s=1, p=8, theta=0.5, ncrit=128, dist="plummer",
                                  seed=20260002),
+    # 4,096 independent uniform-cube systems, N log-uniform in [256, 65536], quadrupoles
+    "quadrupole_batch_4096_p5": dict(batch=4096, nlo=256, nhi=65536, s=2, p=5, theta=0.5,
+                                     ncrit=128, dist="uniform", seed=20260003),
 }
+
+
+def make_batch(count: int, lo: int, hi: int, s: int, seed: int, dist: str = "uniform"):
+    """A batch of independent systems with sizes round(exp(U(ln lo, ln hi))).
+
+    Returns (positions (N,3), moments (N, T(s)), offsets (count+1,)), systems
+    concatenated; system k is drawn from seed*7919 + k.
+    """
+    sizes = log_uniform_int(count, lo, hi, seed)
+    off = np.zeros(count + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    pos = np.empty((int(off[-1]), 3))
+    mom = np.empty((int(off[-1]), (s + 1) * (s + 2) // 2))
+    for k in range(count):
+        p_k, m_k = make_system(int(sizes[k]), s, dist, seed * 7919 + k)
+        pos[off[k]:off[k + 1]] = p_k
+        mom[off[k]:off[k + 1]] = m_k
+    return pos, mom, off
 
 
 def make_system(n: int, s: int, dist: str, seed: int):
