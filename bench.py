@@ -318,6 +318,78 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     return res
 
 
+def serving_stream(count: int, seed: int):
+    """Requests drawn like the serving workload: N log-uniform in [1e3, 2e6],
+    source order uniform over {0, 1, 2}, p uniform over {4..10}, uniform or
+    Plummer positions 50/50, theta 0.5, n_crit 128."""
+    sizes = synth.log_uniform_int(count, 1000, 2_000_000, seed)
+    u = synth.uniform01(seed, 17, 3 * count).reshape(count, 3)
+    reqs = []
+    for k in range(count):
+        s = int(u[k, 0] * 3)
+        p = 4 + int(u[k, 1] * 7)
+        dist = "plummer" if u[k, 2] < 0.5 else "uniform"
+        pos, mom = synth.make_system(int(sizes[k]), s, dist, seed * 31 + k)
+        reqs.append(dict(positions=pos, moments=mom, source_order=s, p=p, theta=0.5,
+                         max_leaf=128, want_potential=False, want_field=True))
+    return reqs
+
+
+def run_serving(args, dev):
+    """Continuous batching on the device: calibrate capacity closed-loop, then
+    replay Poisson arrivals at 0.8 of it and report latency percentiles."""
+    from paper_2005_12351_gb300 import fmm
+    reqs = serving_stream(args.serving_requests, 20260004)
+    total = sum(len(r["positions"]) for r in reqs)
+    budget = 120 << 30
+    sv = fmm.Server(device=dev.index, slots=args.serving_slots, precision=args.serving_precision,
+                    mem_budget_bytes=budget)
+    # warm the slots, then closed loop: everything submitted at once
+    for t in [sv.submit(**r) for r in reqs[:args.serving_slots]]:
+        sv.wait(t)
+    t0 = time.perf_counter()
+    for t in [sv.submit(**r) for r in reqs]:
+        try:
+            sv.wait(t)
+        except fmm.FMMError:
+            pass
+    capacity = total / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at 0.8 x capacity (in particles/s)
+    load = 0.8
+    rate = load * capacity / (total / len(reqs))             # requests per second
+    gaps = -np.log(1.0 - synth.uniform01(20260005, 1, len(reqs))) / rate
+    arrivals = np.cumsum(gaps)
+    start = time.perf_counter()
+    tickets = []
+    for a, r in zip(arrivals, reqs):
+        delay = start + a - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(sv.submit(**r))
+    lat, ends, firsts, failed = [], [], [], 0
+    done_particles = 0
+    for t, r in zip(tickets, reqs):
+        try:
+            _, _, info = sv.wait(t)
+        except fmm.FMMError:
+            failed += 1
+            continue
+        lat.append(1e3 * (info["end_s"] - info["submit_s"]))
+        ends.append(info["end_s"])
+        firsts.append(info["submit_s"])
+        done_particles += len(r["positions"])
+    st = sv.stats()
+    sv.close()
+    span = max(ends) - min(firsts)
+    return {"requests": len(reqs), "failed": failed, "slots": args.serving_slots,
+            "precision": args.serving_precision, "mem_budget_gb": 120,
+            "offered_load": load, "capacity_particles_per_s": capacity,
+            "particles_per_s": done_particles / span, "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)),
+            "peak_device_gb": st["peak_device_bytes"] / 2 ** 30,
+            "mix": "N log-uniform [1e3, 2e6], s in {0,1,2}, p in {4..10}, uniform/Plummer 50/50"}
+
+
 def run_ours(args, w):
     import torch
     world, rank, local = dist_setup()
@@ -353,6 +425,8 @@ def run_ours(args, w):
                                                  "roofline", "phase_ms", "gpu_launches")}
         line["mixed_fp32"]["error_ratio_vs_fp64"] = (mx["rel_err"]["field_rel_rms"]
                                                      / main["rel_err"]["field_rel_rms"])
+    if rank == 0 and args.serving_requests > 0 and "batch" not in w:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, k, cores = oracle_sample(w, args.oracle_sample)
         line["cpu_baseline"] = {
@@ -379,6 +453,10 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra FP32-form measurement in the same run")
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="requests in the serving measurement (0 = skip)")
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-precision", choices=["fp64", "fp32"], default="fp32")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.259)
     ap.add_argument("--fp64-peak-source", default="152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                     "(nominal 1.25 TFLOP/s FP64 of the part)")

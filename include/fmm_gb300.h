@@ -238,6 +238,69 @@ fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const doub
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent evaluation requests.          */
+/* ------------------------------------------------------------------------ */
+typedef struct fmm_server fmm_server;
+
+/* One evaluation request.  All arrays are HOST memory owned by the caller,
+ * who keeps them alive (and does not touch the outputs) until
+ * fmm_server_wait returns for the ticket. */
+typedef struct {
+    const double *positions;  /* n x 3                                       */
+    const double *moments;    /* n x T(s), layout as fmm_set_sources          */
+    int64_t n;
+    int source_order;         /* 0, 1, 2                                      */
+    int p;                    /* expansion order, p + s <= 12                 */
+    double theta;             /* MAC parameter, 0 < theta < 1                 */
+    int max_leaf;             /* n_crit                                       */
+    int want_potential, want_field;
+    double *potential;        /* n, or NULL                                   */
+    double *field;            /* n x 3, or NULL                               */
+} fmm_request;
+
+typedef struct {
+    int64_t ticket;
+    fmm_status status;
+    int slot;                 /* worker that ran it                           */
+    double submit_s, start_s, end_s;   /* steady-clock seconds               */
+    int64_t device_bytes;     /* device memory of the slot after the request  */
+    char message[128];        /* error text when status != FMM_OK             */
+} fmm_request_result;
+
+typedef struct {
+    int64_t completed, failed, queued, running;
+    int64_t device_bytes;      /* held + reserved across slots now            */
+    int64_t peak_device_bytes;
+    int64_t particles_done;
+    double busy_span_s;        /* first start to last completion              */
+} fmm_server_stats;
+
+/*
+ * A server with `slots` workers on `device`.  Each worker owns a CUDA stream
+ * and a resident handle (fmm_create_tree with the given precision), so the
+ * trees, lists and expansions of the requests it runs stay on the device.
+ * Requests are admitted first-in first-out as soon as a worker is idle and
+ * the request's estimated device memory, added to what the other workers
+ * hold or have reserved, stays within mem_budget_bytes (0 = unlimited);
+ * requests admitted while others run overlap on the GPU.  Workers that sit
+ * idle release their buffers when the head of the queue does not fit.
+ * This is the paper's evaluation (§3.2) served to many clients; the paper
+ * itself has no serving layer.
+ */
+fmm_status fmm_server_create(fmm_server **out, int device, int slots, fmm_precision prec,
+                             size_t mem_budget_bytes);
+/* Queue a request; *ticket identifies it.  FMM_EBUDGET if it could never fit. */
+fmm_status fmm_server_submit(fmm_server *s, const fmm_request *r, int64_t *ticket);
+/* *done = 1 once the ticket has completed (successfully or not). */
+fmm_status fmm_server_poll(fmm_server *s, int64_t ticket, int *done);
+/* Block until the ticket completes; fills *res (may be NULL) and releases the
+ * ticket.  Returns the request's own status. */
+fmm_status fmm_server_wait(fmm_server *s, int64_t ticket, fmm_request_result *res);
+fmm_status fmm_server_get_stats(fmm_server *s, fmm_server_stats *out);
+/* Drain the queue, join the workers and free everything. */
+fmm_status fmm_server_destroy(fmm_server *s);
+
 /*
  * Self-check of the library's own FP64 reciprocal square root used by the
  * P2P near field (an FP32 rsqrtf seed refined by one third-order

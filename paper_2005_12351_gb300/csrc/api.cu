@@ -80,7 +80,8 @@ void record(fmm_tree *t, int i)
 
 void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
 {
-    DevBuf *b[] = {&t->b_sys, &t->b_sysoff, &t->b_sysbox, &t->b_syseside, &t->b_o32, &t->b_S32,
+    DevBuf *b[] = {&t->b_req_in, &t->b_req_out, &t->b_sys, &t->b_sysoff, &t->b_sysbox,
+                   &t->b_syseside, &t->b_o32, &t->b_S32,
                    &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
                    &t->b_hist, &t->b_px, &t->b_py, &t->b_pz, &t->b_S, &t->b_perm, &t->b_level,
                    &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,

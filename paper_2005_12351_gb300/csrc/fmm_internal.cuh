@@ -146,6 +146,8 @@ struct fmm_tree {
     DevBuf b_tab_i32, b_tab_u32;
     // mixed-precision state
     DevBuf b_o32, b_S32, b_M32, b_L32, b_D32;
+    // request staging (serving): host inputs and outputs pass through these
+    DevBuf b_req_in, b_req_out;
     int d32_p = -1;                        // p the FP32 D table was built for
 };
 

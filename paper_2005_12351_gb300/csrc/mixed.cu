@@ -18,6 +18,7 @@
 //   L2P  phi = h^-(s+1) sum_n d^n/n! L~_n,  d_k phi = h^-(s+2) sum d^(n-e_k)/(n-e_k)! L~_n
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "fmm_internal.cuh"
 
@@ -548,6 +549,8 @@ void record(fmm_tree *t, int i)
 fmm_status upload_consts32(fmm_tree *t)
 {
     static int ready[64] = {0};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     if (t->device < 64 && ready[t->device]) return FMM_OK;
     const MultiIndex &I = multi_index();
     int8_t x[kMaxTot], y[kMaxTot], z[kMaxTot];

@@ -10,6 +10,7 @@
 // D_n(R) = grad^n (1/|R|) is generated once per distinct M2L offset.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "fmm_internal.cuh"
 
@@ -449,6 +450,8 @@ inline unsigned grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut)
 {
     static int consts_ready[64] = {0};
+    static std::mutex consts_mu;
+    std::lock_guard<std::mutex> consts_lock(consts_mu);
     if (t->device < 64 && !consts_ready[t->device]) {
         const MultiIndex &I = multi_index();
         int8_t x[kMaxTot], y[kMaxTot], z[kMaxTot];

@@ -274,3 +274,109 @@ def morton_order_noalloc(positions, keys_out, perm_out, stream=None):
     st = noalloc_entry()(_stream_ptr(stream), _ptr(positions), n, _ptr(keys_out), _ptr(perm_out))
     _check(st, None, "morton_order_noalloc")
     return keys_out, perm_out
+
+
+# ------------------------------------------------------------------ serving
+class Request(C.Structure):
+    _fields_ = [("positions", C.c_void_p), ("moments", C.c_void_p), ("n", C.c_int64),
+                ("source_order", C.c_int), ("p", C.c_int), ("theta", C.c_double),
+                ("max_leaf", C.c_int), ("want_potential", C.c_int), ("want_field", C.c_int),
+                ("potential", C.c_void_p), ("field", C.c_void_p)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("status", C.c_int), ("slot", C.c_int),
+                ("submit_s", C.c_double), ("start_s", C.c_double), ("end_s", C.c_double),
+                ("device_bytes", C.c_int64), ("message", C.c_char * 128)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
+                ("running", C.c_int64), ("device_bytes", C.c_int64),
+                ("peak_device_bytes", C.c_int64), ("particles_done", C.c_int64),
+                ("busy_span_s", C.c_double)]
+
+
+def _server_fns():
+    L = lib()
+    vp = C.c_void_p
+    L.fmm_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_size_t]
+    L.fmm_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_int64)]
+    L.fmm_server_poll.argtypes = [vp, C.c_int64, C.POINTER(C.c_int)]
+    L.fmm_server_wait.argtypes = [vp, C.c_int64, C.POINTER(RequestResult)]
+    L.fmm_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.fmm_server_destroy.argtypes = [vp]
+    for f in ("fmm_server_create", "fmm_server_submit", "fmm_server_poll", "fmm_server_wait",
+              "fmm_server_get_stats", "fmm_server_destroy"):
+        getattr(L, f).restype = C.c_int
+    return L
+
+
+class Server:
+    """fmm_server_*: continuous batching of evaluation requests on one GPU.
+
+    ``submit`` takes numpy arrays (kept alive here until ``wait``) and returns a
+    ticket; ``wait`` returns (phi, E, result-dict)."""
+
+    def __init__(self, device=0, slots=4, precision="fp64", mem_budget_bytes=0):
+        import numpy as np  # noqa: F401
+        L = _server_fns()
+        h = C.c_void_p()
+        st = L.fmm_server_create(C.byref(h), int(device), int(slots), PRECISIONS[precision],
+                                 int(mem_budget_bytes))
+        if st != FMM_OK:
+            raise FMMError(st, "server_create: %s" % L.fmm_status_string(st).decode())
+        self._h, self._L = h, L
+        self._live = {}
+
+    def submit(self, positions, moments, source_order, p, theta=0.5, max_leaf=64,
+               want_potential=True, want_field=True):
+        import numpy as np
+        pos = np.ascontiguousarray(positions, dtype=np.float64)
+        mom = np.ascontiguousarray(moments, dtype=np.float64)
+        n = pos.shape[0]
+        phi = np.empty(n) if want_potential else None
+        E = np.empty((n, 3)) if want_field else None
+        r = Request(pos.ctypes.data if n else None, mom.ctypes.data if n else None, n,
+                    int(source_order), int(p), float(theta), int(max_leaf),
+                    int(bool(want_potential)), int(bool(want_field)),
+                    phi.ctypes.data if (phi is not None and n) else None,
+                    E.ctypes.data if (E is not None and n) else None)
+        t = C.c_int64()
+        st = self._L.fmm_server_submit(self._h, C.byref(r), C.byref(t))
+        if st != FMM_OK:
+            raise FMMError(st, "server_submit: %s" % self._L.fmm_status_string(st).decode())
+        self._live[t.value] = (pos, mom, phi, E)
+        return t.value
+
+    def done(self, ticket) -> bool:
+        d = C.c_int()
+        _check(self._L.fmm_server_poll(self._h, int(ticket), C.byref(d)), None, "server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket):
+        res = RequestResult()
+        st = self._L.fmm_server_wait(self._h, int(ticket), C.byref(res))
+        pos, mom, phi, E = self._live.pop(ticket)
+        info = {"status": res.status, "slot": res.slot, "submit_s": res.submit_s,
+                "start_s": res.start_s, "end_s": res.end_s, "device_bytes": res.device_bytes,
+                "message": res.message.decode(errors="replace")}
+        if st != FMM_OK:
+            raise FMMError(st, "request %d: %s" % (ticket, info["message"]))
+        return phi, E, info
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._L.fmm_server_get_stats(self._h, C.byref(s)), None, "server_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            self._L.fmm_server_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

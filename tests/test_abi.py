@@ -58,3 +58,13 @@ def test_create_tree_reports_missing_device(libpath):
     h = ctypes.c_void_p()
     st = lib.fmm_create_tree(ctypes.byref(h), 0, None, 64, 0, ctypes.c_size_t(0))
     assert st == -1 and not h.value
+
+
+def test_server_create_without_gpu_returns_status(libpath):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    lib = ctypes.CDLL(libpath)
+    h = ctypes.c_void_p()
+    st = lib.fmm_server_create(ctypes.byref(h), 0, 2, 0, ctypes.c_size_t(0))
+    assert st != 0 and not h.value
