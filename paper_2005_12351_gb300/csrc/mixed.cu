@@ -32,7 +32,10 @@ __constant__ float x_invfact[kMaxOrder + 1];    // 1/q!
 
 inline unsigned gridm(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-__device__ __forceinline__ int shell(int idx) { return x_nx[idx] + x_ny[idx] + x_nz[idx]; }
+// global row stride of the FP32 M and D tables: a multiple of 4 floats, so
+// every row starts on a 16-byte boundary (rows are copied with cp.async)
+__host__ __device__ __forceinline__ int row4(int n) { return (n + 3) & ~3; }
+
 
 // per-axis scaled powers w^q / q!, q <= P
 __device__ __forceinline__ void axis_powers32(float w, int P, float *out)
@@ -81,22 +84,36 @@ __device__ __forceinline__ void two_sum_lo(float a, float b, float c, float &s, 
 // ------------------------------------------------------------------ P2M
 constexpr int kChunk = 32;
 constexpr int kPer = 4;                   // up to 4 * 128 = 512 components per thread block
+constexpr int kMaxSrc = 6;
 
+// One block per leaf; each thread owns up to kPer components with their
+// source-term monomial indices in registers (absent terms hit a zero slot).
+// FP32 sums over groups of 8 particles, FP64 across groups.
 __global__ void __launch_bounds__(128)
 k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
         const float4 *o, const float *S32, DevTables tb, float *M)
 {
     extern __shared__ float sf[];
-    const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nS = tb.nS;
+    const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nK1 = tb.nK + 1, nS = tb.nS;
     float *apow = sf;                              // [chunk][3][P1]
-    float *mono = apow + kChunk * 3 * P1;          // [chunk][nK]
-    float *Ssm = mono + kChunk * nK;               // [chunk][nS]
+    float *mono = apow + kChunk * 3 * P1;          // [chunk][nK + 1], last = 0
+    float *Ssm = mono + kChunk * nK1;              // [chunk][nS]
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
     const float inv_h = (float)(1.0 / half[c]);    // a power of two
+    const int nS32 = nS == 6 ? 7 : nS;
+    int kt[kPer][kMaxSrc];
     double acc[kPer];
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+    for (int u = 0; u < kPer; ++u) {
+        acc[u] = 0.0;
+        const int mi = threadIdx.x + u * 128;
+#pragma unroll
+        for (int a = 0; a < kMaxSrc; ++a) {
+            const int k = (mi < tb.nM && a < nS) ? tb.p2m_terms[mi * nS + a] : -1;
+            kt[u][a] = k >= 0 ? k : nK;
+        }
+    }
     for (int j0 = b; j0 < e; j0 += kChunk) {
         const int nj = min(kChunk, e - j0);
         for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
@@ -105,29 +122,28 @@ k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
             const float d = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
             axis_powers32(-d * inv_h, P, apow + (j * 3 + ax) * P1);
         }
-        const int nS32 = nS == 6 ? 7 : nS;
         for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
             Ssm[t] = S32[(int64_t)(j0 + t / nS) * nS32 + t % nS];
         __syncthreads();
-        for (int t = threadIdx.x; t < nj * nK; t += blockDim.x) {
-            const int j = t / nK, k = t % nK;
+        for (int t = threadIdx.x; t < nj * nK1; t += blockDim.x) {
+            const int j = t / nK1, k = t % nK1;
             const float *a = apow + j * 3 * P1;
-            mono[t] = a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]];
+            const int v = mi_at(tb.mi, k < nK ? k : 0);
+            mono[t] = k < nK ? a[mi_nx(v)] * a[P1 + mi_ny(v)] * a[2 * P1 + mi_nz(v)] : 0.0f;
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
-            const int mi = threadIdx.x + u * 128;
-            if (mi >= tb.nM) break;
-            // FP32 over groups of 8 particles, FP64 across groups (cancellation
-            // between randomly oriented sources is absorbed in FP64)
+            if (threadIdx.x + u * 128 >= tb.nM) break;
             for (int j8 = 0; j8 < nj; j8 += 8) {
                 float sum = 0.0f;
-                for (int j = j8; j < min(j8 + 8, nj); ++j)
-                    for (int a = 0; a < nS; ++a) {
-                        const int k = tb.p2m_terms[mi * nS + a];
-                        if (k >= 0) sum = fmaf(mono[j * nK + k], Ssm[j * nS + a], sum);
-                    }
+                const int je = min(j8 + 8, nj);
+                for (int j = j8; j < je; ++j) {
+                    const float *mj = mono + j * nK1, *sj = Ssm + j * nS;
+#pragma unroll
+                    for (int a = 0; a < kMaxSrc; ++a)
+                        if (a < nS) sum = fmaf(mj[kt[u][a]], sj[a], sum);
+                }
                 acc[u] += (double)sum;
             }
         }
@@ -136,14 +152,15 @@ k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int mi = threadIdx.x + u * 128;
-        if (mi < tb.nM) M[(int64_t)c * tb.nM + mi] = (float)acc[u];
+        if (mi < tb.nM) M[(int64_t)c * row4(tb.nM) + mi] = (float)acc[u];
     }
 }
 
 // sig^k / k! with sig_d = +1 or -1 given by neg_d (1 means -1)
-__device__ __forceinline__ float sign_mono(int k, int nx_neg, int ny_neg, int nz_neg)
+__device__ __forceinline__ float sign_mono(const int *mi, int k, int nx_neg, int ny_neg, int nz_neg)
 {
-    const int kx = x_nx[k], ky = x_ny[k], kz = x_nz[k];
+    const int v = mi_at(mi, k);
+    const int kx = mi_nx(v), ky = mi_ny(v), kz = mi_nz(v);
     const int odd = (nx_neg & kx) ^ (ny_neg & ky) ^ (nz_neg & kz);
     const float m = x_invfact[kx] * x_invfact[ky] * x_invfact[kz];
     return (odd & 1) ? -m : m;
@@ -167,8 +184,8 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
         const int ch = child[c] + i;
         // z_p - z_c = (1 - 2 bit) h_c per axis: negative where the child's low bit is 1
         const int bx = cx[ch] & 1, by = cy[ch] & 1, bz = cz[ch] & 1;
-        for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(k, bx, by, bz);
-        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * tb.nM + t];
+        for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
+        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * row4(tb.nM) + t];
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
@@ -184,7 +201,9 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int ni = threadIdx.x + u * 128;
-        if (ni < tb.nM) M[(int64_t)c * tb.nM + ni] = (float)ldexp(acc[u], -(shell(ni + tb.m0) - tb.s));
+        if (ni < tb.nM)
+            M[(int64_t)c * row4(tb.nM) + ni] =
+                (float)ldexp(acc[u], -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s));
     }
 }
 
@@ -193,7 +212,7 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
 // shifted by the level gap when the target is the coarser cell (h_t = 2^gap u),
 // unchanged otherwise (h_t = u), and rounded once.
 __global__ void k_dtables32(const uint64_t *dkeys, int64_t ndoff, int nD, const double *D,
-                            float *D32)
+                            const int *mi, float *D32)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ndoff * nD) return;
@@ -202,7 +221,7 @@ __global__ void k_dtables32(const uint64_t *dkeys, int64_t ndoff, int nD, const 
     const uint64_t key = dkeys[r];
     const int gap = (int)((key >> 52) & 31), tfiner = (int)((key >> 51) & 1);
     const int e = tfiner ? 0 : gap;
-    D32[i] = (float)ldexp(D[i], (shell(k) + 1) * e);
+    D32[r * row4(nD) + k] = (float)ldexp(D[i], (mi_shell(mi_at(mi, k)) + 1) * e);
 }
 
 // ------------------------------------------------------------------ M2L
@@ -225,22 +244,29 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
     uint32_t *desc = (uint32_t *)(Dsm + kBatch * ldD);  // [T][Tn]
     const int tid = threadIdx.x;
     const int lt = level[c];
+    __shared__ int bsrc[kBatch], bdidx[kBatch], bdl[kBatch];
     for (int i = tid; i < T * Tn; i += Tn) desc[i] = tb.m2l_desc[i];
     for (int i = tid; i < tb.m2l_slots * Tn; i += Tn) part[i] = 0.0;
     for (int k0 = b; k0 < e; k0 += kBatch) {
         const int kb = min(kBatch, e - k0);
         __syncthreads();
-        for (int i = tid; i < kb * nM; i += Tn) {
-            const int k = i / nM, m = i % nM;
-            const int s = src[k0 + k];
-            float v = M[(int64_t)s * nM + m];
-            const int ls = level[s];
-            if (ls != lt) v = ldexpf(v, (lt - ls) * (shell(m + tb.m0) - tb.s));
-            Msm[k * ldM + m] = v;
+        if (tid < kb) {                    // batch metadata, loaded in parallel
+            const int s = src[k0 + tid];
+            bsrc[tid] = s;
+            bdidx[tid] = didx[k0 + tid];
+            bdl[tid] = lt - level[s];
         }
-        for (int i = tid; i < kb * nD; i += Tn) {
-            const int k = i / nD, d = i % nD;
-            Dsm[k * ldD + d] = D32[(int64_t)didx[k0 + k] * nD + d];
+        __syncthreads();
+        for (int k = 0; k < kb; ++k) {
+            const float *Ms = M + (int64_t)bsrc[k] * row4(nM);
+            const int dl = bdl[k];
+            for (int m = tid; m < nM; m += Tn) {
+                float v = Ms[m];
+                if (dl) v = ldexpf(v, dl * (mi_shell(mi_at(tb.mi, m + tb.m0)) - tb.s));
+                Msm[k * ldM + m] = v;
+            }
+            const float *Dk = D32 + (int64_t)bdidx[k] * row4(nD);
+            for (int d = tid; d < nD; d += Tn) Dsm[k * ldD + d] = Dk[d];
         }
         __syncthreads();
         float acc = 0.0f;
@@ -283,12 +309,12 @@ k_l2l32(int lb, const int32_t *parent, const int32_t *cx, const int32_t *cy, con
     const int pa = parent[c];
     // z_c - z_p = (2 bit - 1) h_c: negative where the child's low bit is 0
     const int bx = 1 - (cx[c] & 1), by = 1 - (cy[c] & 1), bz = 1 - (cz[c] & 1);
-    for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(k, bx, by, bz);
+    for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
     for (int q = threadIdx.x; q < tb.nL; q += blockDim.x)
-        Lp[q] = ldexpf(L[(int64_t)pa * tb.nL + q], -(shell(q) + tb.s + 1));
+        Lp[q] = ldexpf(L[(int64_t)pa * tb.nL + q], -(mi_shell(mi_at(tb.mi, q)) + tb.s + 1));
     __syncthreads();
     for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
-        if (shell(n) < tb.n_lo) continue;
+        if (mi_shell(mi_at(tb.mi, n)) < tb.n_lo) continue;
         float acc = 0.0f;
         for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
             acc = fmaf(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
@@ -590,9 +616,9 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     }
     FMM_TRY(build_dtables(t, p, tb, lut));
     if (t->d32_p != p && t->n_doff > 0) {
-        FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * tb.nD));
+        FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
-            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr,
+            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr, tb.mi,
             (float *)t->b_D32.ptr);
         ++t->launches;
         t->d32_p = p;
@@ -600,7 +626,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     record(t, 6);
     FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
     FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));
-    FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * tb.nM));
+    FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * row4(tb.nM)));
     FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
@@ -619,7 +645,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
                                                    (const double *)t->b_S.ptr, t->nS, o, o + n,
                                                    S32);
     {
-        size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * tb.nK + kChunk * tb.nS);
+        size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * (tb.nK + 1) + kChunk * tb.nS);
         cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_p2m32<<<(unsigned)t->nleaves, 128, smem, st>>>(leaves, begin, end, half, o, S32, tb, M);
     }

@@ -10,6 +10,7 @@
 // D_n(R) = grad^n (1/|R|) is generated once per distinct M2L offset.
 #include <algorithm>
 #include <cstring>
+#include <stdexcept>
 #include <mutex>
 
 #include "fmm_internal.cuh"
@@ -119,6 +120,45 @@ void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads)
         max_slots = std::max(max_slots, slot + 1);
     }
     T.m2l_slots = max_slots;
+    T.m2l_terms.clear();
+    T.m2l_run_off.assign(T.nL + 1, 0);
+    for (const Term &tm : terms) T.m2l_terms.push_back((uint32_t)tm.m | ((uint32_t)tm.d << 16));
+    {
+        int q = 0;
+        for (int n = 0; n < T.nL; ++n) {
+            T.m2l_run_off[n] = q;
+            while (q < W && terms[q].n == n) ++q;
+        }
+        T.m2l_run_off[T.nL] = q;
+    }
+    {
+        std::vector<uint16_t> d16;
+        T.m2l_d16_off.assign(T.nL + 1, 0);
+        T.m2l_cnt.assign(T.nL, 0);
+        for (int n = 0; n < T.nL; ++n) {
+            T.m2l_d16_off[n] = (int)d16.size();
+            const int q0 = T.m2l_run_off[n], q1 = T.m2l_run_off[n + 1];
+            T.m2l_cnt[n] = q1 - q0;
+            for (int q = q0; q < q1; ++q) {
+                if (terms[q].m != q - q0) throw std::logic_error("M2L run is not an m prefix");
+                d16.push_back((uint16_t)terms[q].d);
+            }
+            while (d16.size() % 4) d16.push_back((uint16_t)T.nD);
+        }
+        T.m2l_d16_off[T.nL] = (int)d16.size();
+        T.m2l_d16.assign((d16.size() + 1) / 2, 0u);
+        for (size_t i = 0; i < d16.size(); ++i)
+            T.m2l_d16[i / 2] |= (uint32_t)d16[i] << (16 * (i % 2));
+        // four contiguous n-ranges with about equal padded term counts
+        const int total = T.m2l_d16_off[T.nL];
+        T.m2l_split[0] = 0;
+        int n = 0;
+        for (int w = 1; w < 4; ++w) {
+            while (n < T.nL && T.m2l_d16_off[n] < (int64_t)total * w / 4) ++n;
+            T.m2l_split[w] = n;
+        }
+        T.m2l_split[4] = T.nL;
+    }
     T.m2l_red_off.assign(1, 0); T.m2l_red_src.clear();
     for (int n = 0; n < T.nL; ++n) {
         for (int v : red[n]) T.m2l_red_src.push_back(v);
@@ -182,12 +222,14 @@ __global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, int nD, const in
 }
 
 // per-axis scaled powers d^j / j!, j <= P, then monomials d^k / k! = ax[kx] ay[ky] az[kz]
+__constant__ double c_invint[kMaxOrder + 2];     // 1/j
+
 __device__ __forceinline__ void axis_powers(double d, int P, double *out)
 {
     double v = 1.0;
     out[0] = 1.0;
     for (int j = 1; j <= P; ++j) {
-        v = v * d / (double)j;
+        v = v * d * c_invint[j];
         out[j] = v;
     }
 }
@@ -196,49 +238,63 @@ __device__ __forceinline__ void axis_powers(double d, int P, double *out)
 constexpr int kP2MThreads = 128;
 constexpr int kP2MChunk = 16;
 constexpr int kP2MPer = 4;                // up to 4 * 128 = 512 M components
+constexpr int kMaxSrc = 6;                // source terms of one component (s <= 2)
 
+// One block per leaf.  Each thread owns up to kP2MPer components m and keeps
+// the monomial index of m - a for each source term a in registers (an absent
+// term points at a zero slot), so the particle loop is branch-free.
 __global__ void __launch_bounds__(kP2MThreads)
 k_p2m(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
       const double *px, const double *py, const double *pz, const double *S, DevTables tb,
       double *M)
 {
     extern __shared__ double sm[];
-    const int P = tb.p, nK = tb.nK;
+    const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nK1 = tb.nK + 1, nS = tb.nS;
     double *apow = sm;                                  // [chunk][3][P+1]
-    double *mono = apow + kP2MChunk * 3 * (P + 1);      // [chunk][nK]
-    double *Ssm = mono + kP2MChunk * nK;                // [chunk][nS]
+    double *mono = apow + kP2MChunk * 3 * P1;           // [chunk][nK + 1], last = 0
+    double *Ssm = mono + kP2MChunk * nK1;               // [chunk][nS]
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
+    int kt[kP2MPer][kMaxSrc];
     double acc[kP2MPer];
 #pragma unroll
-    for (int u = 0; u < kP2MPer; ++u) acc[u] = 0.0;
+    for (int u = 0; u < kP2MPer; ++u) {
+        acc[u] = 0.0;
+        const int mi = threadIdx.x + u * kP2MThreads;
+#pragma unroll
+        for (int a = 0; a < kMaxSrc; ++a) {
+            const int k = (mi < tb.nM && a < nS) ? tb.p2m_terms[mi * nS + a] : -1;
+            kt[u][a] = k >= 0 ? k : nK;
+        }
+    }
     for (int j0 = b; j0 < e; j0 += kP2MChunk) {
         const int nj = min(kP2MChunk, e - j0);
         for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
             const int j = t / 3, ax = t % 3;
             const double x = ax == 0 ? px[j0 + j] : (ax == 1 ? py[j0 + j] : pz[j0 + j]);
             const double zc = ax == 0 ? z0 : (ax == 1 ? z1 : z2);
-            axis_powers(zc - x, P, apow + (j * 3 + ax) * (P + 1));
+            axis_powers(zc - x, P, apow + (j * 3 + ax) * P1);
         }
-        for (int t = threadIdx.x; t < nj * tb.nS; t += blockDim.x)
-            Ssm[t] = S[(int64_t)j0 * tb.nS + t];
+        for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
+            Ssm[t] = S[(int64_t)j0 * nS + t];
         __syncthreads();
-        for (int t = threadIdx.x; t < nj * nK; t += blockDim.x) {
-            const int j = t / nK, k = t % nK;
-            const double *a = apow + j * 3 * (P + 1);
-            mono[t] = a[c_nx[k]] * a[(P + 1) + c_ny[k]] * a[2 * (P + 1) + c_nz[k]];
+        for (int t = threadIdx.x; t < nj * nK1; t += blockDim.x) {
+            const int j = t / nK1, k = t % nK1;
+            const double *a = apow + j * 3 * P1;
+            const int v = mi_at(tb.mi, k < nK ? k : 0);
+            mono[t] = k < nK ? a[mi_nx(v)] * a[P1 + mi_ny(v)] * a[2 * P1 + mi_nz(v)] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kP2MPer; ++u) {
-            const int mi = threadIdx.x + u * kP2MThreads;
-            if (mi >= tb.nM) break;
-            for (int j = 0; j < nj; ++j)
-                for (int a = 0; a < tb.nS; ++a) {
-                    const int k = tb.p2m_terms[mi * tb.nS + a];
-                    if (k >= 0) acc[u] = fma(mono[j * nK + k], Ssm[j * tb.nS + a], acc[u]);
-                }
+            if (threadIdx.x + u * kP2MThreads >= tb.nM) break;
+            for (int j = 0; j < nj; ++j) {
+                const double *mj = mono + j * nK1, *sj = Ssm + j * nS;
+#pragma unroll
+                for (int a = 0; a < kMaxSrc; ++a)
+                    if (a < nS) acc[u] = fma(mj[kt[u][a]], sj[a], acc[u]);
+            }
         }
         __syncthreads();
     }
@@ -273,8 +329,10 @@ k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre,
                         apow + threadIdx.x * (P + 1));
         for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * tb.nM + t];
         __syncthreads();
-        for (int k = threadIdx.x; k < nK; k += blockDim.x)
-            mono[k] = apow[c_nx[k]] * apow[(P + 1) + c_ny[k]] * apow[2 * (P + 1) + c_nz[k]];
+        for (int k = threadIdx.x; k < nK; k += blockDim.x) {
+            const int v = mi_at(tb.mi, k);
+            mono[k] = apow[mi_nx(v)] * apow[(P + 1) + mi_ny(v)] * apow[2 * (P + 1) + mi_nz(v)];
+        }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kP2MPer; ++u) {
@@ -322,22 +380,27 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t
     uint32_t *desc = (uint32_t *)(part + tb.m2l_slots * Tn);   // [T][Tn]
     const int tid = threadIdx.x;
     const int lt = level[c], es = e_side[sys[c]];
+    __shared__ int bsrc[kM2LBatch], bdidx[kM2LBatch], beu[kM2LBatch];
     for (int i = tid; i < T * Tn; i += Tn) desc[i] = tb.m2l_desc[i];
     for (int i = tid; i < tb.m2l_slots * Tn; i += Tn) part[i] = 0.0;
     for (int k0 = b; k0 < e; k0 += kM2LBatch) {
         const int kb = min(kM2LBatch, e - k0);
         __syncthreads();
-        for (int i = tid; i < kb * nM; i += Tn) {
-            const int k = i / nM, m = i % nM;
-            Msm[k * ldM + m] = M[(int64_t)src[k0 + k] * nM + m];
-        }
-        for (int i = tid; i < kb * nD; i += Tn) {
-            const int k = i / nD, d = i % nD;
+        if (tid < kb) {                    // batch metadata, loaded in parallel
+            const int s = src[k0 + tid];
+            bsrc[tid] = s;
+            bdidx[tid] = didx[k0 + tid];
             // u = side / 2^(lf+1): D_k(u v) = 2^(-(|k|+1) log2 u) D_k(v)
-            const int lf = max(lt, level[src[k0 + k]]);
-            const int eu = es - lf - 1;
-            Dsm[k * ldD + d] = scale_pow2(D[(int64_t)didx[k0 + k] * nD + d],
-                                          -(c_nx[d] + c_ny[d] + c_nz[d] + 1) * eu);
+            beu[tid] = es - max(lt, level[s]) - 1;
+        }
+        __syncthreads();
+        for (int k = 0; k < kb; ++k) {
+            const double *Ms = M + (int64_t)bsrc[k] * nM;
+            for (int m = tid; m < nM; m += Tn) Msm[k * ldM + m] = Ms[m];
+            const double *Dk = D + (int64_t)bdidx[k] * nD;
+            const int eu = beu[k];
+            for (int d = tid; d < nD; d += Tn)
+                Dsm[k * ldD + d] = scale_pow2(Dk[d], -(mi_shell(mi_at(tb.mi, d)) + 1) * eu);
         }
         __syncthreads();
         double acc = 0.0;
@@ -384,11 +447,13 @@ k_l2l(int lb, const int32_t *parent, const double *centre, DevTables tb, double 
                     apow + threadIdx.x * (P + 1));
     for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lp[t] = L[(int64_t)pa * tb.nL + t];
     __syncthreads();
-    for (int k = threadIdx.x; k < nK; k += blockDim.x)
-        mono[k] = apow[c_nx[k]] * apow[(P + 1) + c_ny[k]] * apow[2 * (P + 1) + c_nz[k]];
+    for (int k = threadIdx.x; k < nK; k += blockDim.x) {
+        const int v = mi_at(tb.mi, k);
+        mono[k] = apow[mi_nx(v)] * apow[(P + 1) + mi_ny(v)] * apow[2 * (P + 1) + mi_nz(v)];
+    }
     __syncthreads();
     for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
-        const int kn = c_nx[n] + c_ny[n] + c_nz[n];
+        const int kn = mi_shell(mi_at(tb.mi, n));
         if (kn < tb.n_lo) continue;
         double acc = 0.0;
         for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
@@ -459,6 +524,10 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_nx, x, sizeof(x)), "constants"));
         FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_ny, y, sizeof(y)), "constants"));
         FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_nz, z, sizeof(z)), "constants"));
+        double inv[kMaxOrder + 2];
+        inv[0] = 0.0;
+        for (int q = 1; q < kMaxOrder + 2; ++q) inv[q] = 1.0 / q;
+        FMM_TRY(cuda_check(t, cudaMemcpyToSymbol(c_invint, inv, sizeof(inv)), "constants"));
         consts_ready[t->device] = 1;
     }
     OpTables &T = t->tab;
@@ -482,14 +551,33 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     o_m2m_q = put(T.m2m_q); o_l2l_off = put(T.l2l_off); o_l2l_k = put(T.l2l_k);
     o_l2l_q = put(T.l2l_q); o_grad = put(T.l2p_grad); o_roff = put(T.m2l_red_off);
     o_rsrc = put(T.m2l_red_src);
+    const size_t o_runoff = put(T.m2l_run_off);
+    const size_t o_d16off = put(T.m2l_d16_off);
+    const size_t o_cnt = put(T.m2l_cnt);
+    size_t o_mi;
+    {
+        const MultiIndex &I = multi_index();
+        std::vector<int> mi(kMaxTot);
+        for (int i = 0; i < kMaxTot; ++i)
+            mi[i] = I.nx[i] | I.ny[i] << 5 | I.nz[i] << 10 | (I.nx[i] + I.ny[i] + I.nz[i]) << 15;
+        o_mi = put(mi);
+    }
     FMM_TRY(ensure(t, t->b_tab_i32, 4 * buf.size()));
-    FMM_TRY(ensure(t, t->b_tab_u32, 4 * T.m2l_desc.size()));
+    // the 16-bit d table is read with 8-byte loads: start it on an even word
+    const size_t w_d16 = (T.m2l_desc.size() + T.m2l_terms.size() + 1) & ~(size_t)1;
+    FMM_TRY(ensure(t, t->b_tab_u32, 4 * (w_d16 + T.m2l_d16.size() + 2)));
     if (rebuild) {
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_i32.ptr, buf.data(), 4 * buf.size(),
                                               cudaMemcpyHostToDevice, t->stream), "tables"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_u32.ptr, T.m2l_desc.data(),
                                               4 * T.m2l_desc.size(), cudaMemcpyHostToDevice,
                                               t->stream), "tables"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync((uint32_t *)t->b_tab_u32.ptr + T.m2l_desc.size(),
+                                              T.m2l_terms.data(), 4 * T.m2l_terms.size(),
+                                              cudaMemcpyHostToDevice, t->stream), "tables"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync((uint32_t *)t->b_tab_u32.ptr + w_d16,
+                                              T.m2l_d16.data(), 4 * T.m2l_d16.size(),
+                                              cudaMemcpyHostToDevice, t->stream), "tables"));
         t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo;
     }
     const int32_t *B = (const int32_t *)t->b_tab_i32.ptr;
@@ -501,6 +589,14 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     dt->m2l_red_src = B + o_rsrc;
     dt->m2l_desc = (const uint32_t *)t->b_tab_u32.ptr;
     dt->m2l_T = T.m2l_T; dt->m2l_slots = T.m2l_slots;
+    dt->m2l_terms = (const uint32_t *)t->b_tab_u32.ptr + T.m2l_desc.size();
+    dt->m2l_run_off = B + o_runoff;
+    dt->mi = B + o_mi;
+    dt->m2l_d16 = (const uint32_t *)t->b_tab_u32.ptr + w_d16;
+    dt->m2l_d16_off = B + o_d16off;
+    dt->m2l_cnt = B + o_cnt;
+    for (int w = 0; w < 5; ++w) dt->m2l_split[w] = T.m2l_split[w];
+    dt->m2l_nterms = (int)T.m2l_terms.size();
     *lut = B + o_lut;
     return FMM_OK;
 }
@@ -556,7 +652,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
 
     // P2M at the leaves
     {
-        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * tb.nK + kP2MChunk * tb.nS);
+        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
         cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
                                                                (const double *)t->b_S.ptr, tb, M);

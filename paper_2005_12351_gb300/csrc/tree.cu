@@ -375,40 +375,73 @@ __device__ __forceinline__ bool mac_accept(const CellArrays &c, int a, int b, do
     return lhs < __dmul_rn(theta2, (double)d2);
 }
 
-__device__ __forceinline__ void push(int2 *buf, unsigned *count, unsigned cap, int a, int b)
+// Warp-aggregated reservation: every lane asks for `want` slots of one list;
+// one atomic per warp, lanes get consecutive ranges in lane order.
+__device__ __forceinline__ unsigned warp_reserve(unsigned *count, unsigned want)
 {
-    unsigned k = atomicAdd(count, 1u);
-    if (k < cap) buf[k] = make_int2(a, b);
+    const int lane = threadIdx.x & 31;
+    unsigned incl = want;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - want;
 }
 
-// counters: 0 = m2l, 1 = p2p, 2 = next frontier
+// counters: 0 = m2l, 1 = p2p, 2 = next frontier.  Outputs beyond a list's
+// capacity are counted but not written; the host grows the list and reruns.
 __global__ void k_traverse(CellArrays c, const int2 *front, int nf, double theta2, int2 *m2l,
                            unsigned m2l_cap, int2 *p2p, unsigned p2p_cap, int2 *next,
                            unsigned next_cap, unsigned *counters)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nf) return;
-    const int a = front[t].x, b = front[t].y;
-    const int na = c.nchild[a], nb = c.nchild[b];
-    if (a == b) {
-        if (na == 0) { push(p2p, &counters[1], p2p_cap, a, a); return; }
-        const int f = c.child[a];
-        for (int i = 0; i < na; ++i)
-            for (int j = 0; j < na; ++j) push(next, &counters[2], next_cap, f + i, f + j);
-        return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < nf;
+    int a = 0, b = 0, na = 0, nb = 0;
+    if (valid) {
+        a = front[t].x; b = front[t].y;
+        na = c.nchild[a]; nb = c.nchild[b];
     }
-    if (mac_accept(c, a, b, theta2)) { push(m2l, &counters[0], m2l_cap, a, b); return; }
-    if (na == 0 && nb == 0) { push(p2p, &counters[1], p2p_cap, a, b); return; }
-    bool open_a;
-    if (na == 0) open_a = false;
-    else if (nb == 0) open_a = true;
-    else open_a = c.level[a] <= c.level[b];
-    if (open_a) {
+    // classify: kind 0 = M2L, 1 = P2P, 2 = open a (all children against b, or
+    // all child pairs for a self pair), 3 = open b
+    int kind = -1;
+    if (valid) {
+        if (a == b) kind = na == 0 ? 1 : 2;
+        else if (mac_accept(c, a, b, theta2)) kind = 0;
+        else if (na == 0 && nb == 0) kind = 1;
+        else if (na == 0) kind = 3;
+        else if (nb == 0) kind = 2;
+        else kind = c.level[a] <= c.level[b] ? 2 : 3;
+    }
+    const unsigned n_next = kind == 2 ? (a == b ? (unsigned)(na * na) : (unsigned)na)
+                                      : (kind == 3 ? (unsigned)nb : 0u);
+    const unsigned o_m2l = warp_reserve(&counters[0], kind == 0);
+    const unsigned o_p2p = warp_reserve(&counters[1], kind == 1);
+    const unsigned o_next = warp_reserve(&counters[2], n_next);
+    if (kind == 0) {
+        if (o_m2l < m2l_cap) m2l[o_m2l] = make_int2(a, b);
+    } else if (kind == 1) {
+        if (o_p2p < p2p_cap) p2p[o_p2p] = make_int2(a, b);
+    } else if (kind == 2) {
         const int f = c.child[a];
-        for (int i = 0; i < na; ++i) push(next, &counters[2], next_cap, f + i, b);
-    } else {
+        if (a == b) {
+            for (int i = 0; i < na; ++i)
+                for (int j = 0; j < na; ++j) {
+                    const unsigned k = o_next + (unsigned)(i * na + j);
+                    if (k < next_cap) next[k] = make_int2(f + i, f + j);
+                }
+        } else {
+            for (int i = 0; i < na; ++i)
+                if (o_next + i < next_cap) next[o_next + i] = make_int2(f + i, b);
+        }
+    } else if (kind == 3) {
         const int f = c.child[b];
-        for (int j = 0; j < nb; ++j) push(next, &counters[2], next_cap, a, f + j);
+        for (int j = 0; j < nb; ++j)
+            if (o_next + j < next_cap) next[o_next + j] = make_int2(a, f + j);
     }
 }
 
