@@ -312,6 +312,23 @@ fmm_status fmm_check_rsqrt(void *cuda_stream, const double *x, int64_t n, double
                            double *ref);
 
 /*
+ * Self-check of the tensor-core building blocks of the FMM_3XTF32 M2L
+ * (tcgen05.mma kind::tf32, M = 128, 32-byte-swizzled K-major operand tiles,
+ * accumulator in tensor memory).  Computes, in one block,
+ *     D[i][n] = sum_{kb < nkb, n < kbn[kb]} sum_{k < 8} A[i][8 kb + k] B[n][8 kb + k]
+ * for i < 128, n < N, with every A and B value split into two TF32 halves;
+ * passes = 1 forms hi.hi only, passes = 3 adds hi.lo + lo.hi (3xTF32).
+ * a_tmem != 0 stages A in tensor memory instead of shared memory.
+ * A: DEVICE [128 x 8 nkb] FP32 row-major; B: DEVICE [N x 8 nkb]; D: DEVICE
+ * [128 x N]; kbn: HOST [nkb], multiples of 16 with kbn[0] = N.
+ * 1 <= nkb <= 4, 16 <= N <= 256, N % 16 == 0.  Synchronises the device;
+ * FMM_ETIMEOUT if the block's bounded wait for the MMAs gave up.  The paper
+ * has no counterpart: this pins the hardware layout the M2L relies on.
+ */
+fmm_status fmm_check_umma(const float *A, const float *B, float *D, int nkb, int N,
+                          const int *kbn, int a_tmem, int passes);
+
+/*
  * fmm_morton_order without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate device memory
  * while they call the library -- code running inside a custom allocator or

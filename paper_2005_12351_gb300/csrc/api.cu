@@ -399,6 +399,27 @@ fmm_status fmm_check_rsqrt(void *cuda_stream, const double *x, int64_t n, double
     return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ECUDA;
 }
 
+fmm_status fmm_check_umma(const float *A, const float *B, float *D, int nkb, int N,
+                          const int *kbn, int a_tmem, int passes)
+{
+    if (!A || !B || !D || !kbn) return FMM_EINVAL;
+    unsigned *err = nullptr;
+    if (cudaMalloc(&err, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return FMM_ENOMEM;
+    }
+    fmm_status st = FMM_OK;
+    if (cudaMemset(err, 0, sizeof(unsigned)) != cudaSuccess) st = FMM_ECUDA;
+    if (st == FMM_OK) st = check_umma(nullptr, A, B, D, nkb, N, kbn, a_tmem, passes, err);
+    unsigned h = 0;
+    if (st == FMM_OK && (cudaDeviceSynchronize() != cudaSuccess ||
+                         cudaMemcpy(&h, err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess))
+        st = FMM_ECUDA;
+    if (st == FMM_OK && h) st = FMM_ETIMEOUT;
+    cudaFree(err);
+    return st;
+}
+
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out)
 {

@@ -214,6 +214,9 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
 // p2p.cu
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
 void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref);
+// m2l_tc.cu
+fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D, int nkb, int N,
+                      const int *kbn, int a_tmem, int passes, unsigned *err);
 void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
                    const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches);
 

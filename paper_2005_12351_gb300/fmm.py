@@ -244,6 +244,25 @@ def check_rsqrt(x, stream=None):
     return own, ref
 
 
+def check_umma(A, B, kbn, a_tmem=False, passes=3):
+    """Tensor-core self-check: D [128 x N] from CUDA float32 A [128 x 8 len(kbn)]
+    and B [N x 8 len(kbn)]; K-block kb contributes to columns n < kbn[kb]."""
+    fn = lib().fmm_check_umma
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                   C.c_int]
+    fn.restype = C.c_int
+    for name, t in (("A", A), ("B", B)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and t.dim() == 2):
+            raise TypeError("%s must be a contiguous 2-D CUDA float32 tensor" % name)
+    N = B.shape[0]
+    kb = (C.c_int * len(kbn))(*[int(v) for v in kbn])
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    _check(fn(_ptr(A), _ptr(B), _ptr(D), len(kbn), N, C.cast(kb, C.c_void_p), int(bool(a_tmem)),
+              int(passes)), None, "check_umma")
+    return D
+
+
 def morton_order(positions, stream=None):
     """(keys uint64-as-int64 [n], perm int32 [n]) as CUDA tensors."""
     _dev_f64(positions, "positions", 3)
