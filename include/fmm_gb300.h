@@ -165,6 +165,10 @@ typedef struct {
     double side;            /* root box side (a power of two)                    */
     int64_t device_bytes;   /* device memory held by the handle                  */
     int64_t nsystems;       /* independent systems (1 after fmm_set_sources)      */
+    /* FMM_3XTF32 tensor-core M2L plan of the last evaluate (0 otherwise):
+     * target tiles of 128, (tile, key) rows, chunks of rows; the fill
+     * n_m2l / (128 tc_rows) is the share of MMA rows that carry a pair */
+    int64_t tc_tiles, tc_rows, tc_chunks;
 } fmm_tree_info;
 
 fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
@@ -184,7 +188,9 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
  *   FMM_ARR_MULTIPOLE   double [ncells x n_M] M of the last evaluate
  *   FMM_ARR_LOCAL       double [ncells x n_L] L of the last evaluate
  *   FMM_ARR_CELL_SYSTEM int32  [ncells] system (batch index) of each cell
- * In FMM_FP32 handles M and L are the scaled FP32 expansions (float).
+ * In FMM_FP32 and FMM_3XTF32 handles M and L are the scaled FP32 expansions
+ * (float [ncells x n_M], float [ncells x n_L]): M~ = M / h^(|m|-s),
+ * L~ = L h^(|n|+s+1), h the cell's half side.
  */
 typedef enum {
     FMM_ARR_KEYS = 0, FMM_ARR_PERM, FMM_ARR_CELL_LEVEL, FMM_ARR_CELL_COORD,

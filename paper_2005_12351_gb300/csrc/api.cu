@@ -90,7 +90,11 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_p2p_raw, &t->b_counters, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
                    &t->b_p2p_src, &t->b_p2p_off, &t->b_lkeys, &t->b_lkeys2, &t->b_lval,
                    &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
-                   &t->b_E, &t->b_tab_i32, &t->b_tab_u32};
+                   &t->b_E, &t->b_tab_i32, &t->b_tab_u32, &t->b_tc_keys, &t->b_tc_keys2,
+                   &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
+                   &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,
+                   &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
+                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
 }
 
@@ -140,10 +144,6 @@ fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int ma
     if (e != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
         g_create_err = "no CUDA device " + std::to_string(device);
-        return FMM_EINVAL;
-    }
-    if (prec == FMM_3XTF32) {
-        g_create_err = "FMM_3XTF32 is not available in this build (use FMM_FP64 or FMM_FP32)";
         return FMM_EINVAL;
     }
     DeviceGuard g(device);
@@ -242,6 +242,7 @@ static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const d
     DeviceGuard g(t->device);
     t->have_sources = false;
     t->have_lists = false;
+    t->tc_plan = false;
     t->d_p = -1;
     t->n = n;
     t->s = source_order;
@@ -273,7 +274,7 @@ fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, in
     record(t, 4);
     if (!t->have_lists || t->theta != theta) FMM_TRY(build_lists(t, theta));
     record(t, 5);
-    if (t->prec == FMM_FP32) {
+    if (t->prec == FMM_FP32 || t->prec == FMM_3XTF32) {
         FMM_TRY(run_mixed(t, p, want_potential, want_field, potential, field));
     } else {
         FMM_TRY(run_expansions(t, p, want_potential, want_field));
@@ -305,6 +306,11 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *o)
     o->side = t->side;
     o->device_bytes = (int64_t)t->held;
     o->nsystems = t->sys_off.empty() ? 0 : (int64_t)t->sys_off.size() - 1;
+    if (t->tc_plan && t->have_lists) {
+        o->tc_tiles = t->tc_tiles;
+        o->tc_rows = t->tc_rows;
+        o->tc_chunks = t->tc_chunks;
+    }
     return FMM_OK;
 }
 
@@ -367,9 +373,22 @@ fmm_status fmm_copy_array(const fmm_tree *tc, fmm_array which, void *host_dst, s
     case FMM_ARR_P2P: return pairs(t->b_p2p_off, t->b_p2p_src, t->n_p2p);
     case FMM_ARR_MULTIPOLE:
         if (t->tab_key_p < 0) return fail(t, FMM_ESTATE, "no evaluate yet");
+        if (t->prec != FMM_FP64) {          // scaled FP32 rows, stored padded to 4 floats
+            const int nM = t->tab.nM, ld = (nM + 3) & ~3;
+            const size_t need = 4 * (size_t)nc * nM;
+            if (bytes < need) return fail(t, FMM_EINVAL, "buffer too small");
+            std::vector<float> pad((size_t)nc * ld);
+            if (need) FMM_TRY(dl(t->b_M32, 4 * pad.size(), pad.data()));
+            float *d = (float *)host_dst;
+            for (int64_t c = 0; c < nc; ++c)
+                std::memcpy(d + (size_t)c * nM, pad.data() + (size_t)c * ld, 4 * (size_t)nM);
+            if (written) *written = need;
+            return FMM_OK;
+        }
         return plain(t->b_M, 8 * (size_t)nc * t->tab.nM);
     case FMM_ARR_LOCAL:
         if (t->tab_key_p < 0) return fail(t, FMM_ESTATE, "no evaluate yet");
+        if (t->prec != FMM_FP64) return plain(t->b_L32, 4 * (size_t)nc * t->tab.nL);
         return plain(t->b_L, 8 * (size_t)nc * t->tab.nL);
     case FMM_ARR_CELL_SYSTEM: return plain(t->b_sys, 4 * (size_t)nc);
     }

@@ -29,6 +29,7 @@ constexpr int kKeyBias = 1 << 16;      // D-table key: offsets in [-2^16, 2^16)
 constexpr int kErrNonFinite = 1;
 constexpr int kErrKeyRange = 2;
 constexpr int kErrHashFull = 4;
+constexpr int kErrTcTimeout = 8;       // a tensor-core M2L wait gave up (word 1 of b_err)
 
 inline int ntot(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
 inline int nshell(int k) { return (k + 1) * (k + 2) / 2; }
@@ -74,6 +75,22 @@ struct OpTables {
     int m2l_split[5] = {0, 0, 0, 0, 0};  // n-range boundaries for 4 warps
 };
 void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads);
+
+// Operator layout of the tensor-core M2L (FMM_3XTF32) for one (s, p).  The
+// local-expansion columns are cut into groups of at most 128 (width W); the
+// multipoles into K-blocks of 8, each reaching N <= W columns of a group (a
+// multiple of 16).  A key's operator image holds, per (group, K-block), a
+// 32-byte-swizzled tile of W + N rows: the hi halves of rows 0..N-1, zero
+// rows up to W, then the lo halves.  Per image float: the D entry it takes
+// (d | |n+m| << 16 | (|m|-s) << 24, -1 for zero) and its byte position
+// (offset | 1 << 30 for a lo half).
+struct TcLayout {
+    int s = -1, p = -1, nkb = 0, Np = 0, ngroups = 0, E = 0, b_stage = 0, img_bytes = 0;
+    int g_width[2] = {0, 0}, g_nkb[2] = {0, 0}, g_nkc[2] = {0, 0};
+    std::vector<int> kb_n;        // [nkb] columns a K-block reaches (from column 0)
+    std::vector<int> img_off;     // [2 x (nkb + 1)] byte offset of block (g, kb) in an image
+    std::vector<int> el_src, el_pos;
+};
 
 // threads of the M2L blocks (the per-thread term lists are built for it)
 constexpr int kM2LThreadsShared = 128;
@@ -174,6 +191,16 @@ struct fmm_tree {
     // request staging (serving): host inputs and outputs pass through these
     DevBuf b_req_in, b_req_out;
     int d32_p = -1;                        // p the FP32 D table was built for
+    // tensor-core M2L (FMM_3XTF32): target tiles, their key rows and chunks,
+    // derived from the lists; operator images derived from the D table
+    bool tc_plan = false;
+    int tc_img_p = -1, tc_sms = 0;
+    int64_t tc_T = 0, tc_tiles = 0, tc_W = 0, tc_rows = 0, tc_chunks = 0;
+    int tc_G = 0;                          // key rows per chunk
+    fmm::TcLayout tc_lay;
+    DevBuf b_tc_keys, b_tc_keys2, b_tc_vals, b_tc_vals2, b_tc_hist, b_tc_scan, b_tc_cnt;
+    DevBuf b_tc_tgt, b_tc_bits, b_tc_wpre, b_tc_rcnt, b_tc_ccnt, b_tc_roff, b_tc_coff;
+    DevBuf b_tc_rowkey, b_tc_crb, b_tc_cre, b_tc_slot, b_tc_el, b_tc_img, b_tc_part;
 };
 
 // ---------------------------------------------------------------------------
@@ -211,6 +238,11 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field);
 // mixed.cu (FMM_FP32): scaled FP32 expansions, FP32 pair arithmetic, FP64 outputs
 fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *phi_out,
                      double *E_out);
+// m2l_tc.cu: whether the tensor-core M2L covers (s, p) (fills t->tc_lay), and
+// the M2L of the mixed-precision form on it: M and L are the scaled FP32
+// expansions, L zeroed by the caller
+bool tc_usable(fmm_tree *t, int s, int p);
+fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L);
 // p2p.cu
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
 void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref);

@@ -1,6 +1,7 @@
 // m2l_tc.cu -- the M2L translation of the FMM_3XTF32 form on the tcgen05
 // tensor cores, and a self-check of the tensor-core building blocks.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "fmm_internal.cuh"
@@ -117,7 +118,798 @@ __global__ void __launch_bounds__(128) k_check_umma(const float *A, const float 
     }
 }
 
+
+// ------------------------------------------------------------------ M2L
+// For a fixed D key (level gap, which side is finer, integer offset) the
+// translation of Eq. (8) in the scaled form of the mixed-precision path is
+// a matrix-vector product L~_t += T_key M~_s with
+//     T_key[n][m] = Dh_key[n+m] (h_s/h_t)^(|m|-s)   where |n|+|m| <= p+s, else 0.
+// Targets are grouped 128 to a tile (same level and same position in the
+// parent, in Morton order).  For every key that occurs in a tile, one MMA
+// row block takes the sources of the 128 targets at that key as
+// A [128 x n_M] (a zero row where a target has none) and T_key as
+// B [n_L x n_M]:  D[128 x n_L] += A . B^T  (tcgen05.mma kind::tf32, M = 128).
+// Every FP32 value is split into TF32 halves, hi + lo, and the product is
+// formed as hi.hi + hi.lo + lo.hi (3xTF32) in FP32 accumulators in tensor
+// memory.  The triangle |n|+|m| <= p+s is used per K-block of 8 multipoles:
+// the block's MMA covers only N = (the number of n it reaches, rounded up to
+// 16) columns.  Each key row is accumulated in tensor memory on its own and
+// drained into FP32 registers (round to nearest); a chunk of at most G rows
+// of one tile is summed there, and the chunk partials are summed in FP64.
+//
+// Block roles (320 threads): warps 0-7 stage A (thread = tile row and half
+// of a 32-multipole K-chunk: cp.async gather into a shared ring, split,
+// tcgen05.st into one of 4 tensor-memory A stages) and drain finished
+// rows; lane 0 of warp 8 issues the MMAs (descriptors from a table built
+// once per block) and lane 0 of warp 9 the bulk copies of the operator
+// images, as far ahead as the stages allow.  A work item covers one group
+// of at most W = 128 L columns: when n_L > 128 the columns from 128 on form
+// a second group that needs only the first K-blocks.
+//
+// A tcgen05.mma costs about the same for any N up to ~192, so each K-block
+// takes two instructions: A_hi . [B_hi; 0; B_lo]^T (N = W + N_kb) puts hi.hi
+// in accumulator columns [0, W) and hi.lo in [W, 2 W); A_lo . B_hi^T adds
+// lo.hi to [0, W).  The drain sums the two halves.  Tensor memory: the row
+// accumulators of 2 W columns first (two of them when W <= 96, else one),
+// then 2 to 4 A stages of hi 32 + lo 32 columns at the top.
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 320;
+constexpr int kTcMaxKB = 64;          // n_M <= 512
+constexpr int kTcRawStage = 16384;    // 128 rows x 32 FP32
+
+struct TcArgs {
+    const int32_t *chunk_rb, *chunk_re;   // rows [rb, re) of each chunk
+    const int32_t *row_key;               // D row of each tile row
+    const int32_t *slot;                  // [rows][128] source cell, -1 = none
+    const float *M;                       // scaled FP32 multipoles, row stride ldM
+    const uint8_t *img;                   // per key: K-block tiles of T_key (hi, lo)
+    float *partial;                       // [chunks][128][Np]
+    unsigned *err;
+    long long img_stride;
+    int ldM, nM, n_items, ngroups, nkb, Np, b_stage_bytes;
+    // row accumulators: nacc (1 or 2) buffers acc_stride columns apart; A
+    // stages: nas (2..4) of 64 columns from tensor-memory column a_col0
+    int nacc, acc_stride, nas, a_col0;
+    // column group g covers L columns [128 g, 128 g + g_width[g]) and needs the
+    // K-blocks [0, g_nkb[g]) (those that reach it), g_nkc[g] K-chunks per row
+    int g_width[2], g_nkb[2], g_nkc[2];
+    int kb_n[kTcMaxKB];
+    int img_off[2][kTcMaxKB + 1];         // byte offset of block (g, kb) in a key image
+};
+
+// A work item is (chunk j, column group g), w = j * ngroups + g; items are
+// dealt to the blocks round robin.
+struct TcCursor {
+    int w, j, g, r, re, kc, nkc;          // item, chunk, group, row, row end, K-chunk, K-chunks
+    bool ok;
+};
+
+__device__ __forceinline__ void cur_item(TcCursor &c, const TcArgs &a)
+{
+    c.ok = c.w < a.n_items;
+    if (!c.ok) return;
+    c.j = c.w / a.ngroups;
+    c.g = c.w - c.j * a.ngroups;
+    c.r = a.chunk_rb[c.j];
+    c.re = a.chunk_re[c.j];
+    c.kc = 0;
+    c.nkc = a.g_nkc[c.g];
+}
+
+__device__ __forceinline__ void cur_init(TcCursor &c, const TcArgs &a)
+{
+    c.w = blockIdx.x;
+    cur_item(c, a);
+}
+
+__device__ __forceinline__ void cur_next(TcCursor &c, const TcArgs &a)
+{
+    if (!c.ok) return;
+    if (++c.kc < c.nkc) return;
+    c.kc = 0;
+    if (++c.r < c.re) return;
+    c.w += gridDim.x;
+    cur_item(c, a);
+}
+
+// the row that follows the cursor's row in this block's sequence, -1 if none
+__device__ __forceinline__ int cur_next_row(const TcCursor &c, const TcArgs &a)
+{
+    if (!c.ok) return -1;
+    if (c.r + 1 < c.re) return c.r + 1;
+    const int w = c.w + gridDim.x;
+    return w < a.n_items ? a.chunk_rb[w / a.ngroups] : -1;
+}
+
+// bounded wait that ignores the abort flag (used only while cleaning up)
+__device__ __forceinline__ void mbar_wait_cleanup(uint32_t bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity) && clock64() - t0 < (1ll << 28)) {
+    }
+}
+
+template <int RS>   // shared raw ring stages; RS - 1 units of A in flight
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
+{
+    extern __shared__ uint8_t sm_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *bst = sm;                                   // kTcStages x b_stage_bytes
+    uint8_t *raw = bst + kTcStages * a.b_stage_bytes;    // RS x kTcRawStage
+    uint64_t *bars = (uint64_t *)(raw + RS * kTcRawStage);
+    // a_full[4] | b_full[4] | mma_done[4] | acc_empty[2]
+    uint32_t *tslot = (uint32_t *)(bars + 3 * kTcStages + 2);
+    volatile int *abort = (volatile int *)(tslot + 1);
+    // per (column group, K-block): instruction descriptor, byte offsets of the
+    // block's hi and lo rows in an operator stage
+    // per (column group, K-block): instruction descriptors of the hi-pair MMA
+    // (N = W + N_kb) and of the lo.hi MMA (N = N_kb), the block's byte offset
+    // in an operator stage
+    uint32_t *t_idw = (uint32_t *)(tslot + 4), *t_idn = t_idw + 2 * kTcMaxKB, *t_boff = t_idn + 2 * kTcMaxKB;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bar0 = smem_u32(bars);
+    auto a_full = [&](int i) { return bar0 + 8 * i; };
+    auto b_full = [&](int i) { return bar0 + 8 * (kTcStages + i); };
+    auto mma_done = [&](int i) { return bar0 + 8 * (2 * kTcStages + i); };
+    auto acc_empty = [&](int i) { return bar0 + 8 * (3 * kTcStages + i); };
+    if (tid == 0) {
+        for (int i = 0; i < kTcStages; ++i) {
+            mbar_init(a_full(i), 256);
+            mbar_init(b_full(i), 1);
+            mbar_init(mma_done(i), 1);
+        }
+        mbar_init(acc_empty(0), 256);
+        mbar_init(acc_empty(1), 256);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 8) {
+        tmem_alloc(smem_u32(tslot), 512);
+        tmem_relinquish();
+    }
+    if (warp == 9) {
+        for (int e = tid - 288; e < 2 * kTcMaxKB; e += 32) {
+            const int g = e / kTcMaxKB, kb = e % kTcMaxKB;
+            if (g >= a.ngroups || kb >= a.g_nkb[g]) continue;
+            const int c0 = 128 * g, N = min(a.kb_n[kb], c0 + 128) - c0;
+            t_idw[e] = idesc_tf32_m128(a.g_width[g] + N);
+            t_idn[e] = idesc_tf32_m128(N);
+            t_boff[e] = (uint32_t)(a.img_off[g][kb] - a.img_off[g][kb & ~3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 8) {
+        // ------------------------------------------------ A producers
+        const int i = tid & 127, h = tid >> 7;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        const uint32_t raw0 = smem_u32(raw) + (uint32_t)((4 * h * 128 + i) * 16);
+        TcCursor cu, ci;
+        cur_init(cu, a);
+        ci = cu;
+        int cur_row = -1, cur_src = -1, pf_row = -1, pf_src = -1;
+        int ui = 0, u = 0;
+        auto issue = [&]() {
+            if (ci.ok) {
+                if (ci.r != cur_row) {
+                    cur_src = ci.r == pf_row ? pf_src : __ldg(a.slot + (size_t)ci.r * 128 + i);
+                    cur_row = ci.r;
+                    pf_row = cur_next_row(ci, a);
+                    pf_src = pf_row >= 0 ? __ldg(a.slot + (size_t)pf_row * 128 + i) : -1;
+                }
+                const uint32_t dst = raw0 + (uint32_t)((ui % RS) * kTcRawStage);
+                const int m0 = 32 * ci.kc + 16 * h;
+                const float *row = a.M + (size_t)(cur_src < 0 ? 0 : cur_src) * a.ldM;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int m = m0 + 4 * c;
+                    const int bytes = cur_src < 0 ? 0 : min(16, max(0, 4 * (a.nM - m)));
+                    cp_async16(dst + c * 128 * 16, bytes ? row + m : a.M, bytes);
+                }
+                cur_next(ci, a);
+            }
+            cp_async_commit();
+            ++ui;
+        };
+        // Each key row accumulates in its own tensor-memory buffer (alternating
+        // between two when n_L <= 128); once its MMAs are done it is drained into
+        // FP32 registers (round to nearest), one row behind the staging.  A
+        // chunk's register sum is written to `partial` after its last row.
+        float acc[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) acc[c] = 0.0f;
+        int pend_j = -1, pend_b = 0, pend_end = 0, pend_g = 0;
+        int pend_L = 0, rows_seen = 0;
+        auto drain = [&]() -> bool {
+            const bool ok = mbar_wait(mma_done(pend_L & 3), (unsigned)((pend_L >> 2) & 1), abort);
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            tc_fence_after();
+            const int W = a.g_width[pend_g], half = W >> 1;
+            const uint32_t col = tmem + lane_off + (uint32_t)(pend_b * a.acc_stride + h * half);
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {       // hi.hi (+ lo.hi) and hi.lo halves, 4 loads per wait
+                if (c < half) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int q = 0; q < 16; q += 8)
+                        if (c + q < half) {
+                            tmem_ld8_nw(col + c + q, v + q);
+                            tmem_ld8_nw(col + W + c + q, v + 16 + q);
+                        }
+#pragma unroll
+                    for (int q = 0; q < 16; q += 8)
+                        if (c + q < half) {
+                            tmem_wait_ld8(v + q);
+                            tmem_wait_ld8(v + 16 + q);
+                        }
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (c + k < half) acc[c + k] += __uint_as_float(v[k]) + __uint_as_float(v[16 + k]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty(pend_b));
+            if (pend_end) {
+                float *out = a.partial + ((size_t)pend_j * 128 + i) * a.Np + 128 * pend_g + h * half;
+#pragma unroll
+                for (int c = 0; c < 64; c += 4) {
+                    if (c < half) {
+                        *(float4 *)(out + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                        acc[c] = acc[c + 1] = acc[c + 2] = acc[c + 3] = 0.0f;
+                    }
+                }
+            }
+            pend_j = -1;
+            return true;
+        };
+        int sa = 0;                                  // A stage of unit u
+        for (int k = 0; k < RS - 1; ++k) issue();
+        while (cu.ok) {
+            issue();
+            cp_async_wait<RS - 1>();
+            float hi[16], lo[16];
+            {
+                const uint32_t src = raw0 + (uint32_t)((u % RS) * kTcRawStage);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float4 v;
+                    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                                 : "r"(src + c * 128 * 16));
+                    split_tf32(v.x, hi[4 * c], lo[4 * c]);
+                    split_tf32(v.y, hi[4 * c + 1], lo[4 * c + 1]);
+                    split_tf32(v.z, hi[4 * c + 2], lo[4 * c + 2]);
+                    split_tf32(v.w, hi[4 * c + 3], lo[4 * c + 3]);
+                }
+            }
+            // A stage sa (of nas) is free once the MMAs of unit u - nas are done
+            bool ok = u < a.nas ||
+                      mbar_wait_backoff(mma_done((u - a.nas) & 3), (unsigned)(((u - a.nas) >> 2) & 1), abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const uint32_t acol = tmem + lane_off + (uint32_t)(a.a_col0 + 64 * sa + 16 * h);
+            tmem_st16(acol, hi);
+            tmem_st16(acol + 32, lo);
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(a_full(sa));
+            if (++sa == a.nas) sa = 0;
+            if (pend_j >= 0 && !drain()) break;
+            if (cu.kc == cu.nkc - 1) {
+                pend_j = cu.j;
+                pend_g = cu.g;
+                pend_L = u;
+                pend_b = rows_seen & (a.nacc - 1);
+                pend_end = cu.r + 1 == cu.re;
+                ++rows_seen;
+            }
+            cur_next(cu, a);
+            ++u;
+        }
+        if (pend_j >= 0 && !*abort) drain();
+        cp_async_wait<0>();
+    } else if (tid == 256) {
+        // ------------------------------------------------ MMA issuer
+        TcCursor cm;
+        cur_init(cm, a);
+        int u = 0, row_seq = 0, sa = 0, pa = 0;       // unit, key rows begun, A stage and its phase
+        const uint32_t bst0 = smem_u32(bst);
+        const uint64_t dconst = sdesc_sw32(0);     // descriptor bits other than the address
+        const int lg = a.nacc == 2 ? 1 : 0;
+        while (cm.ok) {
+            const int st = u & 3;
+            const bool first = cm.kc == 0;            // first unit of a key row
+            const int b = row_seq & (a.nacc - 1);
+            if (first && row_seq >= a.nacc &&
+                !mbar_wait(acc_empty(b), (unsigned)(((row_seq >> lg) - 1) & 1), abort))
+                break;
+            if (!mbar_wait(a_full(sa), (unsigned)pa, abort)) break;
+            if (!mbar_wait(b_full(st), (unsigned)((u >> 2) & 1), abort)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(b * a.acc_stride);
+            const uint32_t abase = tmem + (uint32_t)(a.a_col0 + 64 * sa);
+            const uint32_t sbase = bst0 + st * a.b_stage_bytes;
+            const int kb0 = 4 * cm.kc, kb1 = min(kb0 + 4, a.g_nkb[cm.g]), e0 = cm.g * kTcMaxKB;
+            for (int kb = kb0; kb < kb1; ++kb) {
+                const uint64_t bd = dconst + ((sbase + t_boff[e0 + kb]) >> 4);
+                const uint32_t ah = abase + 8 * (kb - kb0), al = ah + 32;
+                mma_tf32_ts(d, ah, bd, t_idw[e0 + kb], (first && kb == kb0) ? 0u : 1u);
+                mma_tf32_ts(d, al, bd, t_idn[e0 + kb], 1u);
+            }
+            mma_commit(mma_done(st));
+            if (cm.kc == cm.nkc - 1) ++row_seq;
+            if (++sa == a.nas) {
+                sa = 0;
+                pa ^= 1;
+            }
+            cur_next(cm, a);
+            ++u;
+        }
+    } else if (tid == 288) {
+        // ------------------------------------------------ operator image loader
+        TcCursor cb;
+        cur_init(cb, a);
+        int vb = 0;
+        int key_row = -1, key = 0, kpf_row = -1, kpf = 0;
+        const uint32_t bst0 = smem_u32(bst);
+        while (cb.ok) {
+            const int st = vb & 3;
+            if (vb >= kTcStages && !mbar_wait(mma_done(st), (unsigned)(((vb >> 2) - 1) & 1), abort))
+                break;
+            if (cb.r != key_row) {
+                key = cb.r == kpf_row ? kpf : __ldg(a.row_key + cb.r);
+                key_row = cb.r;
+                kpf_row = cur_next_row(cb, a);
+                kpf = kpf_row >= 0 ? __ldg(a.row_key + kpf_row) : 0;
+            }
+            const int kb0 = 4 * cb.kc, kb1 = min(kb0 + 4, a.g_nkb[cb.g]);
+            const unsigned bytes = (unsigned)(a.img_off[cb.g][kb1] - a.img_off[cb.g][kb0]);
+            mbar_expect_tx(b_full(st), bytes);
+            bulk_g2s(bst0 + st * a.b_stage_bytes, a.img + (size_t)key * a.img_stride + a.img_off[cb.g][kb0], bytes,
+                     b_full(st));
+            cur_next(cb, a);
+            ++vb;
+        }
+        if (*abort) {   // let the copies still in flight land before the block exits
+            for (int v = vb > kTcStages ? vb - kTcStages : 0; v < vb; ++v)
+                mbar_wait_cleanup(b_full(v & 3), (unsigned)((v >> 2) & 1));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (tid == 0 && *abort) atomicOr(a.err, (unsigned)kErrTcTimeout);
+}
+
+// L~_t[n] = sum of the tile's chunk partials of target t, in FP64, in chunk order
+// (NaN everywhere if a wait of the M2L block gave up: the failure shows in the output)
+__global__ void k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile_chunk_off,
+                            const float *partial, int Np, int nL, const unsigned *err, float *L)
+{
+    const int q = blockIdx.x;
+    if (q >= T) return;
+    const bool bad = (*err & kErrTcTimeout) != 0;
+    const int tile = q >> 7, lane = q & 127, c = tile_tgt[q];
+    const int j0 = (int)tile_chunk_off[tile], j1 = (int)tile_chunk_off[tile + 1];
+    for (int n = threadIdx.x; n < nL; n += blockDim.x) {
+        double v = 0.0;
+        for (int j = j0; j < j1; ++j) v += (double)partial[((size_t)j * 128 + lane) * Np + n];
+        L[(size_t)c * nL + n] = bad ? __int_as_float(0x7fc00000) : (float)v;
+    }
+}
+
+// ------------------------------------------------------------ the plan
+// class of a target cell: (level, position in its parent); cells without
+// an M2L list sort last
+__global__ void k_tc_class(int64_t nc, const int32_t *m2l_off, const int32_t *level, const int32_t *cx,
+                           const int32_t *cy, const int32_t *cz, uint64_t *keys, uint32_t *vals,
+                           unsigned *count)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool has = false;
+    if (c < nc) {
+        has = m2l_off[c + 1] > m2l_off[c];
+        keys[c] = has ? ((uint64_t)level[c] << 3 | (uint64_t)((cx[c] & 1) | (cy[c] & 1) << 1 | (cz[c] & 1) << 2))
+                      : 0xFFFFull;
+        vals[c] = (uint32_t)c;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, has);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned)__popc(b));
+}
+
+__global__ void k_tc_tiles(int T, int slots, const uint32_t *vals, int32_t *tile_tgt)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < slots) tile_tgt[q] = q < T ? (int32_t)vals[q] : -1;
+}
+
+// one warp per target: mark the keys of its list in its tile's bitmap
+__global__ void k_tc_bits(int T, const int32_t *tile_tgt, const int32_t *m2l_off, const int32_t *didx, int W,
+                          uint32_t *bits)
+{
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= T) return;
+    const int c = tile_tgt[w];
+    uint32_t *tb = bits + (size_t)(w >> 7) * W;
+    for (int e = m2l_off[c] + lane; e < m2l_off[c + 1]; e += 32) {
+        const int d = didx[e];
+        atomicOr(tb + (d >> 5), 1u << (d & 31));
+    }
+}
+
+// block-wide exclusive scan of one value per thread (256 threads); returns the block total
+__device__ __forceinline__ uint32_t block_scan256(uint32_t v, uint32_t &excl)
+{
+    __shared__ uint32_t wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < w) before += wsum[k];
+        total += wsum[k];
+    }
+    excl = before + x - v;
+    __syncthreads();
+    return total;
+}
+
+// per tile: rows = keys present; prefix of the per-word counts
+__global__ void __launch_bounds__(256) k_tc_rowcount(int W, int G, const uint32_t *bits, uint32_t *wpre,
+                                                      uint32_t *tile_rows, uint32_t *tile_chunks)
+{
+    const int tile = blockIdx.x;
+    uint32_t carry = 0;
+    for (int base = 0; base < W; base += 256) {
+        const int w = base + threadIdx.x;
+        const uint32_t cnt = w < W ? (uint32_t)__popc(bits[(size_t)tile * W + w]) : 0u;
+        uint32_t ex;
+        const uint32_t tot = block_scan256(cnt, ex);
+        if (w < W) wpre[(size_t)tile * W + w] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        tile_rows[tile] = carry;
+        tile_chunks[tile] = (carry + G - 1) / G;
+    }
+}
+
+__global__ void k_tc_rows(int W, int G, const uint32_t *bits, const uint32_t *wpre, const uint32_t *row_off,
+                          const uint32_t *chunk_off, int32_t *row_key, int32_t *chunk_rb, int32_t *chunk_re)
+{
+    const int tile = blockIdx.x;
+    const uint32_t rb = row_off[tile], re = row_off[tile + 1];
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        uint32_t word = bits[(size_t)tile * W + w];
+        uint32_t r = rb + wpre[(size_t)tile * W + w];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            row_key[r++] = 32 * w + b;
+            word &= word - 1;
+        }
+    }
+    const int nch = (int)(chunk_off[tile + 1] - chunk_off[tile]);
+    for (int k = threadIdx.x; k < nch; k += blockDim.x) {
+        const int j = (int)chunk_off[tile] + k;
+        chunk_rb[j] = (int32_t)(rb + (uint32_t)k * G);
+        chunk_re[j] = (int32_t)min(re, rb + (uint32_t)(k + 1) * G);
+    }
+}
+
+// one warp per target: place each source in its key's row, at the target's lane
+__global__ void k_tc_slots(int T, const int32_t *tile_tgt, const int32_t *m2l_off, const int32_t *m2l_src,
+                           const int32_t *didx, int W, const uint32_t *bits, const uint32_t *wpre,
+                           const uint32_t *row_off, int32_t *slot)
+{
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= T) return;
+    const int c = tile_tgt[w], tile = w >> 7;
+    const uint32_t *tb = bits + (size_t)tile * W, *tp = wpre + (size_t)tile * W;
+    for (int e = m2l_off[c] + lane; e < m2l_off[c + 1]; e += 32) {
+        const int d = didx[e], wd = d >> 5;
+        const uint32_t r = row_off[tile] + tp[wd] + (uint32_t)__popc(tb[wd] & ((1u << (d & 31)) - 1u));
+        slot[(size_t)r * 128 + (w & 127)] = m2l_src[e];
+    }
+}
+
+// operator images: float e of a key's image is the hi or lo TF32 half of D
+// row entry el_src[e] (or zero), at its swizzled position
+__global__ void k_tc_images(int64_t ndoff, int E, const uint64_t *dkeys, const double *D, int nD,
+                            const int32_t *el_src, const int32_t *el_pos, long long stride, uint8_t *img)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ndoff * E) return;
+    const int64_t r = g / E;
+    const int e = (int)(g % E);
+    const int src = el_src[e], pos = el_pos[e];
+    float hi = 0.0f, lo = 0.0f;
+    if (src >= 0) {
+        const uint64_t key = dkeys[r];
+        const int gap = (int)((key >> 52) & 31), tfiner = (int)((key >> 51) & 1);
+        const int esc = tfiner ? 0 : gap, dl = tfiner ? gap : -gap;
+        const int k = src & 0xFFFF, nm = (src >> 16) & 0xFF, msh = src >> 24;
+        const double v = ldexp(D[r * nD + k], (nm + 1) * esc + dl * msh);
+        hi = tf32_rna((float)v);
+        lo = tf32_rna((float)(v - (double)hi));
+    }
+    *(float *)(img + r * stride + (pos & 0x3FFFFFFF)) = (pos >> 30) & 1 ? lo : hi;
+}
+
 }  // namespace
+
+
+// ------------------------------------------------------------------ host
+namespace {
+
+inline unsigned gridn(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+inline int up16(int n) { return std::max(16, (n + 15) & ~15); }
+
+constexpr int kSmemMax = 232448;         // dynamic shared memory a block may opt into
+constexpr int kSmemOneBlock = 120 * 1024;  // at least this much: two blocks never share an SM (and its TMEM)
+
+int tc_smem(int b_stage, int rs)
+{
+    return 1024 + kTcStages * b_stage + rs * kTcRawStage + 8 * (3 * kTcStages + 2) + 16 + 3 * 2 * kTcMaxKB * 4;
+}
+
+int tc_raw_stages(int b_stage)
+{
+    for (int rs : {8, 6, 4, 3})
+        if (tc_smem(b_stage, rs) <= kSmemMax) return rs;
+    return 0;
+}
+
+void build_layout(TcLayout &Ly, int s, int p)
+{
+    const MultiIndex &I = multi_index();
+    auto shell = [&](int k) { return I.nx[k] + I.ny[k] + I.nz[k]; };
+    const int m0 = ntot(s - 1), nM = ntot(p + s) - m0, nL = ntot(p);
+    Ly.s = s;
+    Ly.p = p;
+    Ly.nkb = (nM + 7) / 8;
+    Ly.kb_n.assign(Ly.nkb, 0);
+    for (int kb = 0; kb < Ly.nkb; ++kb)   // graded order: a block's first multipole has its lowest order
+        Ly.kb_n[kb] = up16(ntot(p + s - shell(m0 + 8 * kb)));
+    Ly.Np = Ly.kb_n[0];
+    Ly.ngroups = Ly.Np > 128 ? 2 : 1;
+    Ly.img_off.assign(2 * (Ly.nkb + 1), 0);
+    int off = 0;
+    Ly.b_stage = 0;
+    for (int g = 0; g < Ly.ngroups; ++g) {
+        const int c0 = 128 * g, W = std::min(128, Ly.Np - c0);
+        int nb = 0;
+        while (nb < Ly.nkb && Ly.kb_n[nb] > c0) ++nb;      // reach falls with kb
+        Ly.g_width[g] = W;
+        Ly.g_nkb[g] = nb;
+        Ly.g_nkc[g] = (nb + 3) / 4;
+        int *go = &Ly.img_off[g * (Ly.nkb + 1)];
+        for (int kb = 0; kb < nb; ++kb) {
+            go[kb] = off;
+            off += 32 * (W + std::min(Ly.kb_n[kb], c0 + 128) - c0);
+        }
+        for (int kb = nb; kb <= Ly.nkb; ++kb) go[kb] = off;
+        for (int kc = 0; kc < Ly.g_nkc[g]; ++kc)
+            Ly.b_stage = std::max(Ly.b_stage, go[std::min(4 * kc + 4, nb)] - go[4 * kc]);
+    }
+    Ly.img_bytes = off;
+    Ly.b_stage = (Ly.b_stage + 1023) & ~1023;
+    Ly.E = off / 4;
+    Ly.el_src.assign(Ly.E, -1);
+    Ly.el_pos.assign(Ly.E, 0);
+    for (int g = 0; g < Ly.ngroups; ++g) {
+        const int c0 = 128 * g, W = Ly.g_width[g];
+        for (int kb = 0; kb < Ly.g_nkb[g]; ++kb) {
+            const int N = std::min(Ly.kb_n[kb], c0 + 128) - c0, base = Ly.img_off[g * (Ly.nkb + 1) + kb];
+            for (int row = 0; row < W + N; ++row)
+                for (int k = 0; k < 8; ++k) {
+                    const int pos = base + (int)swz32(row, k >> 2) + (k & 3) * 4, e = pos / 4;
+                    const bool lo = row >= W;
+                    Ly.el_pos[e] = pos | (lo ? 1 << 30 : 0);
+                    if (row >= N && !lo) continue;               // zero rows between the halves
+                    const int n = c0 + (lo ? row - W : row), m = 8 * kb + k;
+                    if (m >= nM || n >= nL) continue;
+                    const int gm = m0 + m, tot = shell(n) + shell(gm);
+                    if (tot > p + s) continue;
+                    const int d = I(I.nx[n] + I.nx[gm], I.ny[n] + I.ny[gm], I.nz[n] + I.nz[gm]);
+                    Ly.el_src[e] = d | tot << 16 | (shell(gm) - s) << 24;
+                }
+        }
+    }
+}
+
+fmm_status d2h_u32(fmm_tree *t, const void *dev, uint32_t *host, int count)
+{
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(host, dev, 4 * (size_t)count, cudaMemcpyDeviceToHost, t->stream),
+                       "copy"));
+    return cuda_check(t, cudaStreamSynchronize(t->stream), "sync");
+}
+
+fmm_status build_plan(fmm_tree *t)
+{
+    cudaStream_t st = t->stream;
+    const int64_t nc = t->ncells;
+    if (t->tc_G <= 0) {
+        const char *g = getenv("FMM_TC_CHUNK");
+        t->tc_G = g ? std::max(1, atoi(g)) : 16;
+    }
+    const int G = t->tc_G;
+    FMM_TRY(ensure(t, t->b_tc_keys, 8 * (size_t)nc));
+    FMM_TRY(ensure(t, t->b_tc_keys2, 8 * (size_t)nc));
+    FMM_TRY(ensure(t, t->b_tc_vals, 4 * (size_t)nc));
+    FMM_TRY(ensure(t, t->b_tc_vals2, 4 * (size_t)nc));
+    const size_t hb = radix_hist_bytes(nc);
+    FMM_TRY(ensure(t, t->b_tc_hist, hb));
+    FMM_TRY(ensure(t, t->b_tc_scan, scan_scratch_bytes(std::max<int64_t>((int64_t)hb / 4 + 1, nc + 1))));
+    FMM_TRY(ensure(t, t->b_tc_cnt, 16));
+    cudaMemsetAsync(t->b_tc_cnt.ptr, 0, 16, st);
+    k_tc_class<<<gridn(nc, 256), 256, 0, st>>>(nc, (const int32_t *)t->b_m2l_off.ptr,
+                                                (const int32_t *)t->b_level.ptr, (const int32_t *)t->b_cx.ptr,
+                                                (const int32_t *)t->b_cy.ptr, (const int32_t *)t->b_cz.ptr,
+                                                (uint64_t *)t->b_tc_keys.ptr, (uint32_t *)t->b_tc_vals.ptr,
+                                                (unsigned *)t->b_tc_cnt.ptr);
+    ++t->launches;
+    radix_sort_pairs((uint64_t *)t->b_tc_keys.ptr, (uint32_t *)t->b_tc_vals.ptr, (uint64_t *)t->b_tc_keys2.ptr,
+                     (uint32_t *)t->b_tc_vals2.ptr, nc, 16, (uint32_t *)t->b_tc_hist.ptr,
+                     (uint32_t *)t->b_tc_scan.ptr, st, &t->launches);
+    uint32_t T = 0;
+    FMM_TRY(d2h_u32(t, t->b_tc_cnt.ptr, &T, 1));
+    t->tc_T = T;
+    t->tc_tiles = (T + 127) / 128;
+    t->tc_rows = t->tc_chunks = 0;
+    if (T == 0) {
+        t->tc_plan = true;
+        return FMM_OK;
+    }
+    const int64_t tiles = t->tc_tiles, W = (t->n_doff + 31) / 32;
+    t->tc_W = W;
+    FMM_TRY(ensure(t, t->b_tc_tgt, 4 * (size_t)tiles * 128));
+    k_tc_tiles<<<gridn(tiles * 128, 256), 256, 0, st>>>((int)T, (int)(tiles * 128),
+                                                         (const uint32_t *)t->b_tc_vals.ptr,
+                                                         (int32_t *)t->b_tc_tgt.ptr);
+    FMM_TRY(ensure(t, t->b_tc_bits, 4 * (size_t)tiles * W));
+    FMM_TRY(ensure(t, t->b_tc_wpre, 4 * (size_t)tiles * W));
+    cudaMemsetAsync(t->b_tc_bits.ptr, 0, 4 * (size_t)tiles * W, st);
+    k_tc_bits<<<gridn((int64_t)T * 32, 256), 256, 0, st>>>((int)T, (const int32_t *)t->b_tc_tgt.ptr,
+                                                            (const int32_t *)t->b_m2l_off.ptr,
+                                                            (const int32_t *)t->b_m2l_didx.ptr, (int)W,
+                                                            (uint32_t *)t->b_tc_bits.ptr);
+    for (DevBuf *b : {&t->b_tc_rcnt, &t->b_tc_ccnt, &t->b_tc_roff, &t->b_tc_coff}) {
+        FMM_TRY(ensure(t, *b, 4 * (size_t)(tiles + 1)));
+        cudaMemsetAsync(b->ptr, 0, 4 * (size_t)(tiles + 1), st);
+    }
+    k_tc_rowcount<<<(unsigned)tiles, 256, 0, st>>>((int)W, G, (const uint32_t *)t->b_tc_bits.ptr,
+                                                   (uint32_t *)t->b_tc_wpre.ptr, (uint32_t *)t->b_tc_rcnt.ptr,
+                                                   (uint32_t *)t->b_tc_ccnt.ptr);
+    exclusive_scan_u32((const uint32_t *)t->b_tc_rcnt.ptr, (uint32_t *)t->b_tc_roff.ptr, tiles + 1,
+                       (uint32_t *)t->b_tc_scan.ptr, st, &t->launches);
+    exclusive_scan_u32((const uint32_t *)t->b_tc_ccnt.ptr, (uint32_t *)t->b_tc_coff.ptr, tiles + 1,
+                       (uint32_t *)t->b_tc_scan.ptr, st, &t->launches);
+    t->launches += 4;
+    uint32_t R = 0, C = 0;
+    FMM_TRY(d2h_u32(t, (const uint32_t *)t->b_tc_roff.ptr + tiles, &R, 1));
+    FMM_TRY(d2h_u32(t, (const uint32_t *)t->b_tc_coff.ptr + tiles, &C, 1));
+    t->tc_rows = R;
+    t->tc_chunks = C;
+    FMM_TRY(ensure(t, t->b_tc_rowkey, 4 * (size_t)R));
+    FMM_TRY(ensure(t, t->b_tc_crb, 4 * (size_t)C));
+    FMM_TRY(ensure(t, t->b_tc_cre, 4 * (size_t)C));
+    k_tc_rows<<<(unsigned)tiles, 256, 0, st>>>((int)W, G, (const uint32_t *)t->b_tc_bits.ptr,
+                                               (const uint32_t *)t->b_tc_wpre.ptr,
+                                               (const uint32_t *)t->b_tc_roff.ptr,
+                                               (const uint32_t *)t->b_tc_coff.ptr, (int32_t *)t->b_tc_rowkey.ptr,
+                                               (int32_t *)t->b_tc_crb.ptr, (int32_t *)t->b_tc_cre.ptr);
+    FMM_TRY(ensure(t, t->b_tc_slot, 4 * (size_t)R * 128));
+    cudaMemsetAsync(t->b_tc_slot.ptr, 0xff, 4 * (size_t)R * 128, st);
+    k_tc_slots<<<gridn((int64_t)T * 32, 256), 256, 0, st>>>(
+        (int)T, (const int32_t *)t->b_tc_tgt.ptr, (const int32_t *)t->b_m2l_off.ptr,
+        (const int32_t *)t->b_m2l_src.ptr, (const int32_t *)t->b_m2l_didx.ptr, (int)W,
+        (const uint32_t *)t->b_tc_bits.ptr, (const uint32_t *)t->b_tc_wpre.ptr, (const uint32_t *)t->b_tc_roff.ptr,
+        (int32_t *)t->b_tc_slot.ptr);
+    t->launches += 2;
+    t->tc_plan = true;
+    return cuda_check(t, cudaGetLastError(), "tensor-core M2L plan");
+}
+
+}  // namespace
+
+bool tc_usable(fmm_tree *t, int s, int p)
+{
+    if (t->tc_lay.s != s || t->tc_lay.p != p) build_layout(t->tc_lay, s, p);
+    const TcLayout &L = t->tc_lay;
+    return L.Np <= 256 && L.nkb <= kTcMaxKB && tc_raw_stages(L.b_stage) >= 3;
+}
+
+fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L)
+{
+    cudaStream_t st = t->stream;
+    const TcLayout &Ly = t->tc_lay;
+    if (!t->tc_plan) FMM_TRY(build_plan(t));
+    if (t->tc_chunks == 0) return FMM_OK;
+    const long long stride = Ly.img_bytes;
+    if (t->tc_img_p != p) {
+        FMM_TRY(ensure(t, t->b_tc_el, 8 * (size_t)Ly.E));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tc_el.ptr, Ly.el_src.data(), 4 * (size_t)Ly.E,
+                                              cudaMemcpyHostToDevice, st), "upload"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync((int32_t *)t->b_tc_el.ptr + Ly.E, Ly.el_pos.data(),
+                                              4 * (size_t)Ly.E, cudaMemcpyHostToDevice, st), "upload"));
+        FMM_TRY(ensure(t, t->b_tc_img, (size_t)t->n_doff * stride));
+        k_tc_images<<<gridn(t->n_doff * Ly.E, 256), 256, 0, st>>>(
+            t->n_doff, Ly.E, (const uint64_t *)t->b_dkeys.ptr, (const double *)t->b_D.ptr, ntot(p + t->s),
+            (const int32_t *)t->b_tc_el.ptr, (const int32_t *)t->b_tc_el.ptr + Ly.E, stride,
+            (uint8_t *)t->b_tc_img.ptr);
+        ++t->launches;
+        t->tc_img_p = p;
+    }
+    FMM_TRY(ensure(t, t->b_tc_part, 4 * (size_t)t->tc_chunks * 128 * Ly.Np));
+    if (t->tc_sms == 0) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device);
+        t->tc_sms = std::max(1, sms);
+    }
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.chunk_rb = (const int32_t *)t->b_tc_crb.ptr;
+    a.chunk_re = (const int32_t *)t->b_tc_cre.ptr;
+    a.row_key = (const int32_t *)t->b_tc_rowkey.ptr;
+    a.slot = (const int32_t *)t->b_tc_slot.ptr;
+    a.M = M;
+    a.img = (const uint8_t *)t->b_tc_img.ptr;
+    a.partial = (float *)t->b_tc_part.ptr;
+    unsigned *err = (unsigned *)t->b_err.ptr + 1;
+    a.err = err;
+    a.img_stride = stride;
+    a.ldM = ldM;
+    a.nM = nM;
+    a.ngroups = Ly.ngroups;
+    a.n_items = (int)t->tc_chunks * a.ngroups;
+    a.nkb = Ly.nkb;
+    a.Np = Ly.Np;
+    // two row accumulators of 2 W columns when they leave room for at least
+    // two A stages of 64 columns, else one; the rest of the 512 columns hold A
+    a.nacc = 4 * Ly.g_width[0] + 128 <= 512 ? 2 : 1;
+    a.acc_stride = 2 * Ly.g_width[0];
+    a.nas = std::min(kTcStages, (512 - a.nacc * a.acc_stride) / 64);
+    a.a_col0 = 512 - 64 * a.nas;
+    for (int g = 0; g < 2; ++g) {
+        a.g_width[g] = Ly.g_width[g];
+        a.g_nkb[g] = Ly.g_nkb[g];
+        a.g_nkc[g] = Ly.g_nkc[g];
+        for (int kb = 0; kb <= Ly.nkb; ++kb) a.img_off[g][kb] = Ly.img_off[g * (Ly.nkb + 1) + kb];
+    }
+    a.b_stage_bytes = Ly.b_stage;
+    for (int kb = 0; kb < Ly.nkb; ++kb) a.kb_n[kb] = Ly.kb_n[kb];
+    const int rs = tc_raw_stages(Ly.b_stage);
+    const int smem = std::max(tc_smem(Ly.b_stage, rs), kSmemOneBlock);
+    const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, t->tc_sms);
+    cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        kern<<<grid, kTcThreads, smem, st>>>(a);
+    };
+    switch (rs) {
+    case 8: go(k_m2l_tc<8>); break;
+    case 6: go(k_m2l_tc<6>); break;
+    case 4: go(k_m2l_tc<4>); break;
+    default: go(k_m2l_tc<3>); break;
+    }
+    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, st>>>((int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr,
+                                                   (const uint32_t *)t->b_tc_coff.ptr, (const float *)t->b_tc_part.ptr,
+                                                   Ly.Np, nL, err, L);
+    t->launches += 2;
+    return cuda_check(t, cudaGetLastError(), "tensor-core M2L");
+}
 
 fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D, int nkb, int N,
                       const int *kbn, int a_tmem, int passes, unsigned *err)

@@ -615,7 +615,9 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         return FMM_EORDER;
     }
     FMM_TRY(build_dtables(t, p, tb, lut));
-    if (t->d32_p != p && t->n_doff > 0) {
+    // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
+    const bool use_tc = t->prec == FMM_3XTF32 && tc_usable(t, s, p);
+    if (!use_tc && t->d32_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
             (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr, tb.mi,
@@ -662,7 +664,9 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     }
     record(t, 8);
     cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nL, st);
-    if (t->n_m2l > 0) {
+    if (t->n_m2l > 0 && use_tc) {
+        FMM_TRY(run_m2l_tc(t, p, M, row4(tb.nM), tb.nM, tb.nL, L));
+    } else if (t->n_m2l > 0) {
         const int ldM = tb.nM | 1, ldD = tb.nD | 1;
         size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +
                       4 * ((size_t)kBatch * (ldM + ldD) + (size_t)tb.m2l_T * kM2LThreads);

@@ -90,6 +90,23 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity)
                  : "memory");
     return ok != 0;
 }
+// As mbar_wait below, backing off with short sleeps after a few polls (for
+// threads whose waits are not on the critical issue path)
+__device__ __forceinline__ bool mbar_wait_backoff(uint32_t bar, unsigned parity, volatile int *abort)
+{
+    for (int k = 0; k < 4; ++k)
+        if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > (1ll << 31)) {
+            *abort = 1;
+            return false;
+        }
+        __nanosleep(20);
+    }
+    return true;
+}
 // Waits for the phase of the given parity to complete.  Gives up (and sets
 // *abort) after ~2^31 SM cycles, about one second, or as soon as another
 // thread of the block has set *abort; returns whether the phase completed.
@@ -119,6 +136,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
+}
+
+// 16-byte global -> shared copy of the first `bytes` (0..16) bytes, the rest zero-filled
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ------------------------------------------------------- tensor memory
@@ -184,6 +217,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
     v[3] = __uint_as_float(r3); v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5);
     v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
+// 8 consecutive 32-bit columns of this thread's lane, left in flight: the
+// registers may be read only after tmem_wait_ld8 on them
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+// waits for this thread's tensor-memory loads; ties the registers to the wait
+__device__ __forceinline__ void tmem_wait_ld8(uint32_t *r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+}
+
 // 8 consecutive 32-bit columns of this thread's lane, written
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v)
 {
@@ -191,6 +242,19 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v)
                  "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                  "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
                  "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's lane, written
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                 "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                 "r"(__float_as_uint(v[15]))
                  : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st()

@@ -39,7 +39,8 @@ class TreeInfo(C.Structure):
                 ("nlevels", C.c_int32), ("source_order", C.c_int32), ("n_m2l", C.c_int64),
                 ("n_p2p", C.c_int64), ("n_p2p_interactions", C.c_int64),
                 ("n_doffsets", C.c_int64), ("theta", C.c_double), ("lo", C.c_double * 3),
-                ("side", C.c_double), ("device_bytes", C.c_int64), ("nsystems", C.c_int64)]
+                ("side", C.c_double), ("device_bytes", C.c_int64), ("nsystems", C.c_int64),
+                ("tc_tiles", C.c_int64), ("tc_rows", C.c_int64), ("tc_chunks", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -121,6 +122,7 @@ class FMMTree:
     def __init__(self, device=0, stream=None, max_leaf=64, precision="fp64", mem_budget_bytes=0):
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         self.stream = stream
+        self.precision = precision
         h = C.c_void_p()
         st = lib().fmm_create_tree(C.byref(h), self.device.index or 0, _stream_ptr(stream),
                                    int(max_leaf), PRECISIONS[precision], int(mem_budget_bytes))
@@ -174,6 +176,8 @@ class FMMTree:
     def copy_array(self, name: str, width: int = None) -> torch.Tensor:
         """Host copy of an internal array (keys, perm, cells, lists, M, L)."""
         ident, dtype, cols = ARRAYS[name]
+        if name in ("multipole", "local") and self.precision != "fp64":
+            dtype = torch.float32          # scaled FP32 expansions
         need = C.c_size_t()
         inf = self.info()
         rows = {"keys": inf["n"], "perm": inf["n"], "m2l": inf["n_m2l"], "p2p": inf["n_p2p"]}.get(

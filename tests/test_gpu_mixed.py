@@ -1,4 +1,7 @@
-"""Mixed-precision form (FMM_FP32): scaled FP32 expansions and pair terms, FP64 D tables and outputs.
+"""Mixed-precision forms: FMM_FP32 (scaled FP32 expansions and pair terms, FP64 D
+tables and outputs) and FMM_3XTF32 (the same with the M2L on the tcgen05 tensor
+cores in 3xTF32: FP32 operands split into two TF32 halves, FP32 accumulation in
+tensor memory over chunks of keys, FP64 across chunks).
 
 Tolerances: the FP32 form is compared with the FP64 oracle FMM on the same tree
 (difference = FP32 rounding only: ~2e-7 measured, bounded here by 1e-6 relative
@@ -30,6 +33,18 @@ def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=Tr
             E.cpu().numpy() if E is not None else None), tree
 
 
+FORMS = ["fp32", "3xtf32"]
+
+
+def assert_tc_ran(tree, precision):
+    """The 3xTF32 form must have taken the tensor-core M2L (no silent SIMT path)."""
+    info = tree.info()
+    if precision == "3xtf32" and info["n_m2l"] > 0:
+        assert info["tc_rows"] > 0 and info["tc_chunks"] > 0, info
+        assert info["tc_rows"] * 128 >= info["n_m2l"]
+
+
+@pytest.mark.parametrize("precision", FORMS)
 @pytest.mark.parametrize("s,p,dist,n,ncrit", [
     (0, 4, "uniform", 2000, 64),
     (0, 6, "plummer", 20_000, 32),
@@ -38,10 +53,11 @@ def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=Tr
     (2, 5, "uniform", 15_000, 128),
     (2, 3, "plummer", 10_000, 16),
 ])
-def test_fp32_close_to_fp64_oracle(orc, s, p, dist, n, ncrit):
+def test_fp32_close_to_fp64_oracle(orc, precision, s, p, dist, n, ncrit):
     from gpu_util import rel_rms
     pos, S = synth.make_system(n, s, dist, 700 + 10 * s + p)
-    (phi, E), _ = gpu_eval(pos, S, s, p, 0.5, ncrit, "fp32")
+    (phi, E), tree = gpu_eval(pos, S, s, p, 0.5, ncrit, precision)
+    assert_tc_ran(tree, precision)
     t = orc.Tree(pos, ncrit)
     t.lists(0.5)
     phi_o, E_o = t.fmm(S, s, p)
@@ -49,12 +65,14 @@ def test_fp32_close_to_fp64_oracle(orc, s, p, dist, n, ncrit):
     assert rel_rms(E, E_o) < 1e-6, rel_rms(E, E_o)
 
 
+@pytest.mark.parametrize("precision", FORMS)
 @pytest.mark.parametrize("s,p,floor", [(0, 4, 0.0), (0, 8, 0.0), (1, 6, 0.0), (1, 8, 0.0),
                                         (2, 3, FP32_FLOOR), (2, 5, FP32_FLOOR)])
-def test_fp32_error_within_1p1_of_fp64_truncation(orc, s, p, floor):
+def test_fp32_error_within_1p1_of_fp64_truncation(orc, precision, s, p, floor):
     from gpu_util import rel_rms
     pos, S = synth.make_system(12_000, s, "plummer", 800 + s)
-    (phi32, E32), _ = gpu_eval(pos, S, s, p, 0.5, 64, "fp32")
+    (phi32, E32), tree = gpu_eval(pos, S, s, p, 0.5, 64, precision)
+    assert_tc_ran(tree, precision)
     (phi64, E64), _ = gpu_eval(pos, S, s, p, 0.5, 64, "fp64")
     phi_d, E_d = orc.direct(pos, S, s)
     e32, e64 = rel_rms(E32, E_d), rel_rms(E64, E_d)
@@ -63,24 +81,29 @@ def test_fp32_error_within_1p1_of_fp64_truncation(orc, s, p, floor):
 
 
 def test_plummer_4m_p8_fp32_vs_fp64(orc):
-    """4M Plummer dipoles, p=8, n_crit 128: the FP32 form's field error against
-    the FP64 direct sum (4,096 sampled particles) is within 1.1x that of the
-    FP64 GPU form, and the FP64 form matches the oracle FMM on the same tree."""
+    """4M Plummer dipoles, p=8, n_crit 128: the field error of each mixed form
+    against the FP64 direct sum (4,096 sampled particles) is within 1.1x that of
+    the FP64 GPU form, and the FP64 form matches the oracle FMM on the same tree."""
     import torch
     from gpu_util import rel_rms, to_dev
     from paper_2005_12351_gb300 import fmm
     w = synth.WORKLOADS["dipole_plummer_4m_p8"]
     pos, S = synth.make_system(w["n"], w["s"], w["dist"], w["seed"])
-    (_, E32), t32 = gpu_eval(pos, S, 1, 8, 0.5, 128, "fp32", want_phi=False)
+    E_mixed = {}
+    for prec in FORMS:
+        (_, E_mixed[prec]), tm = gpu_eval(pos, S, 1, 8, 0.5, 128, prec, want_phi=False)
+        assert_tc_ran(tm, prec)
+        tm.destroy()
     (_, E64), t64 = gpu_eval(pos, S, 1, 8, 0.5, 128, "fp64", want_phi=False)
-    t32.destroy()
     t64.destroy()
     tg = synth.sample_indices(len(pos), 4096, 11)
     _, E_d = fmm.direct_sum(to_dev(pos), to_dev(S), 1, targets=to_dev(tg.astype(np.int32)),
                             want_potential=False)
     E_d = E_d.cpu().numpy()
-    e32, e64 = rel_rms(E32[tg], E_d), rel_rms(E64[tg], E_d)
-    assert e32 <= 1.1 * e64, (e32, e64)
+    e64 = rel_rms(E64[tg], E_d)
+    for prec in FORMS:
+        e = rel_rms(E_mixed[prec][tg], E_d)
+        assert e <= 1.1 * e64, (prec, e, e64)
     ot = orc.Tree(pos, 128)
     ot.lists(0.5)
     _, E_o = ot.fmm(S, 1, 8, targets=tg[:1024])
@@ -88,11 +111,12 @@ def test_plummer_4m_p8_fp32_vs_fp64(orc):
     torch.cuda.synchronize()
 
 
-def test_fp32_edge_cases():
+@pytest.mark.parametrize("precision", FORMS)
+def test_fp32_edge_cases(precision):
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
-    tree = fmm.create_tree(max_leaf=8, precision="fp32")
+    tree = fmm.create_tree(max_leaf=8, precision=precision)
     tree.set_sources(to_dev(np.array([[0.3, 0.4, 0.5]])), to_dev(np.array([[1.0, 0.0, 0.0]])), 1)
     phi, E = tree.evaluate(3, 0.5)
     assert phi.item() == 0.0 and not E.any()
@@ -100,5 +124,44 @@ def test_fp32_edge_cases():
                      torch.zeros((0, 3), dtype=torch.float64, device="cuda"), 1)
     phi, E = tree.evaluate(3, 0.5)
     assert phi.numel() == 0
-    with pytest.raises(fmm.FMMError):
-        fmm.create_tree(precision="3xtf32")
+
+
+@pytest.mark.parametrize("s,p,dist,n", [(1, 6, "uniform", 60_000), (2, 5, "plummer", 40_000),
+                                         (0, 9, "plummer", 30_000), (1, 10, "uniform", 20_000)])
+def test_3xtf32_matches_fp32_form(s, p, dist, n):
+    """Both mixed forms round the same scaled FP32 expansions; their results agree
+    to FP32 rounding: the field within 1e-6, the potential (whose local term sums
+    ~10^2 contributions of mixed sign per key row in tensor-core FP32) within 2e-6.
+    p=10, s=1 has n_L = 286 > 256 and takes the SIMT M2L."""
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(n, s, dist, 900 + s + p)
+    (phi_a, E_a), ta = gpu_eval(pos, S, s, p, 0.5, 64, "fp32")
+    (phi_b, E_b), tb = gpu_eval(pos, S, s, p, 0.5, 64, "3xtf32")
+    if p < 10:
+        assert_tc_ran(tb, "3xtf32")
+    else:
+        assert tb.info()["tc_rows"] == 0
+    # local expansions column by column: with n_L > 128 the columns from 128 on
+    # come from the second column group of the tensor-core M2L
+    nL = (p + 1) * (p + 2) * (p + 3) // 6
+    La, Lb = ta.copy_array("local", nL).numpy(), tb.copy_array("local", nL).numpy()
+    assert La.dtype == np.float32 and La.shape[1] == Lb.shape[1]
+    for c0 in range(0, La.shape[1], 128):
+        assert rel_rms(Lb[:, c0:c0 + 128], La[:, c0:c0 + 128]) < 1e-5, c0
+    assert rel_rms(E_b, E_a) < 1e-6, rel_rms(E_b, E_a)
+    assert rel_rms(phi_b, phi_a) < 2e-6, rel_rms(phi_b, phi_a)
+
+
+def test_3xtf32_chunk_boundaries(monkeypatch):
+    """Chunks of one key row each and chunks longer than any tile's rows give the
+    same result within FP32 rounding (the chunk partials are summed in FP64).
+    The chunk length is read when a handle builds its first plan."""
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(20_000, 1, "plummer", 77)
+    out = {}
+    for g in ("1", "100000"):
+        monkeypatch.setenv("FMM_TC_CHUNK", g)
+        (_, out[g]), tree = gpu_eval(pos, S, 1, 6, 0.5, 32, "3xtf32", want_phi=False)
+        info = tree.info()
+        assert info["tc_chunks"] == (info["tc_rows"] if g == "1" else info["tc_tiles"])
+    assert rel_rms(out["1"], out["100000"]) < 1e-6
