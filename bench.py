@@ -196,6 +196,18 @@ def config_of(w, args):
 FP32_PEAK_TFLOPS = 80.5     # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 GEMM rate of this machine's GPUs
+    times the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s); TFLOP/s, source."""
+    ratio = 1.1 / 2.25
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        return bf16 * ratio, "measured bf16 %.1f TFLOP/s x nominal TF32/bf16 ratio 1.1/2.25" % bf16
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * ratio, "fallback bf16 1900 TFLOP/s x nominal TF32/bf16 ratio 1.1/2.25"
+
+
 def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, flush):
     """Time K whole steps of one precision form; returns a dict of results."""
     import torch
@@ -307,7 +319,18 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_flops": cand[dom], "peak_source": src}
-    res = {"value": value, "ms_per_step": ms, "rel_err": rel_err,
+    if precision == "3xtf32" and info["tc_rows"] > 0:
+        # the M2L on the tensor cores: 3 TF32 products per FP32 multiply-add of the method
+        tpk, tsrc = tf32_peak()
+        t_ach = 3 * m2l_flops / (ph["m2l"] / 1e3) / 1e12
+        roofline_m2l = {"bound": "tensor", "kernel": "m2l (k_m2l_tc + plan, 3xTF32)", "achieved": t_ach,
+                        "peak": tpk, "unit": "TFLOP/s", "frac": t_ach / tpk, "traffic": None,
+                        "algorithmic_flops": 3 * m2l_flops, "peak_source": tsrc,
+                        "tile_fill": info["n_m2l"] / (128.0 * info["tc_rows"]),
+                        "tc_rows": info["tc_rows"], "tc_chunks": info["tc_chunks"]}
+    else:
+        roofline_m2l = None
+    res = {"value": value, "ms_per_step": ms, "rel_err": rel_err, "roofline_m2l": roofline_m2l,
            "e2e": {"value": n * world / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
            "roofline": roofline, "phase_ms": ph, "clocks": clocks, "gpu_launches": launches,
@@ -425,6 +448,12 @@ def run_ours(args, w):
                                                  "roofline", "phase_ms", "gpu_launches")}
         line["mixed_fp32"]["error_ratio_vs_fp64"] = (mx["rel_err"]["field_rel_rms"]
                                                      / main["rel_err"]["field_rel_rms"])
+        m3 = measure_form(args, w, "3xtf32", dev, world, rank, pos_h, S_h, pos_d, S_d, flush)
+        line["mixed_3xtf32"] = {k: m3[k] for k in ("value", "ms_per_step", "rel_err", "e2e",
+                                                   "roofline", "roofline_m2l", "phase_ms",
+                                                   "gpu_launches")}
+        line["mixed_3xtf32"]["error_ratio_vs_fp64"] = (m3["rel_err"]["field_rel_rms"]
+                                                       / main["rel_err"]["field_rel_rms"])
     if rank == 0 and args.serving_requests > 0 and "batch" not in w:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -450,13 +479,13 @@ def main(argv=None):
     ap.add_argument("--err-samples", type=int, default=4096)
     ap.add_argument("--oracle-sample", type=int, default=65536)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "3xtf32"], default="fp64")
     ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the extra FP32-form measurement in the same run")
+                    help="skip the extra FP32 and 3xTF32 form measurements in the same run")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)
-    ap.add_argument("--serving-precision", choices=["fp64", "fp32"], default="fp32")
+    ap.add_argument("--serving-precision", choices=["fp64", "fp32", "3xtf32"], default="fp32")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.259)
     ap.add_argument("--fp64-peak-source", default="152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                     "(nominal 1.25 TFLOP/s FP64 of the part)")
