@@ -308,6 +308,47 @@ fmm_status fmm_server_get_stats(fmm_server *s, fmm_server_stats *out);
 fmm_status fmm_server_destroy(fmm_server *s);
 
 /*
+ * Repeated evaluation of one geometry.
+ *
+ * fmm_update_moments replaces the source moments of the current tree (DEVICE,
+ * n x T(s), the caller's particle order as in fmm_set_sources) and keeps the
+ * tree, the lists and every cache; asynchronous on the handle's stream.
+ *
+ * fmm_evaluate_graph is fmm_evaluate for a loop that repeats one parameter
+ * set (p, theta, flags, output pointers): the first call evaluates normally,
+ * then captures the evaluate into a CUDA graph; later calls with the same
+ * parameters replay it with one graph launch (every phase of the path, all
+ * systems of a batch).  Any other parameter set recaptures.  fmm_set_sources,
+ * fmm_set_sources_batch and fmm_autotune drop the graph.  Profiling phase
+ * times are not updated by replays.  Errors as fmm_evaluate; FMM_ECUDA if
+ * the capture fails.
+ */
+fmm_status fmm_update_moments(fmm_tree *t, const double *moments);
+fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potential, int want_field,
+                              double *potential, double *field);
+
+/*
+ * Autotuner: times the handle's kernel variants on its own tree and lists
+ * (reps evaluates each, after one warm-up, CUDA events on the handle's
+ * stream) and keeps the fastest for later evaluates.  Candidates:
+ *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1)
+ *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
+ *               the SIMT FP32 M2L (m2l_tensor 0)
+ *   FMM_FP32    none (reports the fixed configuration)
+ * The variants compute the same sums in another order: results agree to the
+ * form's rounding, not bitwise.  Synchronises the stream.  out may be NULL.
+ */
+typedef struct {
+    int p2p_variant;        /* FP64 P2P: 0 one target per thread, 1 two          */
+    int m2l_tensor;         /* FMM_3XTF32: 1 tensor-core M2L, 0 SIMT FP32 M2L   */
+    int tc_chunk_rows;      /* key rows summed per chunk of the tensor-core M2L  */
+    int candidates;         /* variants timed                                    */
+    float ms_per_evaluate;  /* time of the chosen variant                        */
+} fmm_tuning;
+fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, int want_field,
+                        double *potential, double *field, int reps, fmm_tuning *out);
+
+/*
  * Self-check of the library's own FP64 reciprocal square root used by the
  * P2P near field (an FP32 rsqrtf seed refined by one third-order
  * Householder step in FP64): writes own[i] = the library's 1/sqrt(x[i]) and

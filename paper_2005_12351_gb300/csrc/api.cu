@@ -52,6 +52,18 @@ void release(fmm_tree *t, DevBuf &b)
 
 }  // namespace fmm
 
+namespace fmm {
+
+fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E)
+{
+    if (t->prec == FMM_FP32 || t->prec == FMM_3XTF32)
+        return run_mixed(t, p, want_phi, want_field, phi, E);
+    FMM_TRY(run_expansions(t, p, want_phi, want_field));
+    return run_p2p(t, want_phi, want_field, phi, E);
+}
+
+}  // namespace fmm
+
 using namespace fmm;
 
 namespace {
@@ -173,6 +185,8 @@ fmm_status fmm_destroy(fmm_tree *t)
     DeviceGuard g(t->device);
     if (t->stream) cudaStreamSynchronize(t->stream);
     else cudaDeviceSynchronize();
+    drop_graph(t);
+    if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     std::vector<DevBuf *> v;
     all_buffers(t, v);
     for (DevBuf *b : v) release(t, *b);
@@ -240,6 +254,7 @@ static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const d
         return fail(t, FMM_EORDER, "source order must be 0, 1 or 2");
     if (n > 0 && (!positions || !moments)) return fail(t, FMM_EINVAL, "NULL positions or moments");
     DeviceGuard g(t->device);
+    drop_graph(t);
     t->have_sources = false;
     t->have_lists = false;
     t->tc_plan = false;
@@ -274,12 +289,7 @@ fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, in
     record(t, 4);
     if (!t->have_lists || t->theta != theta) FMM_TRY(build_lists(t, theta));
     record(t, 5);
-    if (t->prec == FMM_FP32 || t->prec == FMM_3XTF32) {
-        FMM_TRY(run_mixed(t, p, want_potential, want_field, potential, field));
-    } else {
-        FMM_TRY(run_expansions(t, p, want_potential, want_field));
-        FMM_TRY(run_p2p(t, want_potential, want_field, potential, field));
-    }
+    FMM_TRY(evaluate_body(t, p, want_potential, want_field, potential, field));
     record(t, 12);
     if (t->profiling) {
         FMM_TRY(cuda_check(t, cudaEventSynchronize(t->ev[12]), "event sync"));

@@ -201,6 +201,20 @@ struct fmm_tree {
     DevBuf b_tc_keys, b_tc_keys2, b_tc_vals, b_tc_vals2, b_tc_hist, b_tc_scan, b_tc_cnt;
     DevBuf b_tc_tgt, b_tc_bits, b_tc_wpre, b_tc_rcnt, b_tc_ccnt, b_tc_roff, b_tc_coff;
     DevBuf b_tc_rowkey, b_tc_crb, b_tc_cre, b_tc_slot, b_tc_el, b_tc_img, b_tc_part;
+
+    // tuning (fmm_autotune; defaults otherwise): FP64 P2P kernel (0 one target
+    // per thread, 1 two), FMM_3XTF32 M2L on the SIMT FP32 kernel instead of the
+    // tensor cores, rows per chunk of the tensor-core M2L (tc_G above)
+    int p2p_variant = 1;
+    bool m2l_simt = false;
+    bool tuned = false;
+    // fmm_evaluate_graph: the evaluate of one parameter set captured as a CUDA graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int g_p = -1, g_phi = 0, g_field = 0;
+    double g_theta = 0.0;
+    double *g_pot = nullptr, *g_fld = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -243,6 +257,10 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
 // expansions, L zeroed by the caller
 bool tc_usable(fmm_tree *t, int s, int p);
 fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L);
+// api.cu: the compute of an evaluate whose lists are current (no host sync)
+fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E);
+// graph.cu: drop a captured evaluate graph (the tree or the tuning changed)
+void drop_graph(fmm_tree *t);
 // p2p.cu
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
 void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref);

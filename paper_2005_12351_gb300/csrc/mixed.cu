@@ -616,7 +616,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     }
     FMM_TRY(build_dtables(t, p, tb, lut));
     // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
-    const bool use_tc = t->prec == FMM_3XTF32 && tc_usable(t, s, p);
+    const bool use_tc = t->prec == FMM_3XTF32 && !t->m2l_simt && tc_usable(t, s, p);
     if (!use_tc && t->d32_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(

@@ -396,11 +396,7 @@ void launch_p2p_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr,
             (const int32_t *)t->b_perm.ptr, phi, E);
     };
-    static const int variant = [] {
-        const char *v = getenv("FMM_P2P_VARIANT");
-        return v ? atoi(v) : 1;
-    }();
-    if (variant == 1) {
+    if (t->p2p_variant == 1) {
         if (want_phi && want_field) args(k_p2p_x2<S, true, true>);
         else if (want_phi) args(k_p2p_x2<S, true, false>);
         else args(k_p2p_x2<S, false, true>);

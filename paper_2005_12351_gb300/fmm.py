@@ -48,6 +48,11 @@ class TreeInfo(C.Structure):
         return d
 
 
+class Tuning(C.Structure):
+    _fields_ = [("p2p_variant", C.c_int), ("m2l_tensor", C.c_int), ("tc_chunk_rows", C.c_int),
+                ("candidates", C.c_int), ("ms_per_evaluate", C.c_float)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -167,6 +172,51 @@ class FMMTree:
                                 _ptr(field if want_field else None))
         _check(st, self._h, "evaluate")
         return (potential if want_potential else None), (field if want_field else None)
+
+    def update_moments(self, moments):
+        """Replace the moments of the current tree (caller's order); keeps tree, lists, caches."""
+        _dev_f64(moments, "moments", source_terms(self.s))
+        if moments.shape[0] != self.n:
+            raise ValueError("moments must have %d rows" % self.n)
+        fn = lib().fmm_update_moments
+        fn.argtypes = [C.c_void_p, C.c_void_p]
+        fn.restype = C.c_int
+        _check(fn(self._h, _ptr(moments)), self._h, "update_moments")
+
+    def evaluate_graph(self, p: int, theta: float, want_potential=True, want_field=True,
+                       potential=None, field=None):
+        """fmm_evaluate replayed as one CUDA graph launch while (p, theta, flags, outputs)
+        stay the same.  Output tensors are allocated once per parameter set and reused."""
+        key = (int(p), float(theta), bool(want_potential), bool(want_field))
+        cache = getattr(self, "_graph_out", None)
+        if potential is None and field is None and cache and cache[0] == key:
+            potential, field = cache[1], cache[2]
+        if want_potential and potential is None:
+            potential = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        if want_field and field is None:
+            field = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        self._graph_out = (key, potential, field)
+        fn = lib().fmm_evaluate_graph
+        fn.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        fn.restype = C.c_int
+        st = fn(self._h, int(p), float(theta), int(bool(want_potential)), int(bool(want_field)),
+                _ptr(potential if want_potential else None), _ptr(field if want_field else None))
+        _check(st, self._h, "evaluate_graph")
+        return (potential if want_potential else None), (field if want_field else None)
+
+    def autotune(self, p: int, theta: float, want_potential=True, want_field=True, reps=3):
+        """Time the handle's kernel variants on its own workload; keep the fastest."""
+        pot = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_potential else None
+        fld = torch.empty((self.n, 3), dtype=torch.float64, device=self.device) if want_field else None
+        out = Tuning()
+        fn = lib().fmm_autotune
+        fn.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                       C.c_int, C.POINTER(Tuning)]
+        fn.restype = C.c_int
+        st = fn(self._h, int(p), float(theta), int(bool(want_potential)), int(bool(want_field)),
+                _ptr(pot), _ptr(fld), int(reps), C.byref(out))
+        _check(st, self._h, "autotune")
+        return {k: getattr(out, k) for k, _ in out._fields_}
 
     def info(self) -> dict:
         inf = TreeInfo()
