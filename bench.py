@@ -341,6 +341,57 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     return res
 
 
+def measure_graph(args, w, precision, dev, world, pos_d, S_h, S_d, flush):
+    """Repeated evaluation of one geometry: autotune once (untimed), then K steps of
+    (moment update + the evaluate replayed as one CUDA graph launch)."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    s, p, theta, n = w["s"], w["p"], w["theta"], w["n"]
+    want_phi = bool(w.get("phi", False))
+    stream = torch.cuda.current_stream(dev)
+    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"], precision=precision)
+    if "batch" in w:
+        tree.set_sources_batch(pos_d, S_d, w["offsets"], s)
+    else:
+        tree.set_sources(pos_d, S_d, s)
+    tuning = tree.autotune(p, theta, want_phi, True, reps=2)
+    E_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    step = lambda: (tree.update_moments(S_d), tree.evaluate_graph(p, theta, want_phi, True))
+    for _ in range(max(args.warmup, 1)):
+        _, E_d = step()[1]
+    torch.cuda.synchronize(dev)
+    launches0 = tree.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = tree.launch_count() - launches0
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S_d.copy_(S_h, non_blocking=True)
+        _, E_d = step()[1]
+        E_h.copy_(E_d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = max_over_ranks(float(np.mean(e2e)), world, dev)
+    tree.destroy()
+    return {"precision": precision, "value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "step": "fmm_update_moments + fmm_evaluate_graph (tree and lists fixed; one graph launch)",
+            "gpu_launches": launches,
+            "e2e": {"value": n * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": S_h.numel() * 8, "d2h_bytes_per_step": E_h.numel() * 8},
+            "tuning": tuning}
+
+
 def serving_stream(count: int, seed: int):
     """Requests drawn like the serving workload: N log-uniform in [1e3, 2e6],
     source order uniform over {0, 1, 2}, p uniform over {4..10}, uniform or
@@ -454,6 +505,9 @@ def run_ours(args, w):
                                                    "gpu_launches")}
         line["mixed_3xtf32"]["error_ratio_vs_fp64"] = (m3["rel_err"]["field_rel_rms"]
                                                        / main["rel_err"]["field_rel_rms"])
+    if not args.no_graph:
+        line["graph"] = measure_graph(args, w, args.graph_precision or args.precision, dev, world,
+                                      pos_d, S_h, S_d, flush)
     if rank == 0 and args.serving_requests > 0 and "batch" not in w:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,6 +536,10 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32", "3xtf32"], default="fp64")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra FP32 and 3xTF32 form measurements in the same run")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the repeated-geometry measurement (autotune + graph replay)")
+    ap.add_argument("--graph-precision", choices=["fp64", "fp32", "3xtf32"], default=None,
+                    help="form of the graph measurement (default: --precision)")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)
