@@ -543,7 +543,7 @@ def main(argv=None):
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)
-    ap.add_argument("--serving-precision", choices=["fp64", "fp32", "3xtf32"], default="fp32")
+    ap.add_argument("--serving-precision", choices=["fp64", "fp32", "3xtf32"], default="3xtf32")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.259)
     ap.add_argument("--fp64-peak-source", default="152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                     "(nominal 1.25 TFLOP/s FP64 of the part)")

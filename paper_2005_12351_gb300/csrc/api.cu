@@ -43,6 +43,11 @@ fmm_status ensure(fmm_tree *t, DevBuf &b, size_t bytes)
 void release(fmm_tree *t, DevBuf &b)
 {
     if (b.ptr) {
+        // work already queued on the handle's stream may still read this buffer
+        // (a grow copy, an earlier kernel): once freed, another handle's
+        // allocation on another stream may receive the same memory
+        if (t->stream) cudaStreamSynchronize(t->stream);
+        else cudaDeviceSynchronize();
         cudaFree(b.ptr);
         t->held -= b.bytes;
     }
@@ -101,7 +106,7 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_scan, &t->b_scan_tmp, &t->b_front, &t->b_front2, &t->b_m2l_raw,
                    &t->b_p2p_raw, &t->b_counters, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
                    &t->b_p2p_src, &t->b_p2p_off, &t->b_lkeys, &t->b_lkeys2, &t->b_lval,
-                   &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
+                   &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_dsort, &t->b_dsort_h, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
                    &t->b_E, &t->b_tab_i32, &t->b_tab_u32, &t->b_tc_keys, &t->b_tc_keys2,
                    &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
                    &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,

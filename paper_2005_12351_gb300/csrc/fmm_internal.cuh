@@ -184,6 +184,7 @@ struct fmm_tree {
     DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;
     DevBuf b_m2l_src, b_m2l_off, b_m2l_didx, b_p2p_src, b_p2p_off, b_lkeys, b_lkeys2, b_lval, b_lval2;
     DevBuf b_hash, b_dkeys, b_D;
+    DevBuf b_dsort, b_dsort_h;             // scratch of the canonical D-key numbering
     DevBuf b_M, b_L, b_phi, b_E;
     DevBuf b_tab_i32, b_tab_u32;
     // mixed-precision state
@@ -270,6 +271,26 @@ fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D,
 void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
                    const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches);
 
+}  // namespace fmm
+
+namespace fmm {
+// Raises a kernel's dynamic shared-memory limit to the most a block can take
+// next to its static shared memory.  The value depends only on the kernel, so
+// handles that launch it concurrently from several threads never lower the
+// limit under one another's launches (a per-launch size would race).
+template <typename K>
+inline void allow_max_dynamic_smem(K kern)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
 }  // namespace fmm
 
 #define FMM_TRY(expr)                         \

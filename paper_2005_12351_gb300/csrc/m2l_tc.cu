@@ -895,7 +895,7 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
     const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, t->tc_sms);
     cudaMemsetAsync(err, 0, sizeof(unsigned), st);
     auto go = [&](auto kern) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        allow_max_dynamic_smem(kern);
         kern<<<grid, kTcThreads, smem, st>>>(a);
     };
     switch (rs) {
@@ -928,7 +928,7 @@ fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D,
     // 64 KB of slack past the tiles: every operand read stays inside the
     // block's allocation even for the widest tile a descriptor can describe
     const int smem = 1024 + 32768 + kCheckBBytes + 65536 + 64;
-    cudaFuncSetAttribute(k_check_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    allow_max_dynamic_smem(k_check_umma);
     k_check_umma<<<1, 128, smem, st>>>(A, B, D, a, err);
     return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ECUDA;
 }

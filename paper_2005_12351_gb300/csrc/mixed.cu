@@ -648,7 +648,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
                                                    S32);
     {
         size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * (tb.nK + 1) + kChunk * tb.nS);
-        cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_p2m32);
         k_p2m32<<<(unsigned)t->nleaves, 128, smem, st>>>(leaves, begin, end, half, o, S32, tb, M);
     }
     t->launches += 2;
@@ -670,7 +670,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         const int ldM = tb.nM | 1, ldD = tb.nD | 1;
         size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +
                       4 * ((size_t)kBatch * (ldM + ldD) + (size_t)tb.m2l_T * kM2LThreads);
-        cudaFuncSetAttribute(k_m2l32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_m2l32);
         k_m2l32<<<(unsigned)nc, kM2LThreads, smem, st>>>(
             (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
             (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr, M,
@@ -689,7 +689,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     record(t, 10);
     {
         size_t smem = 4 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
-        cudaFuncSetAttribute(k_l2p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_l2p32);
         k_l2p32<<<(unsigned)t->nleaves, kL2PThreads, smem, st>>>(
             leaves, begin, end, half, o, L, tb, want_phi, want_field, (double *)t->b_phi.ptr,
             (double *)t->b_E.ptr);

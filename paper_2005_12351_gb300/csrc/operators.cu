@@ -654,7 +654,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
     // P2M at the leaves
     {
         size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
-        cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_p2m);
         k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
                                                                (const double *)t->b_S.ptr, tb, M);
         ++t->launches;
@@ -677,7 +677,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
         const int ldM = tb.nM | 1, ldD = tb.nD | 1;
         size_t fixed = 8 * (size_t)tb.m2l_slots * kM2LThreads + 4 * (size_t)tb.m2l_T * kM2LThreads;
         size_t smem = fixed + 8 * (size_t)kM2LBatch * (ldM + ldD);
-        cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_m2l);
         k_m2l<<<(unsigned)nc, kM2LThreads, smem, st>>>(
             (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
             (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr,
@@ -698,7 +698,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
     // L2P
     {
         size_t smem = 8 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
-        cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_l2p);
         k_l2p<<<(unsigned)t->nleaves, kL2PThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
                                                                L, tb, want_phi, want_field,
                                                                (double *)t->b_phi.ptr,

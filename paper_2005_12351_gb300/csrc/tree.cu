@@ -546,10 +546,25 @@ __global__ void k_slot_compact(const unsigned long long *table, uint32_t H, cons
     if (h < H && table[h] != ~0ull) dkeys[dense[h]] = table[h];
 }
 
-__global__ void k_slot_to_dense(int32_t *didx, int64_t np, const uint32_t *dense)
+// Which colliding key wins a hash slot depends on timing, so slot order is
+// not reproducible: the distinct keys are sorted by value and a pair's D row
+// is the rank of its key (rank_of[dense index]).
+__global__ void k_slot_to_dense(int32_t *didx, int64_t np, const uint32_t *dense, const uint32_t *rank_of)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < np) didx[k] = (int32_t)dense[(uint32_t)didx[k]];
+    if (k < np) didx[k] = (int32_t)rank_of[dense[(uint32_t)didx[k]]];
+}
+
+__global__ void k_iota(uint32_t *v, int64_t n)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) v[k] = (uint32_t)k;
+}
+
+__global__ void k_rank_of(const uint32_t *old_of_rank, int64_t n, uint32_t *rank_of)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) rank_of[old_of_rank[r]] = (uint32_t)r;
 }
 
 inline unsigned grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -921,8 +936,20 @@ fmm_status build_lists(fmm_tree *t, double theta)
         FMM_TRY(ensure(t, t->b_dkeys, 8 * std::max<int64_t>(ndoff, 1)));
         k_slot_compact<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, dense,
                                                        (uint64_t *)t->b_dkeys.ptr);
-        k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense);
-        t->launches += 3;
+        // canonical numbering: keys by value (57-bit keys: gap, side, offsets)
+        const int64_t nd1 = std::max<int64_t>(ndoff, 1);
+        FMM_TRY(ensure(t, t->b_dsort, 20 * (size_t)nd1));
+        const size_t hb = radix_hist_bytes(nd1);
+        FMM_TRY(ensure(t, t->b_dsort_h, hb + scan_scratch_bytes((int64_t)hb / 4 + 1)));
+        uint64_t *keys2 = (uint64_t *)t->b_dsort.ptr;
+        uint32_t *vals = (uint32_t *)(keys2 + nd1), *vals2 = vals + nd1, *rank_of = vals2 + nd1;
+        k_iota<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff);
+        radix_sort_pairs((uint64_t *)t->b_dkeys.ptr, vals, keys2, vals2, ndoff, 57,
+                         (uint32_t *)t->b_dsort_h.ptr, (uint32_t *)((char *)t->b_dsort_h.ptr + hb), st,
+                         &t->launches);
+        k_rank_of<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff, rank_of);
+        k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense, rank_of);
+        t->launches += 5;
     }
     FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
     t->n_m2l = nm2l;

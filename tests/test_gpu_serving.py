@@ -22,7 +22,7 @@ def request_mix(count, seed, nmax=60_000):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "3xtf32"])
 def test_results_same_alone_and_in_mix(precision):
     from paper_2005_12351_gb300 import fmm
     reqs = request_mix(10, 5)
