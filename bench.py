@@ -440,13 +440,15 @@ def run_serving(args, dev):
         if delay > 0:
             time.sleep(delay)
         tickets.append(sv.submit(**r))
-    lat, ends, firsts, failed = [], [], [], 0
+    lat, ends, firsts, failed, failures = [], [], [], 0, []
     done_particles = 0
     for t, r in zip(tickets, reqs):
         try:
             _, _, info = sv.wait(t)
-        except fmm.FMMError:
+        except fmm.FMMError as e:
             failed += 1
+            failures.append({"n": len(r["positions"]), "s": r["source_order"], "p": r["p"],
+                             "error": str(e)[:200]})
             continue
         lat.append(1e3 * (info["end_s"] - info["submit_s"]))
         ends.append(info["end_s"])
@@ -455,7 +457,7 @@ def run_serving(args, dev):
     st = sv.stats()
     sv.close()
     span = max(ends) - min(firsts)
-    return {"requests": len(reqs), "failed": failed, "slots": args.serving_slots,
+    return {"requests": len(reqs), "failed": failed, "failures": failures, "slots": args.serving_slots,
             "precision": args.serving_precision, "mem_budget_gb": 120,
             "offered_load": load, "capacity_particles_per_s": capacity,
             "particles_per_s": done_particles / span, "p50_latency_ms": float(np.percentile(lat, 50)),

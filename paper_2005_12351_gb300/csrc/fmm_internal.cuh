@@ -257,6 +257,10 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
 // the M2L of the mixed-precision form on it: M and L are the scaled FP32
 // expansions, L zeroed by the caller
 bool tc_usable(fmm_tree *t, int s, int p);
+// builds the plan, the operator images and the partial buffer for p (FMM_EBUDGET
+// when they do not fit the handle's budget); tc_release frees all of it
+fmm_status tc_prepare(fmm_tree *t, int p);
+void tc_release(fmm_tree *t);
 fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L);
 // api.cu: the compute of an evaluate whose lists are current (no host sync)
 fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E);

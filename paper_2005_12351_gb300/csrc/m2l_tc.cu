@@ -831,7 +831,17 @@ bool tc_usable(fmm_tree *t, int s, int p)
     return L.Np <= 256 && L.nkb <= kTcMaxKB && tc_raw_stages(L.b_stage) >= 3;
 }
 
-fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L)
+void tc_release(fmm_tree *t)
+{
+    for (DevBuf *b : {&t->b_tc_keys, &t->b_tc_keys2, &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist,
+                      &t->b_tc_scan, &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rowkey,
+                      &t->b_tc_crb, &t->b_tc_cre, &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part})
+        release(t, *b);
+    t->tc_plan = false;
+    t->tc_img_p = -1;
+}
+
+fmm_status tc_prepare(fmm_tree *t, int p)
 {
     cudaStream_t st = t->stream;
     const TcLayout &Ly = t->tc_lay;
@@ -852,7 +862,16 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
         ++t->launches;
         t->tc_img_p = p;
     }
-    FMM_TRY(ensure(t, t->b_tc_part, 4 * (size_t)t->tc_chunks * 128 * Ly.Np));
+    return ensure(t, t->b_tc_part, 4 * (size_t)t->tc_chunks * 128 * Ly.Np);
+}
+
+fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L)
+{
+    cudaStream_t st = t->stream;
+    const TcLayout &Ly = t->tc_lay;
+    if (!t->tc_plan || t->tc_img_p != p) FMM_TRY(tc_prepare(t, p));
+    if (t->tc_chunks == 0) return FMM_OK;
+    const long long stride = Ly.img_bytes;
     if (t->tc_sms == 0) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device);

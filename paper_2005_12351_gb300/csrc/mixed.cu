@@ -615,8 +615,27 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         return FMM_EORDER;
     }
     FMM_TRY(build_dtables(t, p, tb, lut));
+    // the buffers every evaluate of this form needs come first
+    FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
+    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));
+    FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * row4(tb.nM)));
+    FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
+    FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
+    FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
     // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
-    const bool use_tc = t->prec == FMM_3XTF32 && !t->m2l_simt && tc_usable(t, s, p);
+    bool use_tc = t->prec == FMM_3XTF32 && !t->m2l_simt && tc_usable(t, s, p);
+    if (use_tc && t->n_m2l > 0) {
+        // the tensor-core plan and operator images must fit the handle's memory
+        // budget; otherwise this evaluate takes the SIMT FP32 M2L
+        const fmm_status pst = tc_prepare(t, p);
+        if (pst == FMM_EBUDGET) {
+            tc_release(t);
+            t->err.clear();
+            use_tc = false;
+        } else {
+            FMM_TRY(pst);
+        }
+    }
     if (!use_tc && t->d32_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
@@ -626,12 +645,6 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         t->d32_p = p;
     }
     record(t, 6);
-    FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
-    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));
-    FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * row4(tb.nM)));
-    FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
-    FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
-    FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
     const int32_t *leaves = (const int32_t *)t->b_leaves.ptr;
     const int32_t *begin = (const int32_t *)t->b_begin.ptr, *end = (const int32_t *)t->b_end.ptr;
     const int32_t *cx = (const int32_t *)t->b_cx.ptr, *cy = (const int32_t *)t->b_cy.ptr,

@@ -165,3 +165,30 @@ def test_3xtf32_chunk_boundaries(monkeypatch):
         info = tree.info()
         assert info["tc_chunks"] == (info["tc_rows"] if g == "1" else info["tc_tiles"])
     assert rel_rms(out["1"], out["100000"]) < 1e-6
+
+
+def test_3xtf32_falls_back_to_simt_within_budget():
+    """When the tensor-core plan and operator images do not fit the handle's memory
+    budget, the 3xTF32 form takes the SIMT FP32 M2L: the evaluate succeeds and is
+    bitwise the FP32 form's result."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    pos, S = synth.make_system(40_000, 2, "plummer", 931)
+    P, Sd = to_dev(pos), to_dev(S)
+    f32 = fmm.create_tree(max_leaf=64, precision="fp32")
+    f32.set_sources(P, Sd, 2)
+    _, E32 = f32.evaluate(9, 0.5, False, True)
+    torch.cuda.synchronize()
+    need32 = f32.info()["device_bytes"]
+    full = fmm.create_tree(max_leaf=64, precision="3xtf32")
+    full.set_sources(P, Sd, 2)
+    full.evaluate(9, 0.5, False, True)
+    torch.cuda.synchronize()
+    assert full.info()["tc_rows"] > 0 and full.info()["device_bytes"] > need32 * 1.05
+    t = fmm.create_tree(max_leaf=64, precision="3xtf32", mem_budget_bytes=int(need32 * 1.02))
+    t.set_sources(P, Sd, 2)
+    _, E = t.evaluate(9, 0.5, False, True)
+    torch.cuda.synchronize()
+    assert t.info()["tc_rows"] == 0
+    assert np.array_equal(E.cpu().numpy(), E32.cpu().numpy())
