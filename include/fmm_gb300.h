@@ -331,7 +331,8 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  * Autotuner: times the handle's kernel variants on its own tree and lists
  * (reps evaluates each, after one warm-up, CUDA events on the handle's
  * stream) and keeps the fastest for later evaluates.  Candidates:
- *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1)
+ *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1),
+ *               or each mirrored leaf pair once for both directions (2)
  *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
  *               the SIMT FP32 M2L (m2l_tensor 0)
  *   FMM_FP32    none (reports the fixed configuration)
@@ -339,7 +340,8 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  * form's rounding, not bitwise.  Synchronises the stream.  out may be NULL.
  */
 typedef struct {
-    int p2p_variant;        /* FP64 P2P: 0 one target per thread, 1 two          */
+    int p2p_variant;        /* FP64 P2P: 0 one target per thread, 1 two, 2 each  */
+                            /* mirrored leaf pair once for both directions       */
     int m2l_tensor;         /* FMM_3XTF32: 1 tensor-core M2L, 0 SIMT FP32 M2L   */
     int tc_chunk_rows;      /* key rows summed per chunk of the tensor-core M2L  */
     int candidates;         /* variants timed                                    */
@@ -347,6 +349,19 @@ typedef struct {
 } fmm_tuning;
 fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field, int reps, fmm_tuning *out);
+
+/*
+ * Applies a tuning, e.g. one fmm_autotune reported for the same workload on
+ * an earlier run, without timing anything: p2p_variant 0, 1 or 2,
+ * m2l_tensor 0 or 1, tc_chunk_rows in [1, 64]; a negative value keeps the
+ * handle's current setting, and candidates and ms_per_evaluate are ignored.
+ * Variant 2 (the near field by Newton's third law, §3.1 P2P) keeps per
+ * mirrored leaf pair a row of reverse terms for each source particle; where
+ * those rows exceed the handle's budget, evaluates take variant 1.  The paper
+ * has no counterpart for this call.  FMM_EINVAL for a value out of range or a
+ * NULL tuning.
+ */
+fmm_status fmm_set_tuning(fmm_tree *t, const fmm_tuning *tuning);
 
 /*
  * Self-check of the library's own FP64 reciprocal square root used by the

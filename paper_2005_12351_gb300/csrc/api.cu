@@ -111,7 +111,9 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
                    &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,
                    &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
-                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part};
+                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
+                   &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
+                   &t->b_sym_fwd};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
 }
 
@@ -263,6 +265,7 @@ static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const d
     t->have_sources = false;
     t->have_lists = false;
     t->tc_plan = false;
+    t->sym_plan = false;
     t->d_p = -1;
     t->n = n;
     t->s = source_order;

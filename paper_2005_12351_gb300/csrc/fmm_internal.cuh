@@ -203,10 +203,19 @@ struct fmm_tree {
     DevBuf b_tc_tgt, b_tc_bits, b_tc_wpre, b_tc_rcnt, b_tc_ccnt, b_tc_roff, b_tc_coff;
     DevBuf b_tc_rowkey, b_tc_crb, b_tc_cre, b_tc_slot, b_tc_el, b_tc_img, b_tc_part;
 
-    // tuning (fmm_autotune; defaults otherwise): FP64 P2P kernel (0 one target
-    // per thread, 1 two), FMM_3XTF32 M2L on the SIMT FP32 kernel instead of the
+    // symmetric FP64 P2P (p2p_variant 2), derived from the lists: per list
+    // entry its mirror entry (-1: none) and, for an entry (A, B) with B > A,
+    // the first of B's rows in the reverse-term buffer; sym_rows = total rows
+    // (-1: more than the 32-bit row index covers)
+    bool sym_plan = false;
+    int64_t sym_rows = 0;
+    DevBuf b_sym_mir, b_sym_cnt, b_sym_base, b_sym_scan, b_sym_tot, b_sym_rev, b_sym_fwd;
+
+    // tuning (fmm_autotune, fmm_set_tuning; defaults otherwise): FP64 P2P kernel
+    // (0 one target per thread, 1 two, 2 each leaf pair once for both
+    // directions), FMM_3XTF32 M2L on the SIMT FP32 kernel instead of the
     // tensor cores, rows per chunk of the tensor-core M2L (tc_G above)
-    int p2p_variant = 1;
+    int p2p_variant = 2;
     bool m2l_simt = false;
     bool tuned = false;
     // fmm_evaluate_graph: the evaluate of one parameter set captured as a CUDA graph

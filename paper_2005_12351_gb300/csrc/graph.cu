@@ -135,7 +135,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     if (!t) return FMM_EINVAL;
     if (reps < 1 || reps > 1000) return fail(t, FMM_EINVAL, "reps must be in [1, 1000]");
     // candidates: variants that compute the same sums in another order (the
-    // two FP64 P2P kernels agree to FP64 rounding; the M2L paths of FMM_3XTF32
+    // three FP64 P2P kernels agree to FP64 rounding; the M2L paths of FMM_3XTF32
     // and its chunk lengths agree to FP32 rounding)
     std::vector<fmm_tuning> cand;
     fmm_tuning base;
@@ -144,7 +144,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     base.m2l_tensor = t->m2l_simt ? 0 : 1;
     base.tc_chunk_rows = t->tc_G > 0 ? t->tc_G : 16;
     if (t->prec == FMM_FP64) {
-        for (int v : {0, 1}) {
+        for (int v : {0, 1, 2}) {
             fmm_tuning c = base;
             c.p2p_variant = v;
             cand.push_back(c);
@@ -208,6 +208,26 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     if (out) {
         *out = c;
         out->candidates = (int)cand.size();
+    }
+    return FMM_OK;
+}
+
+fmm_status fmm_set_tuning(fmm_tree *t, const fmm_tuning *tuning)
+{
+    if (!t) return FMM_EINVAL;
+    t->err.clear();
+    if (!tuning) return fail(t, FMM_EINVAL, "NULL tuning");
+    const fmm_tuning &c = *tuning;
+    if (c.p2p_variant > 2) return fail(t, FMM_EINVAL, "p2p_variant must be 0, 1 or 2");
+    if (c.m2l_tensor > 1) return fail(t, FMM_EINVAL, "m2l_tensor must be 0 or 1");
+    if (c.tc_chunk_rows == 0 || c.tc_chunk_rows > 64)
+        return fail(t, FMM_EINVAL, "tc_chunk_rows must be in [1, 64]");
+    drop_graph(t);
+    if (c.p2p_variant >= 0) t->p2p_variant = c.p2p_variant;
+    if (c.m2l_tensor >= 0) t->m2l_simt = c.m2l_tensor == 0;
+    if (c.tc_chunk_rows > 0 && t->tc_G != c.tc_chunk_rows) {
+        t->tc_G = c.tc_chunk_rows;
+        t->tc_plan = false;
     }
     return FMM_OK;
 }

@@ -791,6 +791,7 @@ fmm_status build_lists(fmm_tree *t, double theta)
     cudaStream_t st = t->stream;
     t->have_lists = false;
     t->tc_plan = false;
+    t->sym_plan = false;
     t->n_m2l = t->n_p2p = t->n_p2p_inter = t->n_doff = 0;
     t->d_p = -1;
     if (t->n == 0) { t->theta = theta; t->have_lists = true; return FMM_OK; }

@@ -218,6 +218,15 @@ class FMMTree:
         _check(st, self._h, "autotune")
         return {k: getattr(out, k) for k, _ in out._fields_}
 
+    def set_tuning(self, p2p_variant: int = -1, m2l_tensor: int = -1, tc_chunk_rows: int = -1):
+        """Applies a tuning without timing (-1 keeps the current setting)."""
+        tu = Tuning()
+        tu.p2p_variant, tu.m2l_tensor, tu.tc_chunk_rows = int(p2p_variant), int(m2l_tensor), int(tc_chunk_rows)
+        fn = lib().fmm_set_tuning
+        fn.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+        fn.restype = C.c_int
+        _check(fn(self._h, C.byref(tu)), self._h, "set_tuning")
+
     def info(self) -> dict:
         inf = TreeInfo()
         _check(lib().fmm_get_info(self._h, C.byref(inf)), self._h, "get_info")

@@ -1,0 +1,150 @@
+"""GPU FP64 FMM with the symmetric near field (P2P variant 2: each mirrored
+leaf pair evaluated once for both directions) against the oracle, and its
+agreement, determinism, fallback and tuning calls."""
+import numpy as np
+import pytest
+
+from paper_2005_12351_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12        # relative RMS, GPU FP64 form vs CPU FP64 oracle on the same tree
+
+
+def run(pos, S, s, p, ncrit, variant, want_phi=True, want_field=True, budget=0, theta=0.5):
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    t = fmm.create_tree(max_leaf=ncrit, mem_budget_bytes=budget)
+    t.set_tuning(p2p_variant=variant)
+    t.set_sources(to_dev(pos), to_dev(S), s)
+    phi, E = t.evaluate(p, theta, want_phi, want_field)
+    torch.cuda.synchronize()
+    out = (phi.cpu().numpy() if phi is not None else None, E.cpu().numpy() if E is not None else None)
+    return out, t
+
+
+# rows of more than 32 list entries (several segments) occur in the Plummer
+# cases; leaves above 128 particles (several target rounds) at n_crit 300, 400
+@pytest.mark.parametrize("s,p,dist,n,ncrit,outs", [
+    (0, 4, "uniform", 5000, 32, "both"),
+    (0, 6, "plummer", 7000, 16, "phi"),
+    (1, 6, "uniform", 20_000, 128, "field"),
+    (1, 4, "plummer", 12_000, 24, "both"),
+    (1, 3, "uniform", 3000, 400, "both"),
+    (1, 5, "plummer", 9000, 40, "phi"),
+    (2, 5, "uniform", 9000, 64, "both"),
+    (2, 3, "plummer", 8000, 300, "field"),
+])
+def test_symmetric_p2p_matches_oracle(orc, s, p, dist, n, ncrit, outs):
+    pos, S = synth.make_system(n, s, dist, 700 + 10 * s + p)
+    wp, wf = outs in ("phi", "both"), outs in ("field", "both")
+    (phi, E), tree = run(pos, S, s, p, ncrit, 2, wp, wf)
+    t = orc.Tree(pos, ncrit)
+    t.lists(0.5)
+    phi_o, E_o = t.fmm(S, s, p)
+    from gpu_util import rel_rms
+    if wp:
+        assert rel_rms(phi, phi_o) < TOL, rel_rms(phi, phi_o)
+    else:
+        assert phi is None
+    if wf:
+        assert rel_rms(E, E_o) < TOL, rel_rms(E, E_o)
+    inf = tree.info()
+    assert inf["n_p2p"] > 0
+    tree.destroy()
+
+
+def test_symmetric_agrees_with_one_way_and_is_deterministic():
+    """200k dipoles: variant 2 against variant 1 (same sums, other order) and
+    bitwise against itself on a second evaluate and a second handle."""
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(200_000, 1, "uniform", 771)
+    (phi1, E1), t1 = run(pos, S, 1, 6, 128, 1)
+    (phi2, E2), t2 = run(pos, S, 1, 6, 128, 2)
+    assert rel_rms(E2, E1) < 1e-14 and rel_rms(phi2, phi1) < 1e-14
+    phi2b, E2b = t2.evaluate(6, 0.5)
+    (phi3, E3), t3 = run(pos, S, 1, 6, 128, 2)
+    assert np.array_equal(E2b.cpu().numpy(), E2) and np.array_equal(phi2b.cpu().numpy(), phi2)
+    assert np.array_equal(E3, E2) and np.array_equal(phi3, phi2)
+    for t in (t1, t2, t3):
+        t.destroy()
+
+
+def test_symmetric_batch_matches_alone():
+    """A system evaluated inside a batch gives the bits it gives alone."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    pos, S, off = synth.make_batch(24, 500, 6000, 1, 781, dist="plummer")
+    tb = fmm.create_tree(max_leaf=32)
+    tb.set_tuning(p2p_variant=2)
+    tb.set_sources_batch(to_dev(pos), to_dev(S), off, 1)
+    phi_b, E_b = tb.evaluate(5, 0.5)
+    torch.cuda.synchronize()
+    phi_b, E_b = phi_b.cpu().numpy(), E_b.cpu().numpy()
+    for k in (0, 7, 23):
+        a, b = int(off[k]), int(off[k + 1])
+        (phi, E), t = run(pos[a:b], S[a:b], 1, 5, 32, 2)
+        assert np.array_equal(phi, phi_b[a:b]) and np.array_equal(E, E_b[a:b])
+        t.destroy()
+    tb.destroy()
+
+
+def test_symmetric_graph_replay_and_moment_update():
+    """The captured evaluate with variant 2 replays the ordinary one bit for bit,
+    also after new moments on the same geometry."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    pos, S = synth.make_system(30_000, 1, "plummer", 791)
+    S2 = synth.sources(len(pos), 792, 1)
+    t = fmm.create_tree(max_leaf=64)
+    t.set_tuning(p2p_variant=2)
+    t.set_sources(to_dev(pos), to_dev(S), 1)
+    phi0, E0 = t.evaluate(5, 0.5)
+    phi0, E0 = phi0.cpu().numpy(), E0.cpu().numpy()
+    phi1, E1 = t.evaluate_graph(5, 0.5)
+    phi1, E1 = t.evaluate_graph(5, 0.5)
+    torch.cuda.synchronize()
+    assert np.array_equal(E1.cpu().numpy(), E0) and np.array_equal(phi1.cpu().numpy(), phi0)
+    t.update_moments(to_dev(S2))
+    _, E2 = t.evaluate_graph(5, 0.5)
+    torch.cuda.synchronize()
+    u = fmm.create_tree(max_leaf=64)
+    u.set_tuning(p2p_variant=2)
+    u.set_sources(to_dev(pos), to_dev(S2), 1)
+    _, Eu = u.evaluate(5, 0.5)
+    torch.cuda.synchronize()
+    assert np.array_equal(E2.cpu().numpy(), Eu.cpu().numpy())
+    t.destroy()
+    u.destroy()
+
+
+def test_symmetric_over_budget_takes_one_way(orc):
+    """With a budget that holds the FMM but not the reverse-term rows, variant 2
+    evaluates through variant 1 and stays correct."""
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(60_000, 1, "uniform", 801)
+    (_, E_free), tf = run(pos, S, 1, 4, 64, 2, want_phi=False)
+    held = tf.info()["device_bytes"]
+    tf.destroy()
+    (_, E1), t1 = run(pos, S, 1, 4, 64, 1, want_phi=False)
+    need1 = t1.info()["device_bytes"]
+    t1.destroy()
+    assert held > need1 + (1 << 20)          # the symmetric form holds its rows
+    (_, E), t = run(pos, S, 1, 4, 64, 2, want_phi=False, budget=need1 + (1 << 20))
+    assert np.array_equal(E, E1)             # the one-way kernel ran
+    assert rel_rms(E_free, E1) < 1e-14
+    t.destroy()
+
+
+def test_set_tuning_rejects_out_of_range():
+    from paper_2005_12351_gb300 import fmm
+    t = fmm.create_tree(max_leaf=64)
+    for kw in ({"p2p_variant": 3}, {"m2l_tensor": 2}, {"tc_chunk_rows": 0}, {"tc_chunk_rows": 65}):
+        with pytest.raises(Exception):
+            t.set_tuning(**kw)
+    t.set_tuning(p2p_variant=0, m2l_tensor=1, tc_chunk_rows=8)
+    t.set_tuning()                            # all kept
+    t.destroy()
