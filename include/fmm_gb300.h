@@ -346,6 +346,9 @@ typedef struct {
     int tc_chunk_rows;      /* key rows summed per chunk of the tensor-core M2L  */
     int candidates;         /* variants timed                                    */
     float ms_per_evaluate;  /* time of the chosen variant                        */
+    int m2l_harmonic;       /* SIMT M2L (FP64, FP32, 3xTF32 off the tensor cores)*/
+                            /* over the traceless components (§3.1): 1 (default) */
+                            /* or the full Cartesian sums: 0                     */
 } fmm_tuning;
 fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field, int reps, fmm_tuning *out);
@@ -353,8 +356,13 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
 /*
  * Applies a tuning, e.g. one fmm_autotune reported for the same workload on
  * an earlier run, without timing anything: p2p_variant 0, 1 or 2,
- * m2l_tensor 0 or 1, tc_chunk_rows in [1, 64]; a negative value keeps the
- * handle's current setting, and candidates and ms_per_evaluate are ignored.
+ * m2l_tensor 0 or 1, tc_chunk_rows in [1, 64], m2l_harmonic 0 or 1; a
+ * negative value keeps the handle's current setting, and candidates and
+ * ms_per_evaluate are ignored.  The harmonic M2L contracts only the 2k+1
+ * components of degree k with m_z <= 1 of the folded multipole and derives
+ * the L_n with n_z >= 2 from the Laplace identity D_{k+2x} + D_{k+2y} +
+ * D_{k+2z} = 0: the same sums as the full M2L up to rounding, about half the
+ * work at p = 6.
  * Variant 2 (the near field by Newton's third law, §3.1 P2P) keeps per
  * mirrored leaf pair a row of reverse terms for each source particle; where
  * those rows exceed the handle's budget, evaluates take variant 1.  The paper

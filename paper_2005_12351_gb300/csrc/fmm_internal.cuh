@@ -73,8 +73,20 @@ struct OpTables {
     std::vector<int> m2l_d16_off;        // [nL + 1], in 16-bit entries (multiples of 4)
     std::vector<int> m2l_cnt;            // [nL] kept m per n
     int m2l_split[5] = {0, 0, 0, 0, 0};  // n-range boundaries for 4 warps
+    // Harmonic M2L (D_k = grad^k 1/r is traceless: D_{k+2x} + D_{k+2y} + D_{k+2z} = 0).
+    // The M2L terms then run over the m with m_z <= 1 of the folded multipole M'
+    // and the n with n_z <= 1; the other L_n follow from the same identity.
+    bool harmonic = false;
+    int nMh = 0;                         // m kept: storage index h_rm[r], graded order
+    std::vector<int> h_rm;
+    // fold: (t, a, b) per entry, M'_t = M_t - M'_a - M'_b (a, b = t - 2x + 2z,
+    // t - 2y + 2z; -1 absent), levels of decreasing t_z, CSR over levels
+    std::vector<int> h_fold, h_fold_off;
+    // unfold: (n, a, b), L_n = -L_a - L_b (a, b = n + 2x - 2z, n + 2y - 2z),
+    // levels of increasing n_z >= 2, CSR over levels
+    std::vector<int> h_unfold, h_unfold_off;
 };
-void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads);
+void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads, bool harmonic);
 
 // Operator layout of the tensor-core M2L (FMM_3XTF32) for one (s, p).  The
 // local-expansion columns are cut into groups of at most 128 (width W); the
@@ -114,6 +126,9 @@ struct DevTables {
     // packed multi-indices nx | ny << 5 | nz << 10 | |n| << 15 (global memory:
     // lanes may index it divergently, which the constant cache would serialise)
     const int *mi;
+    // harmonic M2L (OpTables): nMh = nM and no levels when off
+    int harmonic, nMh, h_fold_lev, h_unfold_lev;
+    const int *h_rm, *h_fold, *h_fold_off, *h_unfold, *h_unfold_off;
 };
 
 __device__ __forceinline__ int mi_at(const int *mi, int k) { return __ldg(mi + k); }
@@ -162,7 +177,7 @@ struct fmm_tree {
     // D tables / operator tables
     int d_p = -1;                          // p the D table was built for
     fmm::OpTables tab;
-    int tab_key_s = -1, tab_key_p = -1, tab_key_nlo = -1;
+    int tab_key_s = -1, tab_key_p = -1, tab_key_nlo = -1, tab_key_h = -1;
     int64_t m_cells = 0;                   // rows of the M/L buffers as sized
 
     // profiling
@@ -186,6 +201,7 @@ struct fmm_tree {
     DevBuf b_hash, b_dkeys, b_D;
     DevBuf b_dsort, b_dsort_h;             // scratch of the canonical D-key numbering
     DevBuf b_M, b_L, b_phi, b_E;
+    DevBuf b_Mh, b_Mh32;                   // folded multipoles of the harmonic M2L
     DevBuf b_tab_i32, b_tab_u32;
     // mixed-precision state
     DevBuf b_o32, b_S32, b_M32, b_L32, b_D32;
@@ -217,6 +233,7 @@ struct fmm_tree {
     // tensor cores, rows per chunk of the tensor-core M2L (tc_G above)
     int p2p_variant = 2;
     bool m2l_simt = false;
+    bool m2l_harmonic = true;              // SIMT M2L over the traceless components
     bool tuned = false;
     // fmm_evaluate_graph: the evaluate of one parameter set captured as a CUDA graph
     cudaGraph_t graph = nullptr;
@@ -259,6 +276,11 @@ fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint6
 fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut);
 fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t *lut);
 fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field);
+// M' of the harmonic M2L for every cell: Mh[c][r] = fold(M[c])[h_rm[r]]
+void launch_fold_m(cudaStream_t st, const double *M, int ldM, int64_t nc, const DevTables &tb,
+                   double *Mh, int ldH);
+void launch_fold_m(cudaStream_t st, const float *M, int ldM, int64_t nc, const DevTables &tb,
+                   float *Mh, int ldH);
 // mixed.cu (FMM_FP32): scaled FP32 expansions, FP32 pair arithmetic, FP64 outputs
 fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *phi_out,
                      double *E_out);

@@ -143,6 +143,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     base.p2p_variant = t->p2p_variant;
     base.m2l_tensor = t->m2l_simt ? 0 : 1;
     base.tc_chunk_rows = t->tc_G > 0 ? t->tc_G : 16;
+    base.m2l_harmonic = t->m2l_harmonic ? 1 : 0;
     if (t->prec == FMM_FP64) {
         for (int v : {0, 1, 2}) {
             fmm_tuning c = base;
@@ -222,9 +223,11 @@ fmm_status fmm_set_tuning(fmm_tree *t, const fmm_tuning *tuning)
     if (c.m2l_tensor > 1) return fail(t, FMM_EINVAL, "m2l_tensor must be 0 or 1");
     if (c.tc_chunk_rows == 0 || c.tc_chunk_rows > 64)
         return fail(t, FMM_EINVAL, "tc_chunk_rows must be in [1, 64]");
+    if (c.m2l_harmonic > 1) return fail(t, FMM_EINVAL, "m2l_harmonic must be 0 or 1");
     drop_graph(t);
     if (c.p2p_variant >= 0) t->p2p_variant = c.p2p_variant;
     if (c.m2l_tensor >= 0) t->m2l_simt = c.m2l_tensor == 0;
+    if (c.m2l_harmonic >= 0) t->m2l_harmonic = c.m2l_harmonic == 1;
     if (c.tc_chunk_rows > 0 && t->tc_G != c.tc_chunk_rows) {
         t->tc_G = c.tc_chunk_rows;
         t->tc_plan = false;

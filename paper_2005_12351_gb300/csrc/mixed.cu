@@ -236,7 +236,8 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
     const int c = blockIdx.x;
     const int b = off[c], e = off[c + 1];
     if (b == e) return;
-    const int nM = tb.nM, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
+    // M: the kept (folded, when harmonic) scaled multipole rows, row4(nMh) per cell
+    const int nM = tb.nMh, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
     const int ldM = nM | 1, ldD = nD | 1;
     double *part = (double *)sf;                   // [slots][Tn], FP64 across batches
     float *Msm = (float *)(part + tb.m2l_slots * Tn);   // [batch][ldM]
@@ -262,7 +263,7 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
             const int dl = bdl[k];
             for (int m = tid; m < nM; m += Tn) {
                 float v = Ms[m];
-                if (dl) v = ldexpf(v, dl * (mi_shell(mi_at(tb.mi, m + tb.m0)) - tb.s));
+                if (dl) v = ldexpf(v, dl * (mi_shell(mi_at(tb.mi, tb.h_rm[m] + tb.m0)) - tb.s));
                 Msm[k * ldM + m] = v;
             }
             const float *Dk = D32 + (int64_t)bdidx[k] * row4(nD);
@@ -290,11 +291,21 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
         }
     }
     __syncthreads();
+    // nL doubles fit in the D rows (16 nD floats), 8-byte aligned: the row
+    // block before them holds an even number of floats
+    double *Ls = (double *)Dsm;
     for (int n = tid; n < tb.nL; n += Tn) {
         double v = 0.0;
         for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
-        L[(int64_t)c * tb.nL + n] = (float)v;
+        Ls[n] = v;
     }
+    for (int l = 0; l < tb.h_unfold_lev; ++l) {
+        __syncthreads();
+        for (int q = tb.h_unfold_off[l] + tid; q < tb.h_unfold_off[l + 1]; q += Tn)
+            Ls[tb.h_unfold[3 * q]] = -Ls[tb.h_unfold[3 * q + 1]] - Ls[tb.h_unfold[3 * q + 2]];
+    }
+    __syncthreads();
+    for (int n = tid; n < tb.nL; n += Tn) L[(int64_t)c * tb.nL + n] = (float)Ls[n];
 }
 
 // ------------------------------------------------------------------ L2L
@@ -680,13 +691,20 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     if (t->n_m2l > 0 && use_tc) {
         FMM_TRY(run_m2l_tc(t, p, M, row4(tb.nM), tb.nM, tb.nL, L));
     } else if (t->n_m2l > 0) {
-        const int ldM = tb.nM | 1, ldD = tb.nD | 1;
+        const float *Ms = M;
+        if (tb.harmonic) {
+            FMM_TRY(ensure(t, t->b_Mh32, 4 * (size_t)nc * row4(tb.nMh)));
+            launch_fold_m(st, M, row4(tb.nM), nc, tb, (float *)t->b_Mh32.ptr, row4(tb.nMh));
+            ++t->launches;
+            Ms = (const float *)t->b_Mh32.ptr;
+        }
+        const int ldM = tb.nMh | 1, ldD = tb.nD | 1;
         size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +
                       4 * ((size_t)kBatch * (ldM + ldD) + (size_t)tb.m2l_T * kM2LThreads);
         allow_max_dynamic_smem(k_m2l32);
         k_m2l32<<<(unsigned)nc, kM2LThreads, smem, st>>>(
             (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
-            (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr, M,
+            (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr, Ms,
             (const float *)t->b_D32.ptr, tb, L);
         ++t->launches;
     }

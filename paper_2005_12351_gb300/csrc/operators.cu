@@ -36,10 +36,10 @@ const MultiIndex &multi_index()
     return mi;
 }
 
-void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads)
+void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads, bool harmonic)
 {
     const MultiIndex &I = multi_index();
-    T.s = s; T.p = p; T.n_lo = n_lo;
+    T.s = s; T.p = p; T.n_lo = n_lo; T.harmonic = harmonic;
     T.nS = nshell(s); T.m0 = ntot(s - 1); T.nM = ntot(p + s) - T.m0; T.nL = ntot(p);
     T.nD = ntot(p + s);
     const int nK = ntot(p);                   // shift / particle monomials |k| <= p
@@ -85,17 +85,55 @@ void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads)
         T.l2p_grad[3 * k + 2] = I(I.nx[k], I.ny[k], I.nz[k] + 1);
     }
 
+    // ---- harmonic M2L (§3.1 harmonic derivatives).  Since D_{k+2x} + D_{k+2y}
+    // + D_{k+2z} = 0 for every k, a term D_{n+m} M_m with m_z >= 2 equals
+    // -(D_{n+m-2z+2x} + D_{n+m-2z+2y}) M_m, a pair of terms of the same degree
+    // |m|, hence inside the same truncation |n| + |m| <= p + s: moving M_m onto
+    // those two m (in decreasing m_z) leaves the m with m_z <= 1 only, 2k+1
+    // per degree k.  Likewise L_n with n_z >= 2 is -L_{n+2x-2z} - L_{n+2y-2z}
+    // (same degree, same m range).  The same sums, mathematically.
+    T.h_rm.clear();
+    for (int mi = 0; mi < T.nM; ++mi)
+        if (!harmonic || I.nz[mi + T.m0] <= 1) T.h_rm.push_back(mi);
+    T.nMh = (int)T.h_rm.size();
+    std::vector<int> r_of(T.nM, -1);
+    for (int r = 0; r < T.nMh; ++r) r_of[T.h_rm[r]] = r;
+    T.h_fold.clear(); T.h_fold_off.assign(1, 0);
+    T.h_unfold.clear(); T.h_unfold_off.assign(1, 0);
+    if (harmonic) {
+        for (int z = p + s - 2; z >= 0; --z) {
+            for (int mi = 0; mi < T.nM; ++mi) {
+                const int m = mi + T.m0;
+                if (I.nz[m] != z) continue;
+                const int a = I.nx[m] >= 2 ? I(I.nx[m] - 2, I.ny[m], I.nz[m] + 2) - T.m0 : -1;
+                const int b = I.ny[m] >= 2 ? I(I.nx[m], I.ny[m] - 2, I.nz[m] + 2) - T.m0 : -1;
+                if (a < 0 && b < 0) continue;
+                T.h_fold.insert(T.h_fold.end(), {mi, a, b});
+            }
+            T.h_fold_off.push_back((int)T.h_fold.size() / 3);
+        }
+        for (int z = 2; z <= p; ++z) {
+            for (int n = 0; n < T.nL; ++n) {
+                if (I.nz[n] != z) continue;
+                T.h_unfold.insert(T.h_unfold.end(), {n, I(I.nx[n] + 2, I.ny[n], z - 2),
+                                                     I(I.nx[n], I.ny[n] + 2, z - 2)});
+            }
+            T.h_unfold_off.push_back((int)T.h_unfold.size() / 3);
+        }
+    }
+
     // ---- M2L: flat (n, m) term list in n order, cut into equal per-thread
     // chunks; each maximal same-n run inside a chunk owns one partial slot.
+    // m is the position r in the kept list h_rm (all m when not harmonic).
     struct Term { int n, m, d; };
     std::vector<Term> terms;
     for (int n = 0; n < T.nL; ++n) {
         const int kn = I.nx[n] + I.ny[n] + I.nz[n];
-        if (kn < n_lo) continue;
-        for (int mi = 0; mi < T.nM; ++mi) {
-            const int m = mi + T.m0;
+        if (kn < n_lo || (harmonic && I.nz[n] > 1)) continue;
+        for (int r = 0; r < T.nMh; ++r) {
+            const int m = T.h_rm[r] + T.m0;
             if (kn + I.nx[m] + I.ny[m] + I.nz[m] > p + s) continue;
-            terms.push_back({n, mi, I(I.nx[n] + I.nx[m], I.ny[n] + I.ny[m], I.nz[n] + I.nz[m])});
+            terms.push_back({n, r, I(I.nx[n] + I.nx[m], I.ny[n] + I.ny[m], I.nz[n] + I.nz[m])});
         }
     }
     const int W = (int)terms.size(), Tn = m2l_threads;
@@ -363,6 +401,33 @@ __device__ __forceinline__ double scale_pow2(double x, int e)
     return (b & 0x7ff0000000000000ll) ? __longlong_as_double(b + ((long long)e << 52)) : x;
 }
 
+// One warp per cell: the row of M in shared memory (FP64), the fold levels of
+// the harmonic M2L in order (an entry reads only entries of the level two
+// z-steps up, final by then), the kept entries written in graded order.
+template <typename Tm>
+__global__ void __launch_bounds__(128)
+k_fold_m(const Tm *M, int ldM, int64_t nc, DevTables tb, Tm *Mh, int ldH)
+{
+    extern __shared__ double fsm[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = blockIdx.x * 4ll + w;
+    if (c >= nc) return;                 // whole warps; no block barrier below
+    double *v = fsm + w * tb.nM;
+    for (int m = lane; m < tb.nM; m += 32) v[m] = (double)M[c * ldM + m];
+    __syncwarp();
+    for (int l = 0; l < tb.h_fold_lev; ++l) {
+        for (int q = tb.h_fold_off[l] + lane; q < tb.h_fold_off[l + 1]; q += 32) {
+            const int i = tb.h_fold[3 * q], a = tb.h_fold[3 * q + 1], b = tb.h_fold[3 * q + 2];
+            double x = v[i];
+            if (a >= 0) x -= v[a];
+            if (b >= 0) x -= v[b];
+            v[i] = x;
+        }
+        __syncwarp();
+    }
+    for (int r = lane; r < tb.nMh; r += 32) Mh[c * ldH + r] = (Tm)v[tb.h_rm[r]];
+}
+
 __global__ void __launch_bounds__(kM2LThreads)
 k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t *level,
       const int32_t *sys, const int *e_side, const double *M, const double *D, DevTables tb,
@@ -372,7 +437,8 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t
     const int c = blockIdx.x;
     const int b = off[c], e = off[c + 1];
     if (b == e) return;
-    const int nM = tb.nM, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
+    // M: the kept (folded, when harmonic) multipole rows, nMh per cell
+    const int nM = tb.nMh, nD = tb.nD, T = tb.m2l_T, Tn = kM2LThreads;
     const int ldM = nM | 1, ldD = nD | 1;              // odd strides spread banks
     double *Msm = sm;                                  // [batch][ldM]
     double *Dsm = Msm + kM2LBatch * ldM;               // [batch][ldD]
@@ -424,11 +490,19 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t
         }
     }
     __syncthreads();
+    double *Ls = Dsm;                      // nL <= nD: the D rows are done with
     for (int n = tid; n < tb.nL; n += Tn) {
         double v = 0.0;
         for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
-        L[(int64_t)c * tb.nL + n] = v;
+        Ls[n] = v;
     }
+    for (int l = 0; l < tb.h_unfold_lev; ++l) {
+        __syncthreads();
+        for (int q = tb.h_unfold_off[l] + tid; q < tb.h_unfold_off[l + 1]; q += Tn)
+            Ls[tb.h_unfold[3 * q]] = -Ls[tb.h_unfold[3 * q + 1]] - Ls[tb.h_unfold[3 * q + 2]];
+    }
+    __syncthreads();
+    for (int n = tid; n < tb.nL; n += Tn) L[(int64_t)c * tb.nL + n] = Ls[n];
 }
 
 // ------------------------------------------------------------------ L2L
@@ -539,8 +613,10 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         buf.push_back(0);
         return o;
     };
-    const bool rebuild = !(t->tab_key_s == s && t->tab_key_p == p && t->tab_key_nlo == n_lo);
-    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreadsShared);
+    const int h = t->m2l_harmonic ? 1 : 0;
+    const bool rebuild = !(t->tab_key_s == s && t->tab_key_p == p && t->tab_key_nlo == n_lo &&
+                           t->tab_key_h == h);
+    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreadsShared, h != 0);
     {
         const MultiIndex &I = multi_index();
         std::vector<int> lutv((kMaxOrder + 1) * (kMaxOrder + 1) * (kMaxOrder + 1));
@@ -554,6 +630,8 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     const size_t o_runoff = put(T.m2l_run_off);
     const size_t o_d16off = put(T.m2l_d16_off);
     const size_t o_cnt = put(T.m2l_cnt);
+    const size_t o_hrm = put(T.h_rm), o_hf = put(T.h_fold), o_hfo = put(T.h_fold_off);
+    const size_t o_hu = put(T.h_unfold), o_huo = put(T.h_unfold_off);
     size_t o_mi;
     {
         const MultiIndex &I = multi_index();
@@ -578,7 +656,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         FMM_TRY(cuda_check(t, cudaMemcpyAsync((uint32_t *)t->b_tab_u32.ptr + w_d16,
                                               T.m2l_d16.data(), 4 * T.m2l_d16.size(),
                                               cudaMemcpyHostToDevice, t->stream), "tables"));
-        t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo;
+        t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo; t->tab_key_h = h;
     }
     const int32_t *B = (const int32_t *)t->b_tab_i32.ptr;
     dt->s = s; dt->p = p; dt->n_lo = n_lo; dt->nS = T.nS; dt->nM = T.nM; dt->nL = T.nL;
@@ -597,6 +675,12 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     dt->m2l_cnt = B + o_cnt;
     for (int w = 0; w < 5; ++w) dt->m2l_split[w] = T.m2l_split[w];
     dt->m2l_nterms = (int)T.m2l_terms.size();
+    dt->harmonic = T.harmonic ? 1 : 0;
+    dt->nMh = T.nMh;
+    dt->h_fold_lev = (int)T.h_fold_off.size() - 1;
+    dt->h_unfold_lev = (int)T.h_unfold_off.size() - 1;
+    dt->h_rm = B + o_hrm; dt->h_fold = B + o_hf; dt->h_fold_off = B + o_hfo;
+    dt->h_unfold = B + o_hu; dt->h_unfold_off = B + o_huo;
     *lut = B + o_lut;
     return FMM_OK;
 }
@@ -609,6 +693,20 @@ void record(fmm_tree *t, int i)
 }
 
 }  // namespace
+
+void launch_fold_m(cudaStream_t st, const double *M, int ldM, int64_t nc, const DevTables &tb,
+                   double *Mh, int ldH)
+{
+    if (nc > 0)
+        k_fold_m<double><<<(unsigned)((nc + 3) / 4), 128, 32 * (size_t)tb.nM, st>>>(M, ldM, nc, tb, Mh, ldH);
+}
+
+void launch_fold_m(cudaStream_t st, const float *M, int ldM, int64_t nc, const DevTables &tb,
+                   float *Mh, int ldH)
+{
+    if (nc > 0)
+        k_fold_m<float><<<(unsigned)((nc + 3) / 4), 128, 32 * (size_t)tb.nM, st>>>(M, ldM, nc, tb, Mh, ldH);
+}
 
 // derivative tables, one FP64 row per distinct M2L offset key
 fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t *lut)
@@ -671,17 +769,24 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
         }
     }
     record(t, 8);
-    // M2L over the stored lists
+    // M2L over the stored lists (harmonic: on the folded multipoles)
     cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nL, st);
     if (t->n_m2l > 0) {
-        const int ldM = tb.nM | 1, ldD = tb.nD | 1;
+        const double *Ms = M;
+        if (tb.harmonic) {
+            FMM_TRY(ensure(t, t->b_Mh, 8 * (size_t)nc * tb.nMh));
+            launch_fold_m(st, M, tb.nM, nc, tb, (double *)t->b_Mh.ptr, tb.nMh);
+            ++t->launches;
+            Ms = (const double *)t->b_Mh.ptr;
+        }
+        const int ldM = tb.nMh | 1, ldD = tb.nD | 1;
         size_t fixed = 8 * (size_t)tb.m2l_slots * kM2LThreads + 4 * (size_t)tb.m2l_T * kM2LThreads;
         size_t smem = fixed + 8 * (size_t)kM2LBatch * (ldM + ldD);
         allow_max_dynamic_smem(k_m2l);
         k_m2l<<<(unsigned)nc, kM2LThreads, smem, st>>>(
             (const int32_t *)t->b_m2l_off.ptr, (const int32_t *)t->b_m2l_src.ptr,
             (const int32_t *)t->b_m2l_didx.ptr, (const int32_t *)t->b_level.ptr,
-            (const int32_t *)t->b_sys.ptr, t->sys_eside_dev(), M, (const double *)t->b_D.ptr, tb, L);
+            (const int32_t *)t->b_sys.ptr, t->sys_eside_dev(), Ms, (const double *)t->b_D.ptr, tb, L);
         ++t->launches;
     }
     record(t, 9);
