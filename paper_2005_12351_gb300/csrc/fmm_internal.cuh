@@ -98,6 +98,10 @@ void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads, bool har
 // (offset | 1 << 30 for a lo half).
 struct TcLayout {
     int s = -1, p = -1, nkb = 0, Np = 0, ngroups = 0, E = 0, b_stage = 0, img_bytes = 0;
+    // h = 1: the harmonic M2L (K over the kept m of the folded multipole,
+    // columns over the n with n_z <= 1); col_n = full local index per column
+    int h = -1, ncol = 0;
+    std::vector<int> col_n;
     int g_width[2] = {0, 0}, g_nkb[2] = {0, 0}, g_nkc[2] = {0, 0};
     std::vector<int> kb_n;        // [nkb] columns a K-block reaches (from column 0)
     std::vector<int> img_off;     // [2 x (nkb + 1)] byte offset of block (g, kb) in an image
@@ -292,7 +296,10 @@ bool tc_usable(fmm_tree *t, int s, int p);
 // when they do not fit the handle's budget); tc_release frees all of it
 fmm_status tc_prepare(fmm_tree *t, int p);
 void tc_release(fmm_tree *t);
-fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L);
+// (M: folded multipoles, nM = tb.nMh columns, when the handle's M2L is harmonic;
+// tb supplies the unfold of L)
+fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL,
+                      const DevTables &tb, float *L);
 // api.cu: the compute of an evaluate whose lists are current (no host sync)
 fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E);
 // graph.cu: drop a captured evaluate graph (the tree or the tuning changed)

@@ -487,21 +487,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
     if (tid == 0 && *abort) atomicOr(a.err, (unsigned)kErrTcTimeout);
 }
 
-// L~_t[n] = sum of the tile's chunk partials of target t, in FP64, in chunk order
-// (NaN everywhere if a wait of the M2L block gave up: the failure shows in the output)
+// L~_t[col_n[col]] = sum of the tile's chunk partials of target t in column col,
+// in FP64, in chunk order; for the harmonic M2L the other L~_n follow by the
+// unfold levels (L_n = -L_a - L_b).  NaN everywhere if a wait of the M2L block
+// gave up: the failure shows in the output.
 __global__ void k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile_chunk_off,
-                            const float *partial, int Np, int nL, const unsigned *err, float *L)
+                            const float *partial, int Np, int ncol, const int32_t *col_n, int nL,
+                            const int *uf, const int *uf_off, int uf_lev, const unsigned *err,
+                            float *L)
 {
+    __shared__ double Ls[kMaxTot];
     const int q = blockIdx.x;
     if (q >= T) return;
     const bool bad = (*err & kErrTcTimeout) != 0;
     const int tile = q >> 7, lane = q & 127, c = tile_tgt[q];
     const int j0 = (int)tile_chunk_off[tile], j1 = (int)tile_chunk_off[tile + 1];
-    for (int n = threadIdx.x; n < nL; n += blockDim.x) {
+    for (int n = threadIdx.x; n < nL; n += blockDim.x) Ls[n] = 0.0;
+    __syncthreads();
+    for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
         double v = 0.0;
-        for (int j = j0; j < j1; ++j) v += (double)partial[((size_t)j * 128 + lane) * Np + n];
-        L[(size_t)c * nL + n] = bad ? __int_as_float(0x7fc00000) : (float)v;
+        for (int j = j0; j < j1; ++j) v += (double)partial[((size_t)j * 128 + lane) * Np + col];
+        Ls[col_n[col]] = v;
     }
+    for (int l = 0; l < uf_lev; ++l) {
+        __syncthreads();
+        for (int u = uf_off[l] + threadIdx.x; u < uf_off[l + 1]; u += blockDim.x)
+            Ls[uf[3 * u]] = -Ls[uf[3 * u + 1]] - Ls[uf[3 * u + 2]];
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < nL; n += blockDim.x)
+        L[(size_t)c * nL + n] = bad ? __int_as_float(0x7fc00000) : (float)Ls[n];
 }
 
 // ------------------------------------------------------------ the plan
@@ -671,17 +686,32 @@ int tc_raw_stages(int b_stage)
     return 0;
 }
 
-void build_layout(TcLayout &Ly, int s, int p)
+void build_layout(TcLayout &Ly, int s, int p, int h)
 {
     const MultiIndex &I = multi_index();
     auto shell = [&](int k) { return I.nx[k] + I.ny[k] + I.nz[k]; };
-    const int m0 = ntot(s - 1), nM = ntot(p + s) - m0, nL = ntot(p);
+    const int m0 = ntot(s - 1);
+    // K runs over the kept multipoles, columns over the kept locals, both in
+    // graded order (all of them, or those with z-index <= 1 when harmonic)
+    std::vector<int> ms, ns;
+    for (int k = m0; k < ntot(p + s); ++k)
+        if (!h || I.nz[k] <= 1) ms.push_back(k);
+    for (int n = 0; n < ntot(p); ++n)
+        if (!h || I.nz[n] <= 1) ns.push_back(n);
+    const int nM = (int)ms.size(), nL = (int)ns.size();
     Ly.s = s;
     Ly.p = p;
+    Ly.h = h;
+    Ly.ncol = nL;
+    Ly.col_n = ns;
     Ly.nkb = (nM + 7) / 8;
     Ly.kb_n.assign(Ly.nkb, 0);
-    for (int kb = 0; kb < Ly.nkb; ++kb)   // graded order: a block's first multipole has its lowest order
-        Ly.kb_n[kb] = up16(ntot(p + s - shell(m0 + 8 * kb)));
+    for (int kb = 0; kb < Ly.nkb; ++kb) {  // a block's first multipole has its lowest order
+        const int reach = p + s - shell(ms[8 * kb]);
+        int cnt = 0;                        // the columns of order <= reach: a prefix
+        while (cnt < nL && shell(ns[cnt]) <= reach) ++cnt;
+        Ly.kb_n[kb] = up16(cnt);
+    }
     Ly.Np = Ly.kb_n[0];
     Ly.ngroups = Ly.Np > 128 ? 2 : 1;
     Ly.img_off.assign(2 * (Ly.nkb + 1), 0);
@@ -718,9 +748,9 @@ void build_layout(TcLayout &Ly, int s, int p)
                     const bool lo = row >= W;
                     Ly.el_pos[e] = pos | (lo ? 1 << 30 : 0);
                     if (row >= N && !lo) continue;               // zero rows between the halves
-                    const int n = c0 + (lo ? row - W : row), m = 8 * kb + k;
-                    if (m >= nM || n >= nL) continue;
-                    const int gm = m0 + m, tot = shell(n) + shell(gm);
+                    const int col = c0 + (lo ? row - W : row), m = 8 * kb + k;
+                    if (m >= nM || col >= nL) continue;
+                    const int n = ns[col], gm = ms[m], tot = shell(n) + shell(gm);
                     if (tot > p + s) continue;
                     const int d = I(I.nx[n] + I.nx[gm], I.ny[n] + I.ny[gm], I.nz[n] + I.nz[gm]);
                     Ly.el_src[e] = d | tot << 16 | (shell(gm) - s) << 24;
@@ -826,7 +856,11 @@ fmm_status build_plan(fmm_tree *t)
 
 bool tc_usable(fmm_tree *t, int s, int p)
 {
-    if (t->tc_lay.s != s || t->tc_lay.p != p) build_layout(t->tc_lay, s, p);
+    const int h = t->m2l_harmonic ? 1 : 0;
+    if (t->tc_lay.s != s || t->tc_lay.p != p || t->tc_lay.h != h) {
+        build_layout(t->tc_lay, s, p, h);
+        t->tc_img_p = -1;                   // images and element maps of the old layout
+    }
     const TcLayout &L = t->tc_lay;
     return L.Np <= 256 && L.nkb <= kTcMaxKB && tc_raw_stages(L.b_stage) >= 3;
 }
@@ -849,11 +883,13 @@ fmm_status tc_prepare(fmm_tree *t, int p)
     if (t->tc_chunks == 0) return FMM_OK;
     const long long stride = Ly.img_bytes;
     if (t->tc_img_p != p) {
-        FMM_TRY(ensure(t, t->b_tc_el, 8 * (size_t)Ly.E));
+        FMM_TRY(ensure(t, t->b_tc_el, 4 * (2 * (size_t)Ly.E + Ly.ncol)));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tc_el.ptr, Ly.el_src.data(), 4 * (size_t)Ly.E,
                                               cudaMemcpyHostToDevice, st), "upload"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync((int32_t *)t->b_tc_el.ptr + Ly.E, Ly.el_pos.data(),
                                               4 * (size_t)Ly.E, cudaMemcpyHostToDevice, st), "upload"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync((int32_t *)t->b_tc_el.ptr + 2 * Ly.E, Ly.col_n.data(),
+                                              4 * (size_t)Ly.ncol, cudaMemcpyHostToDevice, st), "upload"));
         FMM_TRY(ensure(t, t->b_tc_img, (size_t)t->n_doff * stride));
         k_tc_images<<<gridn(t->n_doff * Ly.E, 256), 256, 0, st>>>(
             t->n_doff, Ly.E, (const uint64_t *)t->b_dkeys.ptr, (const double *)t->b_D.ptr, ntot(p + t->s),
@@ -865,10 +901,15 @@ fmm_status tc_prepare(fmm_tree *t, int p)
     return ensure(t, t->b_tc_part, 4 * (size_t)t->tc_chunks * 128 * Ly.Np);
 }
 
-fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL, float *L)
+fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL,
+                      const DevTables &tb, float *L)
 {
     cudaStream_t st = t->stream;
     const TcLayout &Ly = t->tc_lay;
+    if ((Ly.h == 1) != (tb.harmonic == 1) || nM != tb.nMh) {
+        t->err = "tensor-core M2L: layout and tables disagree";
+        return FMM_EINVAL;                   // not reachable: both follow the handle's flag
+    }
     if (!t->tc_plan || t->tc_img_p != p) FMM_TRY(tc_prepare(t, p));
     if (t->tc_chunks == 0) return FMM_OK;
     const long long stride = Ly.img_bytes;
@@ -923,9 +964,10 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
     case 4: go(k_m2l_tc<4>); break;
     default: go(k_m2l_tc<3>); break;
     }
-    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, st>>>((int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr,
-                                                   (const uint32_t *)t->b_tc_coff.ptr, (const float *)t->b_tc_part.ptr,
-                                                   Ly.Np, nL, err, L);
+    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, st>>>(
+        (int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr, (const uint32_t *)t->b_tc_coff.ptr,
+        (const float *)t->b_tc_part.ptr, Ly.Np, Ly.ncol, (const int32_t *)t->b_tc_el.ptr + 2 * Ly.E, nL,
+        tb.h_unfold, tb.h_unfold_off, tb.h_unfold_lev, err, L);
     t->launches += 2;
     return cuda_check(t, cudaGetLastError(), "tensor-core M2L");
 }

@@ -688,16 +688,17 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     }
     record(t, 8);
     cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nL, st);
+    // harmonic M2L: the folded multipoles, for either M2L
+    const float *Ms = M;
+    if (t->n_m2l > 0 && tb.harmonic) {
+        FMM_TRY(ensure(t, t->b_Mh32, 4 * (size_t)nc * row4(tb.nMh)));
+        launch_fold_m(st, M, row4(tb.nM), nc, tb, (float *)t->b_Mh32.ptr, row4(tb.nMh));
+        ++t->launches;
+        Ms = (const float *)t->b_Mh32.ptr;
+    }
     if (t->n_m2l > 0 && use_tc) {
-        FMM_TRY(run_m2l_tc(t, p, M, row4(tb.nM), tb.nM, tb.nL, L));
+        FMM_TRY(run_m2l_tc(t, p, Ms, row4(tb.nMh), tb.nMh, tb.nL, tb, L));
     } else if (t->n_m2l > 0) {
-        const float *Ms = M;
-        if (tb.harmonic) {
-            FMM_TRY(ensure(t, t->b_Mh32, 4 * (size_t)nc * row4(tb.nMh)));
-            launch_fold_m(st, M, row4(tb.nM), nc, tb, (float *)t->b_Mh32.ptr, row4(tb.nMh));
-            ++t->launches;
-            Ms = (const float *)t->b_Mh32.ptr;
-        }
         const int ldM = tb.nMh | 1, ldD = tb.nD | 1;
         size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +
                       4 * ((size_t)kBatch * (ldM + ldD) + (size_t)tb.m2l_T * kM2LThreads);

@@ -21,11 +21,12 @@ from paper_2005_12351_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True):
+def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True, harmonic=1):
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
     tree = fmm.create_tree(max_leaf=ncrit, precision=precision)
+    tree.set_tuning(m2l_harmonic=harmonic)
     tree.set_sources(to_dev(pos), to_dev(S), s)
     phi, E = tree.evaluate(p, theta, want_phi, want_field)
     torch.cuda.synchronize()
@@ -126,18 +127,22 @@ def test_fp32_edge_cases(precision):
     assert phi.numel() == 0
 
 
-@pytest.mark.parametrize("s,p,dist,n", [(1, 6, "uniform", 60_000), (2, 5, "plummer", 40_000),
-                                         (0, 9, "plummer", 30_000), (1, 10, "uniform", 20_000)])
-def test_3xtf32_matches_fp32_form(s, p, dist, n):
+@pytest.mark.parametrize("s,p,dist,n,h", [(1, 6, "uniform", 60_000, 1), (2, 5, "plummer", 40_000, 1),
+                                           (0, 9, "plummer", 30_000, 1), (1, 11, "uniform", 20_000, 1),
+                                           (1, 6, "uniform", 60_000, 0), (1, 9, "uniform", 20_000, 0),
+                                           (1, 10, "uniform", 20_000, 0)])
+def test_3xtf32_matches_fp32_form(s, p, dist, n, h):
     """Both mixed forms round the same scaled FP32 expansions; their results agree
     to FP32 rounding: the field within 1e-6, the potential (whose local term sums
     ~10^2 contributions of mixed sign per key row in tensor-core FP32) within 2e-6.
-    p=10, s=1 has n_L = 286 > 256 and takes the SIMT M2L."""
+    Harmonic M2L (h=1): the tensor-core columns are the (p+1)^2 locals with
+    n_z <= 1, two column groups from p = 11.  Full M2L (h=0): two column groups
+    at p = 9; p = 10 has n_L = 286 > 256 and takes the SIMT M2L."""
     from gpu_util import rel_rms
     pos, S = synth.make_system(n, s, dist, 900 + s + p)
-    (phi_a, E_a), ta = gpu_eval(pos, S, s, p, 0.5, 64, "fp32")
-    (phi_b, E_b), tb = gpu_eval(pos, S, s, p, 0.5, 64, "3xtf32")
-    if p < 10:
+    (phi_a, E_a), ta = gpu_eval(pos, S, s, p, 0.5, 64, "fp32", harmonic=h)
+    (phi_b, E_b), tb = gpu_eval(pos, S, s, p, 0.5, 64, "3xtf32", harmonic=h)
+    if h == 1 or p < 10:
         assert_tc_ran(tb, "3xtf32")
     else:
         assert tb.info()["tc_rows"] == 0
