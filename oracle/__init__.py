@@ -75,6 +75,10 @@ def lib():
             L.orc_fmm.argtypes = [C.c_void_p, _f64p, C.c_int, C.c_int, _f64p, C.c_int64,
                                   C.c_void_p, _f64p, _f64p]
             L.orc_fmm.restype = C.c_int
+            L.orc_m2p.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p]
+            L.orc_bh.argtypes = [C.c_void_p, _f64p, C.c_int, C.c_int, _f64p, C.c_double,
+                                 C.c_int64, C.c_void_p, _f64p, _f64p]
+            L.orc_bh.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -147,6 +151,13 @@ def l2p(p, z, L, x):
     phi, g = np.zeros(1), np.zeros(3)
     lib().orc_l2p(p, _f64(z), _f64(L), _f64(x), phi, g)
     return phi[0], g
+
+
+def m2p(s, p, z, M, x):
+    """Multipole of order p (s <= |m| <= p) at centre z evaluated at x: (phi, grad phi)."""
+    f, g = np.zeros(1), np.zeros(3)
+    lib().orc_m2p(s, p, _f64(z), _f64(M), _f64(x), f, g)
+    return float(f[0]), g
 
 
 def p2p_pair(s, xt, xs, S):
@@ -233,10 +244,30 @@ class Tree:
             raise ValueError("oracle FMM rejected s=%d p=%d" % (s, p))
         return phi, E
 
+    def bh(self, S, s: int, p: int, theta: float, targets=None):
+        """FP64 multipolar Barnes-Hut on this tree (order p, opening angle theta):
+        (phi, E) at ``targets`` (original indices)."""
+        S = _f64(S)
+        if targets is None:
+            nt, tp = self.n, None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            nt, tp = len(targets), targets.ctypes.data
+        phi, E = np.zeros(nt), np.zeros((nt, 3))
+        rc = lib().orc_bh(self._h, self.pos.ravel(), s, p, S.ravel(), float(theta), nt, tp, phi,
+                          E.reshape(-1))
+        if rc != 0:
+            raise ValueError("oracle BH rejected s=%d p=%d theta=%g" % (s, p, theta))
+        return phi, E
+
     def __del__(self):
         h, self._h = getattr(self, "_h", None), None
         if h and _lib is not None:
             _lib.orc_tree_free(h)
+
+
+def bh(pos, S, s, p, theta, ncrit, targets=None):
+    return Tree(pos, ncrit).bh(S, s, p, theta, targets)
 
 
 def fmm(pos, S, s, p, theta, ncrit, targets=None):

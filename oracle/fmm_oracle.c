@@ -671,6 +671,115 @@ int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const doubl
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Multipolar Barnes-Hut (§2 multipole potential; §3.2 Methods).             */
+/* M2P: phi(x) = sum_{s <= |m| <= p} M_m D_m(x - z) and grad phi(x) =         */
+/* sum M_m D_{m + e_k}(x - z): the multipole sum of order p that the paper's  */
+/* BH formula runs over (|n| from s to p), differentiated exactly.  The       */
+/* multipoles s <= |m| <= p are those of the FMM storage at order p - s.      */
+/* ------------------------------------------------------------------------ */
+void orc_m2p(int s, int p, const double z[3], const double *M, const double x[3], double *phi,
+             double grad[3])
+{
+    make_tables();
+    double R[3] = {x[0] - z[0], x[1] - z[1], x[2] - z[2]};
+    int m0 = orc_ntot(s - 1), nM = orc_ntot(p) - m0;
+    double *D = malloc(sizeof(double) * orc_ntot(p + 1));
+    orc_derivatives(R[0], R[1], R[2], p + 1, D);
+    *phi = 0.0; grad[0] = grad[1] = grad[2] = 0.0;
+    for (int mi = 0; mi < nM; ++mi) {
+        int m = mi + m0;
+        *phi += M[mi] * D[m];
+        grad[0] += M[mi] * D[orc_index(IX[m] + 1, IY[m], IZ[m])];
+        grad[1] += M[mi] * D[orc_index(IX[m], IY[m] + 1, IZ[m])];
+        grad[2] += M[mi] * D[orc_index(IX[m], IY[m], IZ[m] + 1)];
+    }
+    free(D);
+}
+
+typedef struct {
+    const orc_tree *t;
+    const double *pos, *S, *M;
+    int s, p, nM, nS;
+    double theta2;
+} bh_ctx;
+
+/* The walk of one target from cell c down (§3.2): a cell with
+ * r_cell^2 < theta^2 |x - x_c|^2 (r_cell = half side, strict) is taken by
+ * M2P; otherwise a leaf by P2P with its particles (the target itself and
+ * coincident points excluded), otherwise its children in order. */
+static void bh_walk(const bh_ctx *b, int64_t c, int64_t self, const double x[3], double *f,
+                    double g[3])
+{
+    const orc_tree *t = b->t;
+    const double *zc = t->centre + 3 * c;
+    double d0 = x[0] - zc[0], d1 = x[1] - zc[1], d2 = x[2] - zc[2];
+    double dd = d0 * d0 + d1 * d1 + d2 * d2;
+    double h = t->halfw[c];
+    if (h * h < b->theta2 * dd) {
+        double pf, pg[3];
+        orc_m2p(b->s, b->p, zc, b->M + (size_t)b->nM * c, x, &pf, pg);
+        *f += pf; g[0] += pg[0]; g[1] += pg[1]; g[2] += pg[2];
+        return;
+    }
+    if (t->nchild[c] == 0) {
+        for (int64_t j = t->begin[c]; j < t->end[c]; ++j) {
+            if (j == self) continue;
+            double pf, pg[3];
+            orc_p2p_pair(b->s, x, b->pos + 3 * j, b->S + (size_t)b->nS * j, &pf, pg);
+            *f += pf; g[0] += pg[0]; g[1] += pg[1]; g[2] += pg[2];
+        }
+        return;
+    }
+    for (int i = 0; i < t->nchild[c]; ++i) bh_walk(b, t->child_first[c] + i, self, x, f, g);
+}
+
+/* Barnes-Hut on the tree: P2M at the leaves and M2M upward (order p - s,
+ * i.e. s <= |m| <= p), then one walk from the root per requested target. */
+int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double *S_orig,
+           double theta, int64_t ntarget, const int64_t *targets, double *phi, double *E)
+{
+    make_tables();
+    if (s < 0 || p < s || p + 1 > ORC_MAXORD || !(theta >= 0.0)) return -1;
+    int64_t n = t->n, nc = t->ncells;
+    if (n == 0 || ntarget == 0) return 0;
+    int pt = p - s, nM = orc_n_multipole(s, pt), nS = orc_ntot(s) - orc_ntot(s - 1);
+    double *pos = malloc(sizeof(double) * 3 * n), *S = malloc(sizeof(double) * nS * n);
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t o = t->perm[k];
+        for (int d = 0; d < 3; ++d) pos[3 * k + d] = pos_orig[3 * o + d];
+        for (int a = 0; a < nS; ++a) S[nS * k + a] = S_orig[nS * o + a];
+    }
+    double *M = calloc((size_t)nc * nM, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < nc; ++c)
+        if (t->nchild[c] == 0)
+            orc_p2m(s, pt, t->centre + 3 * c, t->end[c] - t->begin[c], pos + 3 * t->begin[c],
+                    S + nS * t->begin[c], M + (size_t)nM * c);
+    for (int l = t->nlevels - 2; l >= 0; --l) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = t->level_begin[l]; c < t->level_begin[l + 1]; ++c)
+            for (int i = 0; i < t->nchild[c]; ++i) {
+                int64_t ch = t->child_first[c] + i;
+                orc_m2m(s, pt, t->centre + 3 * ch, t->centre + 3 * c, M + (size_t)nM * ch,
+                        M + (size_t)nM * c);
+            }
+    }
+    int64_t *rank = malloc(sizeof(int64_t) * n);
+    for (int64_t k = 0; k < n; ++k) rank[t->perm[k]] = k;
+    bh_ctx b = {t, pos, S, M, s, p, nM, nS, theta * theta};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < ntarget; ++q) {
+        int64_t k = rank[targets ? targets[q] : q];
+        double f = 0.0, g[3] = {0.0, 0.0, 0.0};
+        bh_walk(&b, 0, k, pos + 3 * k, &f, g);
+        phi[q] = f;
+        E[3 * q] = -g[0]; E[3 * q + 1] = -g[1]; E[3 * q + 2] = -g[2];
+    }
+    free(pos); free(S); free(M); free(rank);
+    return 0;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
