@@ -136,6 +136,24 @@ fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const dou
 fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field);
 
+/*
+ * Multipolar Barnes-Hut (§2 multipole potential; §3.2 Methods) on the
+ * current tree: multipoles of order p (s <= |m| <= p) by P2M at the leaves
+ * and M2M upward, then for every particle a walk from its system's root: a
+ * cell with r_cell^2 < theta^2 |x_p - x_c|^2 (r_cell = half the cell side,
+ * strict) contributes by M2P, phi += sum_m M_m D_m(x_p - x_c) and
+ * E -= sum_m M_m D_{m+e_k}(x_p - x_c) (the exact gradient of that sum); a
+ * leaf that fails contributes its particles directly (P2P, the particle
+ * itself and coincident points excluded); any other cell that fails is
+ * opened.  FP64 whatever the handle's precision; theta = 0 opens every cell
+ * (the direct sum).  Outputs as fmm_evaluate (device pointers, the caller's
+ * order).  FMM_EORDER unless s <= p <= 12; FMM_EINVAL for theta < 0 or not
+ * finite.  Replaces the multipole arrays of the handle (copy_array); a
+ * captured fmm_evaluate_graph is dropped.
+ */
+fmm_status fmm_evaluate_bh(fmm_tree *t, int p, double theta, int want_potential, int want_field,
+                           double *potential, double *field);
+
 /* Release all device memory of the handle.  NULL is accepted. */
 fmm_status fmm_destroy(fmm_tree *t);
 

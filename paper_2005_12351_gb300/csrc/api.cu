@@ -113,7 +113,7 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
                    &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
                    &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
-                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32};
+                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
 }
 
@@ -304,6 +304,24 @@ fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, in
         for (int i = 3; i <= 10; ++i) cudaEventElapsedTime(&t->phase_ms[i], t->ev[i + 1], t->ev[i + 2]);
     }
     return FMM_OK;
+}
+
+fmm_status fmm_evaluate_bh(fmm_tree *t, int p, double theta, int want_potential, int want_field,
+                           double *potential, double *field)
+{
+    if (!t) return FMM_EINVAL;
+    t->err.clear();
+    if (!t->have_sources) return fail(t, FMM_ESTATE, "fmm_set_sources has not succeeded");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(t, FMM_EINVAL, "theta must be finite and >= 0");
+    if (!want_potential && !want_field) return fail(t, FMM_EINVAL, "nothing requested");
+    if (p < t->s || p > FMM_MAX_TOTAL_ORDER)
+        return fail(t, FMM_EORDER, "need s <= p <= 12 for the Barnes-Hut multipoles");
+    if (t->n == 0) return FMM_OK;
+    if ((want_potential && !potential) || (want_field && !field))
+        return fail(t, FMM_EINVAL, "NULL output for a requested quantity");
+    DeviceGuard g(t->device);
+    drop_graph(t);                       // the tables a captured evaluate reads change here
+    return run_bh(t, p, theta, want_potential, want_field, potential, field);
 }
 
 fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *o)

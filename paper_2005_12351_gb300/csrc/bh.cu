@@ -1,0 +1,259 @@
+// bh.cu -- multipolar Barnes-Hut (§2 multipole potential; §3.2 Methods), FP64.
+//
+// Multipoles of order p (s <= |m| <= p: the P2M/M2M of the FMM storage at
+// order p - s), then for every target a walk from its system's root: a cell
+// with r_cell^2 < theta^2 |x - x_c|^2 (r_cell = half side, strict) is taken by
+// M2P, phi += sum_m M_m D_m(x - z_c), E -= sum_m M_m D_{m+e_k}(x - z_c); a
+// failing leaf by P2P with its particles; a failing inner cell is opened.
+//
+// One warp walks 32 consecutive targets of the sorted order (neighbours in
+// space) together: a shared stack of (cell, lanes) entries, where "lanes" are
+// the targets for which the cell is reached (their walks opened its parent).
+// Each lane takes its own MAC decision, so every target sees exactly its own
+// walk; a cell is visited once for all the lanes that reach it.  The MAC is
+// evaluated with explicitly rounded operations (no contraction), in the order
+// ((dx dx + dy dy) + dz dz), so the decisions are those of a plain FP64 program.
+#include <algorithm>
+#include <vector>
+
+#include "fmm_internal.cuh"
+#include "pair.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kBHMaxWarps = 4;
+// pending roots (<= 31) + 7 per level (pop one, push <= 8) over 21 levels + 8
+constexpr int kBHStack = 256;
+
+struct BHArgs {
+    int64_t n;
+    int nsys, nM, nD;
+    double theta2;
+    const int32_t *nchild, *child, *begin, *end;
+    const double *centre, *half;
+    const double *px, *py, *pz, *Sm;
+    const int32_t *perm;
+    const double *M;
+    const int4 *mt;          // per multipole term: D index of m, m + e_x, m + e_y, m + e_z
+    const int *mi;           // packed multi-indices of the graded order
+    const int32_t *lut;      // (nx, ny, nz) -> graded index, stride kMaxOrder + 1
+    double *phi_out, *E_out;
+};
+
+// D_n(R) = grad^n (1/|R|) for the graded indices 0 .. nD-1 into D[32 k] (this
+// lane's column of its warp's rows), by the recurrence of the D tables:
+// r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
+//           - sum_{j != i} [2 n_j R_j D_{n-e_j} + n_j (n_j - 1) D_{n-2e_j}],
+// i = the first axis with n_i >= 1.
+__device__ void d_series(const double R[3], int nD, const int *mi, const int32_t *lut, double *D)
+{
+    constexpr int L = kMaxOrder + 1;
+    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    const double inv_r2 = 1.0 / r2;
+    D[0] = rsqrt(r2);
+    for (int idx = 1; idx < nD; ++idx) {
+        const int v = mi_at(mi, idx);
+        const int n[3] = {mi_nx(v), mi_ny(v), mi_nz(v)};
+        const int i = n[0] ? 0 : (n[1] ? 1 : 2);
+        int m[3] = {n[0], n[1], n[2]};
+        m[i] -= 1;
+        double acc = -(2.0 * n[i] - 1.0) * R[i] * D[32 * __ldg(lut + (m[0] * L + m[1]) * L + m[2])];
+        if (n[i] >= 2) {
+            m[i] -= 1;
+            acc -= (double)((n[i] - 1) * (n[i] - 1)) * D[32 * __ldg(lut + (m[0] * L + m[1]) * L + m[2])];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j == i || n[j] == 0) continue;
+            int q[3] = {n[0], n[1], n[2]};
+            q[j] -= 1;
+            acc -= 2.0 * n[j] * R[j] * D[32 * __ldg(lut + (q[0] * L + q[1]) * L + q[2])];
+            if (n[j] >= 2) {
+                q[j] -= 1;
+                acc -= (double)(n[j] * (n[j] - 1)) * D[32 * __ldg(lut + (q[0] * L + q[1]) * L + q[2])];
+            }
+        }
+        D[32 * idx] = acc * inv_r2;
+    }
+}
+
+template <int S, bool PHI, bool FIELD>
+__global__ void __launch_bounds__(32 * kBHMaxWarps)
+k_bh(BHArgs a)
+{
+    constexpr int nS = (S + 1) * (S + 2) / 2;
+    constexpr unsigned kAll = 0xffffffffu;
+    extern __shared__ double bsm[];
+    __shared__ int st_c[kBHMaxWarps][kBHStack];
+    __shared__ unsigned st_m[kBHMaxWarps][kBHStack];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *Dl = bsm + (size_t)w * a.nD * 32 + lane;
+    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * 32 + lane;
+    const bool valid = i < a.n;
+    const double x = valid ? a.px[i] : 0.0, y = valid ? a.py[i] : 0.0, z = valid ? a.pz[i] : 0.0;
+    double f = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    int root = 0;
+    if (valid) {                          // the last root whose particle range starts at or before i
+        int lo = 0, hi = a.nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.begin[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        root = lo;
+    }
+    int top = 0;
+    for (unsigned rem = __ballot_sync(kAll, valid); rem;) {
+        const int r = __shfl_sync(kAll, root, __ffs(rem) - 1);
+        const unsigned m = __ballot_sync(kAll, valid && root == r);
+        if (lane == 0) {
+            st_c[w][top] = r;
+            st_m[w][top] = m;
+        }
+        ++top;
+        rem &= ~m;
+    }
+    __syncwarp();
+    while (top > 0) {
+        --top;
+        const int c = st_c[w][top];
+        const unsigned m = st_m[w][top];
+        __syncwarp();                     // read by every lane before a push overwrites it
+        bool acc = false;
+        double dx = 0.0, dy = 0.0, dz = 0.0;
+        if ((m >> lane) & 1u) {
+            dx = __dsub_rn(x, a.centre[3 * c]);
+            dy = __dsub_rn(y, a.centre[3 * c + 1]);
+            dz = __dsub_rn(z, a.centre[3 * c + 2]);
+            const double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            const double h = a.half[c];
+            acc = __dmul_rn(h, h) < __dmul_rn(a.theta2, dd);
+        }
+        if (acc) {                        // M2P
+            const double R[3] = {dx, dy, dz};
+            d_series(R, a.nD, a.mi, a.lut, Dl);
+            const double *Mc = a.M + (int64_t)c * a.nM;
+            double pf = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+            for (int q = 0; q < a.nM; ++q) {
+                const double mv = Mc[q];
+                const int4 t = a.mt[q];
+                if (PHI) pf = fma(mv, Dl[32 * t.x], pf);
+                if (FIELD) {
+                    g0 = fma(mv, Dl[32 * t.y], g0);
+                    g1 = fma(mv, Dl[32 * t.z], g1);
+                    g2 = fma(mv, Dl[32 * t.w], g2);
+                }
+            }
+            f += pf;
+            e0 -= g0; e1 -= g1; e2 -= g2;
+        }
+        const unsigned om = m & ~__ballot_sync(kAll, acc);    // lanes for which c failed
+        if (om == 0) continue;
+        const int nch = a.nchild[c];
+        if (nch == 0) {                   // P2P with the leaf's particles
+            const bool mine = (om >> lane) & 1u;
+            for (int j = a.begin[c]; j < a.end[c]; ++j) {
+                const double sx = a.px[j], sy = a.py[j], sz = a.pz[j];
+                if (mine)
+                    pair_fp64<S, PHI, FIELD>(x - sx, y - sy, z - sz, a.Sm + (int64_t)j * nS, f, e0, e1, e2);
+            }
+        } else {                          // open: children pushed last-first, taken in order
+            const int ch0 = a.child[c];
+            if (lane == 0)
+                for (int k = 0; k < nch; ++k) {
+                    st_c[w][top + k] = ch0 + nch - 1 - k;
+                    st_m[w][top + k] = om;
+                }
+            top += nch;
+            __syncwarp();
+        }
+    }
+    if (valid) {
+        const int64_t o = a.perm[i];
+        if (PHI) a.phi_out[o] = f;
+        if (FIELD) {
+            a.E_out[3 * o] = e0;
+            a.E_out[3 * o + 1] = e1;
+            a.E_out[3 * o + 2] = e2;
+        }
+    }
+}
+
+template <int S>
+void launch_bh_s(const BHArgs &a, int want_phi, int want_field, unsigned grid, int threads, size_t smem,
+                 cudaStream_t st)
+{
+    auto go = [&](auto kern) {
+        allow_max_dynamic_smem(kern);
+        kern<<<grid, threads, smem, st>>>(a);
+    };
+    if (want_phi && want_field) go(k_bh<S, true, true>);
+    else if (want_phi) go(k_bh<S, true, false>);
+    else go(k_bh<S, false, true>);
+}
+
+}  // namespace
+
+fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field, double *phi_out,
+                  double *E_out)
+{
+    cudaStream_t st = t->stream;
+    const int s = t->s;
+    DevTables tb;
+    const int32_t *lut;
+    FMM_TRY(upload_tables(t, s, p - s, 0, &tb, &lut));
+    FMM_TRY(run_upward(t, tb, false));
+    if (t->bh_key_s != s || t->bh_key_p != p) {
+        // per multipole term m: D indices of m and m + e_k (graded order)
+        const MultiIndex &I = multi_index();
+        std::vector<int4> mt(tb.nM);
+        for (int q = 0; q < tb.nM; ++q) {
+            const int m = q + tb.m0;
+            mt[q] = make_int4(m, I(I.nx[m] + 1, I.ny[m], I.nz[m]), I(I.nx[m], I.ny[m] + 1, I.nz[m]),
+                              I(I.nx[m], I.ny[m], I.nz[m] + 1));
+        }
+        t->bh_key_s = -1;
+        FMM_TRY(ensure(t, t->b_bh_mt, sizeof(int4) * mt.size()));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_bh_mt.ptr, mt.data(), sizeof(int4) * mt.size(),
+                                              cudaMemcpyHostToDevice, st), "Barnes-Hut table"));
+        t->bh_key_s = s;
+        t->bh_key_p = p;
+    }
+    BHArgs a;
+    a.n = t->n;
+    a.nsys = std::max(1, (int)t->sys_off.size() - 1);
+    a.nM = tb.nM;
+    a.nD = ntot(p + (want_field ? 1 : 0));
+    a.theta2 = theta * theta;
+    a.nchild = (const int32_t *)t->b_nchild.ptr;
+    a.child = (const int32_t *)t->b_child.ptr;
+    a.begin = (const int32_t *)t->b_begin.ptr;
+    a.end = (const int32_t *)t->b_end.ptr;
+    a.centre = (const double *)t->b_centre.ptr;
+    a.half = (const double *)t->b_half.ptr;
+    a.px = (const double *)t->b_px.ptr;
+    a.py = (const double *)t->b_py.ptr;
+    a.pz = (const double *)t->b_pz.ptr;
+    a.Sm = (const double *)t->b_S.ptr;
+    a.perm = (const int32_t *)t->b_perm.ptr;
+    a.M = (const double *)t->b_M.ptr;
+    a.mt = (const int4 *)t->b_bh_mt.ptr;
+    a.mi = tb.mi;
+    a.lut = lut;
+    a.phi_out = phi_out;
+    a.E_out = E_out;
+    // D rows in shared memory: 32 lanes x nD doubles per warp
+    const int wpb = std::max(1, std::min(kBHMaxWarps, (200 * 1024) / (a.nD * 256)));
+    const size_t smem = (size_t)wpb * a.nD * 256;
+    const unsigned grid = (unsigned)((t->n + 32 * wpb - 1) / (32 * wpb));
+    switch (s) {
+    case 0: launch_bh_s<0>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    case 1: launch_bh_s<1>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    default: launch_bh_s<2>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    }
+    ++t->launches;
+    return cuda_check(t, cudaGetLastError(), "Barnes-Hut walk");
+}
+
+}  // namespace fmm

@@ -206,6 +206,9 @@ struct fmm_tree {
     DevBuf b_dsort, b_dsort_h;             // scratch of the canonical D-key numbering
     DevBuf b_M, b_L, b_phi, b_E;
     DevBuf b_Mh, b_Mh32;                   // folded multipoles of the harmonic M2L
+    // Barnes-Hut: the M2P term table of (bh_key_s, bh_key_p)
+    int bh_key_s = -1, bh_key_p = -1;
+    DevBuf b_bh_mt;
     DevBuf b_tab_i32, b_tab_u32;
     // mixed-precision state
     DevBuf b_o32, b_S32, b_M32, b_L32, b_D32;
@@ -280,6 +283,11 @@ fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint6
 fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut);
 fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t *lut);
 fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field);
+// P2M + M2M of the tables' (s, p) into b_M; rec: record the phase events
+fmm_status run_upward(fmm_tree *t, const DevTables &tb, bool rec);
+// bh.cu: multipolar Barnes-Hut of order p (multipoles s <= |m| <= p), FP64
+fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field, double *phi_out,
+                  double *E_out);
 // M' of the harmonic M2L for every cell: Mh[c][r] = fold(M[c])[h_rm[r]]
 void launch_fold_m(cudaStream_t st, const double *M, int ldM, int64_t nc, const DevTables &tb,
                    double *Mh, int ldH);

@@ -724,6 +724,39 @@ fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t 
     return FMM_OK;
 }
 
+// P2M at the leaves and M2M upward, level by level, into b_M (FP64, tb.nM per cell)
+fmm_status run_upward(fmm_tree *t, const DevTables &tb, bool rec)
+{
+    cudaStream_t st = t->stream;
+    const int64_t nc = t->ncells;
+    const int P1 = tb.p + 1;
+    FMM_TRY(ensure(t, t->b_M, 8 * (size_t)nc * tb.nM));
+    t->m_cells = nc;
+    double *M = (double *)t->b_M.ptr;
+    const double *centre = (const double *)t->b_centre.ptr;
+    {
+        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
+        allow_max_dynamic_smem(k_p2m);
+        k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(
+            (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
+            (const int32_t *)t->b_end.ptr, centre, (const double *)t->b_px.ptr,
+            (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr, (const double *)t->b_S.ptr, tb, M);
+        ++t->launches;
+    }
+    if (rec) record(t, 7);
+    {
+        size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nM);
+        for (int l = t->nlevels - 2; l >= 0; --l) {
+            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
+            k_m2m<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
+                                          (const int32_t *)t->b_nchild.ptr, centre, tb, M);
+            ++t->launches;
+        }
+    }
+    if (rec) record(t, 8);
+    return FMM_OK;
+}
+
 fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
 {
     cudaStream_t st = t->stream;
@@ -737,38 +770,16 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
 
     FMM_TRY(build_dtables(t, p, tb, lut));
     record(t, 6);
-    FMM_TRY(ensure(t, t->b_M, 8 * (size_t)nc * tb.nM));
     FMM_TRY(ensure(t, t->b_L, 8 * (size_t)nc * tb.nL));
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
-    t->m_cells = nc;
+    FMM_TRY(run_upward(t, tb, true));
     double *M = (double *)t->b_M.ptr, *L = (double *)t->b_L.ptr;
     const int32_t *leaves = (const int32_t *)t->b_leaves.ptr;
     const int32_t *begin = (const int32_t *)t->b_begin.ptr, *end = (const int32_t *)t->b_end.ptr;
     const double *centre = (const double *)t->b_centre.ptr;
     const double *px = (const double *)t->b_px.ptr, *py = (const double *)t->b_py.ptr,
                  *pz = (const double *)t->b_pz.ptr;
-
-    // P2M at the leaves
-    {
-        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
-        allow_max_dynamic_smem(k_p2m);
-        k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(leaves, begin, end, centre, px, py, pz,
-                                                               (const double *)t->b_S.ptr, tb, M);
-        ++t->launches;
-    }
-    record(t, 7);
-    // M2M upward, level by level
-    {
-        size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nM);
-        for (int l = t->nlevels - 2; l >= 0; --l) {
-            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
-            k_m2m<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
-                                          (const int32_t *)t->b_nchild.ptr, centre, tb, M);
-            ++t->launches;
-        }
-    }
-    record(t, 8);
     // M2L over the stored lists (harmonic: on the folded multipoles)
     cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nL, st);
     if (t->n_m2l > 0) {

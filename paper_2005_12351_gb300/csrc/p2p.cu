@@ -12,6 +12,7 @@
 #include <cstdlib>
 
 #include "fmm_internal.cuh"
+#include "pair.cuh"
 
 namespace fmm {
 
@@ -52,50 +53,6 @@ __global__ void k_check_rsqrt(const double *x, int64_t n, double *own, double *r
     if (i >= n) return;
     own[i] = rsqrt_hh(x[i]);
     ref[i] = rsqrt(x[i]);
-}
-
-template <int S, bool PHI, bool FIELD>
-__device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, const double *Sj,
-                                          double &f, double &e0, double &e1, double &e2)
-{
-    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-    const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
-    const double rinv2 = rinv * rinv;
-    if (S == 0) {
-        const double q = Sj[0];
-        if (PHI) f = fma(q, rinv, f);
-        if (FIELD) {
-            const double w = q * rinv * rinv2;
-            e0 = fma(w, dx, e0); e1 = fma(w, dy, e1); e2 = fma(w, dz, e2);
-        }
-    } else if (S == 1) {
-        const double rinv3 = rinv * rinv2;
-        const double sr = fma(Sj[0], dx, fma(Sj[1], dy, Sj[2] * dz));
-        if (PHI) f = fma(-sr, rinv3, f);
-        if (FIELD) {
-            const double w = 3.0 * sr * rinv3 * rinv2;
-            e0 = fma(Sj[0], rinv3, fma(-w, dx, e0));
-            e1 = fma(Sj[1], rinv3, fma(-w, dy, e1));
-            e2 = fma(Sj[2], rinv3, fma(-w, dz, e2));
-        }
-    } else {
-        const double rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2;
-        // half-gradient of q: h = (grad q)/2 is not symmetric in the S layout, so form grad q
-        const double gq0 = fma(2.0 * Sj[0], dx, fma(Sj[1], dy, Sj[2] * dz));
-        const double gq1 = fma(Sj[1], dx, fma(2.0 * Sj[3], dy, Sj[4] * dz));
-        const double gq2 = fma(Sj[2], dx, fma(Sj[4], dy, 2.0 * Sj[5] * dz));
-        // q = (R . grad q) / 2 for a homogeneous quadratic
-        const double q = 0.5 * fma(gq0, dx, fma(gq1, dy, gq2 * dz));
-        const double tr = Sj[0] + Sj[3] + Sj[5];
-        if (PHI) f += 3.0 * q * rinv5 - tr * rinv3;
-        if (FIELD) {
-            const double a = 3.0 * rinv5;
-            const double w = fma(15.0 * q, rinv5 * rinv2, -3.0 * tr * rinv5);
-            e0 = fma(w, dx, fma(-a, gq0, e0));
-            e1 = fma(w, dy, fma(-a, gq1, e1));
-            e2 = fma(w, dz, fma(-a, gq2, e2));
-        }
-    }
 }
 
 constexpr int kP2PThreads = 128;

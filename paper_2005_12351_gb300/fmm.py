@@ -173,6 +173,21 @@ class FMMTree:
         _check(st, self._h, "evaluate")
         return (potential if want_potential else None), (field if want_field else None)
 
+    def evaluate_bh(self, p: int, theta: float, want_potential=True, want_field=True,
+                    potential=None, field=None):
+        """Multipolar Barnes-Hut of order p (FP64); returns like evaluate()."""
+        if want_potential and potential is None:
+            potential = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        if want_field and field is None:
+            field = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        fn = lib().fmm_evaluate_bh
+        fn.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        fn.restype = C.c_int
+        st = fn(self._h, int(p), float(theta), int(bool(want_potential)), int(bool(want_field)),
+                _ptr(potential if want_potential else None), _ptr(field if want_field else None))
+        _check(st, self._h, "evaluate_bh")
+        return (potential if want_potential else None), (field if want_field else None)
+
     def update_moments(self, moments):
         """Replace the moments of the current tree (caller's order); keeps tree, lists, caches."""
         _dev_f64(moments, "moments", source_terms(self.s))
