@@ -42,6 +42,28 @@ def flops_per_pair(s: int, want_phi: bool, want_field: bool) -> int:
     return base + 1 + 15 + 5 + (4 if want_phi else 0) + (19 if want_field else 0)
 
 
+def m2p_flops(s: int, p: int, want_phi: bool, want_field: bool) -> int:
+    """Algorithmic FP64 flops of one Barnes-Hut M2P (multipoles s <= |m| <= p): D_n(R)
+    up to order p + 1 (p without the field) by the recurrence
+    r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
+              - sum_{j != i} [2 n_j R_j D_{n-e_j} + n_j (n_j - 1) D_{n-2e_j}]
+    (3 flops per term with R_j, 2 without, 1 for the 1/r^2 factor; r^2, 1/r^2 and
+    1/r: 7), then 2 flops per multipole term for the potential and 6 for the field."""
+    P = p + (1 if want_field else 0)
+    fl = 7
+    for k in range(1, P + 1):
+        for nx in range(k, -1, -1):
+            for ny in range(k - nx, -1, -1):
+                n = (nx, ny, k - nx - ny)
+                i = 0 if n[0] else (1 if n[1] else 2)
+                fl += 3 + (2 if n[i] >= 2 else 0) + 1
+                for j in range(3):
+                    if j != i and n[j]:
+                        fl += 3 + (2 if n[j] >= 2 else 0)
+    nM = sum((k + 1) * (k + 2) // 2 for k in range(s, p + 1))
+    return fl + nM * ((2 if want_phi else 0) + (6 if want_field else 0))
+
+
 def m2l_macs_per_pair(s: int, p: int, want_phi: bool) -> int:
     """Terms of L_n += D_{n+m} M_m kept by |n| + |m| <= p + s (n from 0 or 1)."""
     tri = lambda k: (k + 1) * (k + 2) // 2
@@ -392,6 +414,62 @@ def measure_graph(args, w, precision, dev, world, pos_d, S_h, S_d, flush):
             "tuning": tuning}
 
 
+def measure_bh(args, w, dev, world, pos_d, S_d, flush):
+    """Multipolar Barnes-Hut on the same workload: a step = tree build + fmm_evaluate_bh
+    at order p, opening angle theta_BH (the paper: theta_FMM ~ 2 theta_BH for a similar
+    error).  The walk kernel is timed alone for its roofline."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    s, p, n = w["s"], w["p"], w["n"]
+    theta = args.bh_theta if args.bh_theta is not None else w["theta"] / 2
+    stream = torch.cuda.current_stream(dev)
+    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"])
+    E_d = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    walk = []
+
+    def step():
+        tree.set_sources(pos_d, S_d, s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tree.evaluate_bh(p, theta, False, True, field=E_d)
+        b.record(stream)
+        walk.append((a, b))
+
+    step()
+    torch.cuda.synchronize(dev)
+    walk.clear()
+    steps = max(1, min(args.steps, 2))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    walk_ms = float(np.mean([a.elapsed_time(b) for a, b in walk]))
+    info = tree.info()
+    tg = synth.sample_indices(n, args.err_samples, 23)
+    tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
+    _, E_ref = fmm.direct_sum(pos_d, S_d, s, targets=tg_d, want_potential=False)
+    Ef = E_d[tg_d.long()]
+    err = math.sqrt(((Ef - E_ref) ** 2).sum().item() / (E_ref ** 2).sum().item())
+    flops = (info["bh_m2p"] * m2p_flops(s, p, False, True)
+             + info["bh_p2p"] * flops_per_pair(s, False, True))
+    achieved = flops / (walk_ms / 1e3) / 1e12
+    tree.destroy()
+    return {"theta_bh": theta, "p": p, "value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "step": "tree build + fmm_evaluate_bh (field)", "walk_ms": walk_ms,
+            "field_rel_rms": err, "targets": int(len(tg)),
+            "m2p": info["bh_m2p"], "p2p_pairs": info["bh_p2p"],
+            "roofline": {"bound": "alu", "kernel": "k_bh", "achieved": achieved,
+                         "peak": args.fp64_peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / args.fp64_peak_tflops, "traffic": None,
+                         "algorithmic_flops": flops,
+                         "per_m2p_flops": m2p_flops(s, p, False, True),
+                         "peak_source": args.fp64_peak_source}}
+
+
 def serving_stream(count: int, seed: int):
     """Requests drawn like the serving workload: N log-uniform in [1e3, 2e6],
     source order uniform over {0, 1, 2}, p uniform over {4..10}, uniform or
@@ -507,6 +585,8 @@ def run_ours(args, w):
                                                    "gpu_launches")}
         line["mixed_3xtf32"]["error_ratio_vs_fp64"] = (m3["rel_err"]["field_rel_rms"]
                                                        / main["rel_err"]["field_rel_rms"])
+    if args.precision == "fp64" and not args.no_bh and "batch" not in w:
+        line["bh"] = measure_bh(args, w, dev, world, pos_d, S_d, flush)
     if not args.no_graph:
         line["graph"] = measure_graph(args, w, args.graph_precision or args.precision, dev, world,
                                       pos_d, S_h, S_d, flush)
@@ -542,6 +622,9 @@ def main(argv=None):
                     help="skip the repeated-geometry measurement (autotune + graph replay)")
     ap.add_argument("--graph-precision", choices=["fp64", "fp32", "3xtf32"], default=None,
                     help="form of the graph measurement (default: --precision)")
+    ap.add_argument("--no-bh", action="store_true",
+                    help="skip the Barnes-Hut line (FP64, same workload, theta_BH = theta / 2)")
+    ap.add_argument("--bh-theta", type=float, default=None)
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)

@@ -187,6 +187,10 @@ typedef struct {
      * target tiles of 128, (tile, key) rows, chunks of rows; the fill
      * n_m2l / (128 tc_rows) is the share of MMA rows that carry a pair */
     int64_t tc_tiles, tc_rows, tc_chunks;
+    /* the last fmm_evaluate_bh (0 before one): M2P evaluations (target, cell)
+     * and P2P pairs evaluated (target, leaf particle; the target itself
+     * included, it contributes zero) */
+    int64_t bh_m2p, bh_p2p;
 } fmm_tree_info;
 
 fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);

@@ -113,7 +113,7 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
                    &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
                    &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
-                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt};
+                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
 }
 
@@ -266,6 +266,7 @@ static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const d
     t->have_lists = false;
     t->tc_plan = false;
     t->sym_plan = false;
+    t->bh_ran = false;
     t->d_p = -1;
     t->n = n;
     t->s = source_order;
@@ -346,6 +347,15 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *o)
         o->tc_tiles = t->tc_tiles;
         o->tc_rows = t->tc_rows;
         o->tc_chunks = t->tc_chunks;
+    }
+    if (t->bh_ran && t->b_bh_cnt.ptr) {
+        unsigned long long cnt[2] = {0, 0};
+        DeviceGuard g(t->device);
+        if (cudaMemcpyAsync(cnt, t->b_bh_cnt.ptr, sizeof(cnt), cudaMemcpyDeviceToHost, t->stream) == cudaSuccess &&
+            cudaStreamSynchronize(t->stream) == cudaSuccess) {
+            o->bh_m2p = (int64_t)cnt[0];
+            o->bh_p2p = (int64_t)cnt[1];
+        }
     }
     return FMM_OK;
 }

@@ -37,6 +37,7 @@ struct BHArgs {
     const int32_t *perm;
     const double *M;
     const int4 *mt;          // per multipole term: D index of m, m + e_x, m + e_y, m + e_z
+    unsigned long long *count;   // [M2P evaluations, P2P pairs], added per warp
     const int *mi;           // packed multi-indices of the graded order
     const int32_t *lut;      // (nx, ny, nz) -> graded index, stride kMaxOrder + 1
     double *phi_out, *E_out;
@@ -94,6 +95,7 @@ k_bh(BHArgs a)
     const bool valid = i < a.n;
     const double x = valid ? a.px[i] : 0.0, y = valid ? a.py[i] : 0.0, z = valid ? a.pz[i] : 0.0;
     double f = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    unsigned long long n_m2p = 0, n_p2p = 0;
     int root = 0;
     if (valid) {                          // the last root whose particle range starts at or before i
         int lo = 0, hi = a.nsys - 1;
@@ -147,12 +149,14 @@ k_bh(BHArgs a)
             }
             f += pf;
             e0 -= g0; e1 -= g1; e2 -= g2;
+            ++n_m2p;
         }
         const unsigned om = m & ~__ballot_sync(kAll, acc);    // lanes for which c failed
         if (om == 0) continue;
         const int nch = a.nchild[c];
         if (nch == 0) {                   // P2P with the leaf's particles
             const bool mine = (om >> lane) & 1u;
+            if (mine) n_p2p += (unsigned long long)(a.end[c] - a.begin[c]);
             for (int j = a.begin[c]; j < a.end[c]; ++j) {
                 const double sx = a.px[j], sy = a.py[j], sz = a.pz[j];
                 if (mine)
@@ -168,6 +172,15 @@ k_bh(BHArgs a)
             top += nch;
             __syncwarp();
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_m2p += __shfl_xor_sync(kAll, n_m2p, o);
+        n_p2p += __shfl_xor_sync(kAll, n_p2p, o);
+    }
+    if (lane == 0) {
+        atomicAdd(a.count, n_m2p);
+        atomicAdd(a.count + 1, n_p2p);
     }
     if (valid) {
         const int64_t o = a.perm[i];
@@ -220,7 +233,10 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
         t->bh_key_s = s;
         t->bh_key_p = p;
     }
+    FMM_TRY(ensure(t, t->b_bh_cnt, 16));
+    FMM_TRY(cuda_check(t, cudaMemsetAsync(t->b_bh_cnt.ptr, 0, 16, st), "memset"));
     BHArgs a;
+    a.count = (unsigned long long *)t->b_bh_cnt.ptr;
     a.n = t->n;
     a.nsys = std::max(1, (int)t->sys_off.size() - 1);
     a.nM = tb.nM;
@@ -253,6 +269,7 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
     default: launch_bh_s<2>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
     }
     ++t->launches;
+    t->bh_ran = true;
     return cuda_check(t, cudaGetLastError(), "Barnes-Hut walk");
 }
 

@@ -208,7 +208,8 @@ struct fmm_tree {
     DevBuf b_Mh, b_Mh32;                   // folded multipoles of the harmonic M2L
     // Barnes-Hut: the M2P term table of (bh_key_s, bh_key_p)
     int bh_key_s = -1, bh_key_p = -1;
-    DevBuf b_bh_mt;
+    bool bh_ran = false;                   // b_bh_cnt holds the last walk's counts
+    DevBuf b_bh_mt, b_bh_cnt;
     DevBuf b_tab_i32, b_tab_u32;
     // mixed-precision state
     DevBuf b_o32, b_S32, b_M32, b_L32, b_D32;

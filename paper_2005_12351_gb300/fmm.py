@@ -40,7 +40,8 @@ class TreeInfo(C.Structure):
                 ("n_p2p", C.c_int64), ("n_p2p_interactions", C.c_int64),
                 ("n_doffsets", C.c_int64), ("theta", C.c_double), ("lo", C.c_double * 3),
                 ("side", C.c_double), ("device_bytes", C.c_int64), ("nsystems", C.c_int64),
-                ("tc_tiles", C.c_int64), ("tc_rows", C.c_int64), ("tc_chunks", C.c_int64)]
+                ("tc_tiles", C.c_int64), ("tc_rows", C.c_int64), ("tc_chunks", C.c_int64),
+                ("bh_m2p", C.c_int64), ("bh_p2p", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -7,9 +7,11 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_e3_error_falls_with_order():
+@pytest.mark.parametrize("method", ["fmm", "bh"])
+def test_e3_error_falls_with_order(method):
     from paper_2005_12351_gb300 import experiments
-    res = list(experiments.e3(n=6_000, thetas=(0.25, 0.5), orders=(1, 3, 5, 7)))
+    res = list(experiments.e3(n=6_000, thetas=(0.25, 0.5), orders=(1, 3, 5, 7), methods=(method,)))
+    assert all(r["method"] == method for r in res)
     med = {(r["theta"], r["p"]): r["potential_error"]["median"] for r in res}
     rms = {(r["theta"], r["p"]): r["field_error"]["rel_rms"] for r in res}
     for th in (0.25, 0.5):
@@ -23,10 +25,19 @@ def test_e3_error_falls_with_order():
     assert sum(r0["log10_hist"]["counts"]) == 6_000
 
 
+def test_e2_scaling_bh():
+    from paper_2005_12351_gb300 import experiments
+    res = list(experiments.e2(nmin=20_000, nmax=320_000, points=3, thetas=(0.5,), orders=(4,),
+                              direct_max=0, methods=("bh",)))
+    t = [r["ms_evaluate"] for r in res]
+    assert [r["method"] for r in res] == ["bh"] * 3
+    assert t[0] < t[1] < t[2] and t[-1] / t[0] < 64
+
+
 def test_e2_scaling():
     from paper_2005_12351_gb300 import experiments
     res = list(experiments.e2(nmin=20_000, nmax=320_000, points=3, thetas=(0.5,), orders=(4,),
-                              direct_max=320_000))
+                              direct_max=320_000, methods=("fmm",)))
     ns = [r["n"] for r in res]
     t = [r["ms_evaluate"] for r in res]
     assert ns == sorted(ns) and len(ns) == 3
