@@ -76,6 +76,17 @@ def lib():
                                   C.c_void_p, _f64p, _f64p]
             L.orc_fmm.restype = C.c_int
             L.orc_m2p.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p]
+            L.orc_p2m_orders.argtypes = [C.c_int, C.c_int, C.c_int, _f64p, C.c_int64, _f64p, _f64p,
+                                         _f64p]
+            L.orc_p2p_pair_orders.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _f64p]
+            L.orc_direct_orders.argtypes = [C.c_int, C.c_int, C.c_int64, _f64p, _f64p, C.c_int64,
+                                            C.c_void_p, _f64p, _f64p]
+            L.orc_fmm_orders.argtypes = [C.c_void_p, _f64p, C.c_int, C.c_int, C.c_int, _f64p,
+                                         C.c_int64, C.c_void_p, _f64p, _f64p]
+            L.orc_fmm_orders.restype = C.c_int
+            L.orc_bh_orders.argtypes = [C.c_void_p, _f64p, C.c_int, C.c_int, C.c_int, _f64p,
+                                        C.c_double, C.c_int64, C.c_void_p, _f64p, _f64p]
+            L.orc_bh_orders.restype = C.c_int
             L.orc_bh.argtypes = [C.c_void_p, _f64p, C.c_int, C.c_int, _f64p, C.c_double,
                                  C.c_int64, C.c_void_p, _f64p, _f64p]
             L.orc_bh.restype = C.c_int
@@ -122,10 +133,16 @@ def derivatives(R, order: int) -> np.ndarray:
     return D
 
 
-def p2m(s, p, centre, pos, S):
+def n_source(s, s_hi=None) -> int:
+    """Moments per particle of the source orders s..s_hi (all shells, graded order)."""
+    return ntot(s if s_hi is None else s_hi) - ntot(s - 1)
+
+
+def p2m(s, p, centre, pos, S, s_hi=None):
     pos, S = _f64(pos).reshape(-1, 3), _f64(S)
     M = np.zeros(n_multipole(s, p))
-    lib().orc_p2m(s, p, _f64(centre), len(pos), pos.ravel(), S.ravel(), M)
+    lib().orc_p2m_orders(s, s if s_hi is None else s_hi, p, _f64(centre), len(pos), pos.ravel(),
+                         S.ravel(), M)
     return M
 
 
@@ -160,14 +177,15 @@ def m2p(s, p, z, M, x):
     return float(f[0]), g
 
 
-def p2p_pair(s, xt, xs, S):
+def p2p_pair(s, xt, xs, S, s_hi=None):
     phi, g = np.zeros(1), np.zeros(3)
-    lib().orc_p2p_pair(s, _f64(xt), _f64(xs), _f64(S), phi, g)
+    lib().orc_p2p_pair_orders(s, s if s_hi is None else s_hi, _f64(xt), _f64(xs), _f64(S), phi, g)
     return phi[0], g
 
 
-def direct(pos, S, s, targets=None):
-    """Compensated O(N^2) sum; returns (phi[nt], E[nt,3]) at ``targets``."""
+def direct(pos, S, s, targets=None, s_hi=None):
+    """Compensated O(N^2) sum; returns (phi[nt], E[nt,3]) at ``targets``.  Sources
+    of the orders s..s_hi (s_hi = s: a single order)."""
     pos, S = _f64(pos).reshape(-1, 3), _f64(S)
     n = len(pos)
     if targets is None:
@@ -177,7 +195,8 @@ def direct(pos, S, s, targets=None):
         nt, tp = len(targets), targets.ctypes.data
     phi, E = np.zeros(nt), np.zeros((nt, 3))
     if nt:
-        lib().orc_direct(s, n, pos.ravel(), S.ravel(), nt, tp, phi, E.reshape(-1))
+        lib().orc_direct_orders(s, s if s_hi is None else s_hi, n, pos.ravel(), S.ravel(), nt, tp,
+                                phi, E.reshape(-1))
     return phi, E
 
 
@@ -227,8 +246,9 @@ class Tree:
         self.theta = theta
         return self.m2l, self.p2p
 
-    def fmm(self, S, s: int, p: int, targets=None):
-        """FP64 FMM on this tree; (phi, E) at ``targets`` (original indices)."""
+    def fmm(self, S, s: int, p: int, targets=None, s_hi=None):
+        """FP64 FMM on this tree; (phi, E) at ``targets`` (original indices).  Sources of
+        the orders s..s_hi (the expansion's lowest order is s)."""
         if self.theta is None:
             raise RuntimeError("call lists(theta) first")
         S = _f64(S)
@@ -238,13 +258,13 @@ class Tree:
             targets = np.ascontiguousarray(targets, dtype=np.int64)
             nt, tp = len(targets), targets.ctypes.data
         phi, E = np.zeros(nt), np.zeros((nt, 3))
-        rc = lib().orc_fmm(self._h, self.pos.ravel(), s, p, S.ravel(), nt, tp, phi,
-                           E.reshape(-1))
+        rc = lib().orc_fmm_orders(self._h, self.pos.ravel(), s, s if s_hi is None else s_hi, p,
+                                  S.ravel(), nt, tp, phi, E.reshape(-1))
         if rc != 0:
             raise ValueError("oracle FMM rejected s=%d p=%d" % (s, p))
         return phi, E
 
-    def bh(self, S, s: int, p: int, theta: float, targets=None):
+    def bh(self, S, s: int, p: int, theta: float, targets=None, s_hi=None):
         """FP64 multipolar Barnes-Hut on this tree (order p, opening angle theta):
         (phi, E) at ``targets`` (original indices)."""
         S = _f64(S)
@@ -254,8 +274,8 @@ class Tree:
             targets = np.ascontiguousarray(targets, dtype=np.int64)
             nt, tp = len(targets), targets.ctypes.data
         phi, E = np.zeros(nt), np.zeros((nt, 3))
-        rc = lib().orc_bh(self._h, self.pos.ravel(), s, p, S.ravel(), float(theta), nt, tp, phi,
-                          E.reshape(-1))
+        rc = lib().orc_bh_orders(self._h, self.pos.ravel(), s, s if s_hi is None else s_hi, p,
+                                 S.ravel(), float(theta), nt, tp, phi, E.reshape(-1))
         if rc != 0:
             raise ValueError("oracle BH rejected s=%d p=%d theta=%g" % (s, p, theta))
         return phi, E
@@ -266,12 +286,12 @@ class Tree:
             _lib.orc_tree_free(h)
 
 
-def bh(pos, S, s, p, theta, ncrit, targets=None):
-    return Tree(pos, ncrit).bh(S, s, p, theta, targets)
+def bh(pos, S, s, p, theta, ncrit, targets=None, s_hi=None):
+    return Tree(pos, ncrit).bh(S, s, p, theta, targets, s_hi)
 
 
-def fmm(pos, S, s, p, theta, ncrit, targets=None):
+def fmm(pos, S, s, p, theta, ncrit, targets=None, s_hi=None):
     """Convenience: build the oracle tree and lists, then evaluate."""
     t = Tree(pos, ncrit)
     t.lists(theta)
-    return t.fmm(S, s, p, targets)
+    return t.fmm(S, s, p, targets, s_hi)

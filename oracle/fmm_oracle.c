@@ -137,13 +137,19 @@ void orc_derivatives(double x, double y, double z, int order, double *D)
 int orc_n_multipole(int s, int p) { return orc_ntot(p + s) - orc_ntot(s - 1); }
 int orc_n_local(int p) { return orc_ntot(p); }
 
-/* P2M, §2 Eq. (5) with Eq. (3)'s sign: M_m(z) = sum_j sum_{a<=m,|a|=s}
- * (z - x_j)^(m-a)/(m-a)! S_{j,a}. */
-void orc_p2m(int s, int p, const double zc[3], int64_t cnt, const double *pos,
-             const double *S, double *M)
+/* Source moments of a system whose particles carry the orders s_lo..s_hi
+ * (§2: "mixed systems"): the graded indices ntot(s_lo - 1) .. ntot(s_hi) - 1,
+ * S_{j,a} in that order per particle.  A single order s is s_lo = s_hi = s. */
+static int n_src(int s_lo, int s_hi) { return orc_ntot(s_hi) - orc_ntot(s_lo - 1); }
+
+/* P2M, §2 Eq. (5) with Eq. (3)'s sign: M_m(z) = sum_j sum_{a<=m, s_lo<=|a|<=s_hi}
+ * (z - x_j)^(m-a)/(m-a)! S_{j,a}, for s_lo <= |m| <= p + s_lo. */
+void orc_p2m_orders(int s_lo, int s_hi, int p, const double zc[3], int64_t cnt, const double *pos,
+                    const double *S, double *M)
 {
     make_tables();
-    int m0 = orc_ntot(s - 1), nM = orc_n_multipole(s, p), nS = orc_ntot(s) - orc_ntot(s - 1);
+    int s = s_lo;
+    int m0 = orc_ntot(s - 1), nM = orc_n_multipole(s, p), nS = n_src(s_lo, s_hi);
     for (int64_t j = 0; j < cnt; ++j) {
         double d[3] = {zc[0] - pos[3 * j], zc[1] - pos[3 * j + 1], zc[2] - pos[3 * j + 2]};
         for (int mi = 0; mi < nM; ++mi) {
@@ -156,6 +162,12 @@ void orc_p2m(int s, int p, const double zc[3], int64_t cnt, const double *pos,
             }
         }
     }
+}
+
+void orc_p2m(int s, int p, const double zc[3], int64_t cnt, const double *pos, const double *S,
+             double *M)
+{
+    orc_p2m_orders(s, s, p, zc, cnt, pos, S, M);
 }
 
 /* M2M, §2 Eq. (4) with the sign fixed by Eq. (3):
@@ -234,16 +246,16 @@ void orc_l2p(int p, const double z[3], const double *L, const double x[3], doubl
 
 /* One source j seen at target x (P2P, §3.1): phi = sum_{|a|=s} S_a D_a(x - x_j),
  * d_k phi = sum_a S_a D_{a+e_k}(x - x_j).  A coincident pair contributes 0. */
-void orc_p2p_pair(int s, const double xt[3], const double xs[3], const double *S,
-                  double *phi, double grad[3])
+void orc_p2p_pair_orders(int s_lo, int s_hi, const double xt[3], const double xs[3], const double *S,
+                         double *phi, double grad[3])
 {
     make_tables();
     double R[3] = {xt[0] - xs[0], xt[1] - xs[1], xt[2] - xs[2]};
     *phi = 0.0; grad[0] = grad[1] = grad[2] = 0.0;
     if (R[0] == 0.0 && R[1] == 0.0 && R[2] == 0.0) return;
     double D[64];
-    orc_derivatives(R[0], R[1], R[2], s + 1, D);
-    int m0 = orc_ntot(s - 1), nS = orc_ntot(s) - m0;
+    orc_derivatives(R[0], R[1], R[2], s_hi + 1, D);
+    int m0 = orc_ntot(s_lo - 1), nS = n_src(s_lo, s_hi);
     for (int ai = 0; ai < nS; ++ai) {
         int a = ai + m0;
         *phi += S[ai] * D[a];
@@ -251,6 +263,12 @@ void orc_p2p_pair(int s, const double xt[3], const double xs[3], const double *S
         grad[1] += S[ai] * D[orc_index(IX[a], IY[a] + 1, IZ[a])];
         grad[2] += S[ai] * D[orc_index(IX[a], IY[a], IZ[a] + 1)];
     }
+}
+
+void orc_p2p_pair(int s, const double xt[3], const double xs[3], const double *S, double *phi,
+                  double grad[3])
+{
+    orc_p2p_pair_orders(s, s, xt, xs, S, phi, grad);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -267,11 +285,11 @@ static void nadd(nsum *a, double v)
     a->s = t;
 }
 
-void orc_direct(int s, int64_t n, const double *pos, const double *S,
-                int64_t ntarget, const int64_t *targets, double *phi, double *E)
+void orc_direct_orders(int s_lo, int s_hi, int64_t n, const double *pos, const double *S,
+                       int64_t ntarget, const int64_t *targets, double *phi, double *E)
 {
     make_tables();
-    int nS = orc_ntot(s) - orc_ntot(s - 1);
+    int nS = n_src(s_lo, s_hi);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < ntarget; ++t) {
         int64_t i = targets ? targets[t] : t;
@@ -279,7 +297,7 @@ void orc_direct(int s, int64_t n, const double *pos, const double *S,
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double pf, pg[3];
-            orc_p2p_pair(s, pos + 3 * i, pos + 3 * j, S + nS * j, &pf, pg);
+            orc_p2p_pair_orders(s_lo, s_hi, pos + 3 * i, pos + 3 * j, S + nS * j, &pf, pg);
             nadd(&f, pf); nadd(&g0, pg[0]); nadd(&g1, pg[1]); nadd(&g2, pg[2]);
         }
         phi[t] = f.s + f.c;
@@ -287,6 +305,12 @@ void orc_direct(int s, int64_t n, const double *pos, const double *S,
         E[3 * t + 1] = -(g1.s + g1.c);
         E[3 * t + 2] = -(g2.s + g2.c);
     }
+}
+
+void orc_direct(int s, int64_t n, const double *pos, const double *S, int64_t ntarget,
+                const int64_t *targets, double *phi, double *E)
+{
+    orc_direct_orders(s, s, n, pos, S, ntarget, targets, phi, E);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -562,14 +586,16 @@ void orc_tree_get_lists(const orc_tree *t, int64_t *m2l, int64_t *p2p)
 /* If targets != NULL, only those particles (original indices) are output;  */
 /* the downward pass then runs only on their leaves' ancestor chains.        */
 /* ------------------------------------------------------------------------ */
-int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const double *S_orig,
-                int64_t ntarget, const int64_t *targets, double *phi, double *E)
+int orc_fmm_orders(const orc_tree *t, const double *pos_orig, int s_lo, int s_hi, int p,
+                   const double *S_orig, int64_t ntarget, const int64_t *targets, double *phi,
+                   double *E)
 {
     make_tables();
-    if (p + s + 1 > ORC_MAXORD || p < 0 || s < 0) return -1;
+    int s = s_lo;
+    if (p + s + 1 > ORC_MAXORD || p < 0 || s < 0 || s_hi < s_lo || s_hi > 2) return -1;
     int64_t n = t->n, nc = t->ncells;
     if (n == 0 || ntarget == 0) return 0;
-    int nM = orc_n_multipole(s, p), nL = orc_n_local(p), nS = orc_ntot(s) - orc_ntot(s - 1);
+    int nM = orc_n_multipole(s, p), nL = orc_n_local(p), nS = n_src(s_lo, s_hi);
 
     double *pos = malloc(sizeof(double) * 3 * n), *S = malloc(sizeof(double) * nS * n);
     for (int64_t k = 0; k < n; ++k) {
@@ -587,8 +613,8 @@ int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const doubl
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < nc; ++c)
         if (t->nchild[c] == 0)
-            orc_p2m(s, p, t->centre + 3 * c, t->end[c] - t->begin[c], pos + 3 * t->begin[c],
-                    S + nS * t->begin[c], M + (size_t)nM * c);
+            orc_p2m_orders(s_lo, s_hi, p, t->centre + 3 * c, t->end[c] - t->begin[c],
+                           pos + 3 * t->begin[c], S + nS * t->begin[c], M + (size_t)nM * c);
     for (int l = t->nlevels - 2; l >= 0; --l) {
 #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t c = t->level_begin[l]; c < t->level_begin[l + 1]; ++c)
@@ -659,7 +685,7 @@ int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const doubl
             for (int64_t j = t->begin[b]; j < t->end[b]; ++j) {
                 if (j == k) continue;
                 double pf, pg[3];
-                orc_p2p_pair(s, pos + 3 * k, pos + 3 * j, S + nS * j, &pf, pg);
+                orc_p2p_pair_orders(s_lo, s_hi, pos + 3 * k, pos + 3 * j, S + nS * j, &pf, pg);
                 f += pf; g[0] += pg[0]; g[1] += pg[1]; g[2] += pg[2];
             }
         }
@@ -669,6 +695,12 @@ int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const doubl
     free(pos); free(S); free(leaf_of); free(M); free(need); free(rank); free(tslot);
     free(m2l_first); free(L); free(p2p_first);
     return 0;
+}
+
+int orc_fmm(const orc_tree *t, const double *pos_orig, int s, int p, const double *S_orig,
+            int64_t ntarget, const int64_t *targets, double *phi, double *E)
+{
+    return orc_fmm_orders(t, pos_orig, s, s, p, S_orig, ntarget, targets, phi, E);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -700,7 +732,7 @@ void orc_m2p(int s, int p, const double z[3], const double *M, const double x[3]
 typedef struct {
     const orc_tree *t;
     const double *pos, *S, *M;
-    int s, p, nM, nS;
+    int s, s_hi, p, nM, nS;
     double theta2;
 } bh_ctx;
 
@@ -726,7 +758,7 @@ static void bh_walk(const bh_ctx *b, int64_t c, int64_t self, const double x[3],
         for (int64_t j = t->begin[c]; j < t->end[c]; ++j) {
             if (j == self) continue;
             double pf, pg[3];
-            orc_p2p_pair(b->s, x, b->pos + 3 * j, b->S + (size_t)b->nS * j, &pf, pg);
+            orc_p2p_pair_orders(b->s, b->s_hi, x, b->pos + 3 * j, b->S + (size_t)b->nS * j, &pf, pg);
             *f += pf; g[0] += pg[0]; g[1] += pg[1]; g[2] += pg[2];
         }
         return;
@@ -736,14 +768,16 @@ static void bh_walk(const bh_ctx *b, int64_t c, int64_t self, const double x[3],
 
 /* Barnes-Hut on the tree: P2M at the leaves and M2M upward (order p - s,
  * i.e. s <= |m| <= p), then one walk from the root per requested target. */
-int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double *S_orig,
-           double theta, int64_t ntarget, const int64_t *targets, double *phi, double *E)
+int orc_bh_orders(const orc_tree *t, const double *pos_orig, int s_lo, int s_hi, int p,
+                  const double *S_orig, double theta, int64_t ntarget, const int64_t *targets,
+                  double *phi, double *E)
 {
     make_tables();
-    if (s < 0 || p < s || p + 1 > ORC_MAXORD || !(theta >= 0.0)) return -1;
+    int s = s_lo;
+    if (s < 0 || s_hi < s_lo || s_hi > 2 || p < s || p + 1 > ORC_MAXORD || !(theta >= 0.0)) return -1;
     int64_t n = t->n, nc = t->ncells;
     if (n == 0 || ntarget == 0) return 0;
-    int pt = p - s, nM = orc_n_multipole(s, pt), nS = orc_ntot(s) - orc_ntot(s - 1);
+    int pt = p - s, nM = orc_n_multipole(s, pt), nS = n_src(s_lo, s_hi);
     double *pos = malloc(sizeof(double) * 3 * n), *S = malloc(sizeof(double) * nS * n);
     for (int64_t k = 0; k < n; ++k) {
         int64_t o = t->perm[k];
@@ -754,8 +788,8 @@ int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < nc; ++c)
         if (t->nchild[c] == 0)
-            orc_p2m(s, pt, t->centre + 3 * c, t->end[c] - t->begin[c], pos + 3 * t->begin[c],
-                    S + nS * t->begin[c], M + (size_t)nM * c);
+            orc_p2m_orders(s_lo, s_hi, pt, t->centre + 3 * c, t->end[c] - t->begin[c],
+                           pos + 3 * t->begin[c], S + nS * t->begin[c], M + (size_t)nM * c);
     for (int l = t->nlevels - 2; l >= 0; --l) {
 #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t c = t->level_begin[l]; c < t->level_begin[l + 1]; ++c)
@@ -767,7 +801,7 @@ int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double
     }
     int64_t *rank = malloc(sizeof(int64_t) * n);
     for (int64_t k = 0; k < n; ++k) rank[t->perm[k]] = k;
-    bh_ctx b = {t, pos, S, M, s, p, nM, nS, theta * theta};
+    bh_ctx b = {t, pos, S, M, s, s_hi, p, nM, nS, theta * theta};
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t q = 0; q < ntarget; ++q) {
         int64_t k = rank[targets ? targets[q] : q];
@@ -778,6 +812,12 @@ int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double
     }
     free(pos); free(S); free(M); free(rank);
     return 0;
+}
+
+int orc_bh(const orc_tree *t, const double *pos_orig, int s, int p, const double *S_orig,
+           double theta, int64_t ntarget, const int64_t *targets, double *phi, double *E)
+{
+    return orc_bh_orders(t, pos_orig, s, s, p, S_orig, theta, ntarget, targets, phi, E);
 }
 
 int orc_num_threads(void)

@@ -134,6 +134,12 @@ def sources(n: int, seed: int, s: int) -> np.ndarray:
     raise ValueError("source order must be 0, 1 or 2")
 
 
+def sources_mixed(n: int, seed: int, s_lo: int, s_hi: int) -> np.ndarray:
+    """Moments of every order s_lo..s_hi per particle (charge, dipole, quadrupole
+    shells side by side in graded order), each shell drawn as sources(., ., s)."""
+    return np.hstack([sources(n, seed + 101 * s, s) for s in range(s_lo, s_hi + 1)])
+
+
 def sample_indices(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct particle indices in [0, n), sorted (for sampled checks)."""
     k = min(k, n)
@@ -191,3 +197,9 @@ def make_system(n: int, s: int, dist: str, seed: int):
     else:
         raise ValueError(dist)
     return pos, sources(n, seed, s)
+
+
+def make_system_mixed(n: int, s_lo: int, s_hi: int, dist: str, seed: int):
+    """(positions, moments (n, T(s_lo..s_hi))) with every order s_lo..s_hi per particle."""
+    pos, _ = make_system(n, s_lo, dist, seed)
+    return pos, sources_mixed(n, seed, s_lo, s_hi)
