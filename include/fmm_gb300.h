@@ -105,6 +105,22 @@ fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *m
                            int64_t n, int source_order);
 
 /*
+ * Sources of several orders per particle (§2: "mixed systems"): every
+ * particle carries the moments of each order s_lo..s_hi, e.g. a charge and a
+ * dipole (0..1), in one row of ntot(s_hi) - ntot(s_lo - 1) doubles in graded
+ * order (S_000, then S_100 S_010 S_001, then S_200 S_110 S_101 S_020 S_011
+ * S_002, restricted to the orders present).  The expansion takes the lowest
+ * order: multipoles s_lo <= |m| <= p + s_lo, so fmm_evaluate's order p and
+ * its limit p + s_lo <= 12 refer to s_lo.  Every other rule is that of
+ * fmm_set_sources; fmm_update_moments takes rows of the same width.  The FP64
+ * form only: FMM_EORDER on an FMM_FP32 / FMM_3XTF32 handle with s_hi > s_lo,
+ * and unless 0 <= s_lo <= s_hi <= 2.  The symmetric P2P kernel (tuning
+ * p2p_variant 2) covers single orders: a mixed system takes variant 1.
+ */
+fmm_status fmm_set_sources_mixed(fmm_tree *t, const double *positions, const double *moments,
+                                 int64_t n, int s_lo, int s_hi);
+
+/*
  * Load a batch of `count` independent systems and build one octree per system
  * (a forest): system s owns particles [offsets[s], offsets[s+1]) of the
  * concatenated arrays, has its own root box, and never interacts with
@@ -191,6 +207,8 @@ typedef struct {
      * and P2P pairs evaluated (target, leaf particle; the target itself
      * included, it contributes zero) */
     int64_t bh_m2p, bh_p2p;
+    int64_t source_order_hi; /* highest source order per particle (= source_order */
+                             /* unless fmm_set_sources_mixed)                      */
 } fmm_tree_info;
 
 fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *out);
@@ -252,6 +270,12 @@ int64_t fmm_launch_count(const fmm_tree *t);
 fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const double *moments,
                           int64_t n, int source_order, const int32_t *targets, int64_t n_targets,
                           double *potential, double *field);
+
+/* fmm_direct_sum for sources of the orders s_lo..s_hi per particle (rows as
+ * fmm_set_sources_mixed). */
+fmm_status fmm_direct_sum_mixed(void *cuda_stream, const double *positions, const double *moments,
+                                int64_t n, int s_lo, int s_hi, const int32_t *targets,
+                                int64_t n_targets, double *potential, double *field);
 
 /*
  * Morton order of a point set (the first two steps of fmm_set_sources as a

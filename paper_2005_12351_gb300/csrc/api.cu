@@ -226,7 +226,7 @@ fmm_status fmm_get_phase_times(const fmm_tree *t, float *ms_out)
 int64_t fmm_launch_count(const fmm_tree *t) { return t ? t->launches : -1; }
 
 static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const double *moments,
-                                   int64_t n, int source_order);
+                                   int64_t n, int source_order, int source_order_hi);
 
 fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *moments, int64_t n,
                            int source_order)
@@ -235,7 +235,21 @@ fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *m
     t->err.clear();
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(t, FMM_EINVAL, "n out of range");
     t->sys_off.assign({0, n});
-    return set_sources_impl(t, positions, moments, n, source_order);
+    return set_sources_impl(t, positions, moments, n, source_order, source_order);
+}
+
+fmm_status fmm_set_sources_mixed(fmm_tree *t, const double *positions, const double *moments,
+                                 int64_t n, int s_lo, int s_hi)
+{
+    if (!t) return FMM_EINVAL;
+    t->err.clear();
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(t, FMM_EINVAL, "n out of range");
+    if (s_lo < 0 || s_hi < s_lo || s_hi > FMM_MAX_SOURCE_ORDER)
+        return fail(t, FMM_EORDER, "need 0 <= s_lo <= s_hi <= 2");
+    if (s_hi > s_lo && t->prec != FMM_FP64)
+        return fail(t, FMM_EORDER, "mixed source orders are evaluated by the FP64 form");
+    t->sys_off.assign({0, n});
+    return set_sources_impl(t, positions, moments, n, s_lo, s_hi);
 }
 
 fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const double *moments,
@@ -251,11 +265,11 @@ fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const dou
     const int64_t n = offsets[count];
     if (n >= ((int64_t)1 << 31)) return fail(t, FMM_EINVAL, "total n out of range");
     t->sys_off.assign(offsets, offsets + count + 1);
-    return set_sources_impl(t, positions, moments, n, source_order);
+    return set_sources_impl(t, positions, moments, n, source_order, source_order);
 }
 
 static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const double *moments,
-                                   int64_t n, int source_order)
+                                   int64_t n, int source_order, int source_order_hi)
 {
     if (source_order < 0 || source_order > FMM_MAX_SOURCE_ORDER)
         return fail(t, FMM_EORDER, "source order must be 0, 1 or 2");
@@ -270,7 +284,8 @@ static fmm_status set_sources_impl(fmm_tree *t, const double *positions, const d
     t->d_p = -1;
     t->n = n;
     t->s = source_order;
-    t->nS = nshell(source_order);
+    t->s_hi = source_order_hi;
+    t->nS = ntot(source_order_hi) - ntot(source_order - 1);
     fmm_status st = build_tree(t, positions, moments);
     if (st != FMM_OK) return st;
     if (t->profiling && n > 0) {
@@ -334,6 +349,7 @@ fmm_status fmm_get_info(const fmm_tree *t, fmm_tree_info *o)
     o->nleaves = t->nleaves;
     o->nlevels = t->nlevels;
     o->source_order = t->s;
+    o->source_order_hi = t->s_hi;
     o->n_m2l = t->have_lists ? t->n_m2l : 0;
     o->n_p2p = t->have_lists ? t->n_p2p : 0;
     o->n_p2p_interactions = t->have_lists ? t->n_p2p_inter : 0;
@@ -450,7 +466,22 @@ fmm_status fmm_direct_sum(void *cuda_stream, const double *positions, const doub
     if (n > 0 && (!positions || !moments)) return FMM_EINVAL;
     if (!targets && n_targets > n) return FMM_EINVAL;
     int64_t launches = 0;
-    launch_direct((cudaStream_t)cuda_stream, positions, moments, n, source_order, targets, n_targets,
+    launch_direct((cudaStream_t)cuda_stream, positions, moments, n, source_order, source_order,
+                  targets, n_targets, potential, field, &launches);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : FMM_ECUDA;
+}
+
+fmm_status fmm_direct_sum_mixed(void *cuda_stream, const double *positions, const double *moments,
+                                int64_t n, int s_lo, int s_hi, const int32_t *targets,
+                                int64_t n_targets, double *potential, double *field)
+{
+    if (n < 0 || n_targets < 0 || s_lo < 0 || s_hi < s_lo || s_hi > FMM_MAX_SOURCE_ORDER)
+        return FMM_EINVAL;
+    if (n > 0 && (!positions || !moments)) return FMM_EINVAL;
+    if (!targets && n_targets > n) return FMM_EINVAL;
+    int64_t launches = 0;
+    launch_direct((cudaStream_t)cuda_stream, positions, moments, n, s_lo, s_hi, targets, n_targets,
                   potential, field, &launches);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : FMM_ECUDA;

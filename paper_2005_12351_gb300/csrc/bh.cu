@@ -80,11 +80,12 @@ __device__ void d_series(const double R[3], int nD, const int *mi, const int32_t
     }
 }
 
-template <int S, bool PHI, bool FIELD>
+// SHI > S: every particle carries the orders S..SHI (mixed systems)
+template <int S, bool PHI, bool FIELD, int SHI = S>
 __global__ void __launch_bounds__(32 * kBHMaxWarps)
 k_bh(BHArgs a)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
+    constexpr int nS = Orders<S, SHI>::n;
     constexpr unsigned kAll = 0xffffffffu;
     extern __shared__ double bsm[];
     __shared__ int st_c[kBHMaxWarps][kBHStack];
@@ -160,7 +161,8 @@ k_bh(BHArgs a)
             for (int j = a.begin[c]; j < a.end[c]; ++j) {
                 const double sx = a.px[j], sy = a.py[j], sz = a.pz[j];
                 if (mine)
-                    pair_fp64<S, PHI, FIELD>(x - sx, y - sy, z - sz, a.Sm + (int64_t)j * nS, f, e0, e1, e2);
+                    pair_orders<S, SHI, PHI, FIELD>(x - sx, y - sy, z - sz, a.Sm + (int64_t)j * nS, f, e0,
+                                                    e1, e2);
             }
         } else {                          // open: children pushed last-first, taken in order
             const int ch0 = a.child[c];
@@ -193,7 +195,7 @@ k_bh(BHArgs a)
     }
 }
 
-template <int S>
+template <int S, int SHI = S>
 void launch_bh_s(const BHArgs &a, int want_phi, int want_field, unsigned grid, int threads, size_t smem,
                  cudaStream_t st)
 {
@@ -201,9 +203,9 @@ void launch_bh_s(const BHArgs &a, int want_phi, int want_field, unsigned grid, i
         allow_max_dynamic_smem(kern);
         kern<<<grid, threads, smem, st>>>(a);
     };
-    if (want_phi && want_field) go(k_bh<S, true, true>);
-    else if (want_phi) go(k_bh<S, true, false>);
-    else go(k_bh<S, false, true>);
+    if (want_phi && want_field) go(k_bh<S, true, true, SHI>);
+    else if (want_phi) go(k_bh<S, true, false, SHI>);
+    else go(k_bh<S, false, true, SHI>);
 }
 
 }  // namespace
@@ -263,9 +265,12 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
     const int wpb = std::max(1, std::min(kBHMaxWarps, (200 * 1024) / (a.nD * 256)));
     const size_t smem = (size_t)wpb * a.nD * 256;
     const unsigned grid = (unsigned)((t->n + 32 * wpb - 1) / (32 * wpb));
-    switch (s) {
+    switch (s * 3 + t->s_hi) {
     case 0: launch_bh_s<0>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
-    case 1: launch_bh_s<1>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    case 1: launch_bh_s<0, 1>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    case 2: launch_bh_s<0, 2>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    case 4: launch_bh_s<1>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
+    case 5: launch_bh_s<1, 2>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
     default: launch_bh_s<2>(a, want_phi, want_field, grid, 32 * wpb, smem, st); break;
     }
     ++t->launches;

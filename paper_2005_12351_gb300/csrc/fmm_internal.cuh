@@ -86,7 +86,9 @@ struct OpTables {
     // levels of increasing n_z >= 2, CSR over levels
     std::vector<int> h_unfold, h_unfold_off;
 };
-void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads, bool harmonic);
+// s: the lowest source order (the expansion's), s_hi: the highest (mixed
+// systems carry every order s..s_hi per particle; P2M reads all of them)
+void build_tables(OpTables &T, int s, int s_hi, int p, int n_lo, int m2l_threads, bool harmonic);
 
 // Operator layout of the tensor-core M2L (FMM_3XTF32) for one (s, p).  The
 // local-expansion columns are cut into groups of at most 128 (width W); the
@@ -163,7 +165,8 @@ struct fmm_tree {
 
     // system
     int64_t n = 0;
-    int s = -1, nS = 0;
+    // source orders s..s_hi per particle (s_hi = s: one order); nS moments each
+    int s = -1, s_hi = -1, nS = 0;
     bool have_sources = false;
     int64_t ncells = 0, nleaves = 0;
     int nlevels = 0;
@@ -181,7 +184,7 @@ struct fmm_tree {
     // D tables / operator tables
     int d_p = -1;                          // p the D table was built for
     fmm::OpTables tab;
-    int tab_key_s = -1, tab_key_p = -1, tab_key_nlo = -1, tab_key_h = -1;
+    int tab_key_s = -1, tab_key_p = -1, tab_key_nlo = -1, tab_key_h = -1, tab_key_shi = -1;
     int64_t m_cells = 0;                   // rows of the M/L buffers as sized
 
     // profiling
@@ -319,7 +322,7 @@ void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own
 // m2l_tc.cu
 fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D, int nkb, int N,
                       const int *kbn, int a_tmem, int passes, unsigned *err);
-void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
+void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s, int s_hi,
                    const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches);
 
 }  // namespace fmm

@@ -613,6 +613,10 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
 {
     cudaStream_t st = t->stream;
     const int s = t->s;
+    if (t->s_hi != t->s) {
+        t->err = "mixed source orders are evaluated by the FP64 form";
+        return FMM_EORDER;
+    }
     FMM_TRY(upload_consts32(t));
     DevTables tb;
     const int32_t *lut;

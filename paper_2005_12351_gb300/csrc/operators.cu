@@ -36,11 +36,12 @@ const MultiIndex &multi_index()
     return mi;
 }
 
-void build_tables(OpTables &T, int s, int p, int n_lo, int m2l_threads, bool harmonic)
+void build_tables(OpTables &T, int s, int s_hi, int p, int n_lo, int m2l_threads, bool harmonic)
 {
     const MultiIndex &I = multi_index();
     T.s = s; T.p = p; T.n_lo = n_lo; T.harmonic = harmonic;
-    T.nS = nshell(s); T.m0 = ntot(s - 1); T.nM = ntot(p + s) - T.m0; T.nL = ntot(p);
+    // source terms a: the orders s..s_hi, graded indices from ntot(s - 1) on
+    T.nS = ntot(s_hi) - ntot(s - 1); T.m0 = ntot(s - 1); T.nM = ntot(p + s) - T.m0; T.nL = ntot(p);
     T.nD = ntot(p + s);
     const int nK = ntot(p);                   // shift / particle monomials |k| <= p
 
@@ -276,7 +277,7 @@ __device__ __forceinline__ void axis_powers(double d, int P, double *out)
 constexpr int kP2MThreads = 128;
 constexpr int kP2MChunk = 16;
 constexpr int kP2MPer = 4;                // up to 4 * 128 = 512 M components
-constexpr int kMaxSrc = 6;                // source terms of one component (s <= 2)
+constexpr int kMaxSrc = 10;               // source terms of one particle (orders 0..2)
 
 // One block per leaf.  Each thread owns up to kP2MPer components m and keeps
 // the monomial index of m - a for each source term a in registers (an absent
@@ -614,9 +615,10 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         return o;
     };
     const int h = t->m2l_harmonic ? 1 : 0;
+    const int s_hi = std::max(s, t->s_hi);
     const bool rebuild = !(t->tab_key_s == s && t->tab_key_p == p && t->tab_key_nlo == n_lo &&
-                           t->tab_key_h == h);
-    if (rebuild) build_tables(T, s, p, n_lo, kM2LThreadsShared, h != 0);
+                           t->tab_key_h == h && t->tab_key_shi == s_hi);
+    if (rebuild) build_tables(T, s, s_hi, p, n_lo, kM2LThreadsShared, h != 0);
     {
         const MultiIndex &I = multi_index();
         std::vector<int> lutv((kMaxOrder + 1) * (kMaxOrder + 1) * (kMaxOrder + 1));
@@ -657,6 +659,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
                                               T.m2l_d16.data(), 4 * T.m2l_d16.size(),
                                               cudaMemcpyHostToDevice, t->stream), "tables"));
         t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo; t->tab_key_h = h;
+        t->tab_key_shi = s_hi;
     }
     const int32_t *B = (const int32_t *)t->b_tab_i32.ptr;
     dt->s = s; dt->p = p; dt->n_lo = n_lo; dt->nS = T.nS; dt->nM = T.nM; dt->nL = T.nL;

@@ -194,16 +194,21 @@ k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int
 // shared memory for two pair evaluations.  A chunk of up to 2*128 targets is
 // split into halves of h = ceil(cnt/2); thread (ti, copy) owns targets ti and
 // ti + h (the second one only if it exists).
-template <int S, bool PHI, bool FIELD>
+// SHI > S: every particle carries the orders S..SHI (mixed systems), the pair
+// terms summed shell by shell; fewer sources staged per round when the rows
+// are wide.
+template <int S, bool PHI, bool FIELD, int SHI = S>
 __global__ void __launch_bounds__(kP2PThreads)
 k_p2p_x2(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
          const int32_t *src, const double *px, const double *py, const double *pz,
          const double *Sm, const double *phi_far, const double *E_far, const int32_t *perm,
          double *phi_out, double *E_out)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
+    constexpr int nS = Orders<S, SHI>::n;
+    constexpr bool kS3 = S == 1 && SHI == 1;           // 3 S staged for the dipole field
+    constexpr int kP2PChunk = nS > 6 ? 256 : fmm::kP2PChunk;
     __shared__ double sx[kP2PChunk], sy[kP2PChunk], sz[kP2PChunk];
-    __shared__ double sS[kP2PChunk * nS], sS3[S == 1 ? kP2PChunk * 3 : 1];
+    __shared__ double sS[kP2PChunk * nS], sS3[kS3 ? kP2PChunk * 3 : 1];
     __shared__ double red[8][kP2PThreads];
     __shared__ int gbeg[kP2PGroups], gpre[kP2PGroups + 1];
     __shared__ int s_next_q, s_next_j, s_ngroups;
@@ -256,16 +261,21 @@ k_p2p_x2(const int32_t *leaves, const int32_t *begin, const int32_t *end, const 
                 for (int a = 0; a < nS; ++a) {
                     const double v = Sm[(int64_t)j * nS + a];
                     sS[d * nS + a] = v;
-                    if (S == 1) sS3[d * 3 + a] = 3.0 * v;
+                    if (kS3) sS3[d * 3 + a] = 3.0 * v;
                 }
             }
             __syncthreads();
             if (act) {
                 for (int j = sp; j < used; j += k) {
                     const double ax = sx[j], ay = sy[j], az = sz[j];
-                    const double *Sj = sS + j * nS, *S3 = S == 1 ? sS3 + j * 3 : sS;
-                    pair_p2p<S, PHI, FIELD>(xi - ax, yi - ay, zi - az, Sj, S3, f, e0, e1, e2);
-                    if (two) pair_p2p<S, PHI, FIELD>(xj - ax, yj - ay, zj - az, Sj, S3, g, g0, g1, g2);
+                    const double *Sj = sS + j * nS, *S3 = kS3 ? sS3 + j * 3 : sS;
+                    if constexpr (SHI == S) {
+                        pair_p2p<S, PHI, FIELD>(xi - ax, yi - ay, zi - az, Sj, S3, f, e0, e1, e2);
+                        if (two) pair_p2p<S, PHI, FIELD>(xj - ax, yj - ay, zj - az, Sj, S3, g, g0, g1, g2);
+                    } else {
+                        pair_orders<S, SHI, PHI, FIELD>(xi - ax, yi - ay, zi - az, Sj, f, e0, e1, e2);
+                        if (two) pair_orders<S, SHI, PHI, FIELD>(xj - ax, yj - ay, zj - az, Sj, g, g0, g1, g2);
+                    }
                 }
             }
             q = s_next_q;
@@ -664,12 +674,12 @@ __global__ void k_sym_plan(const int32_t *leaves, int64_t nleaves, const int32_t
 constexpr int kDirectThreads = 128;
 constexpr int kDirectTile = 256;
 
-template <int S, bool PHI, bool FIELD>
+template <int S, bool PHI, bool FIELD, int SHI = S>
 __global__ void __launch_bounds__(kDirectThreads)
 k_direct(const double *pos, const double *mom, int64_t n, const int32_t *targets, int64_t nt,
          double *phi, double *E)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
+    constexpr int nS = Orders<S, SHI>::n;
     __shared__ double sx[kDirectTile], sy[kDirectTile], sz[kDirectTile], sS[kDirectTile * nS];
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t i = t < nt ? (targets ? (int64_t)targets[t] : t) : 0;
@@ -691,8 +701,8 @@ k_direct(const double *pos, const double *mom, int64_t n, const int32_t *targets
         __syncthreads();
         if (active)
             for (int u = 0; u < cnt; ++u)
-                pair_fp64<S, PHI, FIELD>(xi - sx[u], yi - sy[u], zi - sz[u], sS + u * nS, f, e0,
-                                         e1, e2);
+                pair_orders<S, SHI, PHI, FIELD>(xi - sx[u], yi - sy[u], zi - sz[u], sS + u * nS, f,
+                                                e0, e1, e2);
     }
     if (t < nt) {
         if (!active) f = e0 = e1 = e2 = __longlong_as_double(0x7ff8000000000000ll);
@@ -724,7 +734,7 @@ void launch_sym_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
     else run(k_p2p_sym<S, false, true>, k_p2p_sym_gather<false, true>);
 }
 
-template <int S>
+template <int S, int SHI = S>
 void launch_p2p_s(fmm_tree *t, int want_phi, int want_field, double *phi, double *E)
 {
     auto args = [&](auto kern) {
@@ -736,10 +746,10 @@ void launch_p2p_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr,
             (const int32_t *)t->b_perm.ptr, phi, E);
     };
-    if (t->p2p_variant >= 1) {
-        if (want_phi && want_field) args(k_p2p_x2<S, true, true>);
-        else if (want_phi) args(k_p2p_x2<S, true, false>);
-        else args(k_p2p_x2<S, false, true>);
+    if (t->p2p_variant >= 1 || SHI != S) {         // mixed orders: this kernel only
+        if (want_phi && want_field) args(k_p2p_x2<S, true, true, SHI>);
+        else if (want_phi) args(k_p2p_x2<S, true, false, SHI>);
+        else args(k_p2p_x2<S, false, true, SHI>);
         return;
     }
     if (want_phi && want_field) args(k_p2p<S, true, true>);
@@ -747,14 +757,14 @@ void launch_p2p_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
     else args(k_p2p<S, false, true>);
 }
 
-template <int S>
+template <int S, int SHI = S>
 void launch_direct_s(cudaStream_t st, const double *pos, const double *mom, int64_t n,
                      const int32_t *targets, int64_t nt, double *phi, double *E)
 {
     const unsigned g = (unsigned)((nt + kDirectThreads - 1) / kDirectThreads);
-    if (phi && E) k_direct<S, true, true><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
-    else if (phi) k_direct<S, true, false><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
-    else k_direct<S, false, true><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
+    if (phi && E) k_direct<S, true, true, SHI><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
+    else if (phi) k_direct<S, true, false, SHI><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
+    else k_direct<S, false, true, SHI><<<g, kDirectThreads, 0, st>>>(pos, mom, n, targets, nt, phi, E);
 }
 
 }  // namespace
@@ -798,6 +808,16 @@ fmm_status sym_prepare(fmm_tree *t, int NC)
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out)
 {
     if (t->nleaves == 0) return FMM_OK;
+    const int so = t->s * 3 + t->s_hi;                 // (lowest, highest) source order
+    if (t->s_hi != t->s) {                            // mixed orders: two targets per thread
+        switch (so) {
+        case 1: launch_p2p_s<0, 1>(t, want_phi, want_field, phi_out, E_out); break;
+        case 2: launch_p2p_s<0, 2>(t, want_phi, want_field, phi_out, E_out); break;
+        default: launch_p2p_s<1, 2>(t, want_phi, want_field, phi_out, E_out); break;
+        }
+        ++t->launches;
+        return cuda_check(t, cudaGetLastError(), "p2p kernel");
+    }
     if (t->p2p_variant == 2) {
         const fmm_status ps = sym_prepare(t, (want_phi ? 1 : 0) + (want_field ? 3 : 0));
         if (ps == FMM_OK && t->sym_rows >= 0) {
@@ -827,12 +847,16 @@ void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own
 }
 
 void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_t n, int s,
-                   const int32_t *targets, int64_t nt, double *phi, double *E, int64_t *launches)
+                   int s_hi, const int32_t *targets, int64_t nt, double *phi, double *E,
+                   int64_t *launches)
 {
     if (nt <= 0 || (!phi && !E)) return;
-    switch (s) {
+    switch (s * 3 + s_hi) {
     case 0: launch_direct_s<0>(st, pos, mom, n, targets, nt, phi, E); break;
-    case 1: launch_direct_s<1>(st, pos, mom, n, targets, nt, phi, E); break;
+    case 1: launch_direct_s<0, 1>(st, pos, mom, n, targets, nt, phi, E); break;
+    case 2: launch_direct_s<0, 2>(st, pos, mom, n, targets, nt, phi, E); break;
+    case 4: launch_direct_s<1>(st, pos, mom, n, targets, nt, phi, E); break;
+    case 5: launch_direct_s<1, 2>(st, pos, mom, n, targets, nt, phi, E); break;
     default: launch_direct_s<2>(st, pos, mom, n, targets, nt, phi, E); break;
     }
     ++*launches;

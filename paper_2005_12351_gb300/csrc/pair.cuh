@@ -51,4 +51,25 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, const
     }
 }
 
+// Moments per particle of the orders SLO..SHI (graded order, shell by shell).
+template <int SLO, int SHI>
+struct Orders {
+    static constexpr int n = ((SHI + 1) * (SHI + 2) * (SHI + 3) - SLO * (SLO + 1) * (SLO + 2)) / 6;
+};
+
+// A particle carrying every order SLO..SHI (§2 mixed systems): the sum of the
+// pair terms of its shells, the moments of shell s starting after those of
+// the lower shells.
+template <int SLO, int SHI, bool PHI, bool FIELD>
+__device__ __forceinline__ void pair_orders(double dx, double dy, double dz, const double *Sj,
+                                            double &f, double &e0, double &e1, double &e2)
+{
+    pair_fp64<SLO, PHI, FIELD>(dx, dy, dz, Sj, f, e0, e1, e2);
+    if constexpr (SHI >= SLO + 1)
+        pair_fp64<SLO + 1, PHI, FIELD>(dx, dy, dz, Sj + (SLO + 1) * (SLO + 2) / 2, f, e0, e1, e2);
+    if constexpr (SHI >= SLO + 2)
+        pair_fp64<SLO + 2, PHI, FIELD>(dx, dy, dz, Sj + (SLO + 1) * (SLO + 2) / 2 + (SLO + 2) * (SLO + 3) / 2,
+                                       f, e0, e1, e2);
+}
+
 }  // namespace fmm

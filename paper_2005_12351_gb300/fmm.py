@@ -41,7 +41,7 @@ class TreeInfo(C.Structure):
                 ("n_doffsets", C.c_int64), ("theta", C.c_double), ("lo", C.c_double * 3),
                 ("side", C.c_double), ("device_bytes", C.c_int64), ("nsystems", C.c_int64),
                 ("tc_tiles", C.c_int64), ("tc_rows", C.c_int64), ("tc_chunks", C.c_int64),
-                ("bh_m2p", C.c_int64), ("bh_p2p", C.c_int64)]
+                ("bh_m2p", C.c_int64), ("bh_p2p", C.c_int64), ("source_order_hi", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,8 +118,10 @@ def _dev_f64(x, name, shape1=None):
     return x
 
 
-def source_terms(s: int) -> int:
-    return (s + 1) * (s + 2) // 2
+def source_terms(s: int, s_hi: int = None) -> int:
+    """Moments per particle of the orders s..s_hi (s_hi = s: one order)."""
+    hi = s if s_hi is None else s_hi
+    return sum((k + 1) * (k + 2) // 2 for k in range(s, hi + 1))
 
 
 class FMMTree:
@@ -147,7 +149,19 @@ class FMMTree:
         n = positions.shape[0]
         st = lib().fmm_set_sources(self._h, _ptr(positions), _ptr(moments), n, int(source_order))
         _check(st, self._h, "set_sources")
-        self.n, self.s = n, source_order
+        self.n, self.s, self.s_hi = n, source_order, source_order
+
+    def set_sources_mixed(self, positions, moments, s_lo: int, s_hi: int):
+        """Every particle carries the moments of the orders s_lo..s_hi (graded order)."""
+        _dev_f64(positions, "positions", 3)
+        _dev_f64(moments, "moments", source_terms(s_lo, s_hi))
+        n = positions.shape[0]
+        fn = lib().fmm_set_sources_mixed
+        fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int]
+        fn.restype = C.c_int
+        _check(fn(self._h, _ptr(positions), _ptr(moments), n, int(s_lo), int(s_hi)), self._h,
+               "set_sources_mixed")
+        self.n, self.s, self.s_hi = n, s_lo, s_hi
 
     def set_sources_batch(self, positions, moments, offsets, source_order: int):
         """A forest of independent systems; ``offsets`` is a host int sequence of count+1."""
@@ -159,7 +173,7 @@ class FMMTree:
         fn.restype = C.c_int
         st = fn(self._h, _ptr(positions), _ptr(moments), off, len(offsets) - 1, int(source_order))
         _check(st, self._h, "set_sources_batch")
-        self.n, self.s = int(offsets[-1]), source_order
+        self.n, self.s, self.s_hi = int(offsets[-1]), source_order, source_order
 
     def evaluate(self, p: int, theta: float, want_potential=True, want_field=True,
                  potential=None, field=None):
@@ -191,7 +205,7 @@ class FMMTree:
 
     def update_moments(self, moments):
         """Replace the moments of the current tree (caller's order); keeps tree, lists, caches."""
-        _dev_f64(moments, "moments", source_terms(self.s))
+        _dev_f64(moments, "moments", source_terms(self.s, getattr(self, "s_hi", self.s)))
         if moments.shape[0] != self.n:
             raise ValueError("moments must have %d rows" % self.n)
         fn = lib().fmm_update_moments
@@ -296,10 +310,11 @@ def create_tree(device=0, stream=None, max_leaf=64, precision="fp64", mem_budget
 
 
 def direct_sum(positions, moments, source_order, targets=None, want_potential=True,
-               want_field=True, stream=None):
-    """FP64 O(N^2) sum on the GPU at ``targets`` (int32 CUDA tensor or None)."""
+               want_field=True, stream=None, source_order_hi=None):
+    """FP64 O(N^2) sum on the GPU at ``targets`` (int32 CUDA tensor or None); sources of
+    the orders source_order..source_order_hi per particle when the latter is given."""
     _dev_f64(positions, "positions", 3)
-    _dev_f64(moments, "moments", source_terms(source_order))
+    _dev_f64(moments, "moments", source_terms(source_order, source_order_hi))
     n = positions.shape[0]
     if targets is not None:
         if not (targets.is_cuda and targets.dtype == torch.int32):
@@ -309,8 +324,16 @@ def direct_sum(positions, moments, source_order, targets=None, want_potential=Tr
         nt = n
     phi = torch.empty(nt, dtype=torch.float64, device=positions.device) if want_potential else None
     E = torch.empty((nt, 3), dtype=torch.float64, device=positions.device) if want_field else None
-    st = lib().fmm_direct_sum(_stream_ptr(stream), _ptr(positions), _ptr(moments), n,
-                              int(source_order), _ptr(targets), nt, _ptr(phi), _ptr(E))
+    if source_order_hi is None:
+        st = lib().fmm_direct_sum(_stream_ptr(stream), _ptr(positions), _ptr(moments), n,
+                                  int(source_order), _ptr(targets), nt, _ptr(phi), _ptr(E))
+    else:
+        fn = lib().fmm_direct_sum_mixed
+        fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p,
+                       C.c_int64, C.c_void_p, C.c_void_p]
+        fn.restype = C.c_int
+        st = fn(_stream_ptr(stream), _ptr(positions), _ptr(moments), n, int(source_order),
+                int(source_order_hi), _ptr(targets), nt, _ptr(phi), _ptr(E))
     _check(st, None, "direct_sum")
     return phi, E
 
