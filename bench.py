@@ -470,6 +470,60 @@ def measure_bh(args, w, dev, world, pos_d, S_d, flush):
                          "peak_source": args.fp64_peak_source}}
 
 
+def measure_mixed_orders(args, w, dev, world, flush):
+    """Mixed source orders on the headline geometry: every particle carries a charge and
+    a dipole (orders 0..1; the expansion starts at order 0, so multipoles run to p).  A
+    step = tree build + evaluate, as the main line; FP64."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    n, p, theta = w["n"], w["p"], w["theta"]
+    lo, hi = 0, 1
+    pos_np, S_np = synth.make_system_mixed(n, lo, hi, w["dist"], w["seed"] + 7)
+    pos_d = torch.from_numpy(pos_np).to(dev)
+    S_d = torch.from_numpy(S_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"])
+    tree.set_profiling(True)
+    E_d = torch.empty((n, 3), dtype=torch.float64, device=dev)
+
+    def step():
+        tree.set_sources_mixed(pos_d, S_d, lo, hi)
+        tree.evaluate(p, theta, False, True, field=E_d)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 5))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    phases = []
+    for k in range(steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phases.append(tree.phase_times())
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
+    info = tree.info()
+    tg = synth.sample_indices(n, args.err_samples, 23)
+    tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
+    _, E_ref = fmm.direct_sum(pos_d, S_d, lo, targets=tg_d, want_potential=False, source_order_hi=hi)
+    Ef = E_d[tg_d.long()]
+    err = math.sqrt(((Ef - E_ref) ** 2).sum().item() / (E_ref ** 2).sum().item())
+    pair = flops_per_pair(0, False, True) + flops_per_pair(1, False, True)
+    flops = pair * info["n_p2p_interactions"]
+    achieved = flops / (ph["p2p"] / 1e3) / 1e12
+    tree.destroy()
+    return {"sources": "charge + dipole per particle (orders 0..1)", "p": p, "theta": theta,
+            "value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "field_rel_rms": err,
+            "targets": int(len(tg)), "phase_ms": ph,
+            "roofline": {"bound": "alu", "kernel": "p2p", "achieved": achieved,
+                         "peak": args.fp64_peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / args.fp64_peak_tflops, "traffic": None,
+                         "algorithmic_flops": flops, "peak_source": args.fp64_peak_source}}
+
+
 def serving_stream(count: int, seed: int):
     """Requests drawn like the serving workload: N log-uniform in [1e3, 2e6],
     source order uniform over {0, 1, 2}, p uniform over {4..10}, uniform or
@@ -587,6 +641,8 @@ def run_ours(args, w):
                                                        / main["rel_err"]["field_rel_rms"])
     if args.precision == "fp64" and not args.no_bh and "batch" not in w:
         line["bh"] = measure_bh(args, w, dev, world, pos_d, S_d, flush)
+    if args.precision == "fp64" and not args.no_mixed_orders and "batch" not in w:
+        line["mixed_orders"] = measure_mixed_orders(args, w, dev, world, flush)
     if not args.no_graph:
         line["graph"] = measure_graph(args, w, args.graph_precision or args.precision, dev, world,
                                       pos_d, S_h, S_d, flush)
@@ -625,6 +681,8 @@ def main(argv=None):
     ap.add_argument("--no-bh", action="store_true",
                     help="skip the Barnes-Hut line (FP64, same workload, theta_BH = theta / 2)")
     ap.add_argument("--bh-theta", type=float, default=None)
+    ap.add_argument("--no-mixed-orders", action="store_true",
+                    help="skip the charge + dipole (orders 0..1) line")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)

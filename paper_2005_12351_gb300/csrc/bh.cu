@@ -13,7 +13,17 @@
 // walk; a cell is visited once for all the lanes that reach it.  The MAC is
 // evaluated with explicitly rounded operations (no contraction), in the order
 // ((dx dx + dy dy) + dz dz), so the decisions are those of a plain FP64 program.
+//
+// M2P runs a program built once per (orders, p, outputs, harmonic) on the host:
+// the D_k(x - z_c) to compute in graded order, each as at most six terms
+// (coefficient, axis of R or none, earlier D) of the recurrence, then the
+// contraction with the cell's multipole.  With the harmonic M2L (the handle's
+// default) the multipoles are folded onto m_z <= 1 and only the D_k with
+// k_z <= 2 are needed: D_{k+2z} = -D_{k+2x} - D_{k+2y} moves every other
+// term onto those (the recurrence of such a D_k reads only such D).
+#include <cstring>
 #include <algorithm>
+#include <stdexcept>
 #include <vector>
 
 #include "fmm_internal.cuh"
@@ -35,48 +45,36 @@ struct BHArgs {
     const double *centre, *half;
     const double *px, *py, *pz, *Sm;
     const int32_t *perm;
-    const double *M;
-    const int4 *mt;          // per multipole term: D index of m, m + e_x, m + e_y, m + e_z
+    const double *M;         // the multipole rows the contraction reads (nM terms per cell)
+    const int4 *mt;          // per contraction term: D positions of m, m + e_x, m + e_y, m + e_z
     unsigned long long *count;   // [M2P evaluations, P2P pairs], added per warp
-    const int *mi;           // packed multi-indices of the graded order
-    const int32_t *lut;      // (nx, ny, nz) -> graded index, stride kMaxOrder + 1
+    const int *poff;         // [nD + 1] term ranges of the D program
+    const double *pcoef;     // term coefficients
+    const int *pw;           // term words: (axis of R + 1) | (position of the D read) << 2
     double *phi_out, *E_out;
 };
 
-// D_n(R) = grad^n (1/|R|) for the graded indices 0 .. nD-1 into D[32 k] (this
-// lane's column of its warp's rows), by the recurrence of the D tables:
+// D_k(R) = grad^k (1/|R|) for the program's nD entries into D[32 q] (this
+// lane's column of its warp's rows), each by the recurrence
 // r^2 D_n = -(2 n_i - 1) R_i D_{n-e_i} - (n_i - 1)^2 D_{n-2e_i}
 //           - sum_{j != i} [2 n_j R_j D_{n-e_j} + n_j (n_j - 1) D_{n-2e_j}],
-// i = the first axis with n_i >= 1.
-__device__ void d_series(const double R[3], int nD, const int *mi, const int32_t *lut, double *D)
+// i = the first axis with n_i >= 1, as precomputed terms.
+__device__ __forceinline__ void d_program(double R0, double R1, double R2, const BHArgs &a, double *D)
 {
-    constexpr int L = kMaxOrder + 1;
-    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    const double r2 = R0 * R0 + R1 * R1 + R2 * R2;
     const double inv_r2 = 1.0 / r2;
     D[0] = rsqrt(r2);
-    for (int idx = 1; idx < nD; ++idx) {
-        const int v = mi_at(mi, idx);
-        const int n[3] = {mi_nx(v), mi_ny(v), mi_nz(v)};
-        const int i = n[0] ? 0 : (n[1] ? 1 : 2);
-        int m[3] = {n[0], n[1], n[2]};
-        m[i] -= 1;
-        double acc = -(2.0 * n[i] - 1.0) * R[i] * D[32 * __ldg(lut + (m[0] * L + m[1]) * L + m[2])];
-        if (n[i] >= 2) {
-            m[i] -= 1;
-            acc -= (double)((n[i] - 1) * (n[i] - 1)) * D[32 * __ldg(lut + (m[0] * L + m[1]) * L + m[2])];
+    for (int q = 1; q < a.nD; ++q) {
+        const int t0 = __ldg(a.poff + q), t1 = __ldg(a.poff + q + 1);
+        double acc = 0.0;
+        for (int t = t0; t < t1; ++t) {
+            const int w = __ldg(a.pw + t);
+            const double c = __ldg(a.pcoef + t);
+            const int ax = w & 3;
+            const double cr = ax == 0 ? c : c * (ax == 1 ? R0 : (ax == 2 ? R1 : R2));
+            acc = fma(cr, D[32 * (w >> 2)], acc);
         }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j == i || n[j] == 0) continue;
-            int q[3] = {n[0], n[1], n[2]};
-            q[j] -= 1;
-            acc -= 2.0 * n[j] * R[j] * D[32 * __ldg(lut + (q[0] * L + q[1]) * L + q[2])];
-            if (n[j] >= 2) {
-                q[j] -= 1;
-                acc -= (double)(n[j] * (n[j] - 1)) * D[32 * __ldg(lut + (q[0] * L + q[1]) * L + q[2])];
-            }
-        }
-        D[32 * idx] = acc * inv_r2;
+        D[32 * q] = acc * inv_r2;
     }
 }
 
@@ -134,8 +132,7 @@ k_bh(BHArgs a)
             acc = __dmul_rn(h, h) < __dmul_rn(a.theta2, dd);
         }
         if (acc) {                        // M2P
-            const double R[3] = {dx, dy, dz};
-            d_series(R, a.nD, a.mi, a.lut, Dl);
+            d_program(dx, dy, dz, a, Dl);
             const double *Mc = a.M + (int64_t)c * a.nM;
             double pf = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
             for (int q = 0; q < a.nM; ++q) {
@@ -208,6 +205,55 @@ void launch_bh_s(const BHArgs &a, int want_phi, int want_field, unsigned grid, i
     else go(k_bh<S, false, true, SHI>);
 }
 
+// The M2P program (see the file header): D entries, their recurrence terms,
+// and per contraction term the D positions of m and m + e_k.
+struct BHProgram {
+    std::vector<int> off, w;
+    std::vector<double> coef;
+    std::vector<int4> mt;
+};
+
+BHProgram bh_program(int p, bool field, bool harmonic, const std::vector<int> &terms_m)
+{
+    const MultiIndex &I = multi_index();
+    const int P = p + (field ? 1 : 0);
+    std::vector<int> at(ntot(P), -1), ks;
+    for (int k = 0; k < ntot(P); ++k)
+        if (!harmonic || I.nz[k] <= 2) {
+            at[k] = (int)ks.size();
+            ks.push_back(k);
+        }
+    BHProgram g;
+    g.off.assign(2, 0);                               // D_0 = 1/r: no terms
+    for (size_t q = 1; q < ks.size(); ++q) {
+        const int k = ks[q];
+        const int n[3] = {I.nx[k], I.ny[k], I.nz[k]};
+        const int i = n[0] ? 0 : (n[1] ? 1 : 2);
+        auto term = [&](double c, int axis, int dax, int dcnt) {
+            int m[3] = {n[0], n[1], n[2]};
+            m[dax] -= dcnt;
+            const int src = at[I(m[0], m[1], m[2])];
+            if (src < 0) throw std::logic_error("Barnes-Hut program reads a D it does not compute");
+            g.coef.push_back(c);
+            g.w.push_back((axis + 1) | src << 2);
+        };
+        term(-(2.0 * n[i] - 1.0), i, i, 1);
+        if (n[i] >= 2) term(-(double)((n[i] - 1) * (n[i] - 1)), -1, i, 2);
+        for (int j = 0; j < 3; ++j) {
+            if (j == i || n[j] == 0) continue;
+            term(-2.0 * n[j], j, j, 1);
+            if (n[j] >= 2) term(-(double)(n[j] * (n[j] - 1)), -1, j, 2);
+        }
+        g.off.push_back((int)g.coef.size());
+    }
+    for (int m : terms_m) {
+        const int x = I.nx[m], y = I.ny[m], z = I.nz[m];
+        g.mt.push_back(make_int4(at[m], field ? at[I(x + 1, y, z)] : 0, field ? at[I(x, y + 1, z)] : 0,
+                                 field ? at[I(x, y, z + 1)] : 0));
+    }
+    return g;
+}
+
 }  // namespace
 
 fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field, double *phi_out,
@@ -219,21 +265,35 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
     const int32_t *lut;
     FMM_TRY(upload_tables(t, s, p - s, 0, &tb, &lut));
     FMM_TRY(run_upward(t, tb, false));
-    if (t->bh_key_s != s || t->bh_key_p != p) {
-        // per multipole term m: D indices of m and m + e_k (graded order)
-        const MultiIndex &I = multi_index();
-        std::vector<int4> mt(tb.nM);
-        for (int q = 0; q < tb.nM; ++q) {
-            const int m = q + tb.m0;
-            mt[q] = make_int4(m, I(I.nx[m] + 1, I.ny[m], I.nz[m]), I(I.nx[m], I.ny[m] + 1, I.nz[m]),
-                              I(I.nx[m], I.ny[m], I.nz[m] + 1));
-        }
+    const bool harm = tb.harmonic != 0;
+    const double *Mc = (const double *)t->b_M.ptr;
+    if (harm) {                                          // multipoles folded onto m_z <= 1
+        FMM_TRY(ensure(t, t->b_Mh, 8 * (size_t)t->ncells * tb.nMh));
+        launch_fold_m(st, (const double *)t->b_M.ptr, tb.nM, t->ncells, tb, (double *)t->b_Mh.ptr, tb.nMh);
+        ++t->launches;
+        Mc = (const double *)t->b_Mh.ptr;
+    }
+    const int key = s | t->s_hi << 2 | p << 4 | (want_field ? 1 : 0) << 9 | (harm ? 1 : 0) << 10;
+    if (t->bh_key_s != key) {
+        std::vector<int> terms_m;                        // global index of each contraction term
+        for (int r = 0; r < tb.nMh; ++r) terms_m.push_back(t->tab.h_rm[r] + tb.m0);
+        const BHProgram g = bh_program(p, want_field != 0, harm, terms_m);
+        // one buffer: mt (int4) | coef (double) | off | w
+        const size_t b_mt = sizeof(int4) * g.mt.size(), b_c = sizeof(double) * g.coef.size();
+        const size_t b_off = sizeof(int) * g.off.size(), b_w = sizeof(int) * std::max<size_t>(g.w.size(), 1);
+        std::vector<uint8_t> host(b_mt + b_c + b_off + b_w, 0);
+        std::memcpy(host.data(), g.mt.data(), b_mt);
+        if (b_c) std::memcpy(host.data() + b_mt, g.coef.data(), b_c);
+        std::memcpy(host.data() + b_mt + b_c, g.off.data(), b_off);
+        if (!g.w.empty()) std::memcpy(host.data() + b_mt + b_c + b_off, g.w.data(), sizeof(int) * g.w.size());
         t->bh_key_s = -1;
-        FMM_TRY(ensure(t, t->b_bh_mt, sizeof(int4) * mt.size()));
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_bh_mt.ptr, mt.data(), sizeof(int4) * mt.size(),
-                                              cudaMemcpyHostToDevice, st), "Barnes-Hut table"));
-        t->bh_key_s = s;
-        t->bh_key_p = p;
+        FMM_TRY(ensure(t, t->b_bh_mt, host.size()));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_bh_mt.ptr, host.data(), host.size(), cudaMemcpyHostToDevice,
+                                              st), "Barnes-Hut program"));
+        t->bh_key_s = key;
+        t->bh_nD = (int)g.off.size() - 1;
+        t->bh_nmt = (int)g.mt.size();
+        t->bh_ncoef = (int)g.coef.size();
     }
     FMM_TRY(ensure(t, t->b_bh_cnt, 16));
     FMM_TRY(cuda_check(t, cudaMemsetAsync(t->b_bh_cnt.ptr, 0, 16, st), "memset"));
@@ -241,8 +301,8 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
     a.count = (unsigned long long *)t->b_bh_cnt.ptr;
     a.n = t->n;
     a.nsys = std::max(1, (int)t->sys_off.size() - 1);
-    a.nM = tb.nM;
-    a.nD = ntot(p + (want_field ? 1 : 0));
+    a.nM = t->bh_nmt;
+    a.nD = t->bh_nD;
     a.theta2 = theta * theta;
     a.nchild = (const int32_t *)t->b_nchild.ptr;
     a.child = (const int32_t *)t->b_child.ptr;
@@ -255,10 +315,15 @@ fmm_status run_bh(fmm_tree *t, int p, double theta, int want_phi, int want_field
     a.pz = (const double *)t->b_pz.ptr;
     a.Sm = (const double *)t->b_S.ptr;
     a.perm = (const int32_t *)t->b_perm.ptr;
-    a.M = (const double *)t->b_M.ptr;
-    a.mt = (const int4 *)t->b_bh_mt.ptr;
-    a.mi = tb.mi;
-    a.lut = lut;
+    a.M = Mc;
+    {
+        const uint8_t *base = (const uint8_t *)t->b_bh_mt.ptr;
+        const size_t b_mt = sizeof(int4) * t->bh_nmt, b_c = sizeof(double) * t->bh_ncoef;
+        a.mt = (const int4 *)base;
+        a.pcoef = (const double *)(base + b_mt);
+        a.poff = (const int *)(base + b_mt + b_c);
+        a.pw = a.poff + (t->bh_nD + 1);
+    }
     a.phi_out = phi_out;
     a.E_out = E_out;
     // D rows in shared memory: 32 lanes x nD doubles per warp

@@ -210,7 +210,8 @@ struct fmm_tree {
     DevBuf b_M, b_L, b_phi, b_E;
     DevBuf b_Mh, b_Mh32;                   // folded multipoles of the harmonic M2L
     // Barnes-Hut: the M2P term table of (bh_key_s, bh_key_p)
-    int bh_key_s = -1, bh_key_p = -1;
+    int bh_key_s = -1, bh_key_p = -1;      // bh_key_s: key of the program in b_bh_mt
+    int bh_nD = 0, bh_nmt = 0, bh_ncoef = 0;
     bool bh_ran = false;                   // b_bh_cnt holds the last walk's counts
     DevBuf b_bh_mt, b_bh_cnt;
     DevBuf b_tab_i32, b_tab_u32;
