@@ -31,6 +31,13 @@ METRIC = "FMM particles/sec at p=6 & rel err vs FP64 direct sum; served p50/p99 
 UNIT = "particles/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 
+# DRAM bytes (read + write) per particle of the dominant kernels, from full ncu captures of
+# the 125k-dipole case (same leaf occupancy; the kernels' traffic grows with the particles):
+# k_p2p_sym 7.55 MB + 0.04 MB, k_p2p32 9.65 MB + 0 MB per launch
+# (profiles/k_p2p_sym_k_m2l_fp64_dipole_125k_p6.md, profiles/fp32_kernels_dipole_125k_p6.md)
+TRAFFIC_PER_PARTICLE = {("fp64", 1): 7.5896e6 / 125_000, ("fp32", 1): 9.6481e6 / 125_000,
+                        ("3xtf32", 1): 9.6481e6 / 125_000}
+
 
 def flops_per_pair(s: int, want_phi: bool, want_field: bool) -> int:
     """Algorithmic FP64 flops of one P2P pair (rsqrt counted as one op)."""
@@ -338,8 +345,12 @@ def measure_form(args, w, precision, dev, world, rank, pos_h, S_h, pos_d, S_d, f
     cand = {"p2p": pair_flops, "m2l": m2l_flops}
     dom = max(cand, key=lambda k: ph[k])
     achieved = cand[dom] / (ph[dom] / 1e3) / 1e12
+    tpp = TRAFFIC_PER_PARTICLE.get((precision, s)) if dom == "p2p" and "batch" not in w else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tpp * n if tpp is not None else None,
+                "traffic_source": ("ncu dram bytes of the 125k-dipole capture, scaled by particles"
+                                   if tpp is not None else None),
                 "algorithmic_flops": cand[dom], "peak_source": src}
     if precision == "3xtf32" and info["tc_rows"] > 0:
         # the M2L on the tensor cores: 3 TF32 products per FP32 multiply-add of the method

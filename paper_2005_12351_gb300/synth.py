@@ -162,6 +162,8 @@ WORKLOADS = {
     "dipole_1m_p6": dict(n=1_000_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260001),
     # same leaf occupancy as the 1M workload (leaves one level higher): profiling-size case
     "dipole_125k_p6": dict(n=125_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260011),
+    # inputs larger than L2 (4M x 48 B): the case for HBM counters of the per-particle kernels
+    "dipole_4m_p6": dict(n=4_000_000, s=1, p=6, theta=0.5, ncrit=128, dist="uniform", seed=20260012),
     "dipole_plummer_4m_p8": dict(n=4_000_000, s=1, p=8, theta=0.5, ncrit=128, dist="plummer",
                                  seed=20260002),
     # 4,096 independent uniform-cube systems, N log-uniform in [256, 65536], quadrupoles
