@@ -470,25 +470,42 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         int q = q0, j_in = 0;
         while (q < q1) {
             __syncthreads();
-            if (tid == 0) {
-                int used = 0, g = 0;
-                while (q < q1 && used < CH && g < kGroups) {
-                    const int sl = src[q];
-                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, CH - used);
-                    const long long rs = 1ll << (kLevels - level[sl]);
-                    gbeg[g] = lb;
-                    gpre[g] = used;
-                    gdx[g] = (float)((double)((2ll * cx[sl] + 1) * rs - ccx) * unit);
-                    gdy[g] = (float)((double)((2ll * cy[sl] + 1) * rs - ccy) * unit);
-                    gdz[g] = (float)((double)((2ll * cz[sl] + 1) * rs - ccz) * unit);
-                    ++g;
-                    used += take;
-                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
+            if (tid < 32) {
+                // warp 0 takes up to 32 partner leaves of this round in parallel: lane l
+                // the entry q + l (the first continues at j_in); a prefix sum of their
+                // sizes decides which fit in CH (the last one possibly in part)
+                const int lane = tid, qq = q + lane;
+                int lb = 0, take = 0, sl = 0;
+                if (qq < q1) {
+                    sl = src[qq];
+                    lb = begin[sl] + (lane == 0 ? j_in : 0);
+                    take = end[sl] - lb;
                 }
-                gpre[g] = used;
-                s_ngroups = g;
-                s_next_q = q;
-                s_next_j = j_in;
+                int incl = take;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int excl = incl - take;
+                const bool in = qq < q1 && excl < CH;
+                const int tk = in ? min(take, CH - excl) : 0;
+                if (in) {
+                    const long long rs = 1ll << (kLevels - level[sl]);
+                    gbeg[lane] = lb;
+                    gpre[lane] = excl;
+                    gdx[lane] = (float)((double)((2ll * cx[sl] + 1) * rs - ccx) * unit);
+                    gdy[lane] = (float)((double)((2ll * cy[sl] + 1) * rs - ccy) * unit);
+                    gdz[lane] = (float)((double)((2ll * cz[sl] + 1) * rs - ccz) * unit);
+                }
+                const int ng = __popc(__ballot_sync(0xffffffffu, in));   // the taken entries: a prefix
+                if (lane == ng - 1) {
+                    const bool whole = tk == take;
+                    gpre[ng] = excl + tk;
+                    s_ngroups = ng;
+                    s_next_q = whole ? qq + 1 : qq;
+                    s_next_j = whole ? 0 : (lb - begin[sl]) + tk;
+                }
             }
             __syncthreads();
             const int ng = s_ngroups, used = gpre[ng];

@@ -277,11 +277,13 @@ __device__ __forceinline__ void axis_powers(double d, int P, double *out)
 constexpr int kP2MThreads = 128;
 constexpr int kP2MChunk = 16;
 constexpr int kP2MPer = 4;                // up to 4 * 128 = 512 M components
-constexpr int kMaxSrc = 10;               // source terms of one particle (orders 0..2)
+// source terms of one particle: the kernel is instantiated for 3, 6 and 10 (one
+// order up to a dipole, a quadrupole, mixed orders) and takes the smallest that fits
 
 // One block per leaf.  Each thread owns up to kP2MPer components m and keeps
 // the monomial index of m - a for each source term a in registers (an absent
 // term points at a zero slot), so the particle loop is branch-free.
+template <int kMaxSrc>
 __global__ void __launch_bounds__(kP2MThreads)
 k_p2m(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
       const double *px, const double *py, const double *pz, const double *S, DevTables tb,
@@ -739,11 +741,16 @@ fmm_status run_upward(fmm_tree *t, const DevTables &tb, bool rec)
     const double *centre = (const double *)t->b_centre.ptr;
     {
         size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
-        allow_max_dynamic_smem(k_p2m);
-        k_p2m<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(
-            (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
-            (const int32_t *)t->b_end.ptr, centre, (const double *)t->b_px.ptr,
-            (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr, (const double *)t->b_S.ptr, tb, M);
+        auto go = [&](auto kern) {
+            allow_max_dynamic_smem(kern);
+            kern<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(
+                (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
+                (const int32_t *)t->b_end.ptr, centre, (const double *)t->b_px.ptr,
+                (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr, (const double *)t->b_S.ptr, tb, M);
+        };
+        if (tb.nS <= 3) go(k_p2m<3>);
+        else if (tb.nS <= 6) go(k_p2m<6>);
+        else go(k_p2m<10>);
         ++t->launches;
     }
     if (rec) record(t, 7);
