@@ -11,7 +11,7 @@
  *   |n| = nx + ny + nz, D_n(R) = grad^n (1/|R|).
  * The kernel is phi = q / |x_b - x_a| (§2, Eq. (1)), with no 4 pi eps0.
  *
- * Readings where the paper is garbled or silent (each listed in the design doc):
+ * Readings where the paper is garbled or silent:
  *   - multipole index set  s <= |m| <= p + s, local set |n| <= p, and the
  *     M2L keeps |n| + |m| <= p + s; D_n is needed up to order p + s;
  *   - M2M shift uses (z' - z)^k (new centre minus old), from Eq. (3);
