@@ -89,10 +89,50 @@ __device__ __forceinline__ void pair_p2p(double dx, double dy, double dz, const 
     }
 }
 
+// The partner leaves of one staging round, taken by warp 0 in parallel: lane l
+// the list entry q + l (the first continues at particle j_in of its leaf); a
+// prefix sum of their sizes decides which fit in cap particles (the last one
+// possibly in part).  Writes groups [0, ng): first particle gbeg and offset
+// gpre in the round, gpre[ng] = the round's size, and where the next round
+// starts.  Requires q < q1.
+__device__ __forceinline__ void stage_groups(int lane, int q, int q1, int j_in, int cap,
+                                             const int32_t *src, const int32_t *begin,
+                                             const int32_t *end, int *gbeg, int *gpre, int *ngroups,
+                                             int *next_q, int *next_j)
+{
+    const int qq = q + lane;
+    int lb = 0, take = 0, sl = 0;
+    if (qq < q1) {
+        sl = src[qq];
+        lb = begin[sl] + (lane == 0 ? j_in : 0);
+        take = end[sl] - lb;
+    }
+    int incl = take;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - take;
+    const bool in = qq < q1 && excl < cap;
+    const int tk = in ? min(take, cap - excl) : 0;
+    if (in) {
+        gbeg[lane] = lb;
+        gpre[lane] = excl;
+    }
+    const int ng = __popc(__ballot_sync(0xffffffffu, in));   // the taken entries: a prefix
+    if (lane == ng - 1) {
+        const bool whole = tk == take;
+        gpre[ng] = excl + tk;
+        *ngroups = ng;
+        *next_q = whole ? qq + 1 : qq;
+        *next_j = whole ? 0 : (lb - begin[sl]) + tk;
+    }
+}
+
 // One block per target leaf.  The flattened source list of the leaf (all
 // particles of its P2P partner leaves, in list order) is staged in shared
-// memory in rounds of up to kP2PChunk particles from at most kP2PGroups
-// leaves.  A leaf of nt <= 128 targets is covered k = floor(128/nt) times and
+// memory in rounds of up to kP2PChunk particles from at most 32 leaves.  A leaf of nt <= 128 targets is covered k = floor(128/nt) times and
 // copy c takes the staged sources c, c+k, c+2k, ..., so all threads run the
 // same trip count.  Copies are combined in a fixed order, the L2P far field
 // is added and the result is written at the caller's original index.
@@ -126,22 +166,9 @@ k_p2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int
         int q = q0, j_in = 0;                 // next partner leaf and offset inside it
         while (q < q1) {
             __syncthreads();                  // previous round's staged data is consumed
-            if (tid == 0) {
-                int used = 0, g = 0;
-                while (q < q1 && used < kP2PChunk && g < kP2PGroups) {
-                    const int sl = src[q];
-                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
-                    gbeg[g] = lb;
-                    gpre[g] = used;
-                    ++g;
-                    used += take;
-                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
-                }
-                gpre[g] = used;
-                s_ngroups = g;
-                s_next_q = q;
-                s_next_j = j_in;
-            }
+            if (tid < 32)
+                stage_groups(tid, q, q1, j_in, kP2PChunk, src, begin, end, gbeg, gpre, &s_ngroups,
+                             &s_next_q, &s_next_j);
             __syncthreads();
             const int ng = s_ngroups, used = gpre[ng];
             for (int d = tid; d < used; d += kP2PThreads) {
@@ -231,22 +258,9 @@ k_p2p_x2(const int32_t *leaves, const int32_t *begin, const int32_t *end, const 
         int q = q0, j_in = 0;
         while (q < q1) {
             __syncthreads();
-            if (tid == 0) {
-                int used = 0, gg = 0;
-                while (q < q1 && used < kP2PChunk && gg < kP2PGroups) {
-                    const int sl = src[q];
-                    const int lb = begin[sl] + j_in, take = min(end[sl] - lb, kP2PChunk - used);
-                    gbeg[gg] = lb;
-                    gpre[gg] = used;
-                    ++gg;
-                    used += take;
-                    if (lb + take == end[sl]) { ++q; j_in = 0; } else { j_in += take; }
-                }
-                gpre[gg] = used;
-                s_ngroups = gg;
-                s_next_q = q;
-                s_next_j = j_in;
-            }
+            if (tid < 32)
+                stage_groups(tid, q, q1, j_in, kP2PChunk, src, begin, end, gbeg, gpre, &s_ngroups,
+                             &s_next_q, &s_next_j);
             __syncthreads();
             const int ng = s_ngroups, used = gpre[ng];
             for (int d = tid; d < used; d += kP2PThreads) {

@@ -561,6 +561,24 @@ __global__ void k_iota(uint32_t *v, int64_t n)
     if (k < n) v[k] = (uint32_t)k;
 }
 
+// Distinct keys (n <= kRankSmall) sorted in place in one block: a key's rank
+// is the number of smaller keys.  The result equals the radix sort's.
+constexpr int kRankSmall = 4096;
+
+__global__ void __launch_bounds__(1024) k_rank_small(uint64_t *keys, int n, uint32_t *rank_of)
+{
+    extern __shared__ uint64_t sk[];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = keys[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t v = sk[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += sk[j] < v;
+        rank_of[i] = (uint32_t)r;
+        keys[r] = v;                 // every read is from shared memory
+    }
+}
+
 __global__ void k_rank_of(const uint32_t *old_of_rank, int64_t n, uint32_t *rank_of)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -944,13 +962,18 @@ fmm_status build_lists(fmm_tree *t, double theta)
         FMM_TRY(ensure(t, t->b_dsort_h, hb + scan_scratch_bytes((int64_t)hb / 4 + 1)));
         uint64_t *keys2 = (uint64_t *)t->b_dsort.ptr;
         uint32_t *vals = (uint32_t *)(keys2 + nd1), *vals2 = vals + nd1, *rank_of = vals2 + nd1;
-        k_iota<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff);
-        radix_sort_pairs((uint64_t *)t->b_dkeys.ptr, vals, keys2, vals2, ndoff, 57,
-                         (uint32_t *)t->b_dsort_h.ptr, (uint32_t *)((char *)t->b_dsort_h.ptr + hb), st,
-                         &t->launches);
-        k_rank_of<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff, rank_of);
+        if (ndoff <= kRankSmall) {
+            k_rank_small<<<1, 1024, 8 * (size_t)ndoff, st>>>((uint64_t *)t->b_dkeys.ptr, (int)ndoff, rank_of);
+            t->launches += 2;
+        } else {
+            k_iota<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff);
+            radix_sort_pairs((uint64_t *)t->b_dkeys.ptr, vals, keys2, vals2, ndoff, 57,
+                             (uint32_t *)t->b_dsort_h.ptr, (uint32_t *)((char *)t->b_dsort_h.ptr + hb), st,
+                             &t->launches);
+            k_rank_of<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff, rank_of);
+            t->launches += 3;
+        }
         k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense, rank_of);
-        t->launches += 5;
     }
     FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
     t->n_m2l = nm2l;
