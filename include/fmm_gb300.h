@@ -380,14 +380,18 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1),
  *               or each mirrored leaf pair once for both directions (2)
  *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
- *               the SIMT FP32 M2L (m2l_tensor 0)
- *   FMM_FP32    none (reports the fixed configuration)
+ *               the SIMT FP32 M2L (m2l_tensor 0); then, with the fastest of
+ *               those, the other FP32 P2P (one-way 1 or symmetric 2)
+ *   FMM_FP32    the one-way and the symmetric FP32 P2P
+ * Defaults before tuning: p2p_variant 2 (FP64) or 1 (FP32 forms), the
+ * tensor-core M2L, 16 rows per chunk, harmonic M2L.
  * The variants compute the same sums in another order: results agree to the
  * form's rounding, not bitwise.  Synchronises the stream.  out may be NULL.
  */
 typedef struct {
-    int p2p_variant;        /* FP64 P2P: 0 one target per thread, 1 two, 2 each  */
-                            /* mirrored leaf pair once for both directions       */
+    int p2p_variant;        /* P2P: 0 one target per thread, 1 two, 2 each       */
+                            /* mirrored leaf pair once for both directions (the  */
+                            /* FP32 forms: 0 and 1 are their two-target kernel)  */
     int m2l_tensor;         /* FMM_3XTF32: 1 tensor-core M2L, 0 SIMT FP32 M2L   */
     int tc_chunk_rows;      /* key rows summed per chunk of the tensor-core M2L  */
     int candidates;         /* variants timed                                    */

@@ -172,6 +172,9 @@ fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int ma
     t->stream = (cudaStream_t)cuda_stream;
     t->max_leaf = max_leaf;
     t->prec = prec;
+    // the symmetric near field pays off where pairs are FP64; the FP32 forms'
+    // pairs are cheap next to its warp sums, so they start one-way
+    t->p2p_variant = prec == FMM_FP64 ? 2 : 1;
     t->budget = mem_budget_bytes;
     std::memset(t->phase_ms, 0, sizeof(t->phase_ms));
     fmm_status st = ensure(t, t->b_err, 16);

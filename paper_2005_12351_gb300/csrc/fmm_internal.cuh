@@ -319,6 +319,10 @@ fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, doubl
 void drop_graph(fmm_tree *t);
 // p2p.cu
 fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, double *E_out);
+// the symmetric P2P's plan (mirror entries, reverse-row offsets; one host sync
+// when built) and its buffers for NC output components (rows of NC doubles, or
+// of NC floats in the FP32 forms); FMM_EBUDGET over the handle's budget
+fmm_status sym_prepare(fmm_tree *t, int NC);
 void launch_check_rsqrt(cudaStream_t st, const double *x, int64_t n, double *own, double *ref);
 // m2l_tc.cu
 fmm_status check_umma(cudaStream_t st, const float *A, const float *B, float *D, int nkb, int N,

@@ -575,6 +575,364 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     }
 }
 
+// ---------------------------------------------------------- symmetric P2P
+// The near field by Newton's third law in this form's FP32 pair arithmetic,
+// on the plan of the FP64 symmetric P2P (mirror entries, reverse rows): each
+// mirrored leaf pair (A, B) with B > A is evaluated once by A's block, in A's
+// frame (source positions taken there by the exact hi + lo sum); the forward
+// terms of a target are summed over the warp in FP32 and across warps in
+// FP64, the reverse terms of a source over A's targets in FP32 into its row,
+// which the gather adds in FP64 in list order.  The reverse term is the
+// forward formula with the target's moments and -R (parity (-1)^s for the
+// potential of an order-s source, (-1)^(s+1) for its field).
+constexpr int kSym32Threads = 128;
+constexpr int kSym32Warps = kSym32Threads / 32;
+constexpr int kSym32Targets = 128;
+
+// moment terms a pair reads: S, or for quadrupoles (2 S200, S110, S101, 2 S020,
+// S011, 2 S002, trace) from the S32 row (S, trace)
+template <int S> struct Sym32Mom { static constexpr int n = S == 2 ? 7 : (S + 1) * (S + 2) / 2; };
+
+template <int S>
+__device__ __forceinline__ void sym32_load_mom(const float *Sj, float *m)
+{
+    if (S < 2) {
+#pragma unroll
+        for (int a = 0; a < (S + 1) * (S + 2) / 2; ++a) m[a] = Sj[a];
+    } else {
+        m[0] = 2.0f * Sj[0]; m[1] = Sj[1]; m[2] = Sj[2]; m[3] = 2.0f * Sj[3]; m[4] = Sj[4];
+        m[5] = 2.0f * Sj[5]; m[6] = Sj[6];
+    }
+}
+
+struct Sym32Geo {
+    float dx, dy, dz, y, y3, c1, c2, c3;
+};
+
+template <int S, bool PHI, bool FIELD>
+__device__ __forceinline__ Sym32Geo sym32_geo(float dx, float dy, float dz)
+{
+    Sym32Geo g;
+    g.dx = dx; g.dy = dy; g.dz = dz;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    y = y * fmaf(-0.5f * r2 * y, y, 1.5f);          // one Newton step, as pair32
+    const float y2 = y * y;
+    g.y = y;
+    g.y3 = y * y2;
+    g.c1 = g.c2 = g.c3 = 0.0f;
+    if (S == 1 && FIELD) g.c1 = 3.0f * y2;
+    if (S == 2) {
+        const float y5 = g.y3 * y2;
+        g.c1 = 3.0f * y5;
+        if (PHI) g.c2 = 1.5f * y5;
+        if (FIELD) g.c3 = 7.5f * (y5 * y2);
+    }
+    return g;
+}
+
+// one direction into a = ([phi], [E]): forward (source moments m) or, with REV,
+// reverse (the target's moments, R -> -R)
+template <int S, bool PHI, bool FIELD, bool REV>
+__device__ __forceinline__ void sym32_dir(const Sym32Geo &g, const float *m, float *a)
+{
+    constexpr int e = PHI ? 1 : 0;
+    if (S == 0) {
+        if (PHI) a[0] = fmaf(m[0], g.y, a[0]);
+        if (FIELD) {
+            const float w = REV ? -(m[0] * g.y3) : m[0] * g.y3;
+            a[e] = fmaf(w, g.dx, a[e]);
+            a[e + 1] = fmaf(w, g.dy, a[e + 1]);
+            a[e + 2] = fmaf(w, g.dz, a[e + 2]);
+        }
+    } else if (S == 1) {
+        const float sr = fmaf(m[0], g.dx, fmaf(m[1], g.dy, m[2] * g.dz));
+        if (PHI) a[0] = fmaf(REV ? sr : -sr, g.y3, a[0]);
+        if (FIELD) {
+            const float v = sr * g.c1;
+            a[e] = fmaf(fmaf(-v, g.dx, m[0]), g.y3, a[e]);
+            a[e + 1] = fmaf(fmaf(-v, g.dy, m[1]), g.y3, a[e + 1]);
+            a[e + 2] = fmaf(fmaf(-v, g.dz, m[2]), g.y3, a[e + 2]);
+        }
+    } else {
+        const float gq0 = fmaf(m[0], g.dx, fmaf(m[1], g.dy, m[2] * g.dz));
+        const float gq1 = fmaf(m[1], g.dx, fmaf(m[3], g.dy, m[4] * g.dz));
+        const float gq2 = fmaf(m[2], g.dx, fmaf(m[4], g.dy, m[5] * g.dz));
+        const float q2 = fmaf(gq0, g.dx, fmaf(gq1, g.dy, gq2 * g.dz));   // 2 q(R)
+        const float tr = m[6];
+        if (PHI) a[0] = fmaf(q2, g.c2, fmaf(-tr, g.y3, a[0]));
+        if (FIELD) {
+            const float w = fmaf(q2, g.c3, -tr * g.c1);
+            const float wa = REV ? -w : w, ca = REV ? g.c1 : -g.c1;
+            a[e] = fmaf(wa, g.dx, fmaf(ca, gq0, a[e]));
+            a[e + 1] = fmaf(wa, g.dy, fmaf(ca, gq1, a[e + 1]));
+            a[e + 2] = fmaf(wa, g.dz, fmaf(ca, gq2, a[e + 2]));
+        }
+    }
+}
+
+// warp totals of four partial sums, fixed pattern: lanes 8c .. 8c+7 hold v_c's
+__device__ __forceinline__ float sym32_warp_sum4(float v0, float v1, float v2, float v3)
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    float a = h16 ? v2 : v0, b = h16 ? v3 : v1;
+    const float sa = h16 ? v0 : v2, sb = h16 ? v1 : v3;
+    a += __shfl_xor_sync(0xffffffffu, sa, 16);
+    b += __shfl_xor_sync(0xffffffffu, sb, 16);
+    float c = h8 ? b : a;
+    const float sc = h8 ? a : b;
+    c += __shfl_xor_sync(0xffffffffu, sc, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+__device__ __forceinline__ float sym32_warp_sum1(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// one batch of sources (d0 + u * kSym32Threads + tid, u < TJ) against the
+// staged targets; with REV the reverse terms go to the sources' rows
+template <int S, bool PHI, bool FIELD, bool REV, int TJ>
+__device__ __forceinline__ void sym32_batch(int d0, int used, int ne, const int *seg_q, const int *seg_pre,
+                                            const float *seg_dx, const float *seg_dy, const float *seg_dz,
+                                            const int32_t *src, const int32_t *begin, const uint32_t *rbase,
+                                            const float4 *o, const float4 *olo, const float *S32,
+                                            const float *tx, const float *ty, const float *tz,
+                                            const float *ux, const float *uy, const float *uz,
+                                            const float *tm, int cntT, float (*fw)[4], float *rev, bool first)
+{
+    constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;
+    constexpr int nM = Sym32Mom<S>::n;
+    constexpr int NC = (PHI ? 1 : 0) + (FIELD ? 3 : 0);
+    const int tid = threadIdx.x, lane = tid & 31;
+    float sx[TJ], sy[TJ], sz[TJ], lx[TJ], ly[TJ], lz[TJ], sm[TJ][nM], acc[TJ][NC];
+    int64_t row[TJ];
+    bool val[TJ];
+#pragma unroll
+    for (int u = 0; u < TJ; ++u) {
+        const int d = d0 + u * kSym32Threads + tid;
+        val[u] = d < used;
+        sx[u] = sy[u] = sz[u] = lx[u] = ly[u] = lz[u] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < nM; ++a) sm[u][a] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[u][c] = 0.0f;
+        row[u] = 0;
+        if (val[u]) {
+            int lo = 0, hi = ne - 1;          // last entry with seg_pre <= d
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (seg_pre[mid] <= d) lo = mid; else hi = mid - 1;
+            }
+            const int q = seg_q[lo], k = d - seg_pre[lo];
+            const int j = begin[src[q]] + k;
+            const float4 v = o[j], vl = olo[j];
+            two_sum_lo(v.x, seg_dx[lo], vl.x, sx[u], lx[u]);
+            two_sum_lo(v.y, seg_dy[lo], vl.y, sy[u], ly[u]);
+            two_sum_lo(v.z, seg_dz[lo], vl.z, sz[u], lz[u]);
+            sym32_load_mom<S>(S32 + (int64_t)j * nS, sm[u]);
+            if (REV) row[u] = (int64_t)rbase[q] + k;
+        }
+    }
+    for (int i = 0; i < cntT; ++i) {
+        const float xi = tx[i], yi = ty[i], zi = tz[i], xl = ux[i], yl = uy[i], zl = uz[i];
+        float mi[nM];
+#pragma unroll
+        for (int a = 0; a < nM; ++a) mi[a] = REV ? tm[i * nM + a] : 0.0f;
+        float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int u = 0; u < TJ; ++u) {
+            if (!val[u]) continue;
+            // hi parts of nearby points subtract exactly; the lo parts restore the rest
+            const Sym32Geo g = sym32_geo<S, PHI, FIELD>((xi - sx[u]) + (xl - lx[u]), (yi - sy[u]) + (yl - ly[u]),
+                                                        (zi - sz[u]) + (zl - lz[u]));
+            sym32_dir<S, PHI, FIELD, false>(g, sm[u], f);
+            if (REV) sym32_dir<S, PHI, FIELD, true>(g, mi, acc[u]);
+        }
+        if (NC == 1) {
+            const float v = sym32_warp_sum1(f[0]);
+            if (lane == 0) fw[i][0] += v;
+        } else {
+            const float v = sym32_warp_sum4(f[0], f[1], f[2], NC == 4 ? f[3] : 0.0f);
+            if ((lane & 7) == 0 && (lane >> 3) < NC) fw[i][lane >> 3] += v;
+        }
+    }
+    if (REV) {
+#pragma unroll
+        for (int u = 0; u < TJ; ++u) {
+            if (!val[u]) continue;
+            float *r = rev + row[u] * NC;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) r[c] = first ? acc[u][c] : r[c] + acc[u][c];
+        }
+    }
+}
+
+// One block per target leaf A, rounds of up to kSym32Targets staged targets;
+// pass 0: mirrored entries with B > A (both directions), pass 1: the
+// forward-only entries (A itself, entries without a mirror); A's row walked in
+// segments of 32 entries compacted by warp 0.
+template <int S, bool PHI, bool FIELD>
+__global__ void __launch_bounds__(kSym32Threads)
+k_p2p32_sym(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
+            const int32_t *src, const int32_t *mir, const uint32_t *rbase, const int32_t *level,
+            const int32_t *cx, const int32_t *cy, const int32_t *cz, const int32_t *sys,
+            const double *sys_box, const float4 *o, const float4 *olo, const float *S32, float *rev,
+            double *fwd)
+{
+    constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;
+    constexpr int nM = Sym32Mom<S>::n;
+    constexpr int NC = (PHI ? 1 : 0) + (FIELD ? 3 : 0);
+    constexpr int TJ = 4;
+    __shared__ float tx[kSym32Targets], ty[kSym32Targets], tz[kSym32Targets];
+    __shared__ float ux[kSym32Targets], uy[kSym32Targets], uz[kSym32Targets], tm[kSym32Targets * nM];
+    __shared__ float fw[kSym32Warps][kSym32Targets][4];
+    __shared__ int seg_q[32], seg_pre[33];
+    __shared__ float seg_dx[32], seg_dy[32], seg_dz[32];
+    __shared__ int s_ne;
+    const int A = leaves[blockIdx.x];
+    const int b = begin[A], nA = end[A] - b;
+    const int q0 = off[A], q1 = off[A + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long rc = 1ll << (kLevels - level[A]);
+    const long long ccx = (2ll * cx[A] + 1) * rc, ccy = (2ll * cy[A] + 1) * rc, ccz = (2ll * cz[A] + 1) * rc;
+    const double unit = ldexp(sys_box[4 * sys[A] + 3], -(kLevels + 1));   // finest half-cell
+    for (int t0 = 0; t0 == 0 || t0 < nA; t0 += kSym32Targets) {
+        const int cntT = max(0, min(kSym32Targets, nA - t0));
+        __syncthreads();
+        for (int u = tid; u < cntT; u += kSym32Threads) {
+            const int i = b + t0 + u;
+            const float4 v = o[i], vl = olo[i];
+            tx[u] = v.x; ty[u] = v.y; tz[u] = v.z;
+            ux[u] = vl.x; uy[u] = vl.y; uz[u] = vl.z;
+            sym32_load_mom<S>(S32 + (int64_t)i * nS, tm + u * nM);
+        }
+        for (int u = tid; u < kSym32Warps * kSym32Targets * 4; u += kSym32Threads) (&fw[0][0][0])[u] = 0.0f;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int qs = q0; qs < q1; qs += 32) {
+                __syncthreads();
+                if (warp == 0) {
+                    const int q = qs + lane;
+                    int n = 0, take = 0, B = 0;
+                    if (q < q1) {
+                        B = src[q];
+                        const int m = mir[q];
+                        take = pass == 0 ? (m >= 0 && B > A) : (B == A || m < 0);
+                        if (take) n = end[B] - begin[B];
+                    }
+                    int k = take, c = n;
+#pragma unroll
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const int yk = __shfl_up_sync(0xffffffffu, k, o2);
+                        const int yc = __shfl_up_sync(0xffffffffu, c, o2);
+                        if (lane >= o2) { k += yk; c += yc; }
+                    }
+                    if (take) {
+                        const long long rs = 1ll << (kLevels - level[B]);
+                        seg_q[k - 1] = q;
+                        seg_pre[k - 1] = c - n;
+                        seg_dx[k - 1] = (float)((double)((2ll * cx[B] + 1) * rs - ccx) * unit);
+                        seg_dy[k - 1] = (float)((double)((2ll * cy[B] + 1) * rs - ccy) * unit);
+                        seg_dz[k - 1] = (float)((double)((2ll * cz[B] + 1) * rs - ccz) * unit);
+                    }
+                    if (lane == 31) { s_ne = k; seg_pre[k] = c; }
+                }
+                __syncthreads();
+                const int ne = s_ne, used = seg_pre[ne];
+                for (int d0 = 0; d0 < used; d0 += kSym32Threads * TJ) {
+                    if (pass == 0)
+                        sym32_batch<S, PHI, FIELD, true, TJ>(d0, used, ne, seg_q, seg_pre, seg_dx, seg_dy, seg_dz,
+                                                             src, begin, rbase, o, olo, S32, tx, ty, tz, ux, uy,
+                                                             uz, tm, cntT, fw[warp], rev, t0 == 0);
+                    else
+                        sym32_batch<S, PHI, FIELD, false, TJ>(d0, used, ne, seg_q, seg_pre, seg_dx, seg_dy,
+                                                              seg_dz, src, begin, rbase, o, olo, S32, tx, ty,
+                                                              tz, ux, uy, uz, tm, cntT, fw[warp], rev, false);
+                }
+            }
+        }
+        __syncthreads();
+        for (int u = tid; u < cntT; u += kSym32Threads) {
+            const int64_t i = b + t0 + u;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                double v = (double)fw[0][u][c];
+#pragma unroll
+                for (int w = 1; w < kSym32Warps; ++w) v += (double)fw[w][u][c];
+                fwd[i * NC + c] = v;
+            }
+        }
+    }
+}
+
+// per target of leaf A: the forward sum, the reverse rows of each mirrored
+// entry (A, B) with B < A in list order (FP64), then the far field
+template <bool PHI, bool FIELD>
+__global__ void __launch_bounds__(kSym32Threads)
+k_p2p32_sym_gather(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
+                   const int32_t *src, const int32_t *mir, const uint32_t *rbase, const float *rev,
+                   const double *fwd, const double *phi_far, const double *E_far, const int32_t *perm,
+                   double *phi_out, double *E_out)
+{
+    constexpr int NC = (PHI ? 1 : 0) + (FIELD ? 3 : 0);
+    constexpr int e = PHI ? 1 : 0;
+    const int A = leaves[blockIdx.x];
+    const int b = begin[A], nA = end[A] - b;
+    const int q0 = off[A], q1 = off[A + 1];
+    for (int u = threadIdx.x; u < nA; u += kSym32Threads) {
+        const int64_t i = b + u;
+        double v[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = fwd[i * NC + c];
+        for (int q = q0; q < q1; ++q) {
+            const int B = src[q], m = mir[q];
+            if (m < 0 || B >= A) continue;
+            const float *r = rev + ((int64_t)rbase[m] + u) * NC;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] += (double)r[c];
+        }
+        const int64_t oo = perm[i];
+        if (PHI) phi_out[oo] = phi_far[i] + v[0];
+        if (FIELD) {
+            E_out[3 * oo] = E_far[3 * i] + v[e];
+            E_out[3 * oo + 1] = E_far[3 * i + 1] + v[e + 1];
+            E_out[3 * oo + 2] = E_far[3 * i + 2] + v[e + 2];
+        }
+    }
+}
+
+template <int S>
+void launch_p2p32_sym(fmm_tree *t, int want_phi, int want_field, double *phi, double *E)
+{
+    const unsigned g = (unsigned)t->nleaves;
+    cudaStream_t st = t->stream;
+    const int32_t *lv = (const int32_t *)t->b_leaves.ptr, *bg = (const int32_t *)t->b_begin.ptr,
+                  *en = (const int32_t *)t->b_end.ptr, *of = (const int32_t *)t->b_p2p_off.ptr,
+                  *sr = (const int32_t *)t->b_p2p_src.ptr, *mi = (const int32_t *)t->b_sym_mir.ptr;
+    const uint32_t *rb = (const uint32_t *)t->b_sym_base.ptr;
+    const float4 *o = (const float4 *)t->b_o32.ptr, *olo = o + t->n;
+    float *rev = (float *)t->b_sym_rev.ptr;
+    double *fwd = (double *)t->b_sym_fwd.ptr;
+    auto run = [&](auto kern, auto gath) {
+        kern<<<g, kSym32Threads, 0, st>>>(lv, bg, en, of, sr, mi, rb, (const int32_t *)t->b_level.ptr,
+                                          (const int32_t *)t->b_cx.ptr, (const int32_t *)t->b_cy.ptr,
+                                          (const int32_t *)t->b_cz.ptr, (const int32_t *)t->b_sys.ptr,
+                                          (const double *)t->b_sysbox.ptr, o, olo, (const float *)t->b_S32.ptr,
+                                          rev, fwd);
+        gath<<<g, kSym32Threads, 0, st>>>(lv, bg, en, of, sr, mi, rb, rev, fwd, (const double *)t->b_phi.ptr,
+                                          (const double *)t->b_E.ptr, (const int32_t *)t->b_perm.ptr, phi, E);
+    };
+    if (want_phi && want_field) run(k_p2p32_sym<S, true, true>, k_p2p32_sym_gather<true, true>);
+    else if (want_phi) run(k_p2p32_sym<S, true, false>, k_p2p32_sym_gather<true, false>);
+    else run(k_p2p32_sym<S, false, true>, k_p2p32_sym_gather<false, true>);
+}
+
 template <int S>
 void launch_p2p32(fmm_tree *t, int want_phi, int want_field, double *phi, double *E)
 {
@@ -749,6 +1107,20 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         ++t->launches;
     }
     record(t, 11);
+    if (t->p2p_variant == 2) {             // symmetric near field (the reverse rows hold floats)
+        const fmm_status ps = sym_prepare(t, (want_phi ? 1 : 0) + (want_field ? 3 : 0));
+        if (ps == FMM_OK && t->sym_rows >= 0) {
+            switch (s) {
+            case 0: launch_p2p32_sym<0>(t, want_phi, want_field, phi_out, E_out); break;
+            case 1: launch_p2p32_sym<1>(t, want_phi, want_field, phi_out, E_out); break;
+            default: launch_p2p32_sym<2>(t, want_phi, want_field, phi_out, E_out); break;
+            }
+            t->launches += 2;
+            return cuda_check(t, cudaGetLastError(), "mixed-precision kernels");
+        }
+        if (ps != FMM_OK && ps != FMM_EBUDGET) return ps;
+        t->err.clear();                       // over the budget: the one-way kernel
+    }
     switch (s) {
     case 0: launch_p2p32<0>(t, want_phi, want_field, phi_out, E_out); break;
     case 1: launch_p2p32<1>(t, want_phi, want_field, phi_out, E_out); break;

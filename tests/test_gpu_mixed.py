@@ -21,12 +21,13 @@ from paper_2005_12351_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True, harmonic=1):
+def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True, harmonic=1,
+             p2p_variant=-1):
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
     tree = fmm.create_tree(max_leaf=ncrit, precision=precision)
-    tree.set_tuning(m2l_harmonic=harmonic)
+    tree.set_tuning(m2l_harmonic=harmonic, p2p_variant=p2p_variant)
     tree.set_sources(to_dev(pos), to_dev(S), s)
     phi, E = tree.evaluate(p, theta, want_phi, want_field)
     torch.cuda.synchronize()
@@ -45,6 +46,7 @@ def assert_tc_ran(tree, precision):
         assert info["tc_rows"] * 128 >= info["n_m2l"]
 
 
+@pytest.mark.parametrize("variant", [-1, 2])        # the form's default P2P, and the symmetric one
 @pytest.mark.parametrize("precision", FORMS)
 @pytest.mark.parametrize("s,p,dist,n,ncrit", [
     (0, 4, "uniform", 2000, 64),
@@ -54,10 +56,10 @@ def assert_tc_ran(tree, precision):
     (2, 5, "uniform", 15_000, 128),
     (2, 3, "plummer", 10_000, 16),
 ])
-def test_fp32_close_to_fp64_oracle(orc, precision, s, p, dist, n, ncrit):
+def test_fp32_close_to_fp64_oracle(orc, precision, s, p, dist, n, ncrit, variant):
     from gpu_util import rel_rms
     pos, S = synth.make_system(n, s, dist, 700 + 10 * s + p)
-    (phi, E), tree = gpu_eval(pos, S, s, p, 0.5, ncrit, precision)
+    (phi, E), tree = gpu_eval(pos, S, s, p, 0.5, ncrit, precision, p2p_variant=variant)
     assert_tc_ran(tree, precision)
     t = orc.Tree(pos, ncrit)
     t.lists(0.5)
@@ -197,3 +199,26 @@ def test_3xtf32_falls_back_to_simt_within_budget():
     torch.cuda.synchronize()
     assert t.info()["tc_rows"] == 0
     assert np.array_equal(E.cpu().numpy(), E32.cpu().numpy())
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_fp32_symmetric_batch_matches_alone(s):
+    """The FP32 symmetric P2P gives each system of a batch the bits it gets alone
+    (the FP32 form: its M2L is per target cell, where the tensor-core M2L's tiles
+    mix systems)."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    pos, S, off = synth.make_batch(24, 300, 5000, s, 1901 + s, dist="plummer")
+    tb = fmm.create_tree(max_leaf=32, precision="fp32")
+    tb.set_tuning(p2p_variant=2)
+    tb.set_sources_batch(to_dev(pos), to_dev(S), off, s)
+    phi_b, E_b = tb.evaluate(4, 0.5)
+    torch.cuda.synchronize()
+    phi_b, E_b = phi_b.cpu().numpy(), E_b.cpu().numpy()
+    for k in (0, 11, 23):
+        a, b = int(off[k]), int(off[k + 1])
+        (phi, E), t = gpu_eval(pos[a:b], S[a:b], s, 4, 0.5, 32, "fp32", p2p_variant=2)
+        assert np.array_equal(phi, phi_b[a:b]) and np.array_equal(E, E_b[a:b]), k
+        t.destroy()
+    tb.destroy()
