@@ -63,16 +63,6 @@ struct OpTables {
     int m2l_threads = 0, m2l_T = 0, m2l_slots = 0;
     std::vector<uint32_t> m2l_desc;      // [T x threads]
     std::vector<int> m2l_red_off, m2l_red_src;   // CSR over n: partial slot ids
-    // M2L terms in n-major order, packed m | d << 16, with run offsets per n
-    std::vector<uint32_t> m2l_terms;
-    std::vector<int> m2l_run_off;        // [nL + 1]
-    // For each n the kept m form a prefix 0..cnt-1 of the graded order: the
-    // d = index(n + m) of run n, padded to a multiple of 4 with the value nD
-    // (a zero slot), packed two 16-bit values per word
-    std::vector<uint32_t> m2l_d16;
-    std::vector<int> m2l_d16_off;        // [nL + 1], in 16-bit entries (multiples of 4)
-    std::vector<int> m2l_cnt;            // [nL] kept m per n
-    int m2l_split[5] = {0, 0, 0, 0, 0};  // n-range boundaries for 4 warps
     // Harmonic M2L (D_k = grad^k 1/r is traceless: D_{k+2x} + D_{k+2y} + D_{k+2z} = 0).
     // The M2L terms then run over the m with m_z <= 1 of the folded multipole M'
     // and the n with n_z <= 1; the other L_n follow from the same identity.
@@ -123,12 +113,6 @@ struct DevTables {
     const int *m2l_red_off, *m2l_red_src;
     const uint32_t *m2l_desc;
     int m2l_T, m2l_slots;
-    const uint32_t *m2l_terms;
-    const int *m2l_run_off;
-    int m2l_nterms;
-    const uint32_t *m2l_d16;
-    const int *m2l_d16_off, *m2l_cnt;
-    int m2l_split[5];
     // packed multi-indices nx | ny << 5 | nz << 10 | |n| << 15 (global memory:
     // lanes may index it divergently, which the constant cache would serialise)
     const int *mi;

@@ -159,45 +159,6 @@ void build_tables(OpTables &T, int s, int s_hi, int p, int n_lo, int m2l_threads
         max_slots = std::max(max_slots, slot + 1);
     }
     T.m2l_slots = max_slots;
-    T.m2l_terms.clear();
-    T.m2l_run_off.assign(T.nL + 1, 0);
-    for (const Term &tm : terms) T.m2l_terms.push_back((uint32_t)tm.m | ((uint32_t)tm.d << 16));
-    {
-        int q = 0;
-        for (int n = 0; n < T.nL; ++n) {
-            T.m2l_run_off[n] = q;
-            while (q < W && terms[q].n == n) ++q;
-        }
-        T.m2l_run_off[T.nL] = q;
-    }
-    {
-        std::vector<uint16_t> d16;
-        T.m2l_d16_off.assign(T.nL + 1, 0);
-        T.m2l_cnt.assign(T.nL, 0);
-        for (int n = 0; n < T.nL; ++n) {
-            T.m2l_d16_off[n] = (int)d16.size();
-            const int q0 = T.m2l_run_off[n], q1 = T.m2l_run_off[n + 1];
-            T.m2l_cnt[n] = q1 - q0;
-            for (int q = q0; q < q1; ++q) {
-                if (terms[q].m != q - q0) throw std::logic_error("M2L run is not an m prefix");
-                d16.push_back((uint16_t)terms[q].d);
-            }
-            while (d16.size() % 4) d16.push_back((uint16_t)T.nD);
-        }
-        T.m2l_d16_off[T.nL] = (int)d16.size();
-        T.m2l_d16.assign((d16.size() + 1) / 2, 0u);
-        for (size_t i = 0; i < d16.size(); ++i)
-            T.m2l_d16[i / 2] |= (uint32_t)d16[i] << (16 * (i % 2));
-        // four contiguous n-ranges with about equal padded term counts
-        const int total = T.m2l_d16_off[T.nL];
-        T.m2l_split[0] = 0;
-        int n = 0;
-        for (int w = 1; w < 4; ++w) {
-            while (n < T.nL && T.m2l_d16_off[n] < (int64_t)total * w / 4) ++n;
-            T.m2l_split[w] = n;
-        }
-        T.m2l_split[4] = T.nL;
-    }
     T.m2l_red_off.assign(1, 0); T.m2l_red_src.clear();
     for (int n = 0; n < T.nL; ++n) {
         for (int v : red[n]) T.m2l_red_src.push_back(v);
@@ -631,9 +592,6 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     o_m2m_q = put(T.m2m_q); o_l2l_off = put(T.l2l_off); o_l2l_k = put(T.l2l_k);
     o_l2l_q = put(T.l2l_q); o_grad = put(T.l2p_grad); o_roff = put(T.m2l_red_off);
     o_rsrc = put(T.m2l_red_src);
-    const size_t o_runoff = put(T.m2l_run_off);
-    const size_t o_d16off = put(T.m2l_d16_off);
-    const size_t o_cnt = put(T.m2l_cnt);
     const size_t o_hrm = put(T.h_rm), o_hf = put(T.h_fold), o_hfo = put(T.h_fold_off);
     const size_t o_hu = put(T.h_unfold), o_huo = put(T.h_unfold_off);
     size_t o_mi;
@@ -645,21 +603,13 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
         o_mi = put(mi);
     }
     FMM_TRY(ensure(t, t->b_tab_i32, 4 * buf.size()));
-    // the 16-bit d table is read with 8-byte loads: start it on an even word
-    const size_t w_d16 = (T.m2l_desc.size() + T.m2l_terms.size() + 1) & ~(size_t)1;
-    FMM_TRY(ensure(t, t->b_tab_u32, 4 * (w_d16 + T.m2l_d16.size() + 2)));
+    FMM_TRY(ensure(t, t->b_tab_u32, 4 * (T.m2l_desc.size() + 2)));
     if (rebuild) {
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_i32.ptr, buf.data(), 4 * buf.size(),
                                               cudaMemcpyHostToDevice, t->stream), "tables"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(t->b_tab_u32.ptr, T.m2l_desc.data(),
                                               4 * T.m2l_desc.size(), cudaMemcpyHostToDevice,
                                               t->stream), "tables"));
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync((uint32_t *)t->b_tab_u32.ptr + T.m2l_desc.size(),
-                                              T.m2l_terms.data(), 4 * T.m2l_terms.size(),
-                                              cudaMemcpyHostToDevice, t->stream), "tables"));
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync((uint32_t *)t->b_tab_u32.ptr + w_d16,
-                                              T.m2l_d16.data(), 4 * T.m2l_d16.size(),
-                                              cudaMemcpyHostToDevice, t->stream), "tables"));
         t->tab_key_s = s; t->tab_key_p = p; t->tab_key_nlo = n_lo; t->tab_key_h = h;
         t->tab_key_shi = s_hi;
     }
@@ -672,14 +622,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     dt->m2l_red_src = B + o_rsrc;
     dt->m2l_desc = (const uint32_t *)t->b_tab_u32.ptr;
     dt->m2l_T = T.m2l_T; dt->m2l_slots = T.m2l_slots;
-    dt->m2l_terms = (const uint32_t *)t->b_tab_u32.ptr + T.m2l_desc.size();
-    dt->m2l_run_off = B + o_runoff;
     dt->mi = B + o_mi;
-    dt->m2l_d16 = (const uint32_t *)t->b_tab_u32.ptr + w_d16;
-    dt->m2l_d16_off = B + o_d16off;
-    dt->m2l_cnt = B + o_cnt;
-    for (int w = 0; w < 5; ++w) dt->m2l_split[w] = T.m2l_split[w];
-    dt->m2l_nterms = (int)T.m2l_terms.size();
     dt->harmonic = T.harmonic ? 1 : 0;
     dt->nMh = T.nMh;
     dt->h_fold_lev = (int)T.h_fold_off.size() - 1;
