@@ -484,7 +484,8 @@ def measure_bh(args, w, dev, world, pos_d, S_d, flush):
 def measure_mixed_orders(args, w, dev, world, flush):
     """Mixed source orders on the headline geometry: every particle carries a charge and
     a dipole (orders 0..1; the expansion starts at order 0, so multipoles run to p).  A
-    step = tree build + evaluate, as the main line; FP64."""
+    step = tree build + evaluate, as the main line; FP64, the handle's default P2P (the
+    symmetric kernel, each shell's reverse term with its own parity)."""
     import torch
     from paper_2005_12351_gb300 import fmm
     n, p, theta = w["n"], w["p"], w["theta"]
@@ -528,7 +529,7 @@ def measure_mixed_orders(args, w, dev, world, flush):
     tree.destroy()
     return {"sources": "charge + dipole per particle (orders 0..1)", "p": p, "theta": theta,
             "value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "field_rel_rms": err,
-            "targets": int(len(tg)), "phase_ms": ph,
+            "targets": int(len(tg)), "phase_ms": ph, "p2p_kernel": "symmetric",
             "roofline": {"bound": "alu", "kernel": "p2p", "achieved": achieved,
                          "peak": args.fp64_peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / args.fp64_peak_tflops, "traffic": None,

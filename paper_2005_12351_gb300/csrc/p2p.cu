@@ -338,6 +338,8 @@ k_p2p_x2(const int32_t *leaves, const int32_t *begin, const int32_t *end, const 
 // moments of i and -R: by the parity of D_n (§2), the potential of an order-s
 // source changes sign by (-1)^s under R -> -R and its field by (-1)^(s+1).
 // Self entries (A, A) and entries without a mirror are evaluated forward only.
+// A particle carrying the orders SLO..SHI (§2 mixed systems) takes the sum of
+// its shells' terms in both directions, each shell with its own parity.
 constexpr int kSymThreads = 128;
 constexpr int kSymWarps = kSymThreads / 32;
 constexpr int kSymTargets = 128;           // targets staged in shared memory per round
@@ -346,6 +348,19 @@ constexpr int kSymTargets = 128;           // targets staged in shared memory pe
 // (symmetric) gradient operator of q(R) = sum_{|a|=2} S_a R^a, i.e.
 // (2 S_200, S_110, S_101, 2 S_020, S_011, 2 S_002), and the trace.
 template <int S> struct SymMom { static constexpr int n = S == 2 ? 7 : (S + 1) * (S + 2) / 2; };
+
+__host__ __device__ constexpr int sym_shell(int s) { return (s + 1) * (s + 2) / 2; }
+__host__ __device__ constexpr int sym_terms(int s) { return s == 2 ? 7 : sym_shell(s); }
+// offsets of shell s among the orders slo..: in the particle's moments, in the pair terms
+__host__ __device__ constexpr int sym_shell_off(int slo, int s)
+{
+    return s <= slo ? 0 : sym_shell_off(slo, s - 1) + sym_shell(s - 1);
+}
+__host__ __device__ constexpr int sym_terms_off(int slo, int s)
+{
+    return s <= slo ? 0 : sym_terms_off(slo, s - 1) + sym_terms(s - 1);
+}
+template <int SLO, int SHI> struct SymMomOrders { static constexpr int n = sym_terms_off(SLO, SHI + 1); };
 
 template <int S>
 __device__ __forceinline__ void sym_load_mom(const double *Sj, double *m)
@@ -360,12 +375,22 @@ __device__ __forceinline__ void sym_load_mom(const double *Sj, double *m)
     }
 }
 
-// The part of a pair both directions share.
+template <int SLO, int SHI>
+__device__ __forceinline__ void sym_load_orders(const double *Sj, double *m)
+{
+    sym_load_mom<SLO>(Sj, m);
+    if constexpr (SHI >= SLO + 1)
+        sym_load_mom<SLO + 1>(Sj + sym_shell_off(SLO, SLO + 1), m + sym_terms_off(SLO, SLO + 1));
+    if constexpr (SHI >= SLO + 2)
+        sym_load_mom<SLO + 2>(Sj + sym_shell_off(SLO, SLO + 2), m + sym_terms_off(SLO, SLO + 2));
+}
+
+// The part of a pair both directions share (for the orders SLO..SHI).
 struct SymGeo {
-    double dx, dy, dz, y, y3, c1, c2, c3;
+    double dx, dy, dz, y, y3, a1, c1, c2, c3;
 };
 
-template <int S, bool PHI, bool FIELD>
+template <int SLO, int SHI, bool PHI, bool FIELD>
 __device__ __forceinline__ SymGeo sym_geo(double dx, double dy, double dz)
 {
     SymGeo g;
@@ -374,9 +399,9 @@ __device__ __forceinline__ SymGeo sym_geo(double dx, double dy, double dz)
     g.y = __double_as_longlong(r2) != 0 ? rsqrt_hh(r2) : 0.0;
     const double y2 = g.y * g.y;
     g.y3 = g.y * y2;
-    g.c1 = g.c2 = g.c3 = 0.0;
-    if (S == 1 && FIELD) g.c1 = 3.0 * y2;                 // 3 / r^2
-    if (S == 2) {
+    g.a1 = g.c1 = g.c2 = g.c3 = 0.0;
+    if (SLO <= 1 && SHI >= 1 && FIELD) g.a1 = 3.0 * y2;  // 3 / r^2 (dipole field)
+    if (SHI == 2) {
         const double y5 = g.y3 * y2;
         g.c1 = 3.0 * y5;                                 // 3 / r^5
         if (PHI) g.c2 = 1.5 * y5;
@@ -405,7 +430,7 @@ __device__ __forceinline__ void sym_dir(const SymGeo &g, const double *m, double
         if (PHI) a[0] = fma(REV ? sr : -sr, g.y3, a[0]);
         if (FIELD) {
             // E = (S - 3 (S.R) R / r^2) / r^3, even in R
-            const double v = sr * g.c1;
+            const double v = sr * g.a1;
             a[e] = fma(fma(-v, g.dx, m[0]), g.y3, a[e]);
             a[e + 1] = fma(fma(-v, g.dy, m[1]), g.y3, a[e + 1]);
             a[e + 2] = fma(fma(-v, g.dz, m[2]), g.y3, a[e + 2]);
@@ -425,6 +450,17 @@ __device__ __forceinline__ void sym_dir(const SymGeo &g, const double *m, double
             a[e + 2] = fma(wa, g.dz, fma(ca, gq2, a[e + 2]));
         }
     }
+}
+
+// Both directions' shells of a mixed-order pair, the shells in ascending order.
+template <int SLO, int SHI, bool PHI, bool FIELD, bool REV>
+__device__ __forceinline__ void sym_dir_orders(const SymGeo &g, const double *m, double *a)
+{
+    sym_dir<SLO, PHI, FIELD, REV>(g, m, a);
+    if constexpr (SHI >= SLO + 1)
+        sym_dir<SLO + 1, PHI, FIELD, REV>(g, m + sym_terms_off(SLO, SLO + 1), a);
+    if constexpr (SHI >= SLO + 2)
+        sym_dir<SLO + 2, PHI, FIELD, REV>(g, m + sym_terms_off(SLO, SLO + 2), a);
 }
 
 // Warp totals of four partial sums: lanes 8c .. 8c+7 end with the total of
@@ -460,7 +496,7 @@ __device__ __forceinline__ double sym_warp_sum1(double v)
 // the warp and added to the warp's row fw; with REV the reverse terms of the
 // held sources are accumulated over all targets and stored to (first target
 // round) or added to their rows of rev.
-template <int S, bool PHI, bool FIELD, bool REV, int TJ>
+template <int S, bool PHI, bool FIELD, bool REV, int TJ, int SHI>
 __device__ __forceinline__ void sym_batch(int d0, int used, int ne, const int *seg_q,
                                           const int *seg_pre, const int32_t *src,
                                           const int32_t *begin, const uint32_t *rbase,
@@ -469,8 +505,8 @@ __device__ __forceinline__ void sym_batch(int d0, int used, int ne, const int *s
                                           const double *tz, const double *tm, int cntT,
                                           double (*fw)[4], double *rev, bool first)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
-    constexpr int nM = SymMom<S>::n;
+    constexpr int nS = Orders<S, SHI>::n;
+    constexpr int nM = SymMomOrders<S, SHI>::n;
     constexpr int NC = (PHI ? 1 : 0) + (FIELD ? 3 : 0);
     const int tid = threadIdx.x, lane = tid & 31;
     double sx[TJ], sy[TJ], sz[TJ], sm[TJ][nM], acc[TJ][NC];
@@ -495,7 +531,7 @@ __device__ __forceinline__ void sym_batch(int d0, int used, int ne, const int *s
             const int q = seg_q[lo], k = d - seg_pre[lo];
             const int j = begin[src[q]] + k;
             sx[u] = px[j]; sy[u] = py[j]; sz[u] = pz[j];
-            sym_load_mom<S>(Sm + (int64_t)j * nS, sm[u]);
+            sym_load_orders<S, SHI>(Sm + (int64_t)j * nS, sm[u]);
             if (REV) row[u] = (int64_t)rbase[q] + k;
         }
     }
@@ -508,9 +544,9 @@ __device__ __forceinline__ void sym_batch(int d0, int used, int ne, const int *s
 #pragma unroll
         for (int u = 0; u < TJ; ++u) {
             if (!val[u]) continue;
-            const SymGeo g = sym_geo<S, PHI, FIELD>(xi - sx[u], yi - sy[u], zi - sz[u]);
-            sym_dir<S, PHI, FIELD, false>(g, sm[u], f);
-            if (REV) sym_dir<S, PHI, FIELD, true>(g, mi, acc[u]);
+            const SymGeo g = sym_geo<S, SHI, PHI, FIELD>(xi - sx[u], yi - sy[u], zi - sz[u]);
+            sym_dir_orders<S, SHI, PHI, FIELD, false>(g, sm[u], f);
+            if (REV) sym_dir_orders<S, SHI, PHI, FIELD, true>(g, mi, acc[u]);
         }
         if (NC == 1) {
             const double v = sym_warp_sum1(f[0]);
@@ -536,16 +572,16 @@ __device__ __forceinline__ void sym_batch(int d0, int used, int ne, const int *s
 // directions), pass 1 the forward-only entries; each pass walks A's row in
 // segments of 32 entries, compacted by warp 0 in list order.  The forward sum
 // of a target is the warps' rows added in warp order.
-template <int S, bool PHI, bool FIELD>
+template <int S, bool PHI, bool FIELD, int SHI = S>
 __global__ void __launch_bounds__(kSymThreads)
 k_p2p_sym(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
           const int32_t *src, const int32_t *mir, const uint32_t *rbase, const double *px,
           const double *py, const double *pz, const double *Sm, double *rev, double *fwd)
 {
-    constexpr int nS = (S + 1) * (S + 2) / 2;
-    constexpr int nM = SymMom<S>::n;
+    constexpr int nS = Orders<S, SHI>::n;
+    constexpr int nM = SymMomOrders<S, SHI>::n;
     constexpr int NC = (PHI ? 1 : 0) + (FIELD ? 3 : 0);
-    constexpr int TJ = S == 2 ? 2 : 4;       // sources per thread held in registers
+    constexpr int TJ = nM > 4 ? 2 : 4;       // sources per thread held in registers
     __shared__ double tx[kSymTargets], ty[kSymTargets], tz[kSymTargets], tm[kSymTargets * nM];
     __shared__ double fw[kSymWarps][kSymTargets][4];
     __shared__ int seg_q[32], seg_pre[33];
@@ -561,7 +597,7 @@ k_p2p_sym(const int32_t *leaves, const int32_t *begin, const int32_t *end, const
         for (int u = tid; u < cntT; u += kSymThreads) {
             const int i = b + t0 + u;
             tx[u] = px[i]; ty[u] = py[i]; tz[u] = pz[i];
-            sym_load_mom<S>(Sm + (int64_t)i * nS, tm + u * nM);
+            sym_load_orders<S, SHI>(Sm + (int64_t)i * nS, tm + u * nM);
         }
         for (int u = tid; u < kSymWarps * kSymTargets * 4; u += kSymThreads) (&fw[0][0][0])[u] = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
@@ -589,11 +625,11 @@ k_p2p_sym(const int32_t *leaves, const int32_t *begin, const int32_t *end, const
                 const int ne = s_ne, used = seg_pre[ne];
                 for (int d0 = 0; d0 < used; d0 += kSymThreads * TJ) {
                     if (pass == 0)
-                        sym_batch<S, PHI, FIELD, true, TJ>(d0, used, ne, seg_q, seg_pre, src, begin,
+                        sym_batch<S, PHI, FIELD, true, TJ, SHI>(d0, used, ne, seg_q, seg_pre, src, begin,
                                                            rbase, px, py, pz, Sm, tx, ty, tz, tm,
                                                            cntT, fw[warp], rev, t0 == 0);
                     else
-                        sym_batch<S, PHI, FIELD, false, TJ>(d0, used, ne, seg_q, seg_pre, src,
+                        sym_batch<S, PHI, FIELD, false, TJ, SHI>(d0, used, ne, seg_q, seg_pre, src,
                                                             begin, rbase, px, py, pz, Sm, tx, ty,
                                                             tz, tm, cntT, fw[warp], rev, false);
                 }
@@ -725,7 +761,7 @@ k_direct(const double *pos, const double *mom, int64_t n, const int32_t *targets
     }
 }
 
-template <int S>
+template <int S, int SHI = S>
 void launch_sym_s(fmm_tree *t, int want_phi, int want_field, double *phi, double *E)
 {
     const unsigned g = (unsigned)t->nleaves;
@@ -743,9 +779,9 @@ void launch_sym_s(fmm_tree *t, int want_phi, int want_field, double *phi, double
                                         (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr,
                                         (const int32_t *)t->b_perm.ptr, phi, E);
     };
-    if (want_phi && want_field) run(k_p2p_sym<S, true, true>, k_p2p_sym_gather<true, true>);
-    else if (want_phi) run(k_p2p_sym<S, true, false>, k_p2p_sym_gather<true, false>);
-    else run(k_p2p_sym<S, false, true>, k_p2p_sym_gather<false, true>);
+    if (want_phi && want_field) run(k_p2p_sym<S, true, true, SHI>, k_p2p_sym_gather<true, true>);
+    else if (want_phi) run(k_p2p_sym<S, true, false, SHI>, k_p2p_sym_gather<true, false>);
+    else run(k_p2p_sym<S, false, true, SHI>, k_p2p_sym_gather<false, true>);
 }
 
 template <int S, int SHI = S>
@@ -823,6 +859,23 @@ fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, d
 {
     if (t->nleaves == 0) return FMM_OK;
     const int so = t->s * 3 + t->s_hi;                 // (lowest, highest) source order
+    if (t->p2p_variant == 2) {
+        const fmm_status ps = sym_prepare(t, (want_phi ? 1 : 0) + (want_field ? 3 : 0));
+        if (ps == FMM_OK && t->sym_rows >= 0) {
+            switch (so) {
+            case 0: launch_sym_s<0>(t, want_phi, want_field, phi_out, E_out); break;
+            case 1: launch_sym_s<0, 1>(t, want_phi, want_field, phi_out, E_out); break;
+            case 2: launch_sym_s<0, 2>(t, want_phi, want_field, phi_out, E_out); break;
+            case 4: launch_sym_s<1>(t, want_phi, want_field, phi_out, E_out); break;
+            case 5: launch_sym_s<1, 2>(t, want_phi, want_field, phi_out, E_out); break;
+            default: launch_sym_s<2>(t, want_phi, want_field, phi_out, E_out); break;
+            }
+            t->launches += 2;
+            return cuda_check(t, cudaGetLastError(), "symmetric p2p kernels");
+        }
+        if (ps != FMM_OK && ps != FMM_EBUDGET) return ps;
+        t->err.clear();               // over the budget or the row index: two targets per thread
+    }
     if (t->s_hi != t->s) {                            // mixed orders: two targets per thread
         switch (so) {
         case 1: launch_p2p_s<0, 1>(t, want_phi, want_field, phi_out, E_out); break;
@@ -831,20 +884,6 @@ fmm_status run_p2p(fmm_tree *t, int want_phi, int want_field, double *phi_out, d
         }
         ++t->launches;
         return cuda_check(t, cudaGetLastError(), "p2p kernel");
-    }
-    if (t->p2p_variant == 2) {
-        const fmm_status ps = sym_prepare(t, (want_phi ? 1 : 0) + (want_field ? 3 : 0));
-        if (ps == FMM_OK && t->sym_rows >= 0) {
-            switch (t->s) {
-            case 0: launch_sym_s<0>(t, want_phi, want_field, phi_out, E_out); break;
-            case 1: launch_sym_s<1>(t, want_phi, want_field, phi_out, E_out); break;
-            default: launch_sym_s<2>(t, want_phi, want_field, phi_out, E_out); break;
-            }
-            t->launches += 2;
-            return cuda_check(t, cudaGetLastError(), "symmetric p2p kernels");
-        }
-        if (ps != FMM_OK && ps != FMM_EBUDGET) return ps;
-        t->err.clear();               // over the budget or the row index: two targets per thread
     }
     switch (t->s) {
     case 0: launch_p2p_s<0>(t, want_phi, want_field, phi_out, E_out); break;

@@ -1,6 +1,7 @@
 """Mixed source orders on the GPU (every particle carries the orders s_lo..s_hi,
 §2 "mixed systems"): FMM, direct sum and Barnes-Hut against the oracle's
-mixed-order versions, the P2P kernel variants, moment updates and graph replay,
+mixed-order versions, the P2P kernel variants (the symmetric one against the
+one-way one), moment updates and graph replay,
 and the calls a mixed system is refused by."""
 import numpy as np
 import pytest
@@ -27,7 +28,7 @@ def gpu_mixed(pos, S, lo, hi, ncrit, variant=None):
     (0, 1, 3, "plummer", 8000, 16, "field", 0),
     (1, 2, 5, "plummer", 10_000, 32, "both", None),
     (1, 2, 2, "uniform", 6000, 300, "phi", 1),
-    (0, 2, 4, "uniform", 8000, 64, "field", None),
+    (0, 2, 4, "uniform", 8000, 64, "field", 1),
     (0, 2, 8, "plummer", 6000, 16, "both", 2),
 ])
 def test_mixed_fmm_matches_oracle(orc, lo, hi, p, dist, n, ncrit, outs, variant):
@@ -47,6 +48,28 @@ def test_mixed_fmm_matches_oracle(orc, lo, hi, p, dist, n, ncrit, outs, variant)
     if wf:
         assert rel_rms(E.cpu().numpy(), E_o) < TOL
     t.destroy()
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 1), (1, 2), (0, 2)])
+@pytest.mark.parametrize("outs", ["phi", "field", "both"])
+def test_mixed_symmetric_p2p_matches_one_way(lo, hi, outs):
+    """The symmetric near field (each shell's reverse term with its own parity)
+    against the one-way kernel on the same tree: the same sums in another order."""
+    import torch
+    from gpu_util import rel_rms
+    pos, S = synth.make_system_mixed(30_000, lo, hi, "plummer", 1900 + 3 * lo + hi)
+    wp, wf = outs in ("phi", "both"), outs in ("field", "both")
+    res = {}
+    for v in (1, 2):
+        t = gpu_mixed(pos, S, lo, hi, 64, v)
+        phi, E = t.evaluate(4, 0.5, wp, wf)
+        torch.cuda.synchronize()
+        res[v] = (phi.cpu().numpy() if wp else None, E.cpu().numpy() if wf else None)
+        t.destroy()
+    if wp:
+        assert rel_rms(res[2][0], res[1][0]) < 1e-14
+    if wf:
+        assert rel_rms(res[2][1], res[1][1]) < 1e-14
 
 
 @pytest.mark.parametrize("lo,hi", [(0, 1), (1, 2), (0, 2)])
