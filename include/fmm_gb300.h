@@ -456,7 +456,7 @@ fmm_status fmm_check_umma(const float *A, const float *B, float *D, int nkb, int
  * the library a fixed arena and forbid cudaMalloc/cudaFree because those
  * calls synchronise the device, and latency-critical loops.
  *   Arguments and results are those of fmm_morton_order (DEVICE pointers).
- *   Scratch: a file-scope device array of about 12.3 MB holding room for
+ *   Scratch: a file-scope device array of about 13.6 MB holding room for
  *   FMM_NOALLOC_MAX_POINTS points; every GPU that loads the library holds it
  *   until the process exits.  n > FMM_NOALLOC_MAX_POINTS returns FMM_EBUDGET
  *   and touches nothing; n < 0 or NULL pointers return FMM_EINVAL.

@@ -526,12 +526,11 @@ fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t 
     if (n == 0) return FMM_OK;
     if (!positions || !keys_out || !perm_out) return FMM_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    void *keys2 = nullptr, *idx2 = nullptr, *hist = nullptr, *scan = nullptr, *box = nullptr;
-    const size_t hb = radix_hist_bytes(n), sb = scan_scratch_bytes(hb / 4 + 1);
+    void *keys2 = nullptr, *idx2 = nullptr, *hist = nullptr, *box = nullptr;
+    const size_t hb = radix_hist_bytes(n);
     cudaError_t e = cudaMalloc(&keys2, 8 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&idx2, 4 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&hist, hb);
-    if (e == cudaSuccess) e = cudaMalloc(&scan, sb);
     if (e == cudaSuccess) e = cudaMalloc(&box, 256);
     fmm_status st_out = FMM_OK;
     if (e != cudaSuccess) {
@@ -541,16 +540,16 @@ fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t 
         int64_t launches = 0;
         cudaMemsetAsync((char *)box + 160, 0, 4, st);
         morton_order_raw(st, positions, n, keys_out, (uint32_t *)perm_out, (uint64_t *)keys2,
-                         (uint32_t *)idx2, (uint32_t *)hist, (uint32_t *)scan,
-                         (unsigned long long *)box, (double *)box + 8, (int *)((char *)box + 160),
+                         (uint32_t *)idx2, (uint32_t *)hist, (unsigned long long *)box, (double *)box + 8, (int *)((char *)box + 160),
                          &launches);
         int err = 0;
         e = cudaMemcpyAsync(&err, (char *)box + 160, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) st_out = FMM_ECUDA;
         else if (err & kErrNonFinite) st_out = FMM_EINVAL;
+        else if (err & kErrSortWait) st_out = FMM_ETIMEOUT;
     }
-    cudaFree(keys2); cudaFree(idx2); cudaFree(hist); cudaFree(scan); cudaFree(box);
+    cudaFree(keys2); cudaFree(idx2); cudaFree(hist); cudaFree(box);
     return st_out;
 }
 

@@ -30,6 +30,7 @@ constexpr int kErrNonFinite = 1;
 constexpr int kErrKeyRange = 2;
 constexpr int kErrHashFull = 4;
 constexpr int kErrTcTimeout = 8;       // a tensor-core M2L wait gave up (word 1 of b_err)
+constexpr int kErrSortWait = 16;       // a look-back wait of the radix sort gave up
 
 inline int ntot(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
 inline int nshell(int k) { return (k + 1) * (k + 2) / 2; }
@@ -253,20 +254,30 @@ fmm_status cuda_check(fmm_tree *t, cudaError_t e, const char *what);
 size_t scan_scratch_bytes(int64_t n);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
                         cudaStream_t st, int64_t *launches);
+// Scratch of radix_sort_pairs in 32-bit words: digit counts of up to 8
+// passes and 16 tile counters (kRadixHead words), then two areas of 256
+// 64-bit status words per tile of 4096 keys.
+constexpr int kRadixMaxPasses = 8;
+constexpr int64_t kRadixHead = kRadixMaxPasses * 256 + 16;
+constexpr int64_t radix_hist_words(int64_t n)
+{
+    return kRadixHead + 4 * 256 * ((n + 4095) / 4096 > 0 ? (n + 4095) / 4096 : 1);
+}
 size_t radix_hist_bytes(int64_t n);
-// Stable LSD radix sort of (key, value) pairs on bits [0, end_bit).  The
-// result ends in (keys, vals); (keys2, vals2) are scratch of the same size.
+// Stable LSD radix sort of (key, value) pairs on bits [0, end_bit), end_bit
+// <= 64, n < 2^32.  The result ends in (keys, vals); (keys2, vals2) are
+// scratch of the same size, hist holds radix_hist_bytes(n).  A bounded wait
+// of the one-sweep passes that gave up sets kErrSortWait in *err (device).
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
-                      int end_bit, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t st,
-                      int64_t *launches);
+                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches);
 
 // tree.cu
 fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom);
 fmm_status build_lists(fmm_tree *t, double theta);
 fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
                             uint32_t *idx, uint64_t *keys2, uint32_t *idx2, uint32_t *hist,
-                            uint32_t *scan_scratch, unsigned long long *box_scratch,
-                            double *box_out, int *err, int64_t *launches);
+                            unsigned long long *box_scratch, double *box_out, int *err,
+                            int64_t *launches);
 
 // operators.cu
 fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, const int32_t **lut);

@@ -766,6 +766,12 @@ fmm_status d2h_u32(fmm_tree *t, const void *dev, uint32_t *host, int count)
     return cuda_check(t, cudaStreamSynchronize(t->stream), "sync");
 }
 
+fmm_status fail_wait(fmm_tree *t)
+{
+    t->err = "a bounded wait of the radix sort gave up";
+    return FMM_ETIMEOUT;
+}
+
 fmm_status build_plan(fmm_tree *t)
 {
     cudaStream_t st = t->stream;
@@ -781,7 +787,7 @@ fmm_status build_plan(fmm_tree *t)
     FMM_TRY(ensure(t, t->b_tc_vals2, 4 * (size_t)nc));
     const size_t hb = radix_hist_bytes(nc);
     FMM_TRY(ensure(t, t->b_tc_hist, hb));
-    FMM_TRY(ensure(t, t->b_tc_scan, scan_scratch_bytes(std::max<int64_t>((int64_t)hb / 4 + 1, nc + 1))));
+    FMM_TRY(ensure(t, t->b_tc_scan, scan_scratch_bytes(nc + 1)));
     FMM_TRY(ensure(t, t->b_tc_cnt, 16));
     cudaMemsetAsync(t->b_tc_cnt.ptr, 0, 16, st);
     k_tc_class<<<gridn(nc, 256), 256, 0, st>>>(nc, (const int32_t *)t->b_m2l_off.ptr,
@@ -792,9 +798,11 @@ fmm_status build_plan(fmm_tree *t)
     ++t->launches;
     radix_sort_pairs((uint64_t *)t->b_tc_keys.ptr, (uint32_t *)t->b_tc_vals.ptr, (uint64_t *)t->b_tc_keys2.ptr,
                      (uint32_t *)t->b_tc_vals2.ptr, nc, 16, (uint32_t *)t->b_tc_hist.ptr,
-                     (uint32_t *)t->b_tc_scan.ptr, st, &t->launches);
-    uint32_t T = 0;
-    FMM_TRY(d2h_u32(t, t->b_tc_cnt.ptr, &T, 1));
+                     (int *)t->b_tc_cnt.ptr + 3, st, &t->launches);
+    uint32_t Tw[4] = {0, 0, 0, 0};
+    FMM_TRY(d2h_u32(t, t->b_tc_cnt.ptr, Tw, 4));
+    if (Tw[3] & kErrSortWait) return fail_wait(t);
+    const uint32_t T = Tw[0];
     t->tc_T = T;
     t->tc_tiles = (T + 127) / 128;
     t->tc_rows = t->tc_chunks = 0;

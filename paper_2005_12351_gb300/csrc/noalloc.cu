@@ -18,14 +18,11 @@
 namespace {
 
 constexpr int64_t kMaxPoints = FMM_NOALLOC_MAX_POINTS;
-constexpr int64_t kSortTile = 4096;                    // tile of the radix sort
-constexpr int64_t kHistWords = 256 * (kMaxPoints / kSortTile);
+constexpr int64_t kHistWords = fmm::radix_hist_words(kMaxPoints);
 constexpr size_t kOffKeys2 = 0;                                          // uint64 [max]
 constexpr size_t kOffIdx2 = kOffKeys2 + 8 * (size_t)kMaxPoints;          // uint32 [max]
-constexpr size_t kOffHist = kOffIdx2 + 4 * (size_t)kMaxPoints;           // uint32 [hist]
-constexpr size_t kOffScan = kOffHist + 4 * (size_t)kHistWords;           // scan scratch
-constexpr size_t kScanBytes = 64 * 1024;
-constexpr size_t kOffBox = kOffScan + kScanBytes;                        // 6 x uint64 + 4 x f64
+constexpr size_t kOffHist = kOffIdx2 + 4 * (size_t)kMaxPoints;           // sort scratch
+constexpr size_t kOffBox = kOffHist + 4 * (size_t)kHistWords;            // 6 x uint64 + 4 x f64
 constexpr size_t kOffErr = kOffBox + 256;                                // int error word
 constexpr size_t kScratchBytes = kOffErr + 256;
 
@@ -73,8 +70,8 @@ extern "C" fmm_status fmm_morton_order_noalloc(void *cuda_stream, const double *
     if (st != FMM_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int *err = (int *)(base + kOffErr);
-    // only the error word must start at zero; every other region is fully
-    // written by the kernels before it is read
+    // only the error word must start at zero; the sort clears its own
+    // counters, and every other region is fully written before it is read
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return FMM_ECUDA;
@@ -82,8 +79,7 @@ extern "C" fmm_status fmm_morton_order_noalloc(void *cuda_stream, const double *
     int64_t launches = 0;
     fmm::morton_order_raw(s, positions, n, keys_out, (uint32_t *)perm_out,
                           (uint64_t *)(base + kOffKeys2), (uint32_t *)(base + kOffIdx2),
-                          (uint32_t *)(base + kOffHist), (uint32_t *)(base + kOffScan),
-                          (unsigned long long *)(base + kOffBox), (double *)(base + kOffBox) + 8,
+                          (uint32_t *)(base + kOffHist), (unsigned long long *)(base + kOffBox), (double *)(base + kOffBox) + 8,
                           err, &launches);
     int herr = 0;
     cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -92,5 +88,6 @@ extern "C" fmm_status fmm_morton_order_noalloc(void *cuda_stream, const double *
         cudaGetLastError();
         return FMM_ECUDA;
     }
-    return (herr & fmm::kErrNonFinite) ? FMM_EINVAL : FMM_OK;
+    if (herr & fmm::kErrNonFinite) return FMM_EINVAL;
+    return (herr & fmm::kErrSortWait) ? FMM_ETIMEOUT : FMM_OK;
 }

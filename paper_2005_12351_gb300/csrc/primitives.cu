@@ -2,10 +2,11 @@
 //
 // The radix sort orders the Morton keys of the octree (paper §3.2: the
 // octree is built over key-sorted particles) and the interaction lists.
-// Each 8-bit pass is three launches: per-tile digit histograms, one
-// exclusive scan of the digit-major histogram, and a stable scatter in which
-// every tile ranks its keys round by round with __match_any_sync, so equal
-// digits keep their input order (ties are broken by the original index).
+// It takes 8-bit digits: one launch counts the digits of all passes, then
+// each pass is one launch (see k_os_scatter); equal digits keep their input
+// order, so equal keys keep the order of their values.
+#include <algorithm>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -83,67 +84,176 @@ __global__ void k_scan_add(uint32_t *out, const uint32_t *tile_offsets, int64_t 
     }
 }
 
+// ---- one-sweep LSD radix sort
+// One launch counts the digits of every pass at once (the digit counts of a
+// pass do not depend on the order the earlier passes leave).  Each pass is
+// then one launch: a block takes the next tile in claim order, ranks its keys
+// stably (warp by warp, round by round), publishes its per-digit counts, adds
+// up the counts of the tiles before it by looking back through their
+// published words (decoupled look-back), and writes its keys out grouped by
+// digit through shared memory, so that runs of equal digits leave as
+// contiguous stores.  A status word is (flag << 32) | count, flag 1 = this
+// tile's own count, 2 = the inclusive prefix through this tile.  A block
+// waits only on tiles claimed before its own, whose blocks are running and
+// publish their own counts before they wait on anything, so every wait
+// ends.  The waits are bounded all the same: a block one of whose waits
+// gives up counts the digits of all earlier tiles from the input instead
+// (exact, slow) and sets kErrSortWait in the error word.
+constexpr uint64_t kStAgg = 1ull << 32, kStIncl = 2ull << 32;
+constexpr int kOsWait = 1 << 20;                 // polls before a wait gives up
+
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const uint64_t *keys, int64_t n, int shift, uint32_t *hist, int ntiles)
+k_os_hist(const uint64_t *keys, int64_t n, int passes, uint32_t *ghist, uint64_t *status0,
+          int64_t ntiles)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[kRadixMaxPasses][256];
+    for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0;
+    // zero the status words of the first pass (the pass k scatter zeroes those of pass k + 1)
+    for (int64_t w = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; w < ntiles * 256;
+         w += (int64_t)gridDim.x * kSortThreads)
+        status0[w] = 0ull;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int i = 0; i < kSortItems; ++i) {
-        int64_t k = base + (int64_t)i * kSortThreads + threadIdx.x;
-        if (k < n) atomicAdd(&h[(unsigned)(keys[k] >> shift) & 255u], 1u);
+    for (int64_t k = blockIdx.x * (int64_t)kSortThreads + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * kSortThreads) {
+        const uint64_t key = keys[k];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(key >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int p = 0; p < passes; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// Exclusive scan over the 256 threads of one value each (kSortThreads == 256).
+__device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t *warp_sums)
+{
+    uint32_t total;
+    return block_exclusive_scan(v, &total, warp_sums);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const uint64_t *keys, const uint32_t *vals, uint64_t *okeys, uint32_t *ovals,
-                int64_t n, int shift, const uint32_t *hist_scan, int ntiles)
+k_os_scatter(const uint64_t *keys, const uint32_t *vals, uint64_t *okeys, uint32_t *ovals,
+             int64_t n, int pass, int passes, const uint32_t *ghist, unsigned *tile_ctr,
+             uint64_t *status, uint64_t *status_next, int *err)
 {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wcnt[kSortWarps][256];
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    uint64_t *sk = (uint64_t *)os_smem;                               // [kSortTile]
+    uint32_t *sv = (uint32_t *)(sk + kSortTile);                      // [kSortTile]
+    uint32_t (*wh)[256] = (uint32_t (*)[256])(sv + kSortTile);        // [kSortWarps][256]
+    uint32_t *dst = (uint32_t *)(wh + kSortWarps);                    // [256] output base per digit
+    uint32_t *ls = dst + 256;                                         // [256] digit start in the tile
+    __shared__ uint32_t warp_sums[32];
+    __shared__ int s_tile, s_gave_up;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = hist_scan[(int64_t)tid * ntiles + blockIdx.x];
+    const int shift = 8 * pass;
+    if (tid == 0) {
+        s_tile = (int)atomicAdd(&tile_ctr[pass], 1u);
+        s_gave_up = 0;
+    }
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
+    for (int w = 0; w < kSortWarps; ++w) wh[w][tid] = 0;
     __syncthreads();
+    const int64_t tile = s_tile;
+    if (pass + 1 < passes) status_next[tile * 256 + tid] = 0ull;
+    const int64_t base = tile * kSortTile;
+    const int cnt = (int)min((int64_t)kSortTile, n - base);
+
+    // stable ranking inside the tile: warp w owns items [w*512, (w+1)*512) in
+    // input order, round i holding items w*512 + 32 i + lane
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems], off[kSortItems];
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int64_t k = base + (int64_t)i * kSortThreads + tid;
-        const bool valid = k < n;
-        const uint64_t key = valid ? keys[k] : 0ull;
-        const uint32_t val = valid ? vals[k] : 0u;
-        const unsigned d = valid ? ((unsigned)(key >> shift) & 255u) : 256u;
+        const int e = warp * (kSortItems * 32) + i * 32 + lane;
+        const bool valid = e < cnt;
+        key[i] = valid ? keys[base + e] : 0ull;
+        val[i] = valid ? vals[base + e] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int e = warp * (kSortItems * 32) + i * 32 + lane;
+        const bool valid = e < cnt;
+        const unsigned d = valid ? ((unsigned)(key[i] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned rank = __popc(peers & lt_mask);
-        if (valid && (__ffs(peers) - 1) == lane) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {   // digit `tid`: exclusive prefix over the warps of this round
-            uint32_t r = run[tid];
-#pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = r;
-                r += c;
-            }
-            run[tid] = r;
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && valid) {
+            before = wh[warp][d];
+            wh[warp][d] = before + __popc(peers);
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = wcnt[warp][d] + rank;
-            okeys[pos] = key;
-            ovals[pos] = val;
-        }
-        __syncthreads();
+        before = __shfl_sync(0xffffffffu, before, leader);
+        off[i] = before + __popc(peers & lt_mask);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit tid: warps' exclusive offsets, the tile's count, published at once
+    uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t x = wh[w][tid];
+        wh[w][tid] = c;
+        c += x;
+    }
+    volatile uint64_t *vs = (volatile uint64_t *)status;
+    vs[tile * 256 + tid] = (tile == 0 ? kStIncl : kStAgg) | c;
+    // tiles before this one: the exclusive prefix of digit tid
+    uint32_t excl = 0;
+    bool ok = true;
+    for (int64_t j = tile - 1; j >= 0; --j) {
+        uint64_t w = vs[j * 256 + tid];
+        int polls = 0;
+        while ((w >> 32) == 0 && polls < kOsWait) {
+            if (++polls > 64) __nanosleep(64);
+            w = vs[j * 256 + tid];
+        }
+        if ((w >> 32) == 0) { ok = false; break; }
+        excl += (uint32_t)w;
+        if ((w >> 32) == 2) break;
+    }
+    if (!ok) s_gave_up = 1;
+    else if (tile > 0) vs[tile * 256 + tid] = kStIncl | (excl + c);
+    __syncthreads();
+    if (s_gave_up) {
+        // a wait gave up: count the digits of every earlier tile from the
+        // input instead (slow, still exact), publish, and flag the event
+        dst[tid] = 0;
+        __syncthreads();
+        for (int64_t k = tid; k < base; k += kSortThreads)
+            atomicAdd(&dst[(unsigned)(keys[k] >> shift) & 255u], 1u);
+        __syncthreads();
+        excl = dst[tid];
+        vs[tile * 256 + tid] = kStIncl | (excl + c);
+        if (tid == 0) atomicOr(err, kErrSortWait);
         __syncthreads();
     }
+    const uint32_t lstart = scan256(c, warp_sums);           // digit start inside the tile
+    __syncthreads();
+    const uint32_t gstart = scan256(ghist[pass * 256 + tid], warp_sums);
+    dst[tid] = gstart + excl - lstart;
+    ls[tid] = lstart;
+    __syncthreads();
+    // the tile in digit order in shared memory, then out: element q of that
+    // order goes to dst[digit] + q, so equal digits leave as contiguous runs
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int e = warp * (kSortItems * 32) + i * 32 + lane;
+        if (e < cnt) {
+            const unsigned d = (unsigned)(key[i] >> shift) & 255u;
+            const uint32_t q = ls[d] + wh[warp][d] + off[i];
+            sk[q] = key[i];
+            sv[q] = val[i];
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < cnt; q += kSortThreads) {
+        const uint64_t k = sk[q];
+        const uint32_t pos = dst[(unsigned)(k >> shift) & 255u] + (uint32_t)q;
+        okeys[pos] = k;
+        ovals[pos] = sv[q];
+    }
 }
+
+constexpr size_t kOsSmem = (size_t)kSortTile * 12 + (size_t)kSortWarps * 256 * 4 + 2 * 256 * 4;
 
 }  // namespace
 
@@ -177,26 +287,37 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
 
 size_t radix_hist_bytes(int64_t n)
 {
-    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
-    return (size_t)(256 * (tiles > 0 ? tiles : 1)) * sizeof(uint32_t);
+    return 4 * (size_t)radix_hist_words(n);
 }
 
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
-                      int end_bit, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t st,
-                      int64_t *launches)
+                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches)
 {
     if (n <= 1) return;
-    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int passes = std::min((end_bit + 7) / 8, kRadixMaxPasses);
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    // hist: digit counts [passes][256], tile counters [16], two status areas [ntiles][256]
+    uint32_t *ghist = hist, *ctr = hist + kRadixMaxPasses * 256;
+    uint64_t *status[2] = {(uint64_t *)(hist + kRadixHead), (uint64_t *)(hist + kRadixHead) + ntiles * 256};
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem);
+        attr_set[dev] = true;
+    }
+    cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
+    const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads, 152 * 4);
+    k_os_hist<<<hgrid, kSortThreads, 0, st>>>(keys, n, passes, ghist, status[0], ntiles);
+    ++*launches;
     uint64_t *ka = keys, *kb = keys2;
     uint32_t *va = vals, *vb = vals2;
-    int passes = 0;
-    for (int shift = 0; shift < end_bit; shift += 8, ++passes) {
-        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles);
-        exclusive_scan_u32(hist, hist, (int64_t)256 * ntiles, scan_scratch, st, launches);
-        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles);
-        *launches += 2;
-        uint64_t *tk = ka; ka = kb; kb = tk;
-        uint32_t *tv = va; va = vb; vb = tv;
+    for (int p = 0; p < passes; ++p) {
+        k_os_scatter<<<(unsigned)ntiles, kSortThreads, kOsSmem, st>>>(
+            ka, va, kb, vb, n, p, passes, ghist, ctr, status[p & 1], status[(p + 1) & 1], err);
+        ++*launches;
+        std::swap(ka, kb);
+        std::swap(va, vb);
     }
     if (passes & 1) {
         cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);

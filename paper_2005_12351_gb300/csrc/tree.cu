@@ -624,6 +624,7 @@ fmm_status read_err(fmm_tree *t)
         t->err = "an accepted M2L offset exceeds 2^16 finer half-cells (theta too small for the tree)";
         return FMM_EINVAL;
     }
+    if (e & kErrSortWait) { t->err = "a bounded wait of the radix sort gave up"; return FMM_ETIMEOUT; }
     return FMM_OK;
 }
 
@@ -648,11 +649,11 @@ static void morton_keys(cudaStream_t st, const double *pos, int64_t n, uint64_t 
 
 fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
                             uint32_t *idx, uint64_t *keys2, uint32_t *idx2, uint32_t *hist,
-                            uint32_t *scan_scratch, unsigned long long *box_scratch,
-                            double *box_out, int *err, int64_t *launches)
+                            unsigned long long *box_scratch, double *box_out, int *err,
+                            int64_t *launches)
 {
     morton_keys(st, pos, n, keys, idx, box_scratch, box_out, err, launches);
-    radix_sort_pairs(keys, idx, keys2, idx2, n, 3 * kLevels, hist, scan_scratch, st, launches);
+    radix_sort_pairs(keys, idx, keys2, idx2, n, 3 * kLevels, hist, err, st, launches);
     return FMM_OK;
 }
 
@@ -705,8 +706,7 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     }
     record(t, 1);
     radix_sort_pairs(keys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
-                     3 * kLevels, (uint32_t *)t->b_hist.ptr, (uint32_t *)t->b_scan_tmp.ptr, st,
-                     &t->launches);
+                     3 * kLevels, (uint32_t *)t->b_hist.ptr, (int *)t->b_err.ptr, st, &t->launches);
     if (nsys > 1) {
         // stable second pass by system: order = (system, key, original index)
         FMM_TRY(ensure(t, t->b_lkeys, 8 * n));
@@ -717,8 +717,7 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
         int sbits = 1;
         while ((1 << sbits) < nsys) ++sbits;
         radix_sort_pairs(skeys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
-                         sbits, (uint32_t *)t->b_hist.ptr, (uint32_t *)t->b_scan_tmp.ptr, st,
-                         &t->launches);
+                         sbits, (uint32_t *)t->b_hist.ptr, (int *)t->b_err.ptr, st, &t->launches);
         k_regather_keys<<<grid(n, 256), 256, 0, st>>>(key_of, idx, n, keys);
         t->launches += 2;
     }
@@ -890,10 +889,13 @@ fmm_status build_lists(fmm_tree *t, double theta)
     uint64_t *lk = (uint64_t *)t->b_lkeys.ptr, *lk2 = (uint64_t *)t->b_lkeys2.ptr;
     uint32_t *lv = (uint32_t *)t->b_lval.ptr, *lv2 = (uint32_t *)t->b_lval2.ptr;
 
-    // P2P first (its keys are not needed afterwards except for the count)
+    // P2P first (its keys are not needed afterwards except for the count);
+    // the sorts report a wait that gave up in counter word 14
+    int *sort_err = (int *)(cnt + 14);
+    cudaMemsetAsync(sort_err, 0, 4, st);
     k_pack_pairs<<<grid(np2p, 256), 256, 0, st>>>((const int2 *)t->b_p2p_raw.ptr, np2p, cbits, lk, lv);
-    radix_sort_pairs(lk, lv, lk2, lv2, np2p, 2 * cbits, (uint32_t *)t->b_hist.ptr,
-                     (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+    radix_sort_pairs(lk, lv, lk2, lv2, np2p, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err, st,
+                     &t->launches);
     k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, np2p, cbits, nc, (int32_t *)t->b_p2p_off.ptr);
     k_unpack_src<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, (int32_t *)t->b_p2p_src.ptr);
     cudaMemsetAsync(cnt + 8, 0, 8, st);
@@ -906,8 +908,8 @@ fmm_status build_lists(fmm_tree *t, double theta)
     // M2L
     if (nm2l > 0) {
         k_pack_pairs<<<grid(nm2l, 256), 256, 0, st>>>((const int2 *)t->b_m2l_raw.ptr, nm2l, cbits, lk, lv);
-        radix_sort_pairs(lk, lv, lk2, lv2, nm2l, 2 * cbits, (uint32_t *)t->b_hist.ptr,
-                         (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+        radix_sort_pairs(lk, lv, lk2, lv2, nm2l, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err,
+                         st, &t->launches);
         k_unpack_src<<<grid(nm2l, 256), 256, 0, st>>>(lk, nm2l, cbits, (int32_t *)t->b_m2l_src.ptr);
         t->launches += 2;
     }
@@ -958,8 +960,7 @@ fmm_status build_lists(fmm_tree *t, double theta)
         // canonical numbering: keys by value (57-bit keys: gap, side, offsets)
         const int64_t nd1 = std::max<int64_t>(ndoff, 1);
         FMM_TRY(ensure(t, t->b_dsort, 20 * (size_t)nd1));
-        const size_t hb = radix_hist_bytes(nd1);
-        FMM_TRY(ensure(t, t->b_dsort_h, hb + scan_scratch_bytes((int64_t)hb / 4 + 1)));
+        FMM_TRY(ensure(t, t->b_dsort_h, radix_hist_bytes(nd1)));
         uint64_t *keys2 = (uint64_t *)t->b_dsort.ptr;
         uint32_t *vals = (uint32_t *)(keys2 + nd1), *vals2 = vals + nd1, *rank_of = vals2 + nd1;
         if (ndoff <= kRankSmall) {
@@ -968,14 +969,19 @@ fmm_status build_lists(fmm_tree *t, double theta)
         } else {
             k_iota<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff);
             radix_sort_pairs((uint64_t *)t->b_dkeys.ptr, vals, keys2, vals2, ndoff, 57,
-                             (uint32_t *)t->b_dsort_h.ptr, (uint32_t *)((char *)t->b_dsort_h.ptr + hb), st,
-                             &t->launches);
+                             (uint32_t *)t->b_dsort_h.ptr, sort_err, st, &t->launches);
             k_rank_of<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff, rank_of);
             t->launches += 3;
         }
         k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense, rank_of);
     }
+    int serr = 0;
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&serr, sort_err, 4, cudaMemcpyDeviceToHost, st), "sort status"));
     FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+    if (serr & kErrSortWait) {
+        t->err = "a bounded wait of the radix sort gave up";
+        return FMM_ETIMEOUT;
+    }
     t->n_m2l = nm2l;
     t->n_p2p = np2p;
     t->n_p2p_inter = (int64_t)inter;

@@ -31,6 +31,20 @@ def test_morton_order_bit_exact(orc, n, dist):
     assert np.array_equal(perm.cpu().numpy().astype(np.int64), t.perm)
 
 
+def test_morton_order_stable_with_repeated_points(orc):
+    """300,000 particles on 997 distinct points: runs of equal keys span many
+    sort tiles, and the sort keeps them in original-index order."""
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    base = synth.make_system(997, 0, "uniform", 4242)[0]
+    pick = np.minimum((synth.uniform01(4243, 1, 300_000) * 997).astype(np.int64), 996)
+    pos = base[pick]
+    keys, perm = fmm.morton_order(to_dev(pos))
+    t = orc.Tree(pos, 1 << 30)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), t.keys)
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), t.perm)
+
+
 def _compare_trees(orc, pos, ncrit, theta):
     t = orc.Tree(pos, ncrit)
     t.lists(theta)
