@@ -273,10 +273,11 @@ __global__ void k_roots(CellArrays c, const int64_t *off, int nsys)
     c.sys[s] = s;
 }
 
-__global__ void k_root_pairs(int2 *front, int nsys)
+__global__ void k_root_pairs(int2 *front, int nsys, unsigned *nf0)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nsys) front[s] = make_int2(s, s);
+    if (s == 0) *nf0 = (unsigned)nsys;
 }
 
 __device__ __forceinline__ int digit_at(uint64_t key, int level)
@@ -393,55 +394,74 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *count, unsigned want)
     return base + incl - want;
 }
 
-// counters: 0 = m2l, 1 = p2p, 2 = next frontier.  Outputs beyond a list's
-// capacity are counted but not written; the host grows the list and reruns.
-__global__ void k_traverse(CellArrays c, const int2 *front, int nf, double theta2, int2 *m2l,
-                           unsigned m2l_cap, int2 *p2p, unsigned p2p_cap, int2 *next,
-                           unsigned next_cap, unsigned *counters)
+// One round of the breadth-first dual traversal.  The rounds are launched
+// back to back without the host: round r reads its frontier size from
+// counters[kTravFront + r] and adds the next round's to the word after it.
+// counters: 0 = m2l, 1 = p2p, kTravOverflow = a frontier exceeded front_cap
+// (every later round then does nothing).  Outputs beyond a list's capacity
+// are counted but not written; the host grows what overflowed and reruns
+// the whole traversal.
+constexpr int kTravOverflow = 16, kTravFront = 32, kTravMaxRounds = 960;
+constexpr int kTravBlocks = 152 * 8;
+
+__global__ void __launch_bounds__(256)
+k_traverse_round(CellArrays c, int round, double theta2, const int2 *front, unsigned front_cap,
+                 int2 *m2l, unsigned m2l_cap, int2 *p2p, unsigned p2p_cap, int2 *next,
+                 unsigned *counters)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < nf;
-    int a = 0, b = 0, na = 0, nb = 0;
-    if (valid) {
-        a = front[t].x; b = front[t].y;
-        na = c.nchild[a]; nb = c.nchild[b];
+    const unsigned nf = counters[kTravFront + round];
+    if (nf == 0 || counters[kTravOverflow]) return;
+    if (nf > front_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&counters[kTravOverflow], 1u);
+        return;
     }
-    // classify: kind 0 = M2L, 1 = P2P, 2 = open a (all children against b, or
-    // all child pairs for a self pair), 3 = open b
-    int kind = -1;
-    if (valid) {
-        if (a == b) kind = na == 0 ? 1 : 2;
-        else if (mac_accept(c, a, b, theta2)) kind = 0;
-        else if (na == 0 && nb == 0) kind = 1;
-        else if (na == 0) kind = 3;
-        else if (nb == 0) kind = 2;
-        else kind = c.level[a] <= c.level[b] ? 2 : 3;
-    }
-    const unsigned n_next = kind == 2 ? (a == b ? (unsigned)(na * na) : (unsigned)na)
-                                      : (kind == 3 ? (unsigned)nb : 0u);
-    const unsigned o_m2l = warp_reserve(&counters[0], kind == 0);
-    const unsigned o_p2p = warp_reserve(&counters[1], kind == 1);
-    const unsigned o_next = warp_reserve(&counters[2], n_next);
-    if (kind == 0) {
-        if (o_m2l < m2l_cap) m2l[o_m2l] = make_int2(a, b);
-    } else if (kind == 1) {
-        if (o_p2p < p2p_cap) p2p[o_p2p] = make_int2(a, b);
-    } else if (kind == 2) {
-        const int f = c.child[a];
-        if (a == b) {
-            for (int i = 0; i < na; ++i)
-                for (int j = 0; j < na; ++j) {
-                    const unsigned k = o_next + (unsigned)(i * na + j);
-                    if (k < next_cap) next[k] = make_int2(f + i, f + j);
-                }
-        } else {
-            for (int i = 0; i < na; ++i)
-                if (o_next + i < next_cap) next[o_next + i] = make_int2(f + i, b);
+    unsigned *next_count = &counters[kTravFront + round + 1];
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < nf; base += stride) {
+        const unsigned t = base + threadIdx.x;
+        const bool valid = t < nf;
+        int a = 0, b = 0, na = 0, nb = 0;
+        if (valid) {
+            a = front[t].x; b = front[t].y;
+            na = c.nchild[a]; nb = c.nchild[b];
         }
-    } else if (kind == 3) {
-        const int f = c.child[b];
-        for (int j = 0; j < nb; ++j)
-            if (o_next + j < next_cap) next[o_next + j] = make_int2(a, f + j);
+        // classify: kind 0 = M2L, 1 = P2P, 2 = open a (all children against b,
+        // or all child pairs for a self pair), 3 = open b
+        int kind = -1;
+        if (valid) {
+            if (a == b) kind = na == 0 ? 1 : 2;
+            else if (mac_accept(c, a, b, theta2)) kind = 0;
+            else if (na == 0 && nb == 0) kind = 1;
+            else if (na == 0) kind = 3;
+            else if (nb == 0) kind = 2;
+            else kind = c.level[a] <= c.level[b] ? 2 : 3;
+        }
+        const unsigned n_next = kind == 2 ? (a == b ? (unsigned)(na * na) : (unsigned)na)
+                                          : (kind == 3 ? (unsigned)nb : 0u);
+        const unsigned o_m2l = warp_reserve(&counters[0], kind == 0);
+        const unsigned o_p2p = warp_reserve(&counters[1], kind == 1);
+        const unsigned o_next = warp_reserve(next_count, n_next);
+        if (kind == 0) {
+            if (o_m2l < m2l_cap) m2l[o_m2l] = make_int2(a, b);
+        } else if (kind == 1) {
+            if (o_p2p < p2p_cap) p2p[o_p2p] = make_int2(a, b);
+        } else if (kind == 2) {
+            const int f = c.child[a];
+            if (a == b) {
+                for (int i = 0; i < na; ++i)
+                    for (int j = 0; j < na; ++j) {
+                        const unsigned k = o_next + (unsigned)(i * na + j);
+                        if (k < front_cap) next[k] = make_int2(f + i, f + j);
+                    }
+            } else {
+                for (int i = 0; i < na; ++i)
+                    if (o_next + i < front_cap) next[o_next + i] = make_int2(f + i, b);
+            }
+        } else if (kind == 3) {
+            const int f = c.child[b];
+            for (int j = 0; j < nb; ++j)
+                if (o_next + j < front_cap) next[o_next + j] = make_int2(a, f + j);
+        }
     }
 }
 
@@ -816,58 +836,60 @@ fmm_status build_lists(fmm_tree *t, double theta)
     CellArrays c = cells_of(t);
     const double theta2 = theta * theta;
 
-    // ---- breadth-first dual traversal
-    FMM_TRY(ensure(t, t->b_counters, 64));
+    // ---- breadth-first dual traversal: a pair's two levels add up to at
+    // least its round, so 2 * nlevels rounds empty the frontier; they run as
+    // one batch of launches with one host sync (more batches if not)
+    FMM_TRY(ensure(t, t->b_counters, 4 * (kTravFront + kTravMaxRounds + 64)));
     unsigned *cnt = (unsigned *)t->b_counters.ptr;
-    size_t m2l_cap = std::max<size_t>(4096, t->m2l_cap_hint), p2p_cap = std::max<size_t>(4096, 40 * (size_t)t->nleaves);
-    FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * m2l_cap, 0));
-    FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * p2p_cap, 0));
-    m2l_cap = t->b_m2l_raw.bytes / 8;
-    p2p_cap = t->b_p2p_raw.bytes / 8;
-    FMM_TRY(grow_keep(t, t->b_front, 8 * 4096, 0));
-    FMM_TRY(grow_keep(t, t->b_front2, 8 * 4096, 0));
     const int nsys = (int)t->sys_off.size() - 1;
-    FMM_TRY(grow_keep(t, t->b_front, 8 * (size_t)nsys, 0));
-    k_root_pairs<<<grid(nsys, 128), 128, 0, st>>>((int2 *)t->b_front.ptr, nsys);
-    ++t->launches;
-    unsigned host_cnt[3] = {0, 0, 0};
-    int64_t nf = nsys;
-    while (nf > 0) {
-        const unsigned base[3] = {host_cnt[0], host_cnt[1], 0};
-        size_t next_cap = t->b_front2.bytes / 8;
+    size_t m2l_cap = std::max<size_t>(4096, t->m2l_cap_hint), p2p_cap = std::max<size_t>(4096, 40 * (size_t)t->nleaves);
+    size_t front_cap = std::max<size_t>({(size_t)4096, (size_t)nsys, 16 * (size_t)t->nleaves,
+                                         t->b_front.bytes / 8, t->b_front2.bytes / 8});
+    std::vector<unsigned> hc((size_t)kTravFront + kTravMaxRounds + 1);
+    const int batch = 2 * std::max(t->nlevels, 1) + 1;
+    for (;;) {
+        FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * m2l_cap, 0));
+        FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * p2p_cap, 0));
+        FMM_TRY(grow_keep(t, t->b_front, 8 * front_cap, 0));
+        FMM_TRY(grow_keep(t, t->b_front2, 8 * front_cap, 0));
+        m2l_cap = t->b_m2l_raw.bytes / 8;
+        p2p_cap = t->b_p2p_raw.bytes / 8;
+        front_cap = std::min(t->b_front.bytes, t->b_front2.bytes) / 8;
+        int2 *fr[2] = {(int2 *)t->b_front.ptr, (int2 *)t->b_front2.ptr};
+        FMM_TRY(cuda_check(t, cudaMemsetAsync(cnt, 0, 4 * (kTravFront + kTravMaxRounds + 1), st),
+                           "counters"));
+        k_root_pairs<<<grid(nsys, 128), 128, 0, st>>>(fr[0], nsys, cnt + kTravFront);
+        ++t->launches;
+        int r = 0;
+        bool retry = false;
         for (;;) {
-            FMM_TRY(cuda_check(t, cudaMemcpyAsync(cnt, base, sizeof(base), cudaMemcpyHostToDevice, st),
-                               "counters"));
-            k_traverse<<<grid(nf, 256), 256, 0, st>>>(c, (const int2 *)t->b_front.ptr, (int)nf,
-                                                      theta2, (int2 *)t->b_m2l_raw.ptr,
-                                                      (unsigned)m2l_cap, (int2 *)t->b_p2p_raw.ptr,
-                                                      (unsigned)p2p_cap, (int2 *)t->b_front2.ptr,
-                                                      (unsigned)next_cap, cnt);
-            ++t->launches;
-            FMM_TRY(cuda_check(t, cudaMemcpyAsync(host_cnt, cnt, sizeof(host_cnt),
+            const int end = std::min(r + batch, kTravMaxRounds);
+            for (; r < end; ++r) {
+                k_traverse_round<<<kTravBlocks, 256, 0, st>>>(
+                    c, r, theta2, fr[r & 1], (unsigned)front_cap, (int2 *)t->b_m2l_raw.ptr,
+                    (unsigned)m2l_cap, (int2 *)t->b_p2p_raw.ptr, (unsigned)p2p_cap, fr[(r + 1) & 1], cnt);
+                ++t->launches;
+            }
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(hc.data(), cnt, 4 * (size_t)(kTravFront + r + 1),
                                                   cudaMemcpyDeviceToHost, st), "counters"));
             FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
-            bool retry = false;
-            if (host_cnt[0] > m2l_cap) {
-                FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * (size_t)host_cnt[0] * 2, 8 * (size_t)base[0]));
-                m2l_cap = t->b_m2l_raw.bytes / 8;
+            unsigned fmax = 0;
+            for (int k = 0; k <= r; ++k) fmax = std::max(fmax, hc[kTravFront + k]);
+            if (hc[kTravOverflow] || fmax > front_cap) {
+                front_cap = std::max<size_t>(2 * front_cap, 2 * (size_t)fmax);
                 retry = true;
             }
-            if (host_cnt[1] > p2p_cap) {
-                FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * (size_t)host_cnt[1] * 2, 8 * (size_t)base[1]));
-                p2p_cap = t->b_p2p_raw.bytes / 8;
-                retry = true;
+            if (hc[0] > m2l_cap) { m2l_cap = 2 * (size_t)hc[0]; retry = true; }
+            if (hc[1] > p2p_cap) { p2p_cap = 2 * (size_t)hc[1]; retry = true; }
+            if (retry || hc[kTravFront + r] == 0) break;
+            if (r >= kTravMaxRounds) {
+                t->err = "the dual traversal did not end within its round limit";
+                return FMM_EINVAL;
             }
-            if (host_cnt[2] > next_cap) {
-                FMM_TRY(grow_keep(t, t->b_front2, 8 * (size_t)host_cnt[2] * 2, 0));
-                next_cap = t->b_front2.bytes / 8;
-                retry = true;
-            }
-            if (!retry) break;
         }
-        nf = host_cnt[2];
-        std::swap(t->b_front, t->b_front2);
+        if (!retry) break;
     }
+    const unsigned host_cnt[2] = {hc[0], hc[1]};
     const int64_t nm2l = host_cnt[0], np2p = host_cnt[1];
     t->m2l_cap_hint = (size_t)nm2l + nm2l / 8;
 
