@@ -100,6 +100,8 @@ fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int ma
  * The library copies (and permutes) both arrays into its own buffers, so the
  * caller may free or overwrite them once the stream has passed this call.
  * Non-finite positions give FMM_EINVAL.  Invalidates cached lists.
+ * FMM_ETIMEOUT if a bounded wait of the radix sort gave up (the sort then
+ * finishes exactly by a slower route, but the call reports the event).
  */
 fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *moments,
                            int64_t n, int source_order);
@@ -114,8 +116,9 @@ fmm_status fmm_set_sources(fmm_tree *t, const double *positions, const double *m
  * its limit p + s_lo <= 12 refer to s_lo.  Every other rule is that of
  * fmm_set_sources; fmm_update_moments takes rows of the same width.  The FP64
  * form only: FMM_EORDER on an FMM_FP32 / FMM_3XTF32 handle with s_hi > s_lo,
- * and unless 0 <= s_lo <= s_hi <= 2.  The symmetric P2P kernel (tuning
- * p2p_variant 2) covers single orders: a mixed system takes variant 1.
+ * and unless 0 <= s_lo <= s_hi <= 2.  The symmetric P2P (p2p_variant 2, the
+ * FP64 default) takes mixed systems, each shell's reverse term with its own
+ * parity; variants 0 and 1 both run the two-targets-per-thread kernel.
  */
 fmm_status fmm_set_sources_mixed(fmm_tree *t, const double *positions, const double *moments,
                                  int64_t n, int s_lo, int s_hi);
@@ -147,7 +150,9 @@ fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const dou
  *               !want_field.
  * Outputs are in the caller's original particle order.  The interaction
  * lists are rebuilt when theta differs from the cached value; the
- * derivative tables when theta or p change.
+ * derivative tables when theta or p change.  FMM_ETIMEOUT if a bounded
+ * device wait gave up (the radix sort of the lists: result still exact; the
+ * tensor-core M2L: outputs NaN).
  */
 fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field);
@@ -284,8 +289,10 @@ fmm_status fmm_direct_sum_mixed(void *cuda_stream, const double *positions, cons
  *   positions : DEVICE n x 3 doubles.
  *   keys_out  : DEVICE uint64 [n], keys in sorted order.
  *   perm_out  : DEVICE int32 [n], perm_out[k] = original index of slot k.
- * Allocates its scratch (about 24 bytes per point) with cudaMalloc and frees
- * it before returning; synchronises cuda_stream.
+ * Allocates its scratch (about 13 bytes per point) with cudaMalloc and frees
+ * it before returning; synchronises cuda_stream.  FMM_EINVAL for non-finite
+ * positions; FMM_ETIMEOUT if a bounded wait of the radix sort gave up (the
+ * result is still exact).
  */
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out);
