@@ -302,10 +302,9 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t 
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem);
-        attr_set[dev] = true;
-    }
+    if (dev >= 0 && dev < 64 && !attr_set[dev])
+        attr_set[dev] = cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kOsSmem) == cudaSuccess;
     cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
     const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads, 152 * 4);
     k_os_hist<<<hgrid, kSortThreads, 0, st>>>(keys, n, passes, ghist, status[0], ntiles);
