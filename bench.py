@@ -661,7 +661,7 @@ def run_ours(args, w):
     if rank == 0 and args.serving_requests > 0 and "batch" not in w:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, k, cores = oracle_sample(w, args.oracle_sample)
+        dt, k, cores = oracle_sample(w, args.cpu_baseline_sample)
         line["cpu_baseline"] = {
             "value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "oracle FMM on the full tree and lists, FMM result for %d sampled particles "
@@ -681,7 +681,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dipole_1m_p6", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--err-samples", type=int, default=4096)
-    ap.add_argument("--oracle-sample", type=int, default=65536)
+    ap.add_argument("--oracle-sample", type=int, default=65536,
+                    help="sampled particles per step of --impl reference")
+    ap.add_argument("--cpu-baseline-sample", type=int, default=163840,
+                    help="sampled particles of the main line's cpu_baseline (about 10 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "fp32", "3xtf32"], default="fp64")
     ap.add_argument("--no-mixed", action="store_true",
