@@ -84,3 +84,20 @@ def test_clock_sampler_reports_thermal_slowdown(monkeypatch):
 def test_clock_sampler_without_nvidia_smi():
     out = bench.ClockSampler(0).stop()
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_line_on_the_small_workload(orc, capsys):
+    """bench.py --impl reference times the oracle and prints the contract's line;
+    its value counts the particles one step evaluated (all 2,000 here)."""
+    import json
+    assert bench.main(["--impl", "reference", "--workload", "monopole_2k_p4", "--steps", "2",
+                       "--warmup", "1"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["unit"] == "particles/s" and line["higher_is_better"] is True
+    assert abs(line["value"] - 2000 / (line["ms_per_step"] / 1e3)) < 1e-6 * line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert "2000 sampled particles" in cb["sample"]
