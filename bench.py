@@ -148,12 +148,12 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def oracle_sample(w: dict, n_sample: int, seed_shift: int = 0):
+def oracle_sample(w: dict, n_sample, seed_shift: int = 0):
     """Time the oracle FMM on a bounded sample: the full tree and lists of the
     workload, then the FMM result for n_sample particles (upward pass on all
-    cells, downward pass on their ancestor chains, L2P and P2P for them).
-    For a batch workload the sample is whole systems (every 64th), each
-    evaluated completely."""
+    cells, downward pass on their ancestor chains, L2P and P2P for them);
+    n_sample None evaluates every particle.  For a batch workload the sample is
+    whole systems (every 64th), each evaluated completely."""
     import oracle
     if "batch" in w:
         pos, S, off = synth.make_batch(w["batch"], w["nlo"], w["nhi"], w["s"], w["seed"] + seed_shift,
@@ -168,7 +168,8 @@ def oracle_sample(w: dict, n_sample: int, seed_shift: int = 0):
             k_tot += b - a
         return time.perf_counter() - t0, k_tot, oracle.num_threads()
     pos, S = synth.make_system(w["n"], w["s"], w["dist"], w["seed"] + seed_shift)
-    tg = synth.sample_indices(w["n"], n_sample, 17)
+    tg = None if n_sample is None else synth.sample_indices(w["n"], n_sample, 17)
+    k = w["n"] if tg is None else len(tg)
     t0 = time.perf_counter()
     tree = oracle.Tree(pos, w["ncrit"])
     tree.lists(w["theta"])
@@ -176,33 +177,58 @@ def oracle_sample(w: dict, n_sample: int, seed_shift: int = 0):
     tree.fmm(S, w["s"], w["p"], targets=tg)
     t2 = time.perf_counter()
     # tree and lists serve all N particles: charge the sample its share; the
-    # upward pass and the ancestors' M2L stay fully charged (a conservative CPU figure)
-    dt = (t2 - t1) + (t1 - t0) * len(tg) / w["n"]
-    return dt, len(tg), oracle.num_threads()
+    # upward pass and the ancestors' M2L are charged in full whatever the sample
+    dt = (t2 - t1) + (t1 - t0) * k / w["n"]
+    return dt, k, oracle.num_threads()
+
+
+def fit_full_rate(counts, times, n: int):
+    """Oracle particles/s on the whole n-particle workload from steps of sampled
+    sizes: t(k) = fixed + per_particle * k by least squares (the fixed part is the
+    upward pass and the sample's ancestor M2L, paid whatever k is), evaluated at
+    k = n.  With one sample size only, the sampled rate."""
+    counts, times = np.asarray(counts, float), np.asarray(times, float)
+    if len(set(counts.tolist())) < 2:
+        return float(counts.sum() / times.sum()), None, None
+    per, fixed = np.polyfit(counts, times, 1)
+    per, fixed = max(float(per), 1e-12), max(float(fixed), 0.0)
+    return n / (fixed + per * n), fixed, per
 
 
 def run_reference(args, w):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    n_sample = args.oracle_sample
-    dt_w = []
-    for _ in range(args.warmup):
-        dt_w.append(oracle_sample(w, n_sample)[0])
-    times = []
+    # steps alternate between two sample sizes so that the fixed part of a step
+    # (upward pass, ancestors' M2L) can be told from the per-particle part
+    n_all = w.get("n") or 0
+    sizes = [max(1, args.oracle_sample // 2), args.oracle_sample * 2]
+    if "batch" not in w:
+        sizes = [None if k >= n_all else k for k in sizes]      # None: every particle
+    for i in range(args.warmup):
+        oracle_sample(w, sizes[i % 2])
+    times, counts = [], []
     cores, k = 1, 0
-    for _ in range(args.steps):
-        dt, k, cores = oracle_sample(w, n_sample)
+    for i in range(args.steps):
+        dt, k, cores = oracle_sample(w, sizes[i % 2])
         times.append(dt)
+        counts.append(k)
     ms = 1e3 * float(np.mean(times))
-    value = k / (ms / 1e3)              # k: the particles one step evaluated
     if "batch" in w:
+        value = float(np.sum(counts) / np.sum(times))
         sample = ("oracle FMM (C, FP64, OpenMP) on every 64th system of the batch, each evaluated "
                   "completely (%d particles per step); value = those particles / step time" % k)
     else:
-        sample = ("oracle FMM (C, FP64, OpenMP) on the full %d-particle tree and lists; FMM result "
-                  "for %d sampled particles per step (full upward pass, downward pass on their "
-                  "ancestor chains, L2P + P2P); value = sampled particles / step time" % (w["n"], k))
+        value, fixed, per = fit_full_rate(counts, times, w["n"])
+        if fixed is None:
+            sample = ("oracle FMM (C, FP64, OpenMP): tree, lists and the FMM result of all %d "
+                      "particles per step; value = %d / step time" % (w["n"], w["n"]))
+        else:
+            sample = ("oracle FMM (C, FP64, OpenMP) on the full %d-particle tree and lists; FMM result "
+                      "for %d or %d sampled particles per step, alternately (full upward pass, "
+                      "downward pass on their ancestor chains, L2P + P2P); value = %d / (fixed + "
+                      "per-particle x %d) fitted to the step times (fixed %.3f s, per particle %.3g s)"
+                      % (w["n"], counts[0], counts[1], w["n"], w["n"], fixed, per))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -540,78 +566,247 @@ def measure_mixed_orders(args, w, dev, world, flush):
                          "algorithmic_flops": flops, "peak_source": args.fp64_peak_source}}
 
 
-def serving_stream(count: int, seed: int):
+def measure_config(args, wname: str, precisions, dev, flush):
+    """One of the other benchmark configurations as a sub-object of the line:
+    per precision form, particles/s of the whole step (tree, lists, evaluate;
+    inputs resident, one untimed warm-up step, min(steps, 3) timed) and the error
+    of its result against the FP64 direct sum -- 4,096 sampled particles of a
+    single system, or 64 sampled whole systems of a batch -- with the ratio to the
+    FP64 form's error on the same targets."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    w = dict(synth.WORKLOADS[wname])
+    s, p, theta = w["s"], w["p"], w["theta"]
+    want_phi = True
+    if "batch" in w:
+        pos_np, S_np, off = synth.make_batch(w["batch"], w["nlo"], w["nhi"], s, w["seed"], w["dist"])
+        offsets = [int(x) for x in off]
+    else:
+        pos_np, S_np = synth.make_system(w["n"], s, w["dist"], w["seed"])
+        offsets = None
+    n = len(pos_np)
+    pos_d = torch.from_numpy(pos_np).to(dev)
+    S_d = torch.from_numpy(S_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    # reference: the GPU FP64 direct sum at the sampled targets
+    if offsets is not None:
+        ks = synth.sample_indices(len(offsets) - 1, 64, 23)
+        idx, refs = [], []
+        for k in ks:
+            a, b = offsets[k], offsets[k + 1]
+            ph, Er = fmm.direct_sum(pos_d[a:b].contiguous(), S_d[a:b].contiguous(), s)
+            refs.append((ph, Er))
+            idx.append(torch.arange(a, b, device=dev))
+        tg_d = torch.cat(idx)
+        phi_ref = torch.cat([r[0] for r in refs])
+        E_ref = torch.cat([r[1] for r in refs])
+        sample = "64 sampled whole systems (%d particles)" % tg_d.numel()
+    else:
+        tg = synth.sample_indices(n, args.err_samples, 23)
+        tg_d = torch.from_numpy(tg.astype(np.int64)).to(dev)
+        phi_ref, E_ref = fmm.direct_sum(pos_d, S_d, s, targets=tg_d.int())
+        sample = "%d sampled particles" % tg_d.numel()
+    out = {"workload": wname, "n": n, "source_order": s, "p": p, "theta": theta,
+           "max_leaf": w["ncrit"], "distribution": w["dist"], "outputs": "potential+field",
+           "error_targets": sample, "reference": "GPU FP64 direct sum (parity-tested vs oracle)"}
+    if offsets is not None:
+        out["systems"] = len(offsets) - 1
+    steps = max(1, min(args.steps, 3))
+    err64 = None
+    for prec in precisions:
+        tree = fmm.create_tree(device=dev.index, stream=stream, max_leaf=w["ncrit"], precision=prec)
+        phi_d = torch.empty(n, dtype=torch.float64, device=dev)
+        E_d = torch.empty((n, 3), dtype=torch.float64, device=dev)
+
+        def step():
+            if offsets is not None:
+                tree.set_sources_batch(pos_d, S_d, offsets, s)
+            else:
+                tree.set_sources(pos_d, S_d, s)
+            tree.evaluate(p, theta, want_phi, True, potential=phi_d, field=E_d)
+
+        step()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        launches0 = tree.launch_count()
+        for k in range(steps):
+            flush.fill_(k)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        E_s, phi_s = E_d[tg_d], phi_d[tg_d]
+        per = (torch.linalg.norm(E_s - E_ref, dim=1) / torch.linalg.norm(E_ref, dim=1)).cpu().numpy()
+        err = {"field_rel_rms": math.sqrt(((E_s - E_ref) ** 2).sum().item() / (E_ref ** 2).sum().item()),
+               "potential_rel_rms": math.sqrt(((phi_s - phi_ref) ** 2).sum().item()
+                                              / (phi_ref ** 2).sum().item()),
+               "field_rel_median": float(np.median(per)), "field_rel_p99": float(np.quantile(per, 0.99)),
+               "field_rel_max": float(per.max())}
+        if prec == "fp64":
+            err64 = err
+        res = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+               "gpu_launches_per_step": (tree.launch_count() - launches0) / steps, "rel_err": err}
+        if err64 is not None and prec != "fp64":
+            res["error_ratio_vs_fp64"] = {"field": err["field_rel_rms"] / err64["field_rel_rms"],
+                                          "potential": err["potential_rel_rms"] / err64["potential_rel_rms"]}
+            res["within_1p1_of_fp64"] = bool(max(res["error_ratio_vs_fp64"].values()) <= 1.1)
+        if prec == "3xtf32":
+            info = tree.info()
+            res["tc_rows"] = info["tc_rows"]
+        out[prec] = res
+        tree.destroy()
+    return out
+
+
+class RequestPools:
+    """Particle pools the serving requests are cut from: per distribution
+    (uniform cube, Plummer) 2,000,000 positions, and per source order that many
+    moments.  A request of size N takes N consecutive particles at a random
+    offset -- an i.i.d. sample of its distribution -- so thousands of requests
+    need no more host memory than the pools."""
+    NMAX = 2_000_000
+
+    def __init__(self, seed: int):
+        self.pos = {d: synth.make_system(self.NMAX, 0, d, seed + k)[0]
+                    for k, d in enumerate(("uniform", "plummer"))}
+        self.mom = {s: synth.sources(self.NMAX, seed + 10 + s, s) for s in (0, 1, 2)}
+
+    def cut(self, n: int, s: int, dist: str, u: float):
+        a = int(u * (self.NMAX - n + 1))
+        return self.pos[dist][a:a + n], self.mom[s][a:a + n]
+
+
+def serving_stream(count: int, seed: int, pools: RequestPools):
     """Requests drawn like the serving workload: N log-uniform in [1e3, 2e6],
     source order uniform over {0, 1, 2}, p uniform over {4..10}, uniform or
     Plummer positions 50/50, theta 0.5, n_crit 128."""
     sizes = synth.log_uniform_int(count, 1000, 2_000_000, seed)
-    u = synth.uniform01(seed, 17, 3 * count).reshape(count, 3)
+    u = synth.uniform01(seed, 17, 4 * count).reshape(count, 4)
     reqs = []
     for k in range(count):
         s = int(u[k, 0] * 3)
         p = 4 + int(u[k, 1] * 7)
         dist = "plummer" if u[k, 2] < 0.5 else "uniform"
-        pos, mom = synth.make_system(int(sizes[k]), s, dist, seed * 31 + k)
+        pos, mom = pools.cut(int(sizes[k]), s, dist, float(u[k, 3]))
         reqs.append(dict(positions=pos, moments=mom, source_order=s, p=p, theta=0.5,
                          max_leaf=128, want_potential=False, want_field=True))
     return reqs
 
 
-def run_serving(args, dev):
-    """Continuous batching on the device: calibrate capacity closed-loop, then
-    replay Poisson arrivals at 0.8 of it and report latency percentiles."""
+def _serve(sv, reqs, arrivals, keep):
+    """Submit reqs at the given arrival offsets (seconds; None = all at once),
+    reaping finished tickets as it goes so that only the requests in flight hold
+    outputs.  Returns (latencies ms, first submit, last end, particles done,
+    failures, kept results {index: field})."""
     from paper_2005_12351_gb300 import fmm
-    reqs = serving_stream(args.serving_requests, 20260004)
+    lat, out, failures = [], {}, []
+    live = {}
+    t_first, t_last, done_particles = None, None, 0
+    start = time.perf_counter()
+
+    def reap(block):
+        nonlocal t_first, t_last, done_particles
+        for k in list(live):
+            if not block and not sv.done(live[k]):
+                continue
+            r = reqs[k]
+            try:
+                _, E, info = sv.wait(live.pop(k))
+            except fmm.FMMError as e:
+                failures.append({"n": len(r["positions"]), "s": r["source_order"], "p": r["p"],
+                                 "error": str(e)[:200]})
+                continue
+            lat.append(1e3 * (info["end_s"] - info["submit_s"]))
+            t_first = info["submit_s"] if t_first is None else min(t_first, info["submit_s"])
+            t_last = info["end_s"] if t_last is None else max(t_last, info["end_s"])
+            done_particles += len(r["positions"])
+            if k in keep:
+                out[k] = E
+
+    for k, r in enumerate(reqs):
+        if arrivals is not None:
+            while True:
+                delay = start + arrivals[k] - time.perf_counter()
+                if delay <= 0:
+                    break
+                reap(False)
+                time.sleep(min(delay, 0.002))
+        live[k] = sv.submit(**r)
+        reap(False)
+    reap(True)
+    return lat, t_first, t_last, done_particles, failures, out
+
+
+def run_serving(args, dev):
+    """Continuous batching on the device: calibrate the server's capacity closed
+    loop, then replay Poisson arrivals at 0.5, 0.8 and 0.95 of it and report
+    latency percentiles per load; a sample of served results is checked against
+    the FP64 direct sum (and the FP64 form's error on the same requests)."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    pools = RequestPools(20260014)
+    reqs = serving_stream(args.serving_requests, 20260004, pools)
     total = sum(len(r["positions"]) for r in reqs)
     budget = 120 << 30
     sv = fmm.Server(device=dev.index, slots=args.serving_slots, precision=args.serving_precision,
                     mem_budget_bytes=budget)
-    # warm the slots, then closed loop: everything submitted at once
-    for t in [sv.submit(**r) for r in reqs[:args.serving_slots]]:
+    for t in [sv.submit(**r) for r in reqs[:args.serving_slots]]:      # warm the slots
         sv.wait(t)
     t0 = time.perf_counter()
-    for t in [sv.submit(**r) for r in reqs]:
-        try:
-            sv.wait(t)
-        except fmm.FMMError:
-            pass
-    capacity = total / (time.perf_counter() - t0)
-    # open loop: Poisson arrivals at 0.8 x capacity (in particles/s)
-    load = 0.8
-    rate = load * capacity / (total / len(reqs))             # requests per second
-    gaps = -np.log(1.0 - synth.uniform01(20260005, 1, len(reqs))) / rate
-    arrivals = np.cumsum(gaps)
-    start = time.perf_counter()
-    tickets = []
-    for a, r in zip(arrivals, reqs):
-        delay = start + a - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(sv.submit(**r))
-    lat, ends, firsts, failed, failures = [], [], [], 0, []
-    done_particles = 0
-    for t, r in zip(tickets, reqs):
-        try:
-            _, _, info = sv.wait(t)
-        except fmm.FMMError as e:
-            failed += 1
-            failures.append({"n": len(r["positions"]), "s": r["source_order"], "p": r["p"],
-                             "error": str(e)[:200]})
-            continue
-        lat.append(1e3 * (info["end_s"] - info["submit_s"]))
-        ends.append(info["end_s"])
-        firsts.append(info["submit_s"])
-        done_particles += len(r["positions"])
+    _, _, _, done0, fail0, _ = _serve(sv, reqs, None, set())
+    capacity = done0 / (time.perf_counter() - t0)
+    keep = set(range(0, len(reqs), max(1, len(reqs) // 16)))
+    loads = []
+    kept = {}
+    for li, load in enumerate((0.5, 0.8, 0.95)):
+        rate = load * capacity / (total / len(reqs))                      # requests per second
+        gaps = -np.log(1.0 - synth.uniform01(20260005 + li, 1, len(reqs))) / rate
+        lat, t_first, t_last, done, failures, out = _serve(sv, reqs, np.cumsum(gaps),
+                                                            keep if li == 1 else set())
+        kept.update(out)
+        loads.append({"offered_load": load, "offered_particles_per_s": load * capacity,
+                      "particles_per_s": done / (t_last - t_first) if done else 0.0,
+                      "p50_latency_ms": float(np.percentile(lat, 50)) if lat else None,
+                      "p99_latency_ms": float(np.percentile(lat, 99)) if lat else None,
+                      "max_latency_ms": float(np.max(lat)) if lat else None,
+                      "completed": len(lat), "failed": len(failures), "failures": failures[:5]})
     st = sv.stats()
     sv.close()
-    span = max(ends) - min(firsts)
-    return {"requests": len(reqs), "failed": failed, "failures": failures, "slots": args.serving_slots,
+    # accuracy of served results: field error at 256 sampled targets of each kept
+    # request against the GPU FP64 direct sum, beside the FP64 form's error
+    acc = []
+    for k in sorted(kept):
+        r = reqs[k]
+        n = len(r["positions"])
+        P = torch.from_numpy(np.ascontiguousarray(r["positions"])).to(dev)
+        Sd = torch.from_numpy(np.ascontiguousarray(r["moments"])).to(dev)
+        tg = synth.sample_indices(n, min(n, 256), 41 + k)
+        tg_d = torch.from_numpy(tg.astype(np.int32)).to(dev)
+        _, E_ref = fmm.direct_sum(P, Sd, r["source_order"], targets=tg_d, want_potential=False)
+        E_ref = E_ref.cpu().numpy()
+        t64 = fmm.create_tree(device=dev.index, max_leaf=r["max_leaf"])
+        t64.set_sources(P, Sd, r["source_order"])
+        _, E64 = t64.evaluate(r["p"], r["theta"], False, True)
+        E64 = E64.cpu().numpy()[tg]
+        t64.destroy()
+        e = float(np.sqrt(((kept[k][tg] - E_ref) ** 2).sum() / (E_ref ** 2).sum()))
+        e64 = float(np.sqrt(((E64 - E_ref) ** 2).sum() / (E_ref ** 2).sum()))
+        acc.append({"n": n, "s": r["source_order"], "p": r["p"], "field_rel_rms": e,
+                    "fp64_field_rel_rms": e64, "ratio": e / e64 if e64 > 0 else None})
+    ratios = [a["ratio"] for a in acc if a["ratio"] is not None]
+    return {"requests": len(reqs), "particles": total, "slots": args.serving_slots,
             "precision": args.serving_precision, "mem_budget_gb": 120,
-            "offered_load": load, "capacity_particles_per_s": capacity,
-            "particles_per_s": done_particles / span, "p50_latency_ms": float(np.percentile(lat, 50)),
-            "p99_latency_ms": float(np.percentile(lat, 99)),
-            "peak_device_gb": st["peak_device_bytes"] / 2 ** 30,
-            "mix": "N log-uniform [1e3, 2e6], s in {0,1,2}, p in {4..10}, uniform/Plummer 50/50"}
+            "capacity_particles_per_s": capacity, "capacity_failed": len(fail0),
+            "loads": loads, "peak_device_gb": st["peak_device_bytes"] / 2 ** 30,
+            "accuracy": {"requests_checked": len(acc), "targets_per_request": 256,
+                         "reference": "GPU FP64 direct sum (parity-tested vs oracle)",
+                         "max_ratio_vs_fp64": max(ratios) if ratios else None,
+                         "median_ratio_vs_fp64": float(np.median(ratios)) if ratios else None,
+                         "per_request": acc},
+            "mix": "N log-uniform [1e3, 2e6], s in {0,1,2}, p in {4..10}, uniform/Plummer 50/50, "
+                   "each request N consecutive particles of a 2M-particle pool at a random offset"}
 
 
 def run_ours(args, w):
@@ -662,14 +857,22 @@ def run_ours(args, w):
     if not args.no_graph:
         line["graph"] = measure_graph(args, w, args.graph_precision or args.precision, dev, world,
                                       pos_d, S_h, S_d, flush)
-    if rank == 0 and args.serving_requests > 0 and "batch" not in w:
+    if world == 1 and not args.no_configs and "batch" not in w:
+        forms = ("fp64", "fp32", "3xtf32")
+        line["plummer_4m_p8"] = measure_config(args, "dipole_plummer_4m_p8", forms, dev, flush)
+        line["quadrupole_batch_4096_p5"] = measure_config(args, "quadrupole_batch_4096_p5", forms,
+                                                          dev, flush)
+    if world == 1 and args.serving_requests > 0 and "batch" not in w:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, k, cores = oracle_sample(w, args.cpu_baseline_sample)
+        full = args.cpu_baseline_sample <= 0 or "batch" in w
+        dt, k, cores = oracle_sample(w, None if full else args.cpu_baseline_sample)
         line["cpu_baseline"] = {
             "value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "oracle FMM on the full tree and lists, FMM result for %d sampled particles "
-                      "(full upward pass, ancestor-chain downward pass, L2P + P2P); %.1f s" % (k, dt)}
+            "sample": ("oracle FMM (C, FP64, OpenMP): tree, lists and the FMM result of every one of "
+                       "the %d particles, one run, %.1f s" % (k, dt)) if full else
+                      ("oracle FMM on the full tree and lists, FMM result for %d sampled particles "
+                       "(full upward pass, ancestor-chain downward pass, L2P + P2P); %.1f s" % (k, dt))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -687,8 +890,11 @@ def main(argv=None):
     ap.add_argument("--err-samples", type=int, default=4096)
     ap.add_argument("--oracle-sample", type=int, default=65536,
                     help="sampled particles per step of --impl reference")
-    ap.add_argument("--cpu-baseline-sample", type=int, default=163840,
-                    help="sampled particles of the main line's cpu_baseline (about 10 s on 16 cores)")
+    ap.add_argument("--cpu-baseline-sample", type=int, default=0,
+                    help="sampled particles of the main line's cpu_baseline; 0 (default) evaluates "
+                         "the whole workload once (about 20 s on 16 cores at 1M particles)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 4M Plummer p=8 and 4,096-system quadrupole batch sub-objects")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "fp32", "3xtf32"], default="fp64")
     ap.add_argument("--no-mixed", action="store_true",
@@ -702,7 +908,7 @@ def main(argv=None):
     ap.add_argument("--bh-theta", type=float, default=None)
     ap.add_argument("--no-mixed-orders", action="store_true",
                     help="skip the charge + dipole (orders 0..1) line")
-    ap.add_argument("--serving-requests", type=int, default=48,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--serving-precision", choices=["fp64", "fp32", "3xtf32"], default="3xtf32")

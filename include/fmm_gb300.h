@@ -84,6 +84,15 @@ typedef enum {
  *   mem_budget_bytes : upper bound on the device memory the handle may hold
  *                 (0 = unlimited); exceeding it returns FMM_EBUDGET.
  * On success *out owns the handle; release it with fmm_destroy.
+ * Allocation failure: a call of any handle that returns FMM_ENOMEM has lost
+ * the buffer it was growing, so the handle drops its tree, lists and every
+ * cache derived from them; the handle itself stays valid, evaluate calls
+ * return FMM_ESTATE until fmm_set_sources (or _batch, _mixed) succeeds again,
+ * and from there on results are those of a fresh handle.  (FMM_EBUDGET
+ * refuses before anything is released and keeps the handle's state.)
+ * Testing hook: when the environment variable FMM_FAIL_ALLOC holds k >= 1 as
+ * the handle is created, the handle's k-th device allocation (counted from
+ * this call, which makes two) fails as cudaMalloc would, once.
  */
 fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int max_leaf,
                            fmm_precision prec, size_t mem_budget_bytes);
@@ -293,6 +302,12 @@ fmm_status fmm_direct_sum_mixed(void *cuda_stream, const double *positions, cons
  * it before returning; synchronises cuda_stream.  FMM_EINVAL for non-finite
  * positions; FMM_ETIMEOUT if a bounded wait of the radix sort gave up (the
  * result is still exact).
+ * The bound of those waits: each look-back of a sort tile reads the word it
+ * waits for at most 2^20 times, or as many times as the environment variable
+ * FMM_SORT_POLLS says when it is set (read on every sort, by every entry point
+ * that sorts); FMM_SORT_POLLS=0 makes every look-back give up at once, so
+ * every tile after the first recounts the digits before it (slow, exact) and
+ * the call returns FMM_ETIMEOUT -- a way to exercise that recovery path.
  */
 fmm_status fmm_morton_order(void *cuda_stream, const double *positions, int64_t n,
                             uint64_t *keys_out, int32_t *perm_out);
@@ -387,9 +402,13 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1),
  *               or each mirrored leaf pair once for both directions (2)
  *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
- *               the SIMT FP32 M2L (m2l_tensor 0); then, with the fastest of
- *               those, the other FP32 P2P (one-way 1 or symmetric 2)
- *   FMM_FP32    the one-way and the symmetric FP32 P2P
+ *               the SIMT FP32 M2L (m2l_tensor 0)
+ *   FMM_FP32    nothing to choose (the handle's settings are timed)
+ * The FP32 forms keep their P2P kernel: the one-way kernel (p2p_variant 1,
+ * their default) evaluates the pairs closer than one mean particle spacing of
+ * the target leaf in double-float arithmetic, which holds the near field's
+ * rounding at the FP64 form's level; their symmetric kernel (2, selectable
+ * with fmm_set_tuning) evaluates every pair in FP32 and is not a candidate.
  * Defaults before tuning: p2p_variant 2 (FP64) or 1 (FP32 forms), the
  * tensor-core M2L, 16 rows per chunk, harmonic M2L.
  * The variants compute the same sums in another order: results agree to the
@@ -468,8 +487,13 @@ fmm_status fmm_check_umma(const float *A, const float *B, float *D, int nkb, int
  *   until the process exits.  n > FMM_NOALLOC_MAX_POINTS returns FMM_EBUDGET
  *   and touches nothing; n < 0 or NULL pointers return FMM_EINVAL.
  *   Device: the calling thread's current device.  The first call on each
- *   device looks up the array's device address (cudaGetSymbolAddress); make
- *   that first call before any stream capture.
+ *   device does a set-up: the CUDA runtime loads the library's module for
+ *   that device (which places the scratch array and may itself allocate),
+ *   the array's device address is looked up (cudaGetSymbolAddress) and the
+ *   sort's shared-memory limit is raised.  A call with n == 0 does only this
+ *   set-up (pointers may then be NULL); make it once per device, before any
+ *   stream capture and outside any allocator callback, so that later calls
+ *   allocate nothing.
  *   Sharing: all calls on a device use the same array, and each call leaves
  *   its contents behind.  Calls that overlap on the GPU (different streams
  *   or threads without ordering between them) race on it: serialise them.

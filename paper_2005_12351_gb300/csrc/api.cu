@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary declared in include/fmm_gb300.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -16,6 +17,53 @@ fmm_status cuda_check(fmm_tree *t, cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA;
 }
 
+void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
+{
+    DevBuf *b[] = {&t->b_req_in, &t->b_req_out, &t->b_sys, &t->b_sysoff, &t->b_sysbox,
+                   &t->b_syseside, &t->b_o32, &t->b_S32,
+                   &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
+                   &t->b_hist, &t->b_px, &t->b_py, &t->b_pz, &t->b_S, &t->b_perm, &t->b_level,
+                   &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,
+                   &t->b_cy, &t->b_cz, &t->b_centre, &t->b_half, &t->b_leaves, &t->b_flags,
+                   &t->b_scan, &t->b_scan_tmp, &t->b_front, &t->b_front2, &t->b_m2l_raw,
+                   &t->b_p2p_raw, &t->b_counters, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
+                   &t->b_p2p_src, &t->b_p2p_off, &t->b_lkeys, &t->b_lkeys2, &t->b_lval,
+                   &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_dsort, &t->b_dsort_h, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
+                   &t->b_E, &t->b_tab_i32, &t->b_tab_u32, &t->b_tc_keys, &t->b_tc_keys2,
+                   &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
+                   &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,
+                   &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
+                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
+                   &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
+                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt, &t->b_ctl};
+    v.assign(b, b + sizeof(b) / sizeof(b[0]));
+}
+
+// After a failed allocation the buffer being grown is gone (ensure releases it
+// first), and with it whatever state lived there.  The handle goes back to the
+// state of a fresh one (keeping its tuning): every buffer but the error word
+// and the box scratch released, the tree, the lists, the captured graph and
+// every cache keyed on them dropped, so that no later call reads a buffer that
+// is not there.  fmm_set_sources rebuilds all of it.
+static void forget_state(fmm_tree *t)
+{
+    drop_graph(t);
+    std::vector<DevBuf *> v;
+    all_buffers(t, v);
+    for (DevBuf *b : v)
+        if (b != &t->b_err && b != &t->b_box) release(t, *b);
+    t->have_sources = false;
+    t->have_lists = false;
+    t->tc_plan = false;
+    t->tc_img_p = -1;
+    t->sym_plan = false;
+    t->bh_ran = false;
+    t->bh_key_s = -1;
+    t->d_p = -1;
+    t->d32_p = -1;
+    t->tab_key_s = t->tab_key_p = t->tab_key_nlo = t->tab_key_h = t->tab_key_shi = -1;
+}
+
 fmm_status ensure(fmm_tree *t, DevBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
@@ -28,10 +76,13 @@ fmm_status ensure(fmm_tree *t, DevBuf &b, size_t bytes)
     }
     release(t, b);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    const bool injected = t->fail_alloc_at > 0 && ++t->alloc_count == t->fail_alloc_at;
+    cudaError_t e = injected ? cudaErrorMemoryAllocation : cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
-        cudaGetLastError();
-        t->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+        if (!injected) cudaGetLastError();
+        t->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e) +
+                 (injected ? " (injected by FMM_FAIL_ALLOC)" : "");
+        forget_state(t);
         return FMM_ENOMEM;
     }
     b.ptr = p;
@@ -95,27 +146,6 @@ void record(fmm_tree *t, int i)
     if (t->profiling) cudaEventRecord(t->ev[i], t->stream);
 }
 
-void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
-{
-    DevBuf *b[] = {&t->b_req_in, &t->b_req_out, &t->b_sys, &t->b_sysoff, &t->b_sysbox,
-                   &t->b_syseside, &t->b_o32, &t->b_S32,
-                   &t->b_M32, &t->b_L32, &t->b_D32, &t->b_err, &t->b_box, &t->b_keys, &t->b_keys2, &t->b_idx, &t->b_idx2,
-                   &t->b_hist, &t->b_px, &t->b_py, &t->b_pz, &t->b_S, &t->b_perm, &t->b_level,
-                   &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,
-                   &t->b_cy, &t->b_cz, &t->b_centre, &t->b_half, &t->b_leaves, &t->b_flags,
-                   &t->b_scan, &t->b_scan_tmp, &t->b_front, &t->b_front2, &t->b_m2l_raw,
-                   &t->b_p2p_raw, &t->b_counters, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
-                   &t->b_p2p_src, &t->b_p2p_off, &t->b_lkeys, &t->b_lkeys2, &t->b_lval,
-                   &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_dsort, &t->b_dsort_h, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
-                   &t->b_E, &t->b_tab_i32, &t->b_tab_u32, &t->b_tc_keys, &t->b_tc_keys2,
-                   &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
-                   &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,
-                   &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
-                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
-                   &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
-                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt};
-    v.assign(b, b + sizeof(b) / sizeof(b[0]));
-}
 
 fmm_status fail(fmm_tree *t, fmm_status s, const std::string &msg)
 {
@@ -176,6 +206,7 @@ fmm_status fmm_create_tree(fmm_tree **out, int device, void *cuda_stream, int ma
     // pairs are cheap next to its warp sums, so they start one-way
     t->p2p_variant = prec == FMM_FP64 ? 2 : 1;
     t->budget = mem_budget_bytes;
+    if (const char *env = getenv("FMM_FAIL_ALLOC")) t->fail_alloc_at = std::max(0ll, atoll(env));
     std::memset(t->phase_ms, 0, sizeof(t->phase_ms));
     fmm_status st = ensure(t, t->b_err, 16);
     if (st == FMM_OK) st = ensure(t, t->b_box, 256);
@@ -453,8 +484,8 @@ fmm_status fmm_copy_array(const fmm_tree *tc, fmm_array which, void *host_dst, s
         return plain(t->b_M, 8 * (size_t)nc * t->tab.nM);
     case FMM_ARR_LOCAL:
         if (t->tab_key_p < 0) return fail(t, FMM_ESTATE, "no evaluate yet");
-        if (t->prec != FMM_FP64) return plain(t->b_L32, 4 * (size_t)nc * t->tab.nL);
-        return plain(t->b_L, 8 * (size_t)nc * t->tab.nL);
+        if (t->prec != FMM_FP64) return plain(t->b_L32, 4 * (size_t)nc * t->tab.nLh);
+        return plain(t->b_L, 8 * (size_t)nc * t->tab.nLh);
     case FMM_ARR_CELL_SYSTEM: return plain(t->b_sys, 4 * (size_t)nc);
     }
     return fail(t, FMM_EINVAL, "unknown array id");

@@ -76,6 +76,10 @@ struct OpTables {
     // unfold: (n, a, b), L_n = -L_a - L_b (a, b = n + 2x - 2z, n + 2y - 2z),
     // levels of increasing n_z >= 2, CSR over levels
     std::vector<int> h_unfold, h_unfold_off;
+    // stored local components: nLh per cell, the n with n_z <= 1 (graded order)
+    // when harmonic, all nL otherwise; h_rn[r] = full index of stored slot r
+    int nLh = 0;
+    std::vector<int> h_rn;
 };
 // s: the lowest source order (the expansion's), s_hi: the highest (mixed
 // systems carry every order s..s_hi per particle; P2M reads all of them)
@@ -120,7 +124,27 @@ struct DevTables {
     // harmonic M2L (OpTables): nMh = nM and no levels when off
     int harmonic, nMh, h_fold_lev, h_unfold_lev;
     const int *h_rm, *h_fold, *h_fold_off, *h_unfold, *h_unfold_off;
+    // stored local components (OpTables): nLh per cell, slot r holds L_{h_rn[r]}
+    int nLh;
+    const int *h_rn;
 };
+
+// A cell's full local expansion in shared memory (Lf[nL]) from its stored row:
+// the stored components, then -- harmonic storage -- the others in increasing
+// n_z from the trace identity L_n = -L_{n+2x-2z} - L_{n+2y-2z} (§3.1: 1/r is
+// harmonic, so are the local expansions of its M2L and their L2L shifts).
+// Called by every thread of the block; ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void expand_local(const T *row, const DevTables &tb, T *Lf)
+{
+    for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x) Lf[tb.h_rn[r]] = row[r];
+    for (int l = 0; l < tb.h_unfold_lev; ++l) {
+        __syncthreads();
+        for (int q = tb.h_unfold_off[l] + threadIdx.x; q < tb.h_unfold_off[l + 1]; q += blockDim.x)
+            Lf[tb.h_unfold[3 * q]] = -Lf[tb.h_unfold[3 * q + 1]] - Lf[tb.h_unfold[3 * q + 2]];
+    }
+    __syncthreads();
+}
 
 __device__ __forceinline__ int mi_at(const int *mi, int k) { return __ldg(mi + k); }
 __device__ __forceinline__ int mi_nx(int v) { return v & 31; }
@@ -147,6 +171,9 @@ struct fmm_tree {
     size_t held = 0;
     std::string err;
     int64_t launches = 0;
+    // allocation-failure injection (FMM_FAIL_ALLOC at create): the fail_alloc_at-th
+    // device allocation of the handle fails once; 0 = off
+    int64_t alloc_count = 0, fail_alloc_at = 0;
 
     // system
     int64_t n = 0;
@@ -188,6 +215,7 @@ struct fmm_tree {
     const int *sys_eside_dev() const { return (const int *)b_syseside.ptr; }
     DevBuf b_centre, b_half, b_leaves;
     DevBuf b_flags, b_scan, b_scan_tmp;
+    DevBuf b_ctl;                          // level counts of the cell build
     DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;
     DevBuf b_m2l_src, b_m2l_off, b_m2l_didx, b_p2p_src, b_p2p_off, b_lkeys, b_lkeys2, b_lval, b_lval2;
     DevBuf b_hash, b_dkeys, b_D;
@@ -270,10 +298,16 @@ size_t radix_hist_bytes(int64_t n);
 // of the one-sweep passes that gave up sets kErrSortWait in *err (device).
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
                       int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches);
+// Per-device set-up of the sort (its kernels loaded, the scatter's shared-
+// memory limit raised); radix_sort_pairs calls it, and callers that must not
+// trigger module loading later call it ahead of time.
+void radix_sort_prepare();
 
 // tree.cu
 fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom);
 fmm_status build_lists(fmm_tree *t, double theta);
+// loads the Morton-order kernels on the current device (no launch)
+void morton_order_prepare();
 fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
                             uint32_t *idx, uint64_t *keys2, uint32_t *idx2, uint32_t *hist,
                             unsigned long long *box_scratch, double *box_out, int *err,
@@ -328,6 +362,19 @@ void launch_direct(cudaStream_t st, const double *pos, const double *mom, int64_
 }  // namespace fmm
 
 namespace fmm {
+// Streaming multiprocessors of the current device (grid caps of the
+// grid-stride kernels scale with it); 1 if the query fails.
+inline int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return sms;
+}
+
 // Raises a kernel's dynamic shared-memory limit to the most a block can take
 // next to its static shared memory.  The value depends only on the kernel, so
 // handles that launch it concurrently from several threads never lower the

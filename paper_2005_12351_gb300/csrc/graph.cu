@@ -136,9 +136,9 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     if (reps < 1 || reps > 1000) return fail(t, FMM_EINVAL, "reps must be in [1, 1000]");
     // candidates: variants that compute the same sums in another order (the
     // three FP64 P2P kernels agree to FP64 rounding; the M2L paths of FMM_3XTF32
-    // and its chunk lengths, and the FP32 forms' one-way and symmetric P2P,
-    // agree to FP32 rounding).  The FP32 forms take two stages: the M2L
-    // candidates with the handle's P2P, then the other P2P with the winner.
+    // and its chunk lengths agree to FP32 rounding).  The FP32 forms keep their
+    // P2P kernel: only the one-way kernel evaluates the close pairs in
+    // double-float, so the symmetric one would trade accuracy for time.
     std::vector<fmm_tuning> cand;
     fmm_tuning base;
     std::memset(&base, 0, sizeof(base));
@@ -173,7 +173,6 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     fmm_status st = FMM_OK;
     int best = -1;
     float best_ms = std::numeric_limits<float>::infinity();
-    const size_t stage1 = cand.size();
     for (size_t k = 0; k < cand.size() && st == FMM_OK; ++k) {
         const fmm_tuning c = cand[k];
         t->p2p_variant = c.p2p_variant;
@@ -196,12 +195,6 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
         if (ms < best_ms) {
             best_ms = ms;
             best = (int)k;
-        }
-        if (k + 1 == stage1 && t->prec != FMM_FP64) {
-            // stage two: the winning M2L configuration with the other P2P kernel
-            fmm_tuning c2 = cand[best];
-            c2.p2p_variant = c2.p2p_variant == 2 ? 1 : 2;
-            cand.push_back(c2);
         }
     }
     cudaEventDestroy(a);

@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(128) k_check_umma(const float *A, const float 
         }
     } else if (tid == 0) {
         atomicOr(err, 1u);
+        // the MMAs may still be running: free tensor memory only after their commit
+        mbar_wait_cleanup(smem_u32(bar), 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -219,14 +221,6 @@ __device__ __forceinline__ int cur_next_row(const TcCursor &c, const TcArgs &a)
     if (c.r + 1 < c.re) return c.r + 1;
     const int w = c.w + gridDim.x;
     return w < a.n_items ? a.chunk_rb[w / a.ngroups] : -1;
-}
-
-// bounded wait that ignores the abort flag (used only while cleaning up)
-__device__ __forceinline__ void mbar_wait_cleanup(uint32_t bar, unsigned parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_test(bar, parity) && clock64() - t0 < (1ll << 28)) {
-    }
 }
 
 template <int RS>   // shared raw ring stages; RS - 1 units of A in flight
@@ -448,6 +442,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             cur_next(cm, a);
             ++u;
         }
+        // On an abort the stagers no longer drain, so MMAs this thread issued may
+        // still be running: the last commit arrives once all of them are done, and
+        // tensor memory is freed below only after that (bounded) wait.
+        if (*abort && u > 0) mbar_wait_cleanup(mma_done((u - 1) & 3), (unsigned)(((u - 1) >> 2) & 1));
     } else if (tid == 288) {
         // ------------------------------------------------ operator image loader
         TcCursor cb;
@@ -488,13 +486,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
 }
 
 // L~_t[col_n[col]] = sum of the tile's chunk partials of target t in column col,
-// in FP64, in chunk order; for the harmonic M2L the other L~_n follow by the
-// unfold levels (L_n = -L_a - L_b).  NaN everywhere if a wait of the M2L block
-// gave up: the failure shows in the output.
+// in FP64, in chunk order; the stored components (slot r holds n = h_rn[r]:
+// for the harmonic M2L exactly its columns, the n with n_z <= 1) are written.
+// NaN everywhere if a wait of the M2L block gave up: the failure shows in the
+// output.
 __global__ void k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile_chunk_off,
                             const float *partial, int Np, int ncol, const int32_t *col_n, int nL,
-                            const int *uf, const int *uf_off, int uf_lev, const unsigned *err,
-                            float *L)
+                            int nLh, const int *h_rn, const unsigned *err, float *L)
 {
     __shared__ double Ls[kMaxTot];
     const int q = blockIdx.x;
@@ -509,14 +507,9 @@ __global__ void k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile
         for (int j = j0; j < j1; ++j) v += (double)partial[((size_t)j * 128 + lane) * Np + col];
         Ls[col_n[col]] = v;
     }
-    for (int l = 0; l < uf_lev; ++l) {
-        __syncthreads();
-        for (int u = uf_off[l] + threadIdx.x; u < uf_off[l + 1]; u += blockDim.x)
-            Ls[uf[3 * u]] = -Ls[uf[3 * u + 1]] - Ls[uf[3 * u + 2]];
-    }
     __syncthreads();
-    for (int n = threadIdx.x; n < nL; n += blockDim.x)
-        L[(size_t)c * nL + n] = bad ? __int_as_float(0x7fc00000) : (float)Ls[n];
+    for (int r = threadIdx.x; r < nLh; r += blockDim.x)
+        L[(size_t)c * nLh + r] = bad ? __int_as_float(0x7fc00000) : (float)Ls[h_rn[r]];
 }
 
 // ------------------------------------------------------------ the plan
@@ -975,7 +968,7 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
     k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, st>>>(
         (int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr, (const uint32_t *)t->b_tc_coff.ptr,
         (const float *)t->b_tc_part.ptr, Ly.Np, Ly.ncol, (const int32_t *)t->b_tc_el.ptr + 2 * Ly.E, nL,
-        tb.h_unfold, tb.h_unfold_off, tb.h_unfold_lev, err, L);
+        tb.nLh, tb.h_rn, err, L);
     t->launches += 2;
     return cuda_check(t, cudaGetLastError(), "tensor-core M2L");
 }

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "df32.cuh"
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -52,24 +53,35 @@ __device__ __forceinline__ void axis_powers32(float w, int P, float *out)
 // o_j = x_j - z_leaf formed in FP64 and kept as an unevaluated float pair
 // hi + lo (hi = o rounded, lo = the remainder rounded): together they carry
 // ~48 bits, so pair separations can later be formed accurately relative to
-// their own size.  S32 = (float)S.
+// their own size.  S32 = (float)S, and after the n rows of S32 the rows of
+// S32lo = (float)(S - S32), the moments' low halves for the close pairs that
+// the P2P evaluates in double-float.
 __global__ void k_prep32(const int32_t *leaves, const int32_t *begin, const int32_t *end,
                          const double *centre, const double *px, const double *py,
-                         const double *pz, const double *S, int nS, float4 *o, float4 *olo,
-                         float *S32)
+                         const double *pz, const double *S, int nS, int64_t n, float4 *o,
+                         float4 *olo, float *S32)
 {
     const int c = leaves[blockIdx.x];
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
+    const int nS32 = nS == 6 ? 7 : nS;
+    float *S32lo = S32 + n * nS32;
     for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
         const double dx = px[j] - z0, dy = py[j] - z1, dz = pz[j] - z2;
         const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
         o[j] = make_float4(hx, hy, hz, 0.0f);
         olo[j] = make_float4((float)(dx - hx), (float)(dy - hy), (float)(dz - hz), 0.0f);
-        const int nS32 = nS == 6 ? 7 : nS;
-        for (int a = 0; a < nS; ++a) S32[(int64_t)j * nS32 + a] = (float)S[(int64_t)j * nS + a];
-        if (nS == 6)      // quadrupole trace summed in FP64: zero stays ~zero for traceless input
-            S32[(int64_t)j * 7 + 6] = (float)(S[(int64_t)j * 6] + S[(int64_t)j * 6 + 3] +
-                                             S[(int64_t)j * 6 + 5]);
+        for (int a = 0; a < nS; ++a) {
+            const double v = S[(int64_t)j * nS + a];
+            const float vh = (float)v;
+            S32[(int64_t)j * nS32 + a] = vh;
+            S32lo[(int64_t)j * nS32 + a] = (float)(v - (double)vh);
+        }
+        if (nS == 6) {    // quadrupole trace summed in FP64: zero stays ~zero for traceless input
+            const double tr = S[(int64_t)j * 6] + S[(int64_t)j * 6 + 3] + S[(int64_t)j * 6 + 5];
+            const float th = (float)tr;
+            S32[(int64_t)j * 7 + 6] = th;
+            S32lo[(int64_t)j * 7 + 6] = (float)(tr - (double)th);
+        }
     }
 }
 
@@ -291,21 +303,13 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
         }
     }
     __syncthreads();
-    // nL doubles fit in the D rows (16 nD floats), 8-byte aligned: the row
-    // block before them holds an even number of floats
-    double *Ls = (double *)Dsm;
-    for (int n = tid; n < tb.nL; n += Tn) {
+    // the stored components (n_z <= 1 when harmonic, the traceless form)
+    for (int r = tid; r < tb.nLh; r += Tn) {
+        const int n = tb.h_rn[r];
         double v = 0.0;
         for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
-        Ls[n] = v;
+        L[(int64_t)c * tb.nLh + r] = (float)v;
     }
-    for (int l = 0; l < tb.h_unfold_lev; ++l) {
-        __syncthreads();
-        for (int q = tb.h_unfold_off[l] + tid; q < tb.h_unfold_off[l + 1]; q += Tn)
-            Ls[tb.h_unfold[3 * q]] = -Ls[tb.h_unfold[3 * q + 1]] - Ls[tb.h_unfold[3 * q + 2]];
-    }
-    __syncthreads();
-    for (int n = tid; n < tb.nL; n += Tn) L[(int64_t)c * tb.nL + n] = (float)Ls[n];
 }
 
 // ------------------------------------------------------------------ L2L
@@ -321,15 +325,19 @@ k_l2l32(int lb, const int32_t *parent, const int32_t *cx, const int32_t *cy, con
     // z_c - z_p = (2 bit - 1) h_c: negative where the child's low bit is 0
     const int bx = 1 - (cx[c] & 1), by = 1 - (cy[c] & 1), bz = 1 - (cz[c] & 1);
     for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
+    // the parent's full expansion (the identity holds degree by degree, so the
+    // power-of-two rescaling may follow the unfold)
+    expand_local(L + (int64_t)pa * tb.nLh, tb, Lp);
     for (int q = threadIdx.x; q < tb.nL; q += blockDim.x)
-        Lp[q] = ldexpf(L[(int64_t)pa * tb.nL + q], -(mi_shell(mi_at(tb.mi, q)) + tb.s + 1));
+        Lp[q] = ldexpf(Lp[q], -(mi_shell(mi_at(tb.mi, q)) + tb.s + 1));
     __syncthreads();
-    for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
+    for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x) {
+        const int n = tb.h_rn[r];
         if (mi_shell(mi_at(tb.mi, n)) < tb.n_lo) continue;
         float acc = 0.0f;
         for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
             acc = fmaf(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
-        L[(int64_t)c * tb.nL + n] += acc;
+        L[(int64_t)c * tb.nLh + r] += acc;
     }
 }
 
@@ -351,8 +359,7 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
     const float inv_h = (float)(1.0 / h);
     const int eh = ilogb(h);
     const double sphi = ldexp(1.0, -(tb.s + 1) * eh), sfield = ldexp(1.0, -(tb.s + 2) * eh);
-    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lsm[t] = L[(int64_t)c * tb.nL + t];
-    __syncthreads();
+    expand_local(L + (int64_t)c * tb.nLh, tb, Lsm);
     for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
         const float4 v = o[j];
         axis_powers32(v.x * inv_h, P, a);
@@ -384,11 +391,22 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
 // target o_i, source o_j + (z_B - z_A), the centre offset formed exactly from
 // the integer cell coordinates.  Each thread sums a staged round in FP32 and
 // adds it to FP64 totals; the far field is added in FP64.
+//
+// Close pairs.  A target's field error in FP32 pair arithmetic is set by its
+// nearest neighbours (the pair terms grow as r^-(s+2) and the rounding of
+// each is relative to its own size), so the pairs closer than one mean
+// particle spacing of the target leaf, a = 2 h / count^(1/3), are evaluated in
+// double-float arithmetic instead (df32.cuh; ~4 pairs per particle in a
+// uniform set, ~0.2 % of the near field), which puts the near field's
+// rounding at the level of the FP64 form.  The FP32 loop zeroes such a pair
+// and queues it for its thread and target; when a queue of the warp is full,
+// and at the end of each staged round, every lane evaluates its own queue
+// into its own double-float sums, in queue order, so the result stays
+// deterministic.
 template <int S, bool PHI, bool FIELD>
-__device__ __forceinline__ void pair32(float dx, float dy, float dz, const float *Sj, float &f,
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, const float *Sj, float &f,
                                        float &e0, float &e1, float &e2)
 {
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
     y = y * fmaf(-0.5f * r2 * y, y, 1.5f);          // one Newton step: ~1 ulp
     const float y2 = y * y;
@@ -426,27 +444,50 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, const float
     }
 }
 
+// the same separation as a double-float: (oi - a) by TwoSum, the low parts added
+__device__ __forceinline__ df32 sep_df(float oi, float li, float a, float b)
+{
+    const df32 d = df_two_sum(oi, -a);
+    return df_fast2(d.hi, __fadd_rn(d.lo, __fsub_rn(li, b)));
+}
+
 constexpr int kP2PThreads = 128;
 constexpr int kP2PChunk = 768;
 constexpr int kGroups = 64;
+constexpr int kLaneQ = 8;                 // close pairs a thread queues per target
+constexpr double kCloseSpacings = 1.0;    // close: r < this many mean spacings of the target leaf
 
 template <int S, bool PHI, bool FIELD>
 __global__ void __launch_bounds__(kP2PThreads)
 k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
         const int32_t *src, const int32_t *level, const int32_t *cx, const int32_t *cy,
-        const int32_t *cz, const int32_t *sys, const double *sys_box, const float4 *o,
-        const float4 *olo, const float *S32,
+        const int32_t *cz, const int32_t *sys, const double *sys_box, const double *half,
+        const float4 *o, const float4 *olo, const float *S32, const float *S32lo,
         const double *phi_far, const double *E_far, const int32_t *perm, double *phi_out,
         double *E_out)
 {
     constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;     // + trace for quadrupoles
+    constexpr int nR = S == 2 ? 8 : (S == 1 ? 2 : 0);           // moments after the first, padded
     constexpr int CH = S == 2 ? 704 : kP2PChunk;                // static smem stays < 48 KB
-    __shared__ float sx[CH], sy[CH], sz[CH], sS[CH * nS];
-    __shared__ float lx[CH], ly[CH], lz[CH];
-    __shared__ double red[8][kP2PThreads];
+    // a round stages at most CHU sources; the slots up to CH take the padding
+    // that gives every thread the same number of steps
+    constexpr int CHU = CH - kP2PThreads;
+    // staged sources of a round: (x, y, z, S_0) hi position in the target leaf's
+    // frame and first moment, the other moments, the positions' low parts; the
+    // per-thread totals of the final reduction reuse the same bytes once the
+    // last round is done
+    constexpr int kStageFloats = CH * (4 + nR + 3);
+    static_assert(kStageFloats >= 2 * 8 * kP2PThreads, "reduction area");
+    __shared__ __align__(16) float stage[kStageFloats];
+    float4 *P4 = (float4 *)stage;
+    float *SR = stage + 4 * CH;
+    float *lx = SR + nR * CH, *ly = lx + CH, *lz = ly + CH;
+    double (*red)[kP2PThreads] = (double (*)[kP2PThreads])stage;
     __shared__ int gbeg[kGroups], gpre[kGroups + 1];
     __shared__ float gdx[kGroups], gdy[kGroups], gdz[kGroups];
     __shared__ int s_next_q, s_next_j, s_ngroups;
+    // per thread and target: staged indices of its queued close pairs
+    __shared__ uint16_t closeq[2][kLaneQ][kP2PThreads];
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c], nt = e - b;
     const int q0 = off[c], q1 = off[c + 1];
@@ -456,6 +497,9 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     const long long ccx = (2ll * cx[c] + 1) * rc, ccy = (2ll * cy[c] + 1) * rc,
                     ccz = (2ll * cz[c] + 1) * rc;
     const double unit = ldexp(sys_box[4 * sys[c] + 3], -(kLevels + 1));   // finest half-cell
+    // squared close-pair radius of this leaf's targets
+    const double sp_a = kCloseSpacings * 2.0 * half[c] / cbrt((double)max(nt, 1));
+    const float close2 = (float)(sp_a * sp_a);
     for (int t0 = 0; t0 < nt; t0 += 2 * kP2PThreads) {
         const int cnt = min(2 * kP2PThreads, nt - t0);
         const int h = (cnt + 1) / 2;
@@ -464,17 +508,56 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         const bool act = sp < k;
         const bool two = act && (ti + h < cnt);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 oi = act ? o[b + t0 + ti] : zero4, li = act ? olo[b + t0 + ti] : zero4;
-        const float4 oj = two ? o[b + t0 + ti + h] : zero4, lj = two ? olo[b + t0 + ti + h] : zero4;
+        const float4 oi = act ? o[b + t0 + ti] : zero4;
+        const float4 oj = two ? o[b + t0 + ti + h] : oi;
         double F[2] = {0.0, 0.0}, A[2] = {0.0, 0.0}, B[2] = {0.0, 0.0}, C[2] = {0.0, 0.0};
+        df32 cF[2] = {{0.f, 0.f}, {0.f, 0.f}}, cA[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        df32 cB[2] = {{0.f, 0.f}, {0.f, 0.f}}, cC[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        int qa = 0, qb = 0;                          // close pairs queued for each target
+        // Evaluate this thread's queued close pairs in double-float into its own
+        // sums, in queue order; the lanes of a warp work side by side.
+        auto flush = [&]() {
+            const int ma = __reduce_max_sync(0xffffffffu, (unsigned)max(qa, qb));
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int nq = w ? qb : qa;
+                const int ot = ti + w * h;                   // this thread's target in the tile
+                const float4 po = (act && (w == 0 || two)) ? o[b + t0 + ot] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 pl = (act && (w == 0 || two)) ? olo[b + t0 + ot] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int u = 0; u < ma; ++u) {
+                    if (u < nq) {
+                        const int d = closeq[w][u][tid];
+                        // the staged source's particle index: its group by the prefix of sizes
+                        int lo = 0, hi = s_ngroups - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+                        }
+                        const int64_t j = gbeg[lo] + (d - gpre[lo]);
+                        float sl[nS], sh[nS];
+                        const float4 P = P4[d];
+                        sh[0] = P.w;
+#pragma unroll
+                        for (int a2 = 1; a2 < nS; ++a2) sh[a2] = SR[d * nR + a2 - 1];
+#pragma unroll
+                        for (int a2 = 0; a2 < nS; ++a2) sl[a2] = S32lo[j * nS + a2];
+                        df32 &rf = cF[w], &r0 = cA[w], &r1 = cB[w], &r2 = cC[w];
+                        pair_df<S, PHI, FIELD>(sep_df(po.x, pl.x, P.x, lx[d]), sep_df(po.y, pl.y, P.y, ly[d]),
+                                               sep_df(po.z, pl.z, P.z, lz[d]), sh, sl, rf, r0, r1, r2);
+                    }
+                }
+            }
+            qa = qb = 0;
+        };
         int q = q0, j_in = 0;
         while (q < q1) {
             __syncthreads();
             if (tid < 32) {
                 // warp 0 takes up to 32 partner leaves of this round in parallel: lane l
                 // the entry q + l (the first continues at j_in); a prefix sum of their
-                // sizes decides which fit in CH (the last one possibly in part)
-                const int lane = tid, qq = q + lane;
+                // sizes decides which fit in CHU (the last one possibly in part)
+                const int lane = tid;
+                const int qq = q + lane;
                 int lb = 0, take = 0, sl = 0;
                 if (qq < q1) {
                     sl = src[qq];
@@ -488,8 +571,8 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                     if (lane >= o) incl += y;
                 }
                 const int excl = incl - take;
-                const bool in = qq < q1 && excl < CH;
-                const int tk = in ? min(take, CH - excl) : 0;
+                const bool in = qq < q1 && excl < CHU;
+                const int tk = in ? min(take, CHU - excl) : 0;
                 if (in) {
                     const long long rs = 1ll << (kLevels - level[sl]);
                     gbeg[lane] = lb;
@@ -509,7 +592,18 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             }
             __syncthreads();
             const int ng = s_ngroups, used = gpre[ng];
-            for (int d = tid; d < used; d += kP2PThreads) {
+            // every thread takes the same number of steps (the close-pair
+            // evaluation between stretches of them is warp-collective)
+            const int steps = (used + k - 1) / k;
+            for (int d = tid; d < steps * k; d += kP2PThreads) {
+                if (d >= used) {
+                    // padding: a far-away source with zero moments adds exactly 0
+                    P4[d] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+#pragma unroll
+                    for (int a = 0; a < nR; ++a) SR[d * nR + a] = 0.0f;
+                    lx[d] = ly[d] = lz[d] = 0.0f;
+                    continue;
+                }
                 int lo = 0, hi = ng - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -518,32 +612,69 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                 const int j = gbeg[lo] + (d - gpre[lo]);
                 const float4 v = o[j], vl = olo[j];
                 // source position in the target leaf's frame, as an exact hi + lo pair
-                two_sum_lo(v.x, gdx[lo], vl.x, sx[d], lx[d]);
-                two_sum_lo(v.y, gdy[lo], vl.y, sy[d], ly[d]);
-                two_sum_lo(v.z, gdz[lo], vl.z, sz[d], lz[d]);
+                float hx, hy, hz;
+                two_sum_lo(v.x, gdx[lo], vl.x, hx, lx[d]);
+                two_sum_lo(v.y, gdy[lo], vl.y, hy, ly[d]);
+                two_sum_lo(v.z, gdz[lo], vl.z, hz, lz[d]);
+                P4[d] = make_float4(hx, hy, hz, S32[(int64_t)j * nS]);
 #pragma unroll
-                for (int a = 0; a < nS; ++a) sS[d * nS + a] = S32[(int64_t)j * nS + a];
+                for (int a = 0; a < nR; ++a) SR[d * nR + a] = a + 1 < nS ? S32[(int64_t)j * nS + a + 1] : 0.0f;
             }
             __syncthreads();
-            if (act) {
-                float f = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, g = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-                for (int j = sp; j < used; j += k) {
-                    const float ax = sx[j], ay = sy[j], az = sz[j];
-                    const float bx = lx[j], by = ly[j], bz = lz[j];
-                    const float *Sj = sS + j * nS;
-                    // hi parts of nearby points subtract exactly; the lo parts restore
-                    // the bits lost when the positions were rounded
-                    pair32<S, PHI, FIELD>((oi.x - ax) + (li.x - bx), (oi.y - ay) + (li.y - by),
-                                          (oi.z - az) + (li.z - bz), Sj, f, e0, e1, e2);
-                    if (two)
-                        pair32<S, PHI, FIELD>((oj.x - ax) + (lj.x - bx), (oj.y - ay) + (lj.y - by),
-                                              (oj.z - az) + (lj.z - bz), Sj, g, g0, g1, g2);
+            // The pair loop only queues close pairs; they are evaluated when a
+            // queue of the warp is full and after the round.  Threads without a
+            // target (and the second target of a thread that has one only) run
+            // the loop on a copy with a zero close radius; their sums are never read.
+            float f = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, g = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            const int spx = act ? sp : 0;
+            const float c2a = act ? close2 : 0.0f, c2b = two ? close2 : 0.0f;
+            int it = 0;
+            while (it < steps) {
+#pragma unroll 2
+                for (; it < steps; ++it) {
+                    const int jj = spx + it * k;
+                    const float4 P = P4[jj];
+                    float Sj[nS];
+                    Sj[0] = P.w;
+                    if constexpr (nR == 2) {
+                        const float2 r = *(const float2 *)(SR + jj * nR);
+                        Sj[1] = r.x; Sj[2] = r.y;
+                    } else if constexpr (nR == 8) {
+                        const float4 r0 = *(const float4 *)(SR + jj * nR);
+                        const float4 r1 = *(const float4 *)(SR + jj * nR + 4);
+                        Sj[1] = r0.x; Sj[2] = r0.y; Sj[3] = r0.z; Sj[4] = r0.w;
+                        Sj[5] = r1.x; Sj[6] = r1.y;
+                    }
+                    // separations from the rounded leaf-frame coordinates: the error is
+                    // ~1 ulp of the leaf size, small next to r for every pair this
+                    // loop keeps (the closer ones go to the double-float queue, which
+                    // takes the low parts too)
+                    const float dx = oi.x - P.x, dy = oi.y - P.y, dz = oi.z - P.z;
+                    const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const bool ca = r2a < c2a && r2a > 0.0f;
+                    pair32<S, PHI, FIELD>(dx, dy, dz, r2a < c2a ? 0.0f : r2a, Sj, f, e0, e1, e2);
+                    const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
+                    const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const bool cb = r2b < c2b && r2b > 0.0f;
+                    pair32<S, PHI, FIELD>(ex, ey, ez, r2b < c2b ? 0.0f : r2b, Sj, g, g0, g1, g2);
+                    if (ca) closeq[0][qa++][tid] = (uint16_t)jj;
+                    if (cb) closeq[1][qb++][tid] = (uint16_t)jj;
+                    if (__any_sync(0xffffffffu, qa == kLaneQ || qb == kLaneQ)) {   // a queue is full
+                        ++it;
+                        break;
+                    }
                 }
-                F[0] += f; A[0] += e0; B[0] += e1; C[0] += e2;
-                F[1] += g; A[1] += g0; B[1] += g1; C[1] += g2;
+                if (__any_sync(0xffffffffu, qa + qb > 0)) flush();   // staged sources change next round
             }
+            F[0] += f; A[0] += e0; B[0] += e1; C[0] += e2;
+            F[1] += g; A[1] += g0; B[1] += g1; C[1] += g2;
             q = s_next_q;
             j_in = s_next_j;
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            F[w] += df_to_double(cF[w]); A[w] += df_to_double(cA[w]);
+            B[w] += df_to_double(cB[w]); C[w] += df_to_double(cC[w]);
         }
         __syncthreads();
         red[0][tid] = F[0]; red[1][tid] = A[0]; red[2][tid] = B[0]; red[3][tid] = C[0];
@@ -943,8 +1074,9 @@ void launch_p2p32(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const int32_t *)t->b_p2p_src.ptr, (const int32_t *)t->b_level.ptr,
             (const int32_t *)t->b_cx.ptr, (const int32_t *)t->b_cy.ptr, (const int32_t *)t->b_cz.ptr,
             (const int32_t *)t->b_sys.ptr, (const double *)t->b_sysbox.ptr,
+            (const double *)t->b_half.ptr,
             (const float4 *)t->b_o32.ptr, (const float4 *)t->b_o32.ptr + t->n,
-            (const float *)t->b_S32.ptr,
+            (const float *)t->b_S32.ptr, (const float *)t->b_S32.ptr + t->n * (t->nS == 6 ? 7 : t->nS),
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr, (const int32_t *)t->b_perm.ptr,
             phi, E);
     };
@@ -1007,9 +1139,9 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     FMM_TRY(build_dtables(t, p, tb, lut));
     // the buffers every evaluate of this form needs come first
     FMM_TRY(ensure(t, t->b_o32, 32 * (size_t)n));          // hi and lo float4 halves
-    FMM_TRY(ensure(t, t->b_S32, 4 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));
+    FMM_TRY(ensure(t, t->b_S32, 8 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));   // hi, then lo
     FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * row4(tb.nM)));
-    FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nL));
+    FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nLh));
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
     // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
@@ -1047,7 +1179,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
                                                    (const double *)t->b_px.ptr,
                                                    (const double *)t->b_py.ptr,
                                                    (const double *)t->b_pz.ptr,
-                                                   (const double *)t->b_S.ptr, t->nS, o, o + n,
+                                                   (const double *)t->b_S.ptr, t->nS, n, o, o + n,
                                                    S32);
     {
         size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * (tb.nK + 1) + kChunk * tb.nS);
@@ -1066,7 +1198,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         }
     }
     record(t, 8);
-    cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nL, st);
+    cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nLh, st);
     // harmonic M2L: the folded multipoles, for either M2L
     const float *Ms = M;
     if (t->n_m2l > 0 && tb.harmonic) {

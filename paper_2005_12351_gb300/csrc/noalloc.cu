@@ -63,9 +63,16 @@ extern "C" fmm_status fmm_morton_order_noalloc(void *cuda_stream, const double *
 {
     if (n < 0) return FMM_EINVAL;
     if (n > kMaxPoints) return FMM_EBUDGET;       // larger than the fixed scratch array
-    if (n == 0) return FMM_OK;
-    if (!positions || !keys_out || !perm_out) return FMM_EINVAL;
     unsigned char *base = nullptr;
+    if (n == 0) {
+        // the per-device set-up alone: load the kernels and this file's module
+        // (which holds the scratch array), look up its address, raise the
+        // sort's shared-memory limit -- everything a later call would
+        // otherwise do on its first use
+        fmm::morton_order_prepare();
+        return scratch_address(&base);
+    }
+    if (!positions || !keys_out || !perm_out) return FMM_EINVAL;
     fmm_status st = scratch_address(&base);
     if (st != FMM_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;

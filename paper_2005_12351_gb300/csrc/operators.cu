@@ -122,6 +122,12 @@ void build_tables(OpTables &T, int s, int s_hi, int p, int n_lo, int m2l_threads
             T.h_unfold_off.push_back((int)T.h_unfold.size() / 3);
         }
     }
+    // stored locals: the n with n_z <= 1 when harmonic (the others follow from
+    // the identity wherever the full expansion is needed), all of them otherwise
+    T.h_rn.clear();
+    for (int n = 0; n < T.nL; ++n)
+        if (!harmonic || I.nz[n] <= 1) T.h_rn.push_back(n);
+    T.nLh = (int)T.h_rn.size();
 
     // ---- M2L: flat (n, m) term list in n order, cut into equal per-thread
     // chunks; each maximal same-n run inside a chunk owns one partial slot.
@@ -454,19 +460,13 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t
         }
     }
     __syncthreads();
-    double *Ls = Dsm;                      // nL <= nD: the D rows are done with
-    for (int n = tid; n < tb.nL; n += Tn) {
+    // the stored components (n_z <= 1 when harmonic, the traceless form)
+    for (int r = tid; r < tb.nLh; r += Tn) {
+        const int n = tb.h_rn[r];
         double v = 0.0;
         for (int q = tb.m2l_red_off[n]; q < tb.m2l_red_off[n + 1]; ++q) v += part[tb.m2l_red_src[q]];
-        Ls[n] = v;
+        L[(int64_t)c * tb.nLh + r] = v;
     }
-    for (int l = 0; l < tb.h_unfold_lev; ++l) {
-        __syncthreads();
-        for (int q = tb.h_unfold_off[l] + tid; q < tb.h_unfold_off[l + 1]; q += Tn)
-            Ls[tb.h_unfold[3 * q]] = -Ls[tb.h_unfold[3 * q + 1]] - Ls[tb.h_unfold[3 * q + 2]];
-    }
-    __syncthreads();
-    for (int n = tid; n < tb.nL; n += Tn) L[(int64_t)c * tb.nL + n] = Ls[n];
 }
 
 // ------------------------------------------------------------------ L2L
@@ -483,20 +483,21 @@ k_l2l(int lb, const int32_t *parent, const double *centre, DevTables tb, double 
     if (threadIdx.x < 3)
         axis_powers(centre[3 * c + threadIdx.x] - centre[3 * pa + threadIdx.x], P,
                     apow + threadIdx.x * (P + 1));
-    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lp[t] = L[(int64_t)pa * tb.nL + t];
-    __syncthreads();
+    expand_local(L + (int64_t)pa * tb.nLh, tb, Lp);          // the parent's full expansion
     for (int k = threadIdx.x; k < nK; k += blockDim.x) {
         const int v = mi_at(tb.mi, k);
         mono[k] = apow[mi_nx(v)] * apow[(P + 1) + mi_ny(v)] * apow[2 * (P + 1) + mi_nz(v)];
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < tb.nL; n += blockDim.x) {
+    // the child's stored components (the shift keeps the expansion harmonic)
+    for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x) {
+        const int n = tb.h_rn[r];
         const int kn = mi_shell(mi_at(tb.mi, n));
         if (kn < tb.n_lo) continue;
         double acc = 0.0;
         for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
             acc = fma(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
-        L[(int64_t)c * tb.nL + n] += acc;
+        L[(int64_t)c * tb.nLh + r] += acc;
     }
 }
 
@@ -516,8 +517,7 @@ k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const dou
     double *a = Lsm + tb.nL + threadIdx.x * 3 * P1;         // this thread's [3][P+1]
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
-    for (int t = threadIdx.x; t < tb.nL; t += blockDim.x) Lsm[t] = L[(int64_t)c * tb.nL + t];
-    __syncthreads();
+    expand_local(L + (int64_t)c * tb.nLh, tb, Lsm);
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
     for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
         axis_powers(px[j] - z0, P, a);
@@ -593,7 +593,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     o_l2l_q = put(T.l2l_q); o_grad = put(T.l2p_grad); o_roff = put(T.m2l_red_off);
     o_rsrc = put(T.m2l_red_src);
     const size_t o_hrm = put(T.h_rm), o_hf = put(T.h_fold), o_hfo = put(T.h_fold_off);
-    const size_t o_hu = put(T.h_unfold), o_huo = put(T.h_unfold_off);
+    const size_t o_hu = put(T.h_unfold), o_huo = put(T.h_unfold_off), o_hrn = put(T.h_rn);
     size_t o_mi;
     {
         const MultiIndex &I = multi_index();
@@ -629,6 +629,7 @@ fmm_status upload_tables(fmm_tree *t, int s, int p, int n_lo, DevTables *dt, con
     dt->h_unfold_lev = (int)T.h_unfold_off.size() - 1;
     dt->h_rm = B + o_hrm; dt->h_fold = B + o_hf; dt->h_fold_off = B + o_hfo;
     dt->h_unfold = B + o_hu; dt->h_unfold_off = B + o_huo;
+    dt->nLh = T.nLh; dt->h_rn = B + o_hrn;
     *lut = B + o_lut;
     return FMM_OK;
 }
@@ -723,7 +724,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
 
     FMM_TRY(build_dtables(t, p, tb, lut));
     record(t, 6);
-    FMM_TRY(ensure(t, t->b_L, 8 * (size_t)nc * tb.nL));
+    FMM_TRY(ensure(t, t->b_L, 8 * (size_t)nc * tb.nLh));
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
     FMM_TRY(run_upward(t, tb, true));
@@ -734,7 +735,7 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
     const double *px = (const double *)t->b_px.ptr, *py = (const double *)t->b_py.ptr,
                  *pz = (const double *)t->b_pz.ptr;
     // M2L over the stored lists (harmonic: on the folded multipoles)
-    cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nL, st);
+    cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nLh, st);
     if (t->n_m2l > 0) {
         const double *Ms = M;
         if (tb.harmonic) {

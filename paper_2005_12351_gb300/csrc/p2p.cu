@@ -26,11 +26,14 @@ namespace {
 //        e = 1 - x y0^2,   y = y0 + y0 e (1/2 + 3/8 e),
 //     which leaves a relative error of about (5/16) e^3 ~ 2^-67 before the
 //     final roundings (e ~ 2^-22 from the seed).  Five FP64 operations.
-// x = 0 returns +inf (the caller masks it); subnormal x is not supported
-// (pairs closer than ~1e-154 do not occur in a dyadic octree of doubles).
+// x = 0 returns a finite value of no meaning (the callers mask r = 0).  A subnormal x (exponent field 0,
+// x != 0: pairs closer than ~1.5e-154) takes CUDA's rsqrt instead: the
+// exponent arithmetic above assumes a normal number.  The test is integer
+// work only, so the FP64 pipe of the common path is unchanged.
 __device__ __forceinline__ double rsqrt_hh(double x)
 {
     const int hi = __double2hiint(x), lo = __double2loint(x);
+    if (__builtin_expect((hi & 0x7ff00000) == 0 && (hi | lo) != 0, 0)) return rsqrt(x);
     const int ex = ((hi >> 20) & 0x7ff) - 1023;                 // unbiased exponent
     const int k = ex >> 1;                                      // floor(ex / 2)
     const int mhi = (hi & 0x000fffff) | ((1023 + (ex - 2 * k)) << 20);   // m in [1, 4)

@@ -6,6 +6,8 @@
 // each pass is one launch (see k_os_scatter); equal digits keep their input
 // order, so equal keys keep the order of their values.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 
 #include "fmm_internal.cuh"
 
@@ -98,7 +100,10 @@ __global__ void k_scan_add(uint32_t *out, const uint32_t *tile_offsets, int64_t 
 // publish their own counts before they wait on anything, so every wait
 // ends.  The waits are bounded all the same: a block one of whose waits
 // gives up counts the digits of all earlier tiles from the input instead
-// (exact, slow) and sets kErrSortWait in the error word.
+// (exact, slow) and sets kErrSortWait in the error word.  The bound is
+// max_polls reads of the awaited word (kOsWait unless the environment
+// variable FMM_SORT_POLLS sets it); 0 makes every look-back give up at once,
+// which runs the recount in every tile after the first.
 constexpr uint64_t kStAgg = 1ull << 32, kStIncl = 2ull << 32;
 constexpr int kOsWait = 1 << 20;                 // polls before a wait gives up
 
@@ -133,7 +138,7 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t *warp_sums)
 __global__ void __launch_bounds__(kSortThreads)
 k_os_scatter(const uint64_t *keys, const uint32_t *vals, uint64_t *okeys, uint32_t *ovals,
              int64_t n, int pass, int passes, const uint32_t *ghist, unsigned *tile_ctr,
-             uint64_t *status, uint64_t *status_next, int *err)
+             uint64_t *status, uint64_t *status_next, int *err, int max_polls)
 {
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t *sk = (uint64_t *)os_smem;                               // [kSortTile]
@@ -202,11 +207,11 @@ k_os_scatter(const uint64_t *keys, const uint32_t *vals, uint64_t *okeys, uint32
     for (int64_t j = tile - 1; j >= 0; --j) {
         uint64_t w = vs[j * 256 + tid];
         int polls = 0;
-        while ((w >> 32) == 0 && polls < kOsWait) {
+        while ((w >> 32) == 0 && polls < max_polls) {
             if (++polls > 64) __nanosleep(64);
             w = vs[j * 256 + tid];
         }
-        if ((w >> 32) == 0) { ok = false; break; }
+        if ((w >> 32) == 0 || max_polls == 0) { ok = false; break; }
         excl += (uint32_t)w;
         if ((w >> 32) == 2) break;
     }
@@ -290,6 +295,25 @@ size_t radix_hist_bytes(int64_t n)
     return 4 * (size_t)radix_hist_words(n);
 }
 
+void radix_sort_prepare()
+{
+    // once per device; threads that race here both set the same value, which is harmless
+    static std::atomic<bool> attr_set[64];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_os_hist) != cudaSuccess) cudaGetLastError();
+        const bool ok = cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kOsSmem) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        if (ok && dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
+    }
+}
+
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
                       int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches)
 {
@@ -299,21 +323,19 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t 
     // hist: digit counts [passes][256], tile counters [16], two status areas [ntiles][256]
     uint32_t *ghist = hist, *ctr = hist + kRadixMaxPasses * 256;
     uint64_t *status[2] = {(uint64_t *)(hist + kRadixHead), (uint64_t *)(hist + kRadixHead) + ntiles * 256};
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev])
-        attr_set[dev] = cudaFuncSetAttribute(k_os_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kOsSmem) == cudaSuccess;
+    radix_sort_prepare();
+    int max_polls = kOsWait;
+    if (const char *env = getenv("FMM_SORT_POLLS")) max_polls = std::max(0, atoi(env));
     cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
-    const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads, 152 * 4);
+    const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads,
+                                                       4 * (int64_t)sm_count());
     k_os_hist<<<hgrid, kSortThreads, 0, st>>>(keys, n, passes, ghist, status[0], ntiles);
     ++*launches;
     uint64_t *ka = keys, *kb = keys2;
     uint32_t *va = vals, *vb = vals2;
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<<<(unsigned)ntiles, kSortThreads, kOsSmem, st>>>(
-            ka, va, kb, vb, n, p, passes, ghist, ctr, status[p & 1], status[(p + 1) & 1], err);
+            ka, va, kb, vb, n, p, passes, ghist, ctr, status[p & 1], status[(p + 1) & 1], err, max_polls);
         ++*launches;
         std::swap(ka, kb);
         std::swap(va, vb);

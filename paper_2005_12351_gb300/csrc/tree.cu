@@ -285,59 +285,150 @@ __device__ __forceinline__ int digit_at(uint64_t key, int level)
     return (int)((key >> (3 * (kLevels - level))) & 7ull);
 }
 
-// For each (cell of this level, octant): the child's particle range.
-__global__ void k_child_ranges(CellArrays c, int lb, int ncl, int level, int ncrit,
-                               const uint64_t *keys, uint32_t *flags, int32_t *cb, int32_t *ce)
+// ---- cells, level by level without host round trips: the range of a level's
+// cells lives in device words (ctl[kCtlLevel + l] = first cell of level l), so
+// the host launches the levels back to back and reads the counts once per
+// batch.  A level that would pass the cell capacity sets ctl[kCtlOverflow]
+// instead; every later kernel then does nothing and the host rebuilds with
+// more room.
+constexpr int kCtlOverflow = 0, kCtlLevel = 1, kCtlWords = 32;
+constexpr int kLevelBatch = 8;                  // levels launched per host round trip
+
+// child ranges of every (cell of this level, octant), and each cell's child count
+__global__ void __launch_bounds__(256)
+k_level_ranges(CellArrays c, const unsigned *ctl, int level, int ncrit, const uint64_t *keys,
+               int32_t *cb, int32_t *ce, uint32_t *cnt)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncl * 8) return;
-    const int cell = lb + t / 8, o = t % 8;
-    const int b = c.begin[cell], e = c.end[cell];
-    uint32_t flag = 0;
-    int lo_i = b, hi_i = b;
-    if (e - b > ncrit && level < kLevels) {
-        // first index in [b, e) whose child digit is >= o (resp. >= o + 1)
-        int L = b, R = e;
-        while (L < R) {
-            int mid = (L + R) >> 1;
-            if (digit_at(keys[mid], level + 1) < o) L = mid + 1; else R = mid;
+    if (ctl[kCtlOverflow]) return;
+    const int lb = (int)ctl[kCtlLevel + level];
+    const int64_t n8 = 8 * ((int64_t)ctl[kCtlLevel + level + 1] - lb);
+    const unsigned lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n8; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        bool flag = false;
+        if (t < n8) {
+            const int cell = lb + (int)(t >> 3), o = (int)(t & 7);
+            const int b = c.begin[cell], e = c.end[cell];
+            int lo_i = b, hi_i = b;
+            if (e - b > ncrit && level < kLevels) {
+                // first index in [b, e) whose child digit is >= o (resp. >= o + 1)
+                int L = b, R = e;
+                while (L < R) {
+                    const int mid = (L + R) >> 1;
+                    if (digit_at(keys[mid], level + 1) < o) L = mid + 1; else R = mid;
+                }
+                lo_i = L;
+                R = e;
+                while (L < R) {
+                    const int mid = (L + R) >> 1;
+                    if (digit_at(keys[mid], level + 1) <= o) L = mid + 1; else R = mid;
+                }
+                hi_i = L;
+                flag = hi_i > lo_i;
+            }
+            cb[t] = lo_i;
+            ce[t] = hi_i;
         }
-        lo_i = L;
-        R = e;
-        while (L < R) {
-            int mid = (L + R) >> 1;
-            if (digit_at(keys[mid], level + 1) <= o) L = mid + 1; else R = mid;
-        }
-        hi_i = L;
-        flag = hi_i > lo_i;
+        // a cell's 8 octants are 8 aligned lanes of one warp
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (t < n8 && (t & 7) == 0) cnt[t >> 3] = __popc((m >> (lane & ~7u)) & 0xffu);
     }
-    flags[t] = flag;
-    cb[t] = lo_i;
-    ce[t] = hi_i;
 }
 
-__global__ void k_write_children(CellArrays c, int lb, int le, int ncl, int level,
-                                 const uint32_t *flags, const uint32_t *pos, const int32_t *cb,
-                                 const int32_t *ce)
+// one block: the first-child offset of every cell of this level (an exclusive
+// scan of the child counts) and the next level's range, or the overflow flag
+__global__ void __launch_bounds__(1024)
+k_level_scan(unsigned *ctl, int level, const uint32_t *cnt, uint32_t *off, int64_t cap)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncl * 8) return;
-    const int i = t / 8, o = t % 8, cell = lb + i;
-    if (o == 0) {
-        const int nch = (int)(pos[8 * i + 8] - pos[8 * i]);
-        c.nchild[cell] = nch;
-        c.child[cell] = nch ? le + (int)pos[8 * i] : -1;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (ctl[kCtlOverflow]) return;
+    const int lb = (int)ctl[kCtlLevel + level], le = (int)ctl[kCtlLevel + level + 1];
+    const int ncl = le - lb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ncl; base += 8 * (int)blockDim.x) {
+        const int i0 = base + 8 * (int)threadIdx.x;
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = i0 + k < ncl ? cnt[i0 + k] : 0u;
+            sum += v[k];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        uint32_t ex = carry + (warp ? wsum[warp - 1] : 0u) + x - sum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (i0 + k < ncl) off[i0 + k] = ex;
+            ex += v[k];
+        }
+        const uint32_t tot = wsum[nw - 1];
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
     }
-    if (!flags[t]) return;
-    const int ch = le + (int)pos[t];
-    c.level[ch] = level + 1;
-    c.parent[ch] = cell;
-    c.begin[ch] = cb[t];
-    c.end[ch] = ce[t];
-    c.cx[ch] = 2 * c.cx[cell] + ((o >> 2) & 1);
-    c.cy[ch] = 2 * c.cy[cell] + ((o >> 1) & 1);
-    c.cz[ch] = 2 * c.cz[cell] + (o & 1);
-    c.sys[ch] = c.sys[cell];
+    if (threadIdx.x == 0) {
+        if ((int64_t)le + carry > cap) ctl[kCtlOverflow] = 1u;
+        else ctl[kCtlLevel + level + 2] = (unsigned)le + carry;
+    }
+}
+
+// the children of this level's cells, in (parent, octant) order
+__global__ void __launch_bounds__(256)
+k_level_write(CellArrays c, const unsigned *ctl, int level, const int32_t *cb, const int32_t *ce,
+              const uint32_t *off)
+{
+    if (ctl[kCtlOverflow]) return;
+    const int lb = (int)ctl[kCtlLevel + level], le = (int)ctl[kCtlLevel + level + 1];
+    const int64_t n8 = 8 * (int64_t)(le - lb);
+    const unsigned lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n8; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const bool valid = t < n8;
+        const bool flag = valid && ce[t] > cb[t];
+        const unsigned grp = (__ballot_sync(0xffffffffu, flag) >> (lane & ~7u)) & 0xffu;
+        if (!valid) continue;
+        const int i = (int)(t >> 3), o = (int)(t & 7), cell = lb + i;
+        if (o == 0) {
+            const int nch = __popc(grp);
+            c.nchild[cell] = nch;
+            c.child[cell] = nch ? le + (int)off[i] : -1;
+        }
+        if (!flag) continue;
+        const int ch = le + (int)off[i] + __popc(grp & ((1u << o) - 1u));
+        c.level[ch] = level + 1;
+        c.parent[ch] = cell;
+        c.begin[ch] = cb[t];
+        c.end[ch] = ce[t];
+        c.cx[ch] = 2 * c.cx[cell] + ((o >> 2) & 1);
+        c.cy[ch] = 2 * c.cy[cell] + ((o >> 1) & 1);
+        c.cz[ch] = 2 * c.cz[cell] + (o & 1);
+        c.sys[ch] = c.sys[cell];
+    }
+}
+
+__global__ void k_level_init(unsigned *ctl, int nsys)
+{
+    const int i = threadIdx.x;
+    if (i < kCtlWords) ctl[i] = i == kCtlLevel + 1 ? (unsigned)nsys : 0u;
 }
 
 __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box, double *centre,
@@ -402,7 +493,8 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *count, unsigned want)
 // are counted but not written; the host grows what overflowed and reruns
 // the whole traversal.
 constexpr int kTravOverflow = 16, kTravFront = 32, kTravMaxRounds = 960;
-constexpr int kTravBlocks = 152 * 8;
+// blocks of a traversal round: 8 resident blocks of 256 threads per SM
+constexpr int kTravBlocksPerSM = 8;
 
 __global__ void __launch_bounds__(256)
 k_traverse_round(CellArrays c, int round, double theta2, const int2 *front, unsigned front_cap,
@@ -661,10 +753,20 @@ static void morton_keys(cudaStream_t st, const double *pos, int64_t n, uint64_t 
                         int64_t *launches)
 {
     k_box_init<<<1, 32, 0, st>>>(box_scratch);
-    k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 152 * 8), 256, 0, st>>>(pos, n, box_scratch, err);
+    k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 8 * (int64_t)sm_count()), 256, 0, st>>>(pos, n, box_scratch, err);
     k_box_final<<<1, 1, 0, st>>>(box_scratch, box_out);
     k_keys<<<grid(n, 256), 256, 0, st>>>(pos, n, box_out, keys, idx);
     *launches += 4;
+}
+
+void morton_order_prepare()
+{
+    cudaFuncAttributes fa;
+    const void *kerns[] = {(const void *)k_box_init, (const void *)k_bbox, (const void *)k_box_final,
+                           (const void *)k_keys};
+    for (const void *k : kerns)
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) cudaGetLastError();
+    radix_sort_prepare();
 }
 
 fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
@@ -747,49 +849,60 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     ++t->launches;
     record(t, 2);
 
-    // ---- cells, level by level (level 0 holds one root per system)
-    int64_t cap = std::max<int64_t>(1024, 2 * (n / std::max(1, t->max_leaf)) + 64 + 2 * nsys);
+    // ---- cells, level by level on the device (level 0 holds one root per system);
+    // the host reads the level counts once per batch of levels
+    FMM_TRY(ensure(t, t->b_ctl, 4 * kCtlWords));
+    unsigned *ctl = (unsigned *)t->b_ctl.ptr;
     DevBuf *cb[10] = {&t->b_level, &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin,
                       &t->b_end, &t->b_cx, &t->b_cy, &t->b_cz, &t->b_sys};
-    for (DevBuf *b : cb) FMM_TRY(ensure(t, *b, 4 * cap));
-    CellArrays c = cells_of(t);
-    k_roots<<<grid(nsys, 128), 128, 0, st>>>(c, off, nsys);
-    ++t->launches;
-    t->level_begin.push_back(0);
-    int64_t lb = 0, le = nsys;
-    int level = 0;
-    uint32_t total = 0;
-    while (le > lb) {
-        const int64_t ncl = le - lb;
-        FMM_TRY(ensure(t, t->b_flags, 4 * (8 * ncl + 1)));
-        FMM_TRY(ensure(t, t->b_scan, 4 * (8 * ncl + 1)));
-        FMM_TRY(grow_keep(t, t->b_front, 8 * 8 * ncl, 0));    // child begin/end scratch
-        uint32_t *flags = (uint32_t *)t->b_flags.ptr, *pos8 = (uint32_t *)t->b_scan.ptr;
-        int32_t *cbeg = (int32_t *)t->b_front.ptr, *cend = cbeg + 8 * ncl;
-        cudaMemsetAsync(flags + 8 * ncl, 0, 4, st);
-        k_child_ranges<<<grid(8 * ncl, 256), 256, 0, st>>>(c, (int)lb, (int)ncl, level,
-                                                            t->max_leaf, keys, flags, cbeg, cend);
-        exclusive_scan_u32(flags, pos8, 8 * ncl + 1, (uint32_t *)t->b_scan_tmp.ptr, st,
-                           &t->launches);
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&total, pos8 + 8 * ncl, 4, cudaMemcpyDeviceToHost, st),
-                           "child count"));
-        FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
-        if (le + (int64_t)total > cap) {
-            int64_t ncap = std::max<int64_t>(2 * cap, le + total);
-            for (DevBuf *b : cb) FMM_TRY(grow_keep(t, *b, 4 * ncap, 4 * le));
-            cap = ncap;
-            c = cells_of(t);
-        }
-        k_write_children<<<grid(8 * ncl, 256), 256, 0, st>>>(c, (int)lb, (int)le, (int)ncl, level,
-                                                              flags, pos8, cbeg, cend);
+    int64_t cap = std::max<int64_t>(t->b_level.bytes / 4,
+                                    std::max<int64_t>(1024, 5 * (n / std::max(1, t->max_leaf)) + 64 + 2 * nsys));
+    const unsigned lgrid = (unsigned)(8 * sm_count());
+    std::vector<unsigned> hc(kCtlWords);
+    int nlev = 0;
+    for (;;) {
+        for (DevBuf *b : cb) FMM_TRY(ensure(t, *b, 4 * cap));
+        FMM_TRY(ensure(t, t->b_flags, 4 * cap));
+        FMM_TRY(ensure(t, t->b_scan, 4 * cap));
+        FMM_TRY(ensure(t, t->b_front, 8 * 8 * cap));      // child begin/end of every octant
+        CellArrays c = cells_of(t);
+        uint32_t *cnt = (uint32_t *)t->b_flags.ptr, *off8 = (uint32_t *)t->b_scan.ptr;
+        int32_t *cbeg = (int32_t *)t->b_front.ptr, *cend = cbeg + 8 * cap;
+        k_roots<<<grid(nsys, 128), 128, 0, st>>>(c, off, nsys);
+        k_level_init<<<1, kCtlWords, 0, st>>>(ctl, nsys);
         t->launches += 2;
-        lb = le;
-        le += total;
-        ++level;
-        t->level_begin.push_back((int)lb);
+        int level = 0;
+        bool overflow = false;
+        for (;;) {
+            const int end = std::min(level + kLevelBatch, kLevels + 1);
+            for (; level < end; ++level) {
+                k_level_ranges<<<lgrid, 256, 0, st>>>(c, ctl, level, t->max_leaf, keys, cbeg, cend, cnt);
+                k_level_scan<<<1, 1024, 0, st>>>(ctl, level, cnt, off8, cap);
+                k_level_write<<<lgrid, 256, 0, st>>>(c, ctl, level, cbeg, cend, off8);
+                t->launches += 3;
+            }
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(hc.data(), ctl, 4 * kCtlWords, cudaMemcpyDeviceToHost, st),
+                               "level counts"));
+            FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+            if (hc[kCtlOverflow]) {
+                overflow = true;
+                break;
+            }
+            // done once a level came out empty (or the deepest level was processed)
+            if (hc[kCtlLevel + level + 1] == hc[kCtlLevel + level] || level > kLevels) break;
+        }
+        if (!overflow) {
+            // levels 0 .. nlev - 1 hold cells
+            nlev = 1;
+            while (nlev <= kLevels && hc[kCtlLevel + nlev + 1] > hc[kCtlLevel + nlev]) ++nlev;
+            break;
+        }
+        cap *= 2;
     }
-    t->ncells = le;
-    t->nlevels = level;       // levels 0 .. level-1 hold cells
+    t->level_begin.assign(hc.begin() + kCtlLevel, hc.begin() + kCtlLevel + nlev + 1);
+    t->ncells = t->level_begin.back();
+    t->nlevels = nlev;
+    CellArrays c = cells_of(t);
     const int64_t nc = t->ncells;
     FMM_TRY(ensure(t, t->b_centre, 8 * 3 * nc));
     FMM_TRY(ensure(t, t->b_half, 8 * nc));
@@ -862,10 +975,11 @@ fmm_status build_lists(fmm_tree *t, double theta)
         ++t->launches;
         int r = 0;
         bool retry = false;
+        const unsigned trav_blocks = (unsigned)(kTravBlocksPerSM * sm_count());
         for (;;) {
             const int end = std::min(r + batch, kTravMaxRounds);
             for (; r < end; ++r) {
-                k_traverse_round<<<kTravBlocks, 256, 0, st>>>(
+                k_traverse_round<<<trav_blocks, 256, 0, st>>>(
                     c, r, theta2, fr[r & 1], (unsigned)front_cap, (int2 *)t->b_m2l_raw.ptr,
                     (unsigned)m2l_cap, (int2 *)t->b_p2p_raw.ptr, (unsigned)p2p_cap, fr[(r + 1) & 1], cnt);
                 ++t->launches;

@@ -124,6 +124,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, volatil
     return true;
 }
 
+// bounded wait that ignores the abort flag (used only while cleaning up after
+// an abort, e.g. before tensor memory that in-flight MMAs use is freed)
+__device__ __forceinline__ void mbar_wait_cleanup(uint32_t bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity) && clock64() - t0 < (1ll << 28)) {
+    }
+}
+
 // --------------------------------------------------------- async copies
 __device__ __forceinline__ void fence_async_smem()
 {

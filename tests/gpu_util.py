@@ -22,3 +22,14 @@ def gpu_fmm(pos, S, s, p, theta, ncrit, want_phi=True, want_field=True):
     torch.cuda.synchronize()
     out = (phi.cpu().numpy() if phi is not None else None, E.cpu().numpy() if E is not None else None)
     return out, tree
+
+
+def close(a, b, tol):
+    """Parity of FP64 results: relative RMS below tol and, element by element,
+    no error above 100 tol of the largest reference magnitude -- so that a few
+    wrong particles cannot hide inside an aggregate over many."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if b.size == 0:
+        return a.size == 0
+    worst = float(np.abs(a - b).max())
+    return rel_rms(a, b) < tol and worst <= 100.0 * tol * float(np.abs(b).max())

@@ -100,4 +100,17 @@ def test_reference_arm_line_on_the_small_workload(orc, capsys):
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
-    assert "2000 sampled particles" in cb["sample"]
+    assert "all 2000 particles" in cb["sample"]
+
+
+def test_full_rate_fit_recovers_fixed_and_per_particle_costs():
+    """The reference arm's step times t(k) = fixed + per * k at two sample sizes
+    give the oracle's rate on the whole workload, n / (fixed + per * n)."""
+    fixed, per, n = 3.0, 1.25e-5, 1_000_000
+    counts = [32768, 131072] * 3
+    times = [fixed + per * k for k in counts]
+    value, f, p = bench.fit_full_rate(counts, times, n)
+    assert abs(f - fixed) < 1e-9 and abs(p - per) < 1e-15
+    assert abs(value - n / (fixed + per * n)) < 1e-6 * value
+    # one sample size: the plain sampled rate
+    assert bench.fit_full_rate([5000, 5000], [1.0, 1.0], n)[0] == 5000.0

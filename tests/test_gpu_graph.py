@@ -82,7 +82,10 @@ def test_batch_graph_replay():
     assert np.array_equal(E.cpu().numpy(), Eu.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 2), ("3xtf32", 5)])
+# candidates: the three FP64 P2P kernels; FP32: the handle's settings only (its
+# one-way P2P evaluates the close pairs in double-float); 3xTF32: 8/16/32 rows
+# per chunk on the tensor cores, or the SIMT M2L
+@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 1), ("3xtf32", 4)])
 def test_autotune(prec, ncand):
     import torch
     from gpu_util import rel_rms, to_dev
@@ -95,7 +98,7 @@ def test_autotune(prec, ncand):
     E0 = E0.cpu().numpy()
     tune = t.autotune(p, 0.5, reps=2)
     assert tune["candidates"] == ncand and tune["ms_per_evaluate"] > 0
-    assert tune["p2p_variant"] in ((0, 1, 2) if prec == "fp64" else (1, 2))
+    assert tune["p2p_variant"] in ((0, 1, 2) if prec == "fp64" else (1,))
     if prec == "3xtf32":
         assert tune["tc_chunk_rows"] in (8, 16, 32) and tune["m2l_tensor"] in (0, 1)
     phi1, E1 = t.evaluate_graph(p, 0.5)

@@ -7,14 +7,15 @@ Tolerances: the FP32 form is compared with the FP64 oracle FMM on the same tree
 (difference = FP32 rounding only: ~2e-7 measured, bounded here by 1e-6 relative
 RMS = ~16 FP32 ulps), and -- the criterion that matters -- its error against the
 FP64 direct sum must stay within 1.1x the FP64 FMM truncation error at the same
-p.  Quadrupole pair terms carry an FP32 rounding floor of ~3.5e-7 (measured);
-where the quadrupole truncation error is within a few times that floor the bound
-is 1.1x truncation + the floor.
+p, with no additive allowance.  That needs the near field's rounding well below
+FP32's: the quadrupole field's FP64 truncation error at p = 5 is ~5e-8, under
+one FP32 ulp, and all-FP32 pair terms leave ~3e-7 of noise, set by each
+particle's nearest neighbours.  The one-way FP32 P2P therefore evaluates the
+pairs closer than one mean spacing of the target leaf in double-float.
 """
 import numpy as np
 import pytest
-
-FP32_FLOOR = 5e-7
+from gpu_util import close
 
 from paper_2005_12351_gb300 import synth
 
@@ -69,18 +70,69 @@ def test_fp32_close_to_fp64_oracle(orc, precision, s, p, dist, n, ncrit, variant
 
 
 @pytest.mark.parametrize("precision", FORMS)
-@pytest.mark.parametrize("s,p,floor", [(0, 4, 0.0), (0, 8, 0.0), (1, 6, 0.0), (1, 8, 0.0),
-                                        (2, 3, FP32_FLOOR), (2, 5, FP32_FLOOR)])
-def test_fp32_error_within_1p1_of_fp64_truncation(orc, precision, s, p, floor):
+@pytest.mark.parametrize("s,p,dist", [(0, 4, "plummer"), (0, 8, "plummer"), (1, 6, "plummer"),
+                                       (1, 8, "plummer"), (2, 3, "plummer"), (2, 5, "plummer"),
+                                       (2, 5, "uniform"), (2, 8, "uniform"), (1, 10, "uniform")])
+def test_fp32_error_within_1p1_of_fp64_truncation(orc, precision, s, p, dist):
+    """The benchmark spec's criterion, no additive term: the mixed form's error against the
+    FP64 direct sum (oracle) is within 1.1x the FP64 FMM's, for the field and the
+    potential.  Quadrupoles at p >= 5 and dipoles at p = 10 have field truncation
+    errors of 1e-8..1e-7, at or below FP32 resolution."""
     from gpu_util import rel_rms
-    pos, S = synth.make_system(12_000, s, "plummer", 800 + s)
+    pos, S = synth.make_system(12_000, s, dist, 800 + s)
     (phi32, E32), tree = gpu_eval(pos, S, s, p, 0.5, 64, precision)
     assert_tc_ran(tree, precision)
     (phi64, E64), _ = gpu_eval(pos, S, s, p, 0.5, 64, "fp64")
     phi_d, E_d = orc.direct(pos, S, s)
     e32, e64 = rel_rms(E32, E_d), rel_rms(E64, E_d)
-    assert e32 <= 1.1 * e64 + floor, (e32, e64)
-    assert rel_rms(phi32, phi_d) <= 1.1 * rel_rms(phi64, phi_d) + floor
+    assert e32 <= 1.1 * e64, (e32, e64)
+    f32, f64 = rel_rms(phi32, phi_d), rel_rms(phi64, phi_d)
+    assert f32 <= 1.1 * f64, (f32, f64)
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_quadrupole_batch_4096_p5_within_1p1(orc, precision):
+    """The 4,096-system quadrupole batch (N log-uniform in [256, 65536], uniform
+    cube, p = 5, theta 0.5, n_crit 128): on 32 sampled systems, each mixed form's
+    field and potential error against the oracle's direct sum is within 1.1x the
+    FP64 batch's, and the FP64 batch matches the oracle FMM system by system."""
+    import torch
+    from gpu_util import rel_rms, to_dev
+    from paper_2005_12351_gb300 import fmm
+    w = synth.WORKLOADS["quadrupole_batch_4096_p5"]
+    pos, S, off = synth.make_batch(w["batch"], w["nlo"], w["nhi"], w["s"], w["seed"], w["dist"])
+    P, Sd = to_dev(pos), to_dev(S)
+    out = {}
+    for prec in ("fp64", precision):
+        t = fmm.create_tree(max_leaf=w["ncrit"], precision=prec)
+        t.set_sources_batch(P, Sd, list(off), w["s"])
+        phi, E = t.evaluate(w["p"], w["theta"], True, True)
+        torch.cuda.synchronize()
+        if prec != "fp64":
+            assert_tc_ran(t, prec)
+        out[prec] = (phi.cpu().numpy(), E.cpu().numpy())
+        t.destroy()
+    ks = synth.sample_indices(w["batch"], 32, 29)
+    num = {k: np.zeros(2) for k in out}
+    den = np.zeros(2)
+    for i, k in enumerate(ks):
+        a, b = int(off[k]), int(off[k + 1])
+        # big systems: the direct sum at 1,024 sampled targets of the system
+        tg = synth.sample_indices(b - a, min(b - a, 1024), 31 + int(k))
+        phi_d, E_d = orc.direct(pos[a:b], S[a:b], w["s"], targets=tg)
+        den += [(phi_d ** 2).sum(), (E_d ** 2).sum()]
+        for prec, (phi, E) in out.items():
+            num[prec] += [((phi[a:b][tg] - phi_d) ** 2).sum(), ((E[a:b][tg] - E_d) ** 2).sum()]
+        if i < 4:
+            ot = orc.Tree(pos[a:b], w["ncrit"])
+            ot.lists(w["theta"])
+            phi_o, E_o = ot.fmm(S[a:b], w["s"], w["p"], targets=tg[:256])
+            assert close(out["fp64"][0][a:b][tg[:256]], phi_o, 1e-12)
+            assert close(out["fp64"][1][a:b][tg[:256]], E_o, 1e-12)
+    e64 = np.sqrt(num["fp64"] / den)
+    e32 = np.sqrt(num[precision] / den)
+    assert e32[0] <= 1.1 * e64[0], (e32, e64)
+    assert e32[1] <= 1.1 * e64[1], (e32, e64)
 
 
 def test_plummer_4m_p8_fp32_vs_fp64(orc):
@@ -110,7 +162,7 @@ def test_plummer_4m_p8_fp32_vs_fp64(orc):
     ot = orc.Tree(pos, 128)
     ot.lists(0.5)
     _, E_o = ot.fmm(S, 1, 8, targets=tg[:1024])
-    assert rel_rms(E64[tg[:1024]], E_o) < 1e-12
+    assert close(E64[tg[:1024]], E_o, 1e-12)
     torch.cuda.synchronize()
 
 
@@ -149,8 +201,10 @@ def test_3xtf32_matches_fp32_form(s, p, dist, n, h):
     else:
         assert tb.info()["tc_rows"] == 0
     # local expansions column by column: with n_L > 128 the columns from 128 on
-    # come from the second column group of the tensor-core M2L
-    nL = (p + 1) * (p + 2) * (p + 3) // 6
+    # come from the second column group of the tensor-core M2L.  A cell stores
+    # the (p+1)^2 traceless components (n_z <= 1) with the harmonic M2L, all
+    # n_L otherwise.
+    nL = (p + 1) ** 2 if h else (p + 1) * (p + 2) * (p + 3) // 6
     La, Lb = ta.copy_array("local", nL).numpy(), tb.copy_array("local", nL).numpy()
     assert La.dtype == np.float32 and La.shape[1] == Lb.shape[1]
     for c0 in range(0, La.shape[1], 128):

@@ -5,6 +5,7 @@ one-way one), moment updates and graph replay,
 and the calls a mixed system is refused by."""
 import numpy as np
 import pytest
+from gpu_util import close
 
 from paper_2005_12351_gb300 import synth
 
@@ -44,9 +45,9 @@ def test_mixed_fmm_matches_oracle(orc, lo, hi, p, dist, n, ncrit, outs, variant)
     ot.lists(0.5)
     phi_o, E_o = ot.fmm(S, lo, p, s_hi=hi)
     if wp:
-        assert rel_rms(phi.cpu().numpy(), phi_o) < TOL
+        assert close(phi.cpu().numpy(), phi_o, TOL)
     if wf:
-        assert rel_rms(E.cpu().numpy(), E_o) < TOL
+        assert close(E.cpu().numpy(), E_o, TOL)
     t.destroy()
 
 
@@ -67,9 +68,9 @@ def test_mixed_symmetric_p2p_matches_one_way(lo, hi, outs):
         res[v] = (phi.cpu().numpy() if wp else None, E.cpu().numpy() if wf else None)
         t.destroy()
     if wp:
-        assert rel_rms(res[2][0], res[1][0]) < 1e-14
+        assert close(res[2][0], res[1][0], 1e-14)
     if wf:
-        assert rel_rms(res[2][1], res[1][1]) < 1e-14
+        assert close(res[2][1], res[1][1], 1e-14)
 
 
 @pytest.mark.parametrize("lo,hi", [(0, 1), (1, 2), (0, 2)])
@@ -80,12 +81,12 @@ def test_mixed_direct_and_bh_match_oracle(orc, lo, hi):
     pos, S = synth.make_system_mixed(4000, lo, hi, "plummer", 1600 + lo + hi)
     phi, E = fmm.direct_sum(to_dev(pos), to_dev(S), lo, source_order_hi=hi)
     phi_o, E_o = orc.direct(pos, S, lo, s_hi=hi)
-    assert rel_rms(phi.cpu().numpy(), phi_o) < 1e-13 and rel_rms(E.cpu().numpy(), E_o) < 1e-13
+    assert close(phi.cpu().numpy(), phi_o, 1e-13) and close(E.cpu().numpy(), E_o, 1e-13)
     t = gpu_mixed(pos, S, lo, hi, 32)
     phi_b, E_b = t.evaluate_bh(5, 0.4)
     torch.cuda.synchronize()
     phi_bo, E_bo = orc.Tree(pos, 32).bh(S, lo, 5, 0.4, s_hi=hi)
-    assert rel_rms(phi_b.cpu().numpy(), phi_bo) < TOL and rel_rms(E_b.cpu().numpy(), E_bo) < TOL
+    assert close(phi_b.cpu().numpy(), phi_bo, TOL) and close(E_b.cpu().numpy(), E_bo, TOL)
     t.destroy()
 
 

@@ -33,3 +33,23 @@ def test_own_rsqrt_within_one_ulp_of_cuda():
     p4 = np.exp2(2.0 * np.arange(-500, 500))
     own4, _ = fmm.check_rsqrt(torch.from_numpy(p4).cuda())
     assert np.array_equal(own4.cpu().numpy(), np.exp2(-np.arange(-500, 500, dtype=float)))
+
+
+def test_own_rsqrt_subnormal_arguments():
+    """Subnormal r^2 (0 < x < 2^-1022: particles closer than ~1.5e-154) are outside
+    the exponent arithmetic of the fast path; they must still be within 1 ulp of
+    the true value (and of CUDA's rsqrt)."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    rng = np.random.default_rng(1)
+    tiny = np.float64(2.0 ** -1074)
+    x = np.concatenate([np.exp2(rng.uniform(-1074, -1022, 50_000)),
+                        np.array([tiny, 2 * tiny, 3 * tiny, np.nextafter(2.0 ** -1022, 0), 2.0 ** -1023]),
+                        np.array([2.0 ** -1022, np.nextafter(2.0 ** -1022, 1)])])
+    assert (x > 0).all() and (x[:-2] < 2.0 ** -1022).all()
+    own, ref = fmm.check_rsqrt(torch.from_numpy(x).cuda())
+    own, ref = own.cpu().numpy(), ref.cpu().numpy()
+    assert np.isfinite(own).all()
+    assert ulp_diff(own, ref).max() <= 2
+    exact = (1.0 / np.sqrt(x.astype(np.longdouble))).astype(np.float64)
+    assert ulp_diff(own, exact).max() <= 1

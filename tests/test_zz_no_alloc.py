@@ -40,6 +40,28 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert torch.equal(keys, ref_keys) and torch.equal(perm, ref_perm)
 
 
+def test_noalloc_call_leaves_free_device_memory_unchanged():
+    """After the per-device set-up (a call with n == 0 and NULL pointers), a call
+    allocates nothing: the device's free memory is the same before and after
+    it, and the result is the allocating entry point's."""
+    import torch
+    from paper_2005_12351_gb300 import fmm
+    f = fmm.noalloc_entry()
+    assert f(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), None, ctypes.c_int64(0),
+             None, None) == fmm.FMM_OK
+    pos_d = torch.from_numpy(synth.make_system(500_000, 0, "plummer", 903)[0]).cuda()
+    ref_keys, ref_perm = fmm.morton_order(pos_d)
+    keys = torch.full_like(ref_keys, -1)
+    perm = torch.full_like(ref_perm, -1)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert _call_noalloc(fmm, pos_d, keys, perm) == fmm.FMM_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(keys, ref_keys) and torch.equal(perm, ref_perm)
+
+
 def test_noalloc_rejects_oversize_and_bad_input():
     import torch
     from paper_2005_12351_gb300 import fmm
