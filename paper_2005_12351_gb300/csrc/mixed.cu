@@ -403,11 +403,22 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
 // and at the end of each staged round, every lane evaluates its own queue
 // into its own double-float sums, in queue order, so the result stays
 // deterministic.
-template <int S, bool PHI, bool FIELD>
-__device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, const float *Sj, float &f,
-                                       float &e0, float &e1, float &e2)
+// the hardware reciprocal square root (PTX rsqrt.approx, relative error ~2^-23);
+// callers pass normal x > 0 only
+__device__ __forceinline__ float rsqrt_mufu(float x)
 {
-    float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// keep = false: the pair contributes nothing (a close pair, evaluated in
+// double-float instead, or r = 0)
+template <int S, bool PHI, bool FIELD>
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, bool keep, const float *Sj,
+                                       float &f, float &e0, float &e1, float &e2)
+{
+    float y = keep ? rsqrt_mufu(r2) : 0.0f;
     y = y * fmaf(-0.5f * r2 * y, y, 1.5f);          // one Newton step: ~1 ulp
     const float y2 = y * y;
     if (S == 0) {
@@ -628,39 +639,42 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             float f = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, g = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
             const int spx = act ? sp : 0;
             const float c2a = act ? close2 : 0.0f, c2b = two ? close2 : 0.0f;
+            // one step: source slot spx + it k against the thread's two targets
+            auto step = [&](int it2) {
+                const int jj = spx + it2 * k;
+                const float4 P = P4[jj];
+                float Sj[nS];
+                Sj[0] = P.w;
+                if constexpr (nR == 2) {
+                    const float2 r = *(const float2 *)(SR + jj * nR);
+                    Sj[1] = r.x; Sj[2] = r.y;
+                } else if constexpr (nR == 8) {
+                    const float4 r0 = *(const float4 *)(SR + jj * nR);
+                    const float4 r1 = *(const float4 *)(SR + jj * nR + 4);
+                    Sj[1] = r0.x; Sj[2] = r0.y; Sj[3] = r0.z; Sj[4] = r0.w;
+                    Sj[5] = r1.x; Sj[6] = r1.y;
+                }
+                // separations from the rounded leaf-frame coordinates: the error is
+                // ~1 ulp of the leaf size, small next to r for every pair this
+                // loop keeps (the closer ones go to the double-float queue, which
+                // takes the low parts too)
+                const float dx = oi.x - P.x, dy = oi.y - P.y, dz = oi.z - P.z;
+                const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                pair32<S, PHI, FIELD>(dx, dy, dz, r2a, r2a >= c2a, Sj, f, e0, e1, e2);
+                const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
+                const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                pair32<S, PHI, FIELD>(ex, ey, ez, r2b, r2b >= c2b, Sj, g, g0, g1, g2);
+                if (r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
+                if (r2b < c2b && r2b > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
+            };
             int it = 0;
             while (it < steps) {
-#pragma unroll 2
-                for (; it < steps; ++it) {
-                    const int jj = spx + it * k;
-                    const float4 P = P4[jj];
-                    float Sj[nS];
-                    Sj[0] = P.w;
-                    if constexpr (nR == 2) {
-                        const float2 r = *(const float2 *)(SR + jj * nR);
-                        Sj[1] = r.x; Sj[2] = r.y;
-                    } else if constexpr (nR == 8) {
-                        const float4 r0 = *(const float4 *)(SR + jj * nR);
-                        const float4 r1 = *(const float4 *)(SR + jj * nR + 4);
-                        Sj[1] = r0.x; Sj[2] = r0.y; Sj[3] = r0.z; Sj[4] = r0.w;
-                        Sj[5] = r1.x; Sj[6] = r1.y;
-                    }
-                    // separations from the rounded leaf-frame coordinates: the error is
-                    // ~1 ulp of the leaf size, small next to r for every pair this
-                    // loop keeps (the closer ones go to the double-float queue, which
-                    // takes the low parts too)
-                    const float dx = oi.x - P.x, dy = oi.y - P.y, dz = oi.z - P.z;
-                    const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool ca = r2a < c2a && r2a > 0.0f;
-                    pair32<S, PHI, FIELD>(dx, dy, dz, r2a < c2a ? 0.0f : r2a, Sj, f, e0, e1, e2);
-                    const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
-                    const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const bool cb = r2b < c2b && r2b > 0.0f;
-                    pair32<S, PHI, FIELD>(ex, ey, ez, r2b < c2b ? 0.0f : r2b, Sj, g, g0, g1, g2);
-                    if (ca) closeq[0][qa++][tid] = (uint16_t)jj;
-                    if (cb) closeq[1][qb++][tid] = (uint16_t)jj;
-                    if (__any_sync(0xffffffffu, qa == kLaneQ || qb == kLaneQ)) {   // a queue is full
-                        ++it;
+                // two steps, then a look at the queues: they have room for two more
+                for (; it < steps; it += 2) {
+                    step(it);
+                    if (it + 1 < steps) step(it + 1);
+                    if (__any_sync(0xffffffffu, qa > kLaneQ - 2 || qb > kLaneQ - 2)) {
+                        it += 2;
                         break;
                     }
                 }
