@@ -260,8 +260,9 @@ fmm_status fmm_copy_array(const fmm_tree *t, fmm_array which, void *host_dst, si
 
 /* Per-phase device times of the last evaluate (milliseconds, CUDA events on
  * the handle's stream) when profiling is on.  Phases, in order:
- *   0 keys+bbox, 1 sort, 2 cells, 3 lists, 4 D tables, 5 P2M, 6 M2M,
- *   7 M2L, 8 L2L, 9 L2P, 10 P2P (incl. un-permute)
+ *   0 keys+bbox, 1 sort, 2 cells, 3 lists, 4 D tables, 5 upward pass (P2M
+ *   and M2M, one launch), 6 fold of the multipoles for the harmonic M2L,
+ *   7 M2L, 8 L2L (all levels, one launch), 9 L2P, 10 P2P (incl. un-permute)
  * Phases 0-2 belong to fmm_set_sources, 3-10 to fmm_evaluate. */
 #define FMM_NUM_PHASES 11
 fmm_status fmm_set_profiling(fmm_tree *t, int enable);
@@ -402,8 +403,9 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1),
  *               or each mirrored leaf pair once for both directions (2)
  *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
- *               the SIMT FP32 M2L (m2l_tensor 0)
- *   FMM_FP32    nothing to choose (the handle's settings are timed)
+ *               the SIMT FP32 M2L (m2l_tensor 0); then, with the fastest of
+ *               those, the P2P tile of the other shape (p2p_targets 1 or 2)
+ *   FMM_FP32    the P2P tile: one or two targets per thread (p2p_targets)
  * The FP32 forms keep their P2P kernel: the one-way kernel (p2p_variant 1,
  * their default) evaluates the pairs closer than one mean particle spacing of
  * the target leaf in double-float arithmetic, which holds the near field's
@@ -425,6 +427,9 @@ typedef struct {
     int m2l_harmonic;       /* SIMT M2L (FP64, FP32, 3xTF32 off the tensor cores)*/
                             /* over the traceless components (§3.1): 1 (default) */
                             /* or the full Cartesian sums: 0                     */
+    int p2p_targets;        /* FP32 forms' one-way P2P tile: targets per thread, */
+                            /* 2 (default; both share each staged source read)   */
+                            /* or 1 (more threads per target, fewer registers)   */
 } fmm_tuning;
 fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field, int reps, fmm_tuning *out);
@@ -432,7 +437,8 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
 /*
  * Applies a tuning, e.g. one fmm_autotune reported for the same workload on
  * an earlier run, without timing anything: p2p_variant 0, 1 or 2,
- * m2l_tensor 0 or 1, tc_chunk_rows in [1, 64], m2l_harmonic 0 or 1; a
+ * m2l_tensor 0 or 1, tc_chunk_rows in [1, 64], m2l_harmonic 0 or 1,
+ * p2p_targets 1 or 2 (0 in a zero-filled struct also keeps the setting); a
  * negative value keeps the handle's current setting, and candidates and
  * ms_per_evaluate are ignored.  The harmonic M2L contracts only the 2k+1
  * components of degree k with m_z <= 1 of the folded multipole and derives

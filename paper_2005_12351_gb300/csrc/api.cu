@@ -35,7 +35,7 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
                    &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
                    &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
-                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt, &t->b_ctl};
+                   &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt, &t->b_ctl, &t->b_ud};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
 }
 

@@ -134,16 +134,39 @@ struct DevTables {
 // n_z from the trace identity L_n = -L_{n+2x-2z} - L_{n+2y-2z} (§3.1: 1/r is
 // harmonic, so are the local expansions of its M2L and their L2L shifts).
 // Called by every thread of the block; ends with a barrier.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ void expand_local(const T *row, const DevTables &tb, T *Lf)
 {
-    for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x) Lf[tb.h_rn[r]] = row[r];
+    for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x) Lf[tb.h_rn[r]] = CG ? __ldcg(row + r) : row[r];
     for (int l = 0; l < tb.h_unfold_lev; ++l) {
         __syncthreads();
         for (int q = tb.h_unfold_off[l] + threadIdx.x; q < tb.h_unfold_off[l + 1]; q += blockDim.x)
             Lf[tb.h_unfold[3 * q]] = -Lf[tb.h_unfold[3 * q + 1]] - Lf[tb.h_unfold[3 * q + 2]];
     }
     __syncthreads();
+}
+
+// the same, for a row another block of the same launch may have written (the
+// loads bypass the incoherent L1)
+template <typename T>
+__device__ __forceinline__ void expand_local_cg(const T *row, const DevTables &tb, T *Lf)
+{
+    expand_local<T, true>(row, tb, Lf);
+}
+
+// Bounded wait of thread 0 of a block for a flag another block of the same
+// launch sets; false if it gave up (about a second).  The caller orders the
+// wait before its reads with a fence.
+__device__ __forceinline__ bool wait_flag(const unsigned *flag)
+{
+    const volatile unsigned *f = flag;
+    if (*f) return true;
+    const long long t0 = clock64();
+    while (!*f) {
+        if (clock64() - t0 > (1ll << 31)) return false;
+        __nanosleep(32);
+    }
+    return true;
 }
 
 __device__ __forceinline__ int mi_at(const int *mi, int k) { return __ldg(mi + k); }
@@ -216,6 +239,7 @@ struct fmm_tree {
     DevBuf b_centre, b_half, b_leaves;
     DevBuf b_flags, b_scan, b_scan_tmp;
     DevBuf b_ctl;                          // level counts of the cell build
+    DevBuf b_ud;                           // upward arrival counters, downward flags
     DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;
     DevBuf b_m2l_src, b_m2l_off, b_m2l_didx, b_p2p_src, b_p2p_off, b_lkeys, b_lkeys2, b_lval, b_lval2;
     DevBuf b_hash, b_dkeys, b_D;
@@ -257,6 +281,7 @@ struct fmm_tree {
     // directions), FMM_3XTF32 M2L on the SIMT FP32 kernel instead of the
     // tensor cores, rows per chunk of the tensor-core M2L (tc_G above)
     int p2p_variant = 2;
+    int p2p_tt = 2;                        // FP32 forms' one-way P2P: targets per thread (1 or 2)
     bool m2l_simt = false;
     bool m2l_harmonic = true;              // SIMT M2L over the traceless components
     bool tuned = false;

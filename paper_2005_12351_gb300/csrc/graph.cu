@@ -146,6 +146,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     base.m2l_tensor = t->m2l_simt ? 0 : 1;
     base.tc_chunk_rows = t->tc_G > 0 ? t->tc_G : 16;
     base.m2l_harmonic = t->m2l_harmonic ? 1 : 0;
+    base.p2p_targets = t->p2p_tt;
     if (t->prec == FMM_FP64) {
         for (int v : {0, 1, 2}) {
             fmm_tuning c = base;
@@ -165,6 +166,8 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     } else {
         cand.push_back(base);
     }
+    // the FP32 forms' second stage: the winner with the other P2P tile shape
+    const size_t stage1 = cand.size();
     Guard g(t->device);
     drop_graph(t);
     cudaEvent_t a = nullptr, b = nullptr;
@@ -176,6 +179,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     for (size_t k = 0; k < cand.size() && st == FMM_OK; ++k) {
         const fmm_tuning c = cand[k];
         t->p2p_variant = c.p2p_variant;
+        t->p2p_tt = c.p2p_targets;
         t->m2l_simt = !c.m2l_tensor;
         if (t->tc_G != c.tc_chunk_rows) {
             t->tc_G = c.tc_chunk_rows;
@@ -196,12 +200,18 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
             best_ms = ms;
             best = (int)k;
         }
+        if (k + 1 == stage1 && t->prec != FMM_FP64) {
+            fmm_tuning c2 = cand[best];
+            c2.p2p_targets = c2.p2p_targets == 1 ? 2 : 1;
+            cand.push_back(c2);
+        }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st != FMM_OK) return st;
     const fmm_tuning &c = cand[best];
     t->p2p_variant = c.p2p_variant;
+    t->p2p_tt = c.p2p_targets;
     t->m2l_simt = !c.m2l_tensor;
     if (t->tc_G != c.tc_chunk_rows) {
         t->tc_G = c.tc_chunk_rows;
@@ -226,10 +236,12 @@ fmm_status fmm_set_tuning(fmm_tree *t, const fmm_tuning *tuning)
     if (c.tc_chunk_rows == 0 || c.tc_chunk_rows > 64)
         return fail(t, FMM_EINVAL, "tc_chunk_rows must be in [1, 64]");
     if (c.m2l_harmonic > 1) return fail(t, FMM_EINVAL, "m2l_harmonic must be 0 or 1");
+    if (c.p2p_targets > 2) return fail(t, FMM_EINVAL, "p2p_targets must be 1 or 2");
     drop_graph(t);
     if (c.p2p_variant >= 0) t->p2p_variant = c.p2p_variant;
     if (c.m2l_tensor >= 0) t->m2l_simt = c.m2l_tensor == 0;
     if (c.m2l_harmonic >= 0) t->m2l_harmonic = c.m2l_harmonic == 1;
+    if (c.p2p_targets > 0) t->p2p_tt = c.p2p_targets;
     if (c.tc_chunk_rows > 0 && t->tc_G != c.tc_chunk_rows) {
         t->tc_G = c.tc_chunk_rows;
         t->tc_plan = false;

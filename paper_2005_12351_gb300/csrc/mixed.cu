@@ -101,16 +101,14 @@ constexpr int kMaxSrc = 6;
 // One block per leaf; each thread owns up to kPer components with their
 // source-term monomial indices in registers (absent terms hit a zero slot).
 // FP32 sums over groups of 8 particles, FP64 across groups.
-__global__ void __launch_bounds__(128)
-k_p2m32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
-        const float4 *o, const float *S32, DevTables tb, float *M)
+__device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const int32_t *end,
+                                           const double *half, const float4 *o, const float *S32,
+                                           const DevTables &tb, float *M, float *sf)
 {
-    extern __shared__ float sf[];
     const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nK1 = tb.nK + 1, nS = tb.nS;
     float *apow = sf;                              // [chunk][3][P1]
     float *mono = apow + kChunk * 3 * P1;          // [chunk][nK + 1], last = 0
     float *Ssm = mono + kChunk * nK1;              // [chunk][nS]
-    const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
     const float inv_h = (float)(1.0 / half[c]);    // a power of two
     const int nS32 = nS == 6 ? 7 : nS;
@@ -179,16 +177,15 @@ __device__ __forceinline__ float sign_mono(const int *mi, int k, int nx_neg, int
 }
 
 // ------------------------------------------------------------------ M2M
-__global__ void __launch_bounds__(128)
-k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, const int32_t *cy,
-        const int32_t *cz, DevTables tb, float *M)
+// parent c from its children (the rows may have been written by other blocks
+// of the same launch: ldcg)
+__device__ __forceinline__ void m2m32_cell(int c, const int32_t *child, const int32_t *nchild,
+                                           const int32_t *cx, const int32_t *cy, const int32_t *cz,
+                                           const DevTables &tb, float *M, float *sf)
 {
-    extern __shared__ float sf[];
     float *mono = sf;               // [nK]
     float *Mc = mono + tb.nK;       // [nM]
-    const int c = lb + blockIdx.x;
     const int nch = nchild[c];
-    if (nch == 0) return;
     double acc[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
@@ -197,7 +194,7 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
         // z_p - z_c = (1 - 2 bit) h_c per axis: negative where the child's low bit is 1
         const int bx = cx[ch] & 1, by = cy[ch] & 1, bz = cz[ch] & 1;
         for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
-        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * row4(tb.nM) + t];
+        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = __ldcg(M + (int64_t)ch * row4(tb.nM) + t);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
@@ -216,6 +213,40 @@ k_m2m32(int lb, const int32_t *child, const int32_t *nchild, const int32_t *cx, 
         if (ni < tb.nM)
             M[(int64_t)c * row4(tb.nM) + ni] =
                 (float)ldexp(acc[u], -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s));
+    }
+}
+
+// The upward pass of this form in one launch: P2M at leaf b, then the block
+// whose child arrives last at a parent forms the parent's multipole, up to the
+// root (the FP64 form's k_upward, same counters and ordering).
+__global__ void __launch_bounds__(128)
+k_upward32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *parent,
+           const int32_t *child, const int32_t *nchild, const int32_t *cx, const int32_t *cy,
+           const int32_t *cz, const double *half, const float4 *o, const float *S32, DevTables tb,
+           float *M, unsigned *arrive)
+{
+    extern __shared__ float sf[];
+    __shared__ int s_go;
+    int c = leaves[blockIdx.x];
+    p2m32_leaf(c, begin, end, half, o, S32, tb, M, sf);
+    for (;;) {
+        const int pa = parent[c];
+        if (pa < 0) break;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned n = atomicAdd(&arrive[pa], 1u) + 1u;
+            const bool last = n == (unsigned)nchild[pa];
+            if (last) {
+                arrive[pa] = 0u;
+                __threadfence();
+            }
+            s_go = last;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        m2m32_cell(pa, child, nchild, cx, cy, cz, tb, M, sf);
+        c = pa;
     }
 }
 
@@ -313,21 +344,17 @@ k_m2l32(const int32_t *off, const int32_t *src, const int32_t *didx, const int32
 }
 
 // ------------------------------------------------------------------ L2L
-__global__ void __launch_bounds__(128)
-k_l2l32(int lb, const int32_t *parent, const int32_t *cx, const int32_t *cy, const int32_t *cz,
-        DevTables tb, float *L)
+__device__ __forceinline__ void l2l32_cell(int c, int pa, const int32_t *cx, const int32_t *cy,
+                                           const int32_t *cz, const DevTables &tb, float *L, float *sf)
 {
-    extern __shared__ float sf[];
     float *mono = sf;               // [nK]
     float *Lp = mono + tb.nK;       // [nL], pre-scaled by 2^-(|q|+s+1)
-    const int c = lb + blockIdx.x;
-    const int pa = parent[c];
     // z_c - z_p = (2 bit - 1) h_c: negative where the child's low bit is 0
     const int bx = 1 - (cx[c] & 1), by = 1 - (cy[c] & 1), bz = 1 - (cz[c] & 1);
     for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
     // the parent's full expansion (the identity holds degree by degree, so the
     // power-of-two rescaling may follow the unfold)
-    expand_local(L + (int64_t)pa * tb.nLh, tb, Lp);
+    expand_local_cg(L + (int64_t)pa * tb.nLh, tb, Lp);
     for (int q = threadIdx.x; q < tb.nL; q += blockDim.x)
         Lp[q] = ldexpf(Lp[q], -(mi_shell(mi_at(tb.mi, q)) + tb.s + 1));
     __syncthreads();
@@ -338,6 +365,40 @@ k_l2l32(int lb, const int32_t *parent, const int32_t *cx, const int32_t *cy, con
         for (int q = tb.l2l_off[n]; q < tb.l2l_off[n + 1]; ++q)
             acc = fmaf(mono[tb.l2l_k[q]], Lp[tb.l2l_q[q]], acc);
         L[(int64_t)c * tb.nLh + r] += acc;
+    }
+}
+
+// All levels' L2L shifts of this form in one launch (the FP64 form's
+// k_downward: cells claimed in breadth-first order, bounded wait on the
+// parent's flag, NaN where a wait gave up).
+__global__ void __launch_bounds__(128)
+k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t *cy,
+             const int32_t *cz, DevTables tb, float *L, unsigned *ctl)
+{
+    extern __shared__ float sf[];
+    __shared__ int s_c, s_ok;
+    if (threadIdx.x == 0) s_c = (int)atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nc) return;
+    const int pa = parent[c];
+    if (pa >= 0) {
+        if (threadIdx.x == 0) {
+            s_ok = wait_flag(ctl + 1 + pa);
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_ok) {
+            l2l32_cell(c, pa, cx, cy, cz, tb, L, sf);
+        } else {
+            for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x)
+                L[(int64_t)c * tb.nLh + r] = __int_as_float(0x7fc00000);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(ctl + 1 + c, 1u);
     }
 }
 
@@ -468,7 +529,9 @@ constexpr int kGroups = 64;
 constexpr int kLaneQ = 8;                 // close pairs a thread queues per target
 constexpr double kCloseSpacings = 1.0;    // close: r < this many mean spacings of the target leaf
 
-template <int S, bool PHI, bool FIELD>
+// TT: targets per thread (1 or 2; the autotuner's tile choice): two share each
+// staged source read, one leaves more threads per target and fewer registers.
+template <int S, bool PHI, bool FIELD, int TT>
 __global__ void __launch_bounds__(kP2PThreads)
 k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
         const int32_t *src, const int32_t *level, const int32_t *cx, const int32_t *cy,
@@ -511,13 +574,13 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     // squared close-pair radius of this leaf's targets
     const double sp_a = kCloseSpacings * 2.0 * half[c] / cbrt((double)max(nt, 1));
     const float close2 = (float)(sp_a * sp_a);
-    for (int t0 = 0; t0 < nt; t0 += 2 * kP2PThreads) {
-        const int cnt = min(2 * kP2PThreads, nt - t0);
-        const int h = (cnt + 1) / 2;
+    for (int t0 = 0; t0 < nt; t0 += TT * kP2PThreads) {
+        const int cnt = min(TT * kP2PThreads, nt - t0);
+        const int h = TT == 2 ? (cnt + 1) / 2 : cnt;
         const int k = max(1, kP2PThreads / h);
         const int ti = tid % h, sp = tid / h;
         const bool act = sp < k;
-        const bool two = act && (ti + h < cnt);
+        const bool two = TT == 2 && act && (ti + h < cnt);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 oi = act ? o[b + t0 + ti] : zero4;
         const float4 oj = two ? o[b + t0 + ti + h] : oi;
@@ -530,7 +593,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         auto flush = [&]() {
             const int ma = __reduce_max_sync(0xffffffffu, (unsigned)max(qa, qb));
 #pragma unroll
-            for (int w = 0; w < 2; ++w) {
+            for (int w = 0; w < TT; ++w) {
                 const int nq = w ? qb : qa;
                 const int ot = ti + w * h;                   // this thread's target in the tile
                 const float4 po = (act && (w == 0 || two)) ? o[b + t0 + ot] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -661,11 +724,13 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                 const float dx = oi.x - P.x, dy = oi.y - P.y, dz = oi.z - P.z;
                 const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 pair32<S, PHI, FIELD>(dx, dy, dz, r2a, r2a >= c2a, Sj, f, e0, e1, e2);
-                const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
-                const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                pair32<S, PHI, FIELD>(ex, ey, ez, r2b, r2b >= c2b, Sj, g, g0, g1, g2);
                 if (r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
-                if (r2b < c2b && r2b > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
+                if constexpr (TT == 2) {
+                    const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
+                    const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    pair32<S, PHI, FIELD>(ex, ey, ez, r2b, r2b >= c2b, Sj, g, g0, g1, g2);
+                    if (r2b < c2b && r2b > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
+                }
             };
             int it = 0;
             while (it < steps) {
@@ -696,7 +761,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         __syncthreads();
         if (tid < h) {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            for (int half = 0; half < TT; ++half) {
                 if (half == 1 && tid + h >= cnt) break;
                 const int r = 4 * half;
                 double Fv = red[r][tid], Av = red[r + 1][tid], Bv = red[r + 2][tid], Cv = red[r + 3][tid];
@@ -1094,9 +1159,15 @@ void launch_p2p32(fmm_tree *t, int want_phi, int want_field, double *phi, double
             (const double *)t->b_phi.ptr, (const double *)t->b_E.ptr, (const int32_t *)t->b_perm.ptr,
             phi, E);
     };
-    if (want_phi && want_field) go(k_p2p32<S, true, true>);
-    else if (want_phi) go(k_p2p32<S, true, false>);
-    else go(k_p2p32<S, false, true>);
+    if (t->p2p_tt == 1) {
+        if (want_phi && want_field) go(k_p2p32<S, true, true, 1>);
+        else if (want_phi) go(k_p2p32<S, true, false, 1>);
+        else go(k_p2p32<S, false, true, 1>);
+    } else {
+        if (want_phi && want_field) go(k_p2p32<S, true, true, 2>);
+        else if (want_phi) go(k_p2p32<S, true, false, 2>);
+        else go(k_p2p32<S, false, true, 2>);
+    }
 }
 
 void record(fmm_tree *t, int i)
@@ -1156,6 +1227,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     FMM_TRY(ensure(t, t->b_S32, 8 * (size_t)n * (t->nS == 6 ? 7 : t->nS)));   // hi, then lo
     FMM_TRY(ensure(t, t->b_M32, 4 * (size_t)nc * row4(tb.nM)));
     FMM_TRY(ensure(t, t->b_L32, 4 * (size_t)nc * tb.nLh));
+    FMM_TRY(ensure(t, t->b_ud, 8 * (size_t)(nc + 1)));      // upward counters, downward flags
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
     // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
@@ -1196,22 +1268,18 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
                                                    (const double *)t->b_S.ptr, t->nS, n, o, o + n,
                                                    S32);
     {
-        size_t smem = 4 * (size_t)(kChunk * 3 * P1 + kChunk * (tb.nK + 1) + kChunk * tb.nS);
-        allow_max_dynamic_smem(k_p2m32);
-        k_p2m32<<<(unsigned)t->nleaves, 128, smem, st>>>(leaves, begin, end, half, o, S32, tb, M);
+        // P2M and M2M in one launch; the arrival counters start (and end) at zero
+        cudaMemsetAsync(t->b_ud.ptr, 0, 4 * (size_t)nc, st);
+        size_t smem = 4 * std::max<size_t>((size_t)kChunk * 3 * P1 + (size_t)kChunk * (tb.nK + 1) +
+                                               (size_t)kChunk * tb.nS,
+                                           (size_t)tb.nK + tb.nM);
+        allow_max_dynamic_smem(k_upward32);
+        k_upward32<<<(unsigned)t->nleaves, 128, smem, st>>>(
+            leaves, begin, end, (const int32_t *)t->b_parent.ptr, (const int32_t *)t->b_child.ptr,
+            (const int32_t *)t->b_nchild.ptr, cx, cy, cz, half, o, S32, tb, M, (unsigned *)t->b_ud.ptr);
     }
     t->launches += 2;
     record(t, 7);
-    {
-        size_t smem = 4 * (size_t)(tb.nK + tb.nM);
-        for (int l = t->nlevels - 2; l >= 0; --l) {
-            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
-            k_m2m32<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
-                                            (const int32_t *)t->b_nchild.ptr, cx, cy, cz, tb, M);
-            ++t->launches;
-        }
-    }
-    record(t, 8);
     cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nLh, st);
     // harmonic M2L: the folded multipoles, for either M2L
     const float *Ms = M;
@@ -1221,6 +1289,7 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         ++t->launches;
         Ms = (const float *)t->b_Mh32.ptr;
     }
+    record(t, 8);
     if (t->n_m2l > 0 && use_tc) {
         FMM_TRY(run_m2l_tc(t, p, Ms, row4(tb.nMh), tb.nMh, tb.nL, tb, L));
     } else if (t->n_m2l > 0) {
@@ -1235,13 +1304,14 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         ++t->launches;
     }
     record(t, 9);
-    {
+    // L2L downward, all levels in one launch (flags and claim counter start at zero)
+    if (t->nlevels > 1) {
+        unsigned *ctl = (unsigned *)t->b_ud.ptr + nc + 1;
+        cudaMemsetAsync(ctl, 0, 4 * (size_t)(nc + 1), st);
         size_t smem = 4 * (size_t)(tb.nK + tb.nL);
-        for (int l = 1; l < t->nlevels; ++l) {
-            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
-            k_l2l32<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_parent.ptr, cx, cy, cz, tb, L);
-            ++t->launches;
-        }
+        k_downward32<<<(unsigned)nc, 128, smem, st>>>(nc, (const int32_t *)t->b_parent.ptr, cx, cy, cz,
+                                                      tb, L, ctl);
+        ++t->launches;
     }
     record(t, 10);
     {

@@ -251,17 +251,15 @@ constexpr int kP2MPer = 4;                // up to 4 * 128 = 512 M components
 // the monomial index of m - a for each source term a in registers (an absent
 // term points at a zero slot), so the particle loop is branch-free.
 template <int kMaxSrc>
-__global__ void __launch_bounds__(kP2MThreads)
-k_p2m(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
-      const double *px, const double *py, const double *pz, const double *S, DevTables tb,
-      double *M)
+__device__ __forceinline__ void p2m_leaf(int c, const int32_t *begin, const int32_t *end,
+                                         const double *centre, const double *px, const double *py,
+                                         const double *pz, const double *S, const DevTables &tb,
+                                         double *M, double *sm)
 {
-    extern __shared__ double sm[];
     const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nK1 = tb.nK + 1, nS = tb.nS;
     double *apow = sm;                                  // [chunk][3][P+1]
     double *mono = apow + kP2MChunk * 3 * P1;           // [chunk][nK + 1], last = 0
     double *Ssm = mono + kP2MChunk * nK1;               // [chunk][nS]
-    const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
     int kt[kP2MPer][kMaxSrc];
@@ -314,19 +312,18 @@ k_p2m(const int32_t *leaves, const int32_t *begin, const int32_t *end, const dou
 }
 
 // ------------------------------------------------------------------ M2M
-// One block per parent cell of one level.
-__global__ void __launch_bounds__(128)
-k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre, DevTables tb,
-      double *M)
+// The multipole of parent cell c from its children (Eq. (4) with the sign of
+// R2), children summed in index order.  ldcg: the children's rows may have been
+// written by other blocks of the same launch.
+__device__ __forceinline__ void m2m_cell(int c, const int32_t *child, const int32_t *nchild,
+                                         const double *centre, const DevTables &tb, double *M,
+                                         double *sm)
 {
-    extern __shared__ double sm[];
     const int P = tb.p, nK = tb.nK;
     double *apow = sm;                  // [3][P+1]
     double *mono = apow + 3 * (P + 1);  // [nK]
     double *Mc = mono + nK;             // [nM]
-    const int c = lb + blockIdx.x;
     const int nch = nchild[c];
-    if (nch == 0) return;
     double acc[kP2MPer];
 #pragma unroll
     for (int u = 0; u < kP2MPer; ++u) acc[u] = 0.0;
@@ -335,7 +332,7 @@ k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre,
         if (threadIdx.x < 3)
             axis_powers(centre[3 * c + threadIdx.x] - centre[3 * ch + threadIdx.x], P,
                         apow + threadIdx.x * (P + 1));
-        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = M[(int64_t)ch * tb.nM + t];
+        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = __ldcg(M + (int64_t)ch * tb.nM + t);
         __syncthreads();
         for (int k = threadIdx.x; k < nK; k += blockDim.x) {
             const int v = mi_at(tb.mi, k);
@@ -355,6 +352,44 @@ k_m2m(int lb, const int32_t *child, const int32_t *nchild, const double *centre,
     for (int u = 0; u < kP2MPer; ++u) {
         const int ni = threadIdx.x + u * 128;
         if (ni < tb.nM) M[(int64_t)c * tb.nM + ni] = acc[u];
+    }
+}
+
+// The upward pass in one launch: block b forms the multipole of leaf b (P2M,
+// Eq. (3)), then climbs -- the block whose child arrives last at a parent
+// (a counter per cell) forms that parent's multipole (M2M), and so on up to
+// the root.  No block waits on another; every parent is formed exactly once,
+// from its finished children, in the same order as a level-by-level pass.
+// arrive[] starts at zero and is left at zero (the winner resets it).
+template <int kMaxSrc>
+__global__ void __launch_bounds__(kP2MThreads)
+k_upward(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *parent,
+         const int32_t *child, const int32_t *nchild, const double *centre, const double *px,
+         const double *py, const double *pz, const double *S, DevTables tb, double *M,
+         unsigned *arrive)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_go;
+    int c = leaves[blockIdx.x];
+    p2m_leaf<kMaxSrc>(c, begin, end, centre, px, py, pz, S, tb, M, sm);
+    for (;;) {
+        const int pa = parent[c];
+        if (pa < 0) break;
+        __syncthreads();                       // every thread's row of c is written
+        if (threadIdx.x == 0) {
+            __threadfence();                   // ... and visible before the arrival counts
+            const unsigned n = atomicAdd(&arrive[pa], 1u) + 1u;
+            const bool last = n == (unsigned)nchild[pa];
+            if (last) {
+                arrive[pa] = 0u;
+                __threadfence();               // the other children's rows are visible now
+            }
+            s_go = last;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        m2m_cell(pa, child, nchild, centre, tb, M, sm);
+        c = pa;
     }
 }
 
@@ -470,20 +505,19 @@ k_m2l(const int32_t *off, const int32_t *src, const int32_t *didx, const int32_t
 }
 
 // ------------------------------------------------------------------ L2L
-__global__ void __launch_bounds__(128)
-k_l2l(int lb, const int32_t *parent, const double *centre, DevTables tb, double *L)
+// The local expansion of cell c shifted from its parent's (Eq. (9)-type Taylor
+// shift), added to c's stored components.
+__device__ __forceinline__ void l2l_cell(int c, int pa, const double *centre, const DevTables &tb,
+                                         double *L, double *sm)
 {
-    extern __shared__ double sm[];
     const int P = tb.p, nK = tb.nK;
     double *apow = sm;
     double *mono = apow + 3 * (P + 1);
     double *Lp = mono + nK;
-    const int c = lb + blockIdx.x;
-    const int pa = parent[c];
     if (threadIdx.x < 3)
         axis_powers(centre[3 * c + threadIdx.x] - centre[3 * pa + threadIdx.x], P,
                     apow + threadIdx.x * (P + 1));
-    expand_local(L + (int64_t)pa * tb.nLh, tb, Lp);          // the parent's full expansion
+    expand_local_cg(L + (int64_t)pa * tb.nLh, tb, Lp);        // the parent's full expansion
     for (int k = threadIdx.x; k < nK; k += blockDim.x) {
         const int v = mi_at(tb.mi, k);
         mono[k] = apow[mi_nx(v)] * apow[(P + 1) + mi_ny(v)] * apow[2 * (P + 1) + mi_nz(v)];
@@ -504,20 +538,19 @@ k_l2l(int lb, const int32_t *parent, const double *centre, DevTables tb, double 
 // ------------------------------------------------------------------ L2P
 constexpr int kL2PThreads = 128;
 
-// One block per leaf; one thread per particle.  Writes the far-field part
-// of phi and E = -grad phi in sorted particle order.
-__global__ void __launch_bounds__(kL2PThreads)
-k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
-      const double *px, const double *py, const double *pz, const double *L, DevTables tb,
-      int want_phi, int want_field, double *phi, double *E)
+// Leaf c: the far-field part of phi and E = -grad phi at its particles (Eqs.
+// (9), (10)), one thread per particle, in sorted particle order.
+__device__ __forceinline__ void l2p_leaf(int c, const int32_t *begin, const int32_t *end,
+                                         const double *centre, const double *px, const double *py,
+                                         const double *pz, const double *L, const DevTables &tb,
+                                         int want_phi, int want_field, double *phi, double *E,
+                                         double *sm)
 {
-    extern __shared__ double sm[];
     const int P = tb.p, P1 = tb.p + 1;
     double *Lsm = sm;                                       // [nL]
     double *a = Lsm + tb.nL + threadIdx.x * 3 * P1;         // this thread's [3][P+1]
-    const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c];
-    expand_local(L + (int64_t)c * tb.nLh, tb, Lsm);
+    expand_local_cg(L + (int64_t)c * tb.nLh, tb, Lsm);
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
     for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
         axis_powers(px[j] - z0, P, a);
@@ -541,6 +574,54 @@ k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const dou
             E[3 * (int64_t)j + 1] = -g1;
             E[3 * (int64_t)j + 2] = -g2;
         }
+    }
+}
+
+
+__global__ void __launch_bounds__(kL2PThreads)
+k_l2p(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *centre,
+      const double *px, const double *py, const double *pz, const double *L, DevTables tb,
+      int want_phi, int want_field, double *phi, double *E)
+{
+    extern __shared__ double sm[];
+    l2p_leaf(leaves[blockIdx.x], begin, end, centre, px, py, pz, L, tb, want_phi, want_field, phi, E, sm);
+}
+
+// The L2L shifts of all levels in one launch.  Blocks claim cells in
+// breadth-first order (a counter), so a cell's parent was claimed earlier by a
+// block that is running or done and waits on nothing later: the block waits
+// (bounded) for the parent's flag, shifts the parent's local expansion into the
+// cell and publishes its own flag.  A wait that gives up fills the cell's
+// expansion with NaN, so the failure shows in the output.  ctl[0] (the claim
+// counter) and the flags ctl[1 + c] start at zero.
+__global__ void __launch_bounds__(128)
+k_downward(int64_t nc, const int32_t *parent, const double *centre, DevTables tb, double *L,
+           unsigned *ctl)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_c, s_ok;
+    if (threadIdx.x == 0) s_c = (int)atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nc) return;
+    const int pa = parent[c];
+    if (pa >= 0) {
+        if (threadIdx.x == 0) {
+            s_ok = wait_flag(ctl + 1 + pa);
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_ok) {
+            l2l_cell(c, pa, centre, tb, L, sm);
+        } else {
+            for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x)
+                L[(int64_t)c * tb.nLh + r] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(ctl + 1 + c, 1u);
     }
 }
 
@@ -680,34 +761,29 @@ fmm_status run_upward(fmm_tree *t, const DevTables &tb, bool rec)
     const int64_t nc = t->ncells;
     const int P1 = tb.p + 1;
     FMM_TRY(ensure(t, t->b_M, 8 * (size_t)nc * tb.nM));
+    FMM_TRY(ensure(t, t->b_ud, 8 * (size_t)(nc + 1)));
     t->m_cells = nc;
     double *M = (double *)t->b_M.ptr;
     const double *centre = (const double *)t->b_centre.ptr;
-    {
-        size_t smem = 8 * (size_t)(kP2MChunk * 3 * P1 + kP2MChunk * (tb.nK + 1) + kP2MChunk * tb.nS);
-        auto go = [&](auto kern) {
-            allow_max_dynamic_smem(kern);
-            kern<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(
-                (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
-                (const int32_t *)t->b_end.ptr, centre, (const double *)t->b_px.ptr,
-                (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr, (const double *)t->b_S.ptr, tb, M);
-        };
-        if (tb.nS <= 3) go(k_p2m<3>);
-        else if (tb.nS <= 6) go(k_p2m<6>);
-        else go(k_p2m<10>);
-        ++t->launches;
-    }
+    // P2M and M2M in one launch; the arrival counters start (and end) at zero
+    cudaMemsetAsync(t->b_ud.ptr, 0, 4 * (size_t)nc, st);
+    const size_t smem = 8 * std::max<size_t>(
+        (size_t)kP2MChunk * 3 * P1 + (size_t)kP2MChunk * (tb.nK + 1) + (size_t)kP2MChunk * tb.nS,
+        3 * (size_t)P1 + tb.nK + tb.nM);
+    auto go = [&](auto kern) {
+        allow_max_dynamic_smem(kern);
+        kern<<<(unsigned)t->nleaves, kP2MThreads, smem, st>>>(
+            (const int32_t *)t->b_leaves.ptr, (const int32_t *)t->b_begin.ptr,
+            (const int32_t *)t->b_end.ptr, (const int32_t *)t->b_parent.ptr,
+            (const int32_t *)t->b_child.ptr, (const int32_t *)t->b_nchild.ptr, centre,
+            (const double *)t->b_px.ptr, (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr,
+            (const double *)t->b_S.ptr, tb, M, (unsigned *)t->b_ud.ptr);
+    };
+    if (tb.nS <= 3) go(k_upward<3>);
+    else if (tb.nS <= 6) go(k_upward<6>);
+    else go(k_upward<10>);
+    ++t->launches;
     if (rec) record(t, 7);
-    {
-        size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nM);
-        for (int l = t->nlevels - 2; l >= 0; --l) {
-            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
-            k_m2m<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_child.ptr,
-                                          (const int32_t *)t->b_nchild.ptr, centre, tb, M);
-            ++t->launches;
-        }
-    }
-    if (rec) record(t, 8);
     return FMM_OK;
 }
 
@@ -736,14 +812,15 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
                  *pz = (const double *)t->b_pz.ptr;
     // M2L over the stored lists (harmonic: on the folded multipoles)
     cudaMemsetAsync(L, 0, 8 * (size_t)nc * tb.nLh, st);
+    const double *Ms = M;
+    if (t->n_m2l > 0 && tb.harmonic) {
+        FMM_TRY(ensure(t, t->b_Mh, 8 * (size_t)nc * tb.nMh));
+        launch_fold_m(st, M, tb.nM, nc, tb, (double *)t->b_Mh.ptr, tb.nMh);
+        ++t->launches;
+        Ms = (const double *)t->b_Mh.ptr;
+    }
+    record(t, 8);
     if (t->n_m2l > 0) {
-        const double *Ms = M;
-        if (tb.harmonic) {
-            FMM_TRY(ensure(t, t->b_Mh, 8 * (size_t)nc * tb.nMh));
-            launch_fold_m(st, M, tb.nM, nc, tb, (double *)t->b_Mh.ptr, tb.nMh);
-            ++t->launches;
-            Ms = (const double *)t->b_Mh.ptr;
-        }
         const int ldM = tb.nMh | 1, ldD = tb.nD | 1;
         size_t fixed = 8 * (size_t)tb.m2l_slots * kM2LThreads + 4 * (size_t)tb.m2l_T * kM2LThreads;
         size_t smem = fixed + 8 * (size_t)kM2LBatch * (ldM + ldD);
@@ -755,14 +832,13 @@ fmm_status run_expansions(fmm_tree *t, int p, int want_phi, int want_field)
         ++t->launches;
     }
     record(t, 9);
-    // L2L downward
-    {
+    // L2L downward, all levels in one launch (flags and claim counter start at zero)
+    if (t->nlevels > 1) {
+        unsigned *ctl = (unsigned *)t->b_ud.ptr + nc + 1;
+        cudaMemsetAsync(ctl, 0, 4 * (size_t)(nc + 1), st);
         size_t smem = 8 * (size_t)(3 * P1 + tb.nK + tb.nL);
-        for (int l = 1; l < t->nlevels; ++l) {
-            const int lb = t->level_begin[l], cnt = t->level_begin[l + 1] - lb;
-            k_l2l<<<cnt, 128, smem, st>>>(lb, (const int32_t *)t->b_parent.ptr, centre, tb, L);
-            ++t->launches;
-        }
+        k_downward<<<(unsigned)nc, 128, smem, st>>>(nc, (const int32_t *)t->b_parent.ptr, centre, tb, L, ctl);
+        ++t->launches;
     }
     record(t, 10);
     // L2P

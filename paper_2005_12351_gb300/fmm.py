@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_EORDER, FMM_ECUDA, FMM_ETIMEOUT, FMM_EBUDGET, FMM_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 PRECISIONS = {"fp64": 0, "fp32": 1, "3xtf32": 2}
-PHASES = ["keys", "sort", "cells", "lists", "dtables", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+PHASES = ["keys", "sort", "cells", "lists", "dtables", "upward", "fold", "m2l", "l2l", "l2p", "p2p"]
 ARRAYS = {"keys": (0, torch.int64, 1), "perm": (1, torch.int32, 1), "level": (2, torch.int32, 1),
           "coord": (3, torch.int32, 3), "range": (4, torch.int32, 2), "parent": (5, torch.int32, 1),
           "child": (6, torch.int32, 2), "centre": (7, torch.float64, 3),
@@ -51,7 +51,8 @@ class TreeInfo(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("p2p_variant", C.c_int), ("m2l_tensor", C.c_int), ("tc_chunk_rows", C.c_int),
-                ("candidates", C.c_int), ("ms_per_evaluate", C.c_float), ("m2l_harmonic", C.c_int)]
+                ("candidates", C.c_int), ("ms_per_evaluate", C.c_float), ("m2l_harmonic", C.c_int),
+                ("p2p_targets", C.c_int)]
 
 
 _lib = None
@@ -249,11 +250,12 @@ class FMMTree:
         return {k: getattr(out, k) for k, _ in out._fields_}
 
     def set_tuning(self, p2p_variant: int = -1, m2l_tensor: int = -1, tc_chunk_rows: int = -1,
-                   m2l_harmonic: int = -1):
+                   m2l_harmonic: int = -1, p2p_targets: int = -1):
         """Applies a tuning without timing (-1 keeps the current setting)."""
         tu = Tuning()
         tu.p2p_variant, tu.m2l_tensor, tu.tc_chunk_rows = int(p2p_variant), int(m2l_tensor), int(tc_chunk_rows)
         tu.m2l_harmonic = int(m2l_harmonic)
+        tu.p2p_targets = int(p2p_targets)
         fn = lib().fmm_set_tuning
         fn.argtypes = [C.c_void_p, C.POINTER(Tuning)]
         fn.restype = C.c_int

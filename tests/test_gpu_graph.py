@@ -82,10 +82,10 @@ def test_batch_graph_replay():
     assert np.array_equal(E.cpu().numpy(), Eu.cpu().numpy())
 
 
-# candidates: the three FP64 P2P kernels; FP32: the handle's settings only (its
-# one-way P2P evaluates the close pairs in double-float); 3xTF32: 8/16/32 rows
-# per chunk on the tensor cores, or the SIMT M2L
-@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 1), ("3xtf32", 4)])
+# candidates: the three FP64 P2P kernels; FP32: the P2P tile with two targets per
+# thread, then one; 3xTF32: 8/16/32 rows per chunk on the tensor cores or the
+# SIMT M2L, then the winner with the other P2P tile
+@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 2), ("3xtf32", 5)])
 def test_autotune(prec, ncand):
     import torch
     from gpu_util import rel_rms, to_dev
@@ -99,9 +99,35 @@ def test_autotune(prec, ncand):
     tune = t.autotune(p, 0.5, reps=2)
     assert tune["candidates"] == ncand and tune["ms_per_evaluate"] > 0
     assert tune["p2p_variant"] in ((0, 1, 2) if prec == "fp64" else (1,))
+    assert tune["p2p_targets"] in (1, 2)
     if prec == "3xtf32":
         assert tune["tc_chunk_rows"] in (8, 16, 32) and tune["m2l_tensor"] in (0, 1)
     phi1, E1 = t.evaluate_graph(p, 0.5)
     torch.cuda.synchronize()
     tol = 1e-13 if prec == "fp64" else 1e-6
     assert rel_rms(E1.cpu().numpy(), E0) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32"])
+def test_launches_per_evaluate_do_not_grow_with_depth(prec):
+    """The upward pass (P2M + M2M) and the L2L shifts each run as one launch
+    whatever the tree depth: a shallow uniform tree and a deep Plummer tree
+    take the same number of kernel launches per evaluate (and a batch of
+    systems as few)."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2005_12351_gb300 import fmm
+    counts = []
+    for dist, n, ncrit in (("uniform", 20_000, 64), ("plummer", 60_000, 16)):
+        pos, S = synth.make_system(n, 1, dist, 777)
+        t = fmm.create_tree(max_leaf=ncrit, precision=prec)
+        t.set_sources(to_dev(pos), to_dev(S), 1)
+        t.evaluate(4, 0.5)                        # lists, tables, plans
+        torch.cuda.synchronize()
+        c0 = t.launch_count()
+        t.evaluate(4, 0.5)
+        torch.cuda.synchronize()
+        counts.append((t.info()["nlevels"], t.launch_count() - c0))
+    (l0, a), (l1, b) = counts
+    assert l1 >= l0 + 3, counts
+    assert a == b and a <= 10, counts

@@ -276,3 +276,30 @@ def test_fp32_symmetric_batch_matches_alone(s):
         assert np.array_equal(phi, phi_b[a:b]) and np.array_equal(E, E_b[a:b]), k
         t.destroy()
     tb.destroy()
+
+
+@pytest.mark.parametrize("precision", FORMS)
+@pytest.mark.parametrize("s,dist", [(1, "uniform"), (2, "plummer")])
+def test_p2p_tile_shapes_agree(orc, precision, s, dist):
+    """The autotuner's P2P tile shapes (one or two targets per thread) sum the
+    same pairs in another order: within FP32 rounding of each other, and each
+    within 1e-6 of the oracle."""
+    from gpu_util import rel_rms
+    pos, S = synth.make_system(15_000, s, dist, 990 + s)
+    out = {}
+    for tt in (1, 2):
+        import torch
+        from gpu_util import to_dev
+        from paper_2005_12351_gb300 import fmm
+        tree = fmm.create_tree(max_leaf=64, precision=precision)
+        tree.set_tuning(p2p_targets=tt)
+        tree.set_sources(to_dev(pos), to_dev(S), s)
+        phi, E = tree.evaluate(5, 0.5)
+        torch.cuda.synchronize()
+        out[tt] = (phi.cpu().numpy(), E.cpu().numpy())
+    t = orc.Tree(pos, 64)
+    t.lists(0.5)
+    phi_o, E_o = t.fmm(S, s, 5)
+    for tt in (1, 2):
+        assert rel_rms(out[tt][1], E_o) < 1e-6 and rel_rms(out[tt][0], phi_o) < 1e-6
+    assert rel_rms(out[1][1], out[2][1]) < 1e-6
