@@ -148,13 +148,16 @@ __global__ void __launch_bounds__(128) k_check_umma(const float *A, const float 
 // of at most W = 128 L columns: when n_L > 128 the columns from 128 on form
 // a second group that needs only the first K-blocks.
 //
-// A tcgen05.mma costs about the same for any N up to ~192, so each K-block
-// takes two instructions: A_hi . [B_hi; 0; B_lo]^T (N = W + N_kb) puts hi.hi
-// in accumulator columns [0, W) and hi.lo in [W, 2 W); A_lo . B_hi^T adds
-// lo.hi to [0, W).  The drain sums the two halves.  Tensor memory: the row
-// accumulators of 2 W columns first (two of them when W <= 96, else one),
-// then 2 to 4 A stages of hi 32 + lo 32 columns at the top.
+// Each K-block takes three instructions into the row's accumulator columns
+// [0, W): A_hi . B_hi^T, A_hi . B_lo^T and A_lo . B_hi^T, each N = N_kb (the
+// operator image holds the hi rows, zero rows up to W, then the lo rows; a
+// row's first instruction takes N = W, so its zero rows clear the columns the
+// first K-block does not reach).
+// Tensor memory: four row accumulators of W columns (two when W > 96), so
+// that the drain of a row overlaps the MMAs of the next ones, then 2 to 4 A
+// stages of hi 32 + lo 32 columns at the top.
 constexpr int kTcStages = 4;
+constexpr int kTcMaxAcc = 4;          // row accumulator buffers in tensor memory
 constexpr int kTcThreads = 320;
 constexpr int kTcMaxKB = 64;          // n_M <= 512
 constexpr int kTcRawStage = 16384;    // 128 rows x 32 FP32
@@ -169,7 +172,7 @@ struct TcArgs {
     unsigned *err;
     long long img_stride;
     int ldM, nM, n_items, ngroups, nkb, Np, b_stage_bytes;
-    // row accumulators: nacc (1 or 2) buffers acc_stride columns apart; A
+    // row accumulators: nacc (2 or 4) buffers acc_stride columns apart; A
     // stages: nas (2..4) of 64 columns from tensor-memory column a_col0
     int nacc, acc_stride, nas, a_col0;
     // column group g covers L columns [128 g, 128 g + g_width[g]) and needs the
@@ -231,15 +234,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
     uint8_t *bst = sm;                                   // kTcStages x b_stage_bytes
     uint8_t *raw = bst + kTcStages * a.b_stage_bytes;    // RS x kTcRawStage
     uint64_t *bars = (uint64_t *)(raw + RS * kTcRawStage);
-    // a_full[4] | b_full[4] | mma_done[4] | acc_empty[2]
-    uint32_t *tslot = (uint32_t *)(bars + 3 * kTcStages + 2);
+    // a_full[4] | b_full[4] | mma_done[4] | acc_empty[kTcMaxAcc]
+    uint32_t *tslot = (uint32_t *)(bars + 3 * kTcStages + kTcMaxAcc);
     volatile int *abort = (volatile int *)(tslot + 1);
-    // per (column group, K-block): instruction descriptor, byte offsets of the
-    // block's hi and lo rows in an operator stage
-    // per (column group, K-block): instruction descriptors of the hi-pair MMA
-    // (N = W + N_kb) and of the lo.hi MMA (N = N_kb), the block's byte offset
-    // in an operator stage
-    uint32_t *t_idw = (uint32_t *)(tslot + 4), *t_idn = t_idw + 2 * kTcMaxKB, *t_boff = t_idn + 2 * kTcMaxKB;
+    // per (column group, K-block): the instruction descriptor (N = N_kb) and the
+    // block's byte offset in an operator stage
+    uint32_t *t_idn = (uint32_t *)(tslot + 4), *t_boff = t_idn + 2 * kTcMaxKB;
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t bar0 = smem_u32(bars);
     auto a_full = [&](int i) { return bar0 + 8 * i; };
@@ -252,8 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             mbar_init(b_full(i), 1);
             mbar_init(mma_done(i), 1);
         }
-        mbar_init(acc_empty(0), 256);
-        mbar_init(acc_empty(1), 256);
+        for (int i = 0; i < kTcMaxAcc; ++i) mbar_init(acc_empty(i), 256);
         *abort = 0;
         fence_mbar_init();
     }
@@ -266,7 +265,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             const int g = e / kTcMaxKB, kb = e % kTcMaxKB;
             if (g >= a.ngroups || kb >= a.g_nkb[g]) continue;
             const int c0 = 128 * g, N = min(a.kb_n[kb], c0 + 128) - c0;
-            t_idw[e] = idesc_tf32_m128(a.g_width[g] + N);
             t_idn[e] = idesc_tf32_m128(N);
             t_boff[e] = (uint32_t)(a.img_off[g][kb] - a.img_off[g][kb & ~3]);
         }
@@ -324,24 +322,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             const int W = a.g_width[pend_g], half = W >> 1;
             const uint32_t col = tmem + lane_off + (uint32_t)(pend_b * a.acc_stride + h * half);
 #pragma unroll
-            for (int c = 0; c < 64; c += 16) {       // hi.hi (+ lo.hi) and hi.lo halves, 4 loads per wait
+            for (int c = 0; c < 64; c += 32) {       // this thread's W / 2 columns, 4 loads per wait
                 if (c < half) {
                     uint32_t v[32];
 #pragma unroll
-                    for (int q = 0; q < 16; q += 8)
-                        if (c + q < half) {
-                            tmem_ld8_nw(col + c + q, v + q);
-                            tmem_ld8_nw(col + W + c + q, v + 16 + q);
-                        }
+                    for (int q = 0; q < 32; q += 8)
+                        if (c + q < half) tmem_ld8_nw(col + c + q, v + q);
 #pragma unroll
-                    for (int q = 0; q < 16; q += 8)
-                        if (c + q < half) {
-                            tmem_wait_ld8(v + q);
-                            tmem_wait_ld8(v + 16 + q);
-                        }
+                    for (int q = 0; q < 32; q += 8)
+                        if (c + q < half) tmem_wait_ld8(v + q);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (c + k < half) acc[c + k] += __uint_as_float(v[k]) + __uint_as_float(v[16 + k]);
+                    for (int k = 0; k < 32; ++k)
+                        if (c + k < half) acc[c + k] += __uint_as_float(v[k]);
                 }
             }
             tc_fence_before();
@@ -412,7 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
         int u = 0, row_seq = 0, sa = 0, pa = 0;       // unit, key rows begun, A stage and its phase
         const uint32_t bst0 = smem_u32(bst);
         const uint64_t dconst = sdesc_sw32(0);     // descriptor bits other than the address
-        const int lg = a.nacc == 2 ? 1 : 0;
+        const int lg = a.nacc == 4 ? 2 : (a.nacc == 2 ? 1 : 0);
         while (cm.ok) {
             const int st = u & 3;
             const bool first = cm.kc == 0;            // first unit of a key row
@@ -427,11 +419,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             const uint32_t abase = tmem + (uint32_t)(a.a_col0 + 64 * sa);
             const uint32_t sbase = bst0 + st * a.b_stage_bytes;
             const int kb0 = 4 * cm.kc, kb1 = min(kb0 + 4, a.g_nkb[cm.g]), e0 = cm.g * kTcMaxKB;
+            const uint32_t idw = idesc_tf32_m128(a.g_width[cm.g]);
+            const uint32_t lo_off = 32u * (uint32_t)a.g_width[cm.g];   // the lo rows start at row W
             for (int kb = kb0; kb < kb1; ++kb) {
-                const uint64_t bd = dconst + ((sbase + t_boff[e0 + kb]) >> 4);
+                const uint32_t bs = sbase + t_boff[e0 + kb];
+                const uint64_t bh = dconst + (bs >> 4), bl = dconst + ((bs + lo_off) >> 4);
                 const uint32_t ah = abase + 8 * (kb - kb0), al = ah + 32;
-                mma_tf32_ts(d, ah, bd, t_idw[e0 + kb], (first && kb == kb0) ? 0u : 1u);
-                mma_tf32_ts(d, al, bd, t_idn[e0 + kb], 1u);
+                const uint32_t idn = t_idn[e0 + kb];
+                // a row's first product overwrites all W columns (the zero rows of
+                // the image clear those its K-block does not reach)
+                const bool clear = first && kb == kb0;
+                mma_tf32_ts(d, ah, bh, clear ? idw : idn, clear ? 0u : 1u);   // hi . hi
+                mma_tf32_ts(d, ah, bl, idn, 1u);                              // hi . lo
+                mma_tf32_ts(d, al, bh, idn, 1u);                              // lo . hi
             }
             mma_commit(mma_done(st));
             if (cm.kc == cm.nkc - 1) ++row_seq;
@@ -669,7 +669,7 @@ constexpr int kSmemOneBlock = 120 * 1024;  // at least this much: two blocks nev
 
 int tc_smem(int b_stage, int rs)
 {
-    return 1024 + kTcStages * b_stage + rs * kTcRawStage + 8 * (3 * kTcStages + 2) + 16 + 3 * 2 * kTcMaxKB * 4;
+    return 1024 + kTcStages * b_stage + rs * kTcRawStage + 8 * (3 * kTcStages + kTcMaxAcc) + 16 + 2 * 2 * kTcMaxKB * 4;
 }
 
 int tc_raw_stages(int b_stage)
@@ -937,10 +937,11 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
     a.n_items = (int)t->tc_chunks * a.ngroups;
     a.nkb = Ly.nkb;
     a.Np = Ly.Np;
-    // two row accumulators of 2 W columns when they leave room for at least
-    // two A stages of 64 columns, else one; the rest of the 512 columns hold A
-    a.nacc = 4 * Ly.g_width[0] + 128 <= 512 ? 2 : 1;
-    a.acc_stride = 2 * Ly.g_width[0];
+    // row accumulators of W columns (hi.hi, hi.lo and lo.hi summed in place):
+    // four when they leave room for two A stages of 64 columns, else two; the
+    // rest of the 512 columns hold A
+    a.nacc = kTcMaxAcc * Ly.g_width[0] + 128 <= 512 ? kTcMaxAcc : 2;
+    a.acc_stride = Ly.g_width[0];
     a.nas = std::min(kTcStages, (512 - a.nacc * a.acc_stride) / 64);
     a.a_col0 = 512 - 64 * a.nas;
     for (int g = 0; g < 2; ++g) {
