@@ -162,6 +162,12 @@ fmm_status fmm_set_sources_batch(fmm_tree *t, const double *positions, const dou
  * derivative tables when theta or p change.  FMM_ETIMEOUT if a bounded
  * device wait gave up (the radix sort of the lists: result still exact; the
  * tensor-core M2L: outputs NaN).
+ * The lists are laid out by target from row positions the traversal hands
+ * out, each row then sorted by source on chip (rows up to 8192 sources); a
+ * longer row sends both lists through a radix sort of (target, source) keys,
+ * with the same result.  The environment variable FMM_ROW_SORT_LIMIT (read
+ * at every list build; 2 .. 8192) lowers that row length, to exercise the
+ * radix path.
  */
 fmm_status fmm_evaluate(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field);

@@ -26,7 +26,8 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_parent, &t->b_child, &t->b_nchild, &t->b_begin, &t->b_end, &t->b_cx,
                    &t->b_cy, &t->b_cz, &t->b_centre, &t->b_half, &t->b_leaves, &t->b_flags,
                    &t->b_scan, &t->b_scan_tmp, &t->b_front, &t->b_front2, &t->b_m2l_raw,
-                   &t->b_p2p_raw, &t->b_counters, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
+                   &t->b_p2p_raw, &t->b_counters, &t->b_tcell, &t->b_rows, &t->b_m2l_slot,
+                   &t->b_p2p_slot, &t->b_long, &t->b_m2l_src, &t->b_m2l_off, &t->b_m2l_didx,
                    &t->b_p2p_src, &t->b_p2p_off, &t->b_lkeys, &t->b_lkeys2, &t->b_lval,
                    &t->b_lval2, &t->b_hash, &t->b_dkeys, &t->b_dsort, &t->b_dsort_h, &t->b_D, &t->b_M, &t->b_L, &t->b_phi,
                    &t->b_E, &t->b_tab_i32, &t->b_tab_u32, &t->b_tc_keys, &t->b_tc_keys2,

@@ -31,6 +31,7 @@ constexpr int kErrKeyRange = 2;
 constexpr int kErrHashFull = 4;
 constexpr int kErrTcTimeout = 8;       // a tensor-core M2L wait gave up (word 1 of b_err)
 constexpr int kErrSortWait = 16;       // a look-back wait of the radix sort gave up
+constexpr int kErrLongRow = 32;        // a row of an interaction list too long for the row sort
 
 inline int ntot(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
 inline int nshell(int k) { return (k + 1) * (k + 2) / 2; }
@@ -241,6 +242,8 @@ struct fmm_tree {
     DevBuf b_ctl;                          // level counts of the cell build
     DevBuf b_ud;                           // upward arrival counters, downward flags
     DevBuf b_front, b_front2, b_m2l_raw, b_p2p_raw, b_counters;
+    DevBuf b_tcell;                        // packed cell records of the traversal
+    DevBuf b_rows, b_m2l_slot, b_p2p_slot, b_long;   // row counts, positions in rows, long rows
     DevBuf b_m2l_src, b_m2l_off, b_m2l_didx, b_p2p_src, b_p2p_off, b_lkeys, b_lkeys2, b_lval, b_lval2;
     DevBuf b_hash, b_dkeys, b_D;
     DevBuf b_dsort, b_dsort_h;             // scratch of the canonical D-key numbering

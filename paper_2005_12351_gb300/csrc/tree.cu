@@ -431,8 +431,10 @@ __global__ void k_level_init(unsigned *ctl, int nsys)
     if (i < kCtlWords) ctl[i] = i == kCtlLevel + 1 ? (unsigned)nsys : 0u;
 }
 
+// Besides the geometry, each cell gets the packed record the traversal reads
+// with one 16-byte load: {cx | level << 21, cy | nchild << 21, cz, child}.
 __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box, double *centre,
-                                double *half, uint32_t *leaf_flag)
+                                double *half, uint32_t *leaf_flag, int4 *tcell)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ncells) return;
@@ -443,6 +445,8 @@ __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box,
     centre[3 * i + 1] = __dadd_rn(bx[1], __dmul_rn((double)(2 * c.cy[i] + 1), h));
     centre[3 * i + 2] = __dadd_rn(bx[2], __dmul_rn((double)(2 * c.cz[i] + 1), h));
     leaf_flag[i] = c.nchild[i] == 0;
+    tcell[i] = make_int4(c.cx[i] | c.level[i] << kLevels, c.cy[i] | c.nchild[i] << kLevels, c.cz[i],
+                         c.child[i]);
 }
 
 __global__ void k_compact_leaves(const uint32_t *flag, const uint32_t *pos, int64_t ncells,
@@ -454,14 +458,16 @@ __global__ void k_compact_leaves(const uint32_t *flag, const uint32_t *pos, int6
 
 // ----------------------------------------------------------- traversal
 // MAC of Eq. (13), exact: centres (2c+1) 2^(21-l) and radii 2^(21-l) in units
-// of the finest half-cell; (rA + rB)^2 < (theta*theta) |dc|^2.
-__device__ __forceinline__ bool mac_accept(const CellArrays &c, int a, int b, double theta2)
+// of the finest half-cell; (rA + rB)^2 < (theta*theta) |dc|^2.  The cells come
+// as the packed records of k_cell_geometry.
+constexpr int kCoordMask = (1 << kLevels) - 1;
+__device__ __forceinline__ bool mac_accept(const int4 A, const int4 B, double theta2)
 {
-    const int la = c.level[a], lb = c.level[b];
+    const int la = A.x >> kLevels, lb = B.x >> kLevels;
     const long long ra = 1ll << (kLevels - la), rb = 1ll << (kLevels - lb);
-    const long long dx = (2ll * c.cx[a] + 1) * ra - (2ll * c.cx[b] + 1) * rb;
-    const long long dy = (2ll * c.cy[a] + 1) * ra - (2ll * c.cy[b] + 1) * rb;
-    const long long dz = (2ll * c.cz[a] + 1) * ra - (2ll * c.cz[b] + 1) * rb;
+    const long long dx = (2ll * (A.x & kCoordMask) + 1) * ra - (2ll * (B.x & kCoordMask) + 1) * rb;
+    const long long dy = (2ll * (A.y & kCoordMask) + 1) * ra - (2ll * (B.y & kCoordMask) + 1) * rb;
+    const long long dz = (2ll * A.z + 1) * ra - (2ll * B.z + 1) * rb;
     const long long d2 = dx * dx + dy * dy + dz * dz;
     const double lhs = (double)((ra + rb) * (ra + rb));
     return lhs < __dmul_rn(theta2, (double)d2);
@@ -485,20 +491,43 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *count, unsigned want)
     return base + incl - want;
 }
 
+// Position of a pair inside its target's row: the lanes that emit a pair of
+// the same list for the same target share one atomic on that row's count.
+// All lanes of the warp call it; lanes with want == false get 0.
+__device__ __forceinline__ unsigned row_slot(unsigned *rows, int a, bool want)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(0xffffffffu, want);
+    unsigned slot = 0;
+    if (want) {
+        const unsigned peers = __match_any_sync(act, a);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(&rows[a], (unsigned)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        slot = base + __popc(peers & ((1u << lane) - 1u));
+    }
+    return slot;
+}
+
 // One round of the breadth-first dual traversal.  The rounds are launched
 // back to back without the host: round r reads its frontier size from
 // counters[kTravFront + r] and adds the next round's to the word after it.
 // counters: 0 = m2l, 1 = p2p, kTravOverflow = a frontier exceeded front_cap
 // (every later round then does nothing).  Outputs beyond a list's capacity
 // are counted but not written; the host grows what overflowed and reruns
-// the whole traversal.
+// the whole traversal.  Each emitted pair also takes the next position in
+// its target's row (rows_m2l / rows_p2p count the pairs of every target),
+// kept in slot_m2l / slot_p2p beside the pair, so that the lists can be laid
+// out by target without a sort by target.
 constexpr int kTravOverflow = 16, kTravFront = 32, kTravMaxRounds = 960;
 // blocks of a traversal round: 8 resident blocks of 256 threads per SM
 constexpr int kTravBlocksPerSM = 8;
 
 __global__ void __launch_bounds__(256)
-k_traverse_round(CellArrays c, int round, double theta2, const int2 *front, unsigned front_cap,
-                 int2 *m2l, unsigned m2l_cap, int2 *p2p, unsigned p2p_cap, int2 *next,
+k_traverse_round(const int4 *__restrict__ tc, int round, double theta2, const int2 *front,
+                 unsigned front_cap, int2 *m2l, uint32_t *slot_m2l, unsigned *rows_m2l, unsigned m2l_cap,
+                 int2 *p2p, uint32_t *slot_p2p, unsigned *rows_p2p, unsigned p2p_cap, int2 *next,
                  unsigned *counters)
 {
     const unsigned nf = counters[kTravFront + round];
@@ -513,32 +542,38 @@ k_traverse_round(CellArrays c, int round, double theta2, const int2 *front, unsi
         const unsigned t = base + threadIdx.x;
         const bool valid = t < nf;
         int a = 0, b = 0, na = 0, nb = 0;
+        int4 A = make_int4(0, 0, 0, 0), B = A;
         if (valid) {
-            a = front[t].x; b = front[t].y;
-            na = c.nchild[a]; nb = c.nchild[b];
+            const int2 pr = front[t];
+            a = pr.x; b = pr.y;
+            A = __ldg(tc + a);
+            B = a == b ? A : __ldg(tc + b);
+            na = A.y >> kLevels; nb = B.y >> kLevels;
         }
         // classify: kind 0 = M2L, 1 = P2P, 2 = open a (all children against b,
         // or all child pairs for a self pair), 3 = open b
         int kind = -1;
         if (valid) {
             if (a == b) kind = na == 0 ? 1 : 2;
-            else if (mac_accept(c, a, b, theta2)) kind = 0;
+            else if (mac_accept(A, B, theta2)) kind = 0;
             else if (na == 0 && nb == 0) kind = 1;
             else if (na == 0) kind = 3;
             else if (nb == 0) kind = 2;
-            else kind = c.level[a] <= c.level[b] ? 2 : 3;
+            else kind = (A.x >> kLevels) <= (B.x >> kLevels) ? 2 : 3;
         }
         const unsigned n_next = kind == 2 ? (a == b ? (unsigned)(na * na) : (unsigned)na)
                                           : (kind == 3 ? (unsigned)nb : 0u);
         const unsigned o_m2l = warp_reserve(&counters[0], kind == 0);
         const unsigned o_p2p = warp_reserve(&counters[1], kind == 1);
         const unsigned o_next = warp_reserve(next_count, n_next);
+        const unsigned r_m2l = row_slot(rows_m2l, a, kind == 0);
+        const unsigned r_p2p = row_slot(rows_p2p, a, kind == 1);
         if (kind == 0) {
-            if (o_m2l < m2l_cap) m2l[o_m2l] = make_int2(a, b);
+            if (o_m2l < m2l_cap) { m2l[o_m2l] = make_int2(a, b); slot_m2l[o_m2l] = r_m2l; }
         } else if (kind == 1) {
-            if (o_p2p < p2p_cap) p2p[o_p2p] = make_int2(a, b);
+            if (o_p2p < p2p_cap) { p2p[o_p2p] = make_int2(a, b); slot_p2p[o_p2p] = r_p2p; }
         } else if (kind == 2) {
-            const int f = c.child[a];
+            const int f = A.w;
             if (a == b) {
                 for (int i = 0; i < na; ++i)
                     for (int j = 0; j < na; ++j) {
@@ -550,10 +585,120 @@ k_traverse_round(CellArrays c, int round, double theta2, const int2 *front, unsi
                     if (o_next + i < front_cap) next[o_next + i] = make_int2(f + i, b);
             }
         } else if (kind == 3) {
-            const int f = c.child[b];
+            const int f = B.w;
             for (int j = 0; j < nb; ++j)
                 if (o_next + j < front_cap) next[o_next + j] = make_int2(a, f + j);
         }
+    }
+}
+
+// ------------------------------------------------- lists laid out by target
+// A pair goes to its row at the position the traversal gave it.
+__global__ void k_list_scatter(const int2 *pairs, const uint32_t *slot, int64_t np,
+                               const uint32_t *off, int32_t *src)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int2 p = pairs[k];
+    src[off[p.x] + slot[k]] = p.y;
+}
+
+// Rows of a list sorted by source, in place, so that every build gives the
+// same lists in the same order whatever order the traversal's atomics took.
+// One warp per row: up to 32 entries in registers, up to kRowWarpMax in the
+// warp's slice of shared memory (bitonic network, padded with ~0); longer rows
+// are queued for k_row_sort_long.  With COUNT, the P2P interactions of every
+// pair (targets x sources) are summed into *inter.
+constexpr int kRowWarpMax = 1024, kRowBlockMax = 8192;
+
+__device__ __forceinline__ void bitonic_smem(uint32_t *v, int n, int tid, int nthreads, bool warp)
+{
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < (n >> 1); i += nthreads) {
+                const int lo = 2 * i - (i & (j - 1)), hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const uint32_t x = v[lo], y = v[hi];
+                if ((x > y) == up) { v[lo] = y; v[hi] = x; }
+            }
+            if (warp) __syncwarp(); else __syncthreads();
+        }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256)
+k_row_sort(const uint32_t *off, int32_t *src, int64_t nrows, const int32_t *cbeg, const int32_t *cend,
+           unsigned long long *inter, uint32_t *long_rows, unsigned *n_long, int warp_max)
+{
+    __shared__ uint32_t buf[8][kRowWarpMax];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    unsigned long long acc = 0;
+    for (int64_t r = blockIdx.x * 8ll + w; r < nrows; r += nwarps) {
+        const uint32_t b0 = off[r], L = off[r + 1] - b0;
+        if (L == 0) continue;
+        if (COUNT) {
+            unsigned long long s = 0;
+            for (uint32_t k = lane; k < L; k += 32) {
+                const int j = src[b0 + k];
+                s += (unsigned long long)(cend[j] - cbeg[j]);
+            }
+            acc += s * (unsigned long long)(cend[r] - cbeg[r]);
+        }
+        if (L == 1) continue;
+        if (L > (uint32_t)warp_max) {
+            if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)r;
+        } else if (L <= 32) {
+            uint32_t v = lane < (int)L ? (uint32_t)src[b0 + lane] : ~0u;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+                    const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                    v = (lower == up) ? min(v, o) : max(v, o);
+                }
+            if (lane < (int)L) src[b0 + lane] = (int32_t)v;
+        } else {
+            int n = 64;
+            while (n < (int)L) n <<= 1;
+            uint32_t *v = buf[w];
+            for (int k = lane; k < n; k += 32) v[k] = k < (int)L ? (uint32_t)src[b0 + k] : ~0u;
+            __syncwarp();
+            bitonic_smem(v, n, lane, 32, true);
+            for (int k = lane; k < (int)L; k += 32) src[b0 + k] = (int32_t)v[k];
+            __syncwarp();
+        }
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && acc) atomicAdd(inter, acc);
+    }
+}
+
+// The queued long rows, one block each; a row longer than block_max (at most
+// kRowBlockMax) sets kErrLongRow in *err and is left for the host, which
+// then sorts the whole list by (target, source) with the radix sort.
+__global__ void __launch_bounds__(1024)
+k_row_sort_long(const uint32_t *off, int32_t *src, const uint32_t *long_rows, const unsigned *n_long,
+                int *err, int block_max)
+{
+    __shared__ uint32_t v[kRowBlockMax];
+    const unsigned nl = *n_long;
+    for (unsigned q = blockIdx.x; q < nl; q += gridDim.x) {
+        const uint32_t r = long_rows[q], b0 = off[r], L = off[r + 1] - b0;
+        if (L > (uint32_t)block_max) {
+            if (threadIdx.x == 0) atomicOr(err, kErrLongRow);
+            continue;
+        }
+        int n = 64;
+        while (n < (int)L) n <<= 1;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) v[k] = k < (int)L ? (uint32_t)src[b0 + k] : ~0u;
+        __syncthreads();
+        bitonic_smem(v, n, threadIdx.x, blockDim.x, false);
+        for (int k = threadIdx.x; k < (int)L; k += blockDim.x) src[b0 + k] = (int32_t)v[k];
+        __syncthreads();
     }
 }
 
@@ -612,37 +757,54 @@ __device__ __forceinline__ uint64_t hash64(uint64_t x)
     return x;
 }
 
-__global__ void k_offset_keys(CellArrays c, const uint64_t *pair_keys, int64_t np, int cbits,
+// Offset keys of the M2L pairs, one warp per target row (CSR order): the
+// key of a pair is its level gap, which side is finer and the centre offset
+// in finer half-cells; equal keys share one derivative row.
+__global__ void k_offset_keys(CellArrays c, const int32_t *off, const int32_t *src, int64_t nrows,
                               unsigned long long *table, uint32_t hmask, uint32_t *slot_of,
                               int *err, unsigned *max_gap)
 {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const int a = (int)(pair_keys[k] >> cbits), b = (int)(pair_keys[k] & ((1ull << cbits) - 1ull));
-    const int la = c.level[a], lb = c.level[b], lf = la > lb ? la : lb;
-    const long long sa = 1ll << (lf - la), sb = 1ll << (lf - lb);
-    long long d[3] = {(2ll * c.cx[a] + 1) * sa - (2ll * c.cx[b] + 1) * sb,
-                      (2ll * c.cy[a] + 1) * sa - (2ll * c.cy[b] + 1) * sb,
-                      (2ll * c.cz[a] + 1) * sa - (2ll * c.cz[b] + 1) * sb};
-    const int gap = la > lb ? la - lb : lb - la;
-    if (gap) atomicMax(max_gap, (unsigned)gap);
-    uint64_t key = (uint64_t)gap << 52 | (uint64_t)(la > lb) << 51;
-    for (int i = 0; i < 3; ++i) {
-        if (d[i] < -kKeyBias || d[i] >= kKeyBias) { atomicOr(err, kErrKeyRange); slot_of[k] = 0; return; }
-        key |= (uint64_t)(d[i] + kKeyBias) << (34 - 17 * i);
-    }
-    uint32_t h = (uint32_t)hash64(key) & hmask;
-    for (uint32_t probe = 0; probe <= hmask; ++probe) {
-        unsigned long long cur = table[h];
-        if (cur == key) { slot_of[k] = h; return; }
-        if (cur == ~0ull) {
-            unsigned long long prev = atomicCAS(&table[h], ~0ull, (unsigned long long)key);
-            if (prev == ~0ull || prev == key) { slot_of[k] = h; return; }
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; a < nrows; a += nwarps) {
+        const int k0 = off[a], k1 = off[a + 1];
+        if (k0 == k1) continue;
+        const int la = c.level[a];
+        const long long ax = 2ll * c.cx[a] + 1, ay = 2ll * c.cy[a] + 1, az = 2ll * c.cz[a] + 1;
+        unsigned gmax = 0;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const int b = src[k];
+            const int lb = c.level[b], lf = la > lb ? la : lb;
+            const long long sa = 1ll << (lf - la), sb = 1ll << (lf - lb);
+            long long d[3] = {ax * sa - (2ll * c.cx[b] + 1) * sb, ay * sa - (2ll * c.cy[b] + 1) * sb,
+                              az * sa - (2ll * c.cz[b] + 1) * sb};
+            const int gap = la > lb ? la - lb : lb - la;
+            gmax = gap > (int)gmax ? (unsigned)gap : gmax;
+            uint64_t key = (uint64_t)gap << 52 | (uint64_t)(la > lb) << 51;
+            bool bad = false;
+            for (int i = 0; i < 3; ++i) {
+                if (d[i] < -kKeyBias || d[i] >= kKeyBias) { bad = true; break; }
+                key |= (uint64_t)(d[i] + kKeyBias) << (34 - 17 * i);
+            }
+            if (bad) { atomicOr(err, kErrKeyRange); slot_of[k] = 0; continue; }
+            uint32_t h = (uint32_t)hash64(key) & hmask;
+            bool placed = false;
+            for (uint32_t probe = 0; probe <= hmask; ++probe) {
+                unsigned long long cur = table[h];
+                if (cur == key) { placed = true; break; }
+                if (cur == ~0ull) {
+                    unsigned long long prev = atomicCAS(&table[h], ~0ull, (unsigned long long)key);
+                    if (prev == ~0ull || prev == key) { placed = true; break; }
+                }
+                h = (h + 1) & hmask;
+            }
+            if (!placed) { atomicOr(err, kErrHashFull); h = 0; }
+            slot_of[k] = h;
         }
-        h = (h + 1) & hmask;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        if (lane == 0 && gmax) atomicMax(max_gap, gmax);
     }
-    atomicOr(err, kErrHashFull);
-    slot_of[k] = 0;
 }
 
 __global__ void k_slot_flags(const unsigned long long *table, uint32_t H, uint32_t *flag)
@@ -910,8 +1072,9 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     FMM_TRY(ensure(t, t->b_scan, 4 * (nc + 1)));
     uint32_t *flags = (uint32_t *)t->b_flags.ptr, *posc = (uint32_t *)t->b_scan.ptr;
     cudaMemsetAsync(flags + nc, 0, 4, st);
+    FMM_TRY(ensure(t, t->b_tcell, 16 * nc));
     k_cell_geometry<<<grid(nc, 256), 256, 0, st>>>(c, nc, sbox, (double *)t->b_centre.ptr,
-                                                    (double *)t->b_half.ptr, flags);
+                                                    (double *)t->b_half.ptr, flags, (int4 *)t->b_tcell.ptr);
     exclusive_scan_u32(flags, posc, nc + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
     uint32_t nleaves = 0;
     FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nleaves, posc + nc, 4, cudaMemcpyDeviceToHost, st),
@@ -954,6 +1117,10 @@ fmm_status build_lists(fmm_tree *t, double theta)
     // one batch of launches with one host sync (more batches if not)
     FMM_TRY(ensure(t, t->b_counters, 4 * (kTravFront + kTravMaxRounds + 64)));
     unsigned *cnt = (unsigned *)t->b_counters.ptr;
+    // row counts of both lists: [0, nc] M2L, [nc + 1, 2 nc + 1] P2P (the last
+    // word of each stays 0 and becomes the total under the exclusive scan)
+    FMM_TRY(ensure(t, t->b_rows, 8 * (size_t)(nc + 1)));
+    unsigned *rows = (unsigned *)t->b_rows.ptr;
     const int nsys = (int)t->sys_off.size() - 1;
     size_t m2l_cap = std::max<size_t>(4096, t->m2l_cap_hint), p2p_cap = std::max<size_t>(4096, 40 * (size_t)t->nleaves);
     size_t front_cap = std::max<size_t>({(size_t)4096, (size_t)nsys, 16 * (size_t)t->nleaves,
@@ -963,6 +1130,8 @@ fmm_status build_lists(fmm_tree *t, double theta)
     for (;;) {
         FMM_TRY(grow_keep(t, t->b_m2l_raw, 8 * m2l_cap, 0));
         FMM_TRY(grow_keep(t, t->b_p2p_raw, 8 * p2p_cap, 0));
+        FMM_TRY(grow_keep(t, t->b_m2l_slot, 4 * (t->b_m2l_raw.bytes / 8), 0));
+        FMM_TRY(grow_keep(t, t->b_p2p_slot, 4 * (t->b_p2p_raw.bytes / 8), 0));
         FMM_TRY(grow_keep(t, t->b_front, 8 * front_cap, 0));
         FMM_TRY(grow_keep(t, t->b_front2, 8 * front_cap, 0));
         m2l_cap = t->b_m2l_raw.bytes / 8;
@@ -971,6 +1140,7 @@ fmm_status build_lists(fmm_tree *t, double theta)
         int2 *fr[2] = {(int2 *)t->b_front.ptr, (int2 *)t->b_front2.ptr};
         FMM_TRY(cuda_check(t, cudaMemsetAsync(cnt, 0, 4 * (kTravFront + kTravMaxRounds + 1), st),
                            "counters"));
+        FMM_TRY(cuda_check(t, cudaMemsetAsync(rows, 0, 8 * (size_t)(nc + 1), st), "row counts"));
         k_root_pairs<<<grid(nsys, 128), 128, 0, st>>>(fr[0], nsys, cnt + kTravFront);
         ++t->launches;
         int r = 0;
@@ -980,8 +1150,10 @@ fmm_status build_lists(fmm_tree *t, double theta)
             const int end = std::min(r + batch, kTravMaxRounds);
             for (; r < end; ++r) {
                 k_traverse_round<<<trav_blocks, 256, 0, st>>>(
-                    c, r, theta2, fr[r & 1], (unsigned)front_cap, (int2 *)t->b_m2l_raw.ptr,
-                    (unsigned)m2l_cap, (int2 *)t->b_p2p_raw.ptr, (unsigned)p2p_cap, fr[(r + 1) & 1], cnt);
+                    (const int4 *)t->b_tcell.ptr, r, theta2, fr[r & 1], (unsigned)front_cap,
+                    (int2 *)t->b_m2l_raw.ptr, (uint32_t *)t->b_m2l_slot.ptr, rows, (unsigned)m2l_cap,
+                    (int2 *)t->b_p2p_raw.ptr, (uint32_t *)t->b_p2p_slot.ptr, rows + nc + 1,
+                    (unsigned)p2p_cap, fr[(r + 1) & 1], cnt);
                 ++t->launches;
             }
             FMM_TRY(cuda_check(t, cudaMemcpyAsync(hc.data(), cnt, 4 * (size_t)(kTravFront + r + 1),
@@ -1007,50 +1179,85 @@ fmm_status build_lists(fmm_tree *t, double theta)
     const int64_t nm2l = host_cnt[0], np2p = host_cnt[1];
     t->m2l_cap_hint = (size_t)nm2l + nm2l / 8;
 
-    // ---- sort both lists by (target, source) and build CSR offsets
-    int cbits = 1;
-    while ((1ll << cbits) < nc) ++cbits;
-    const int64_t nmax = std::max(nm2l, np2p);
-    FMM_TRY(ensure(t, t->b_lkeys, 8 * std::max<int64_t>(nmax, 1)));
-    FMM_TRY(ensure(t, t->b_lkeys2, 8 * std::max<int64_t>(nmax, 1)));
-    FMM_TRY(ensure(t, t->b_lval, 4 * std::max<int64_t>(nmax, 1)));
-    FMM_TRY(ensure(t, t->b_lval2, 4 * std::max<int64_t>(nmax, 1)));
-    FMM_TRY(ensure(t, t->b_hist, radix_hist_bytes(nmax)));
-    FMM_TRY(ensure(t, t->b_scan_tmp, scan_scratch_bytes(std::max<int64_t>(nmax, 1 << 20) * 8)));
+    // ---- both lists laid out by target (CSR).  Normally: offsets from the
+    // row counts of the traversal, each pair to the position it was given,
+    // rows sorted by source.  A row too long for the row sort (flag in
+    // counter word 6, seen at the next host sync) sends both lists through
+    // the radix sort of (target, source) keys instead; both give the same
+    // lists.  The sorts report a wait that gave up in counter word 14.
+    FMM_TRY(ensure(t, t->b_scan_tmp, scan_scratch_bytes(std::max<int64_t>(nc + 1, 1 << 20) * 8)));
     FMM_TRY(ensure(t, t->b_m2l_src, 4 * std::max<int64_t>(nm2l, 1)));
     FMM_TRY(ensure(t, t->b_m2l_didx, 4 * std::max<int64_t>(nm2l, 1)));
     FMM_TRY(ensure(t, t->b_m2l_off, 4 * (nc + 1)));
     FMM_TRY(ensure(t, t->b_p2p_src, 4 * std::max<int64_t>(np2p, 1)));
     FMM_TRY(ensure(t, t->b_p2p_off, 4 * (nc + 1)));
-    uint64_t *lk = (uint64_t *)t->b_lkeys.ptr, *lk2 = (uint64_t *)t->b_lkeys2.ptr;
-    uint32_t *lv = (uint32_t *)t->b_lval.ptr, *lv2 = (uint32_t *)t->b_lval2.ptr;
-
-    // P2P first (its keys are not needed afterwards except for the count);
-    // the sorts report a wait that gave up in counter word 14
-    int *sort_err = (int *)(cnt + 14);
+    FMM_TRY(ensure(t, t->b_long, 8 * (size_t)(nc + 1)));
+    int *sort_err = (int *)(cnt + 14), *long_err = (int *)(cnt + 6);
+    unsigned *n_long = cnt + 4;                          // queued long rows: M2L, P2P
+    unsigned long long *inter_d = (unsigned long long *)(cnt + 8);
+    int32_t *m2l_off = (int32_t *)t->b_m2l_off.ptr, *p2p_off = (int32_t *)t->b_p2p_off.ptr;
+    int32_t *m2l_src = (int32_t *)t->b_m2l_src.ptr, *p2p_src = (int32_t *)t->b_p2p_src.ptr;
+    int cbits = 1;
+    while ((1ll << cbits) < nc) ++cbits;
+    // FMM_ROW_SORT_LIMIT (tests) lowers the longest row the row sorts take
+    int row_lim = kRowBlockMax;
+    if (const char *env = getenv("FMM_ROW_SORT_LIMIT")) row_lim = std::min(std::max(2, atoi(env)), kRowBlockMax);
+    auto layout_rows = [&]() {
+        cudaMemsetAsync(cnt + 4, 0, 4 * 6, st);          // words 4 .. 9: long rows, flag, P2P count
+        exclusive_scan_u32(rows, (uint32_t *)m2l_off, nc + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+        exclusive_scan_u32(rows + nc + 1, (uint32_t *)p2p_off, nc + 1, (uint32_t *)t->b_scan_tmp.ptr, st,
+                           &t->launches);
+        uint32_t *lq = (uint32_t *)t->b_long.ptr;
+        const unsigned rgrid = (unsigned)std::min<int64_t>((nc + 7) / 8, 6 * (int64_t)sm_count());
+        if (nm2l > 0)
+            k_list_scatter<<<grid(nm2l, 256), 256, 0, st>>>((const int2 *)t->b_m2l_raw.ptr,
+                                                            (const uint32_t *)t->b_m2l_slot.ptr, nm2l,
+                                                            (const uint32_t *)m2l_off, m2l_src);
+        if (np2p > 0)
+            k_list_scatter<<<grid(np2p, 256), 256, 0, st>>>((const int2 *)t->b_p2p_raw.ptr,
+                                                            (const uint32_t *)t->b_p2p_slot.ptr, np2p,
+                                                            (const uint32_t *)p2p_off, p2p_src);
+        k_row_sort<false><<<rgrid, 256, 0, st>>>((const uint32_t *)m2l_off, m2l_src, nc, c.begin, c.end,
+                                                  nullptr, lq, n_long, std::min(row_lim, kRowWarpMax));
+        k_row_sort<true><<<rgrid, 256, 0, st>>>((const uint32_t *)p2p_off, p2p_src, nc, c.begin, c.end,
+                                                 inter_d, lq + nc + 1, n_long + 1,
+                                                 std::min(row_lim, kRowWarpMax));
+        k_row_sort_long<<<(unsigned)sm_count(), 1024, 0, st>>>((const uint32_t *)m2l_off, m2l_src, lq,
+                                                                n_long, long_err, row_lim);
+        k_row_sort_long<<<(unsigned)sm_count(), 1024, 0, st>>>((const uint32_t *)p2p_off, p2p_src,
+                                                                lq + nc + 1, n_long + 1, long_err, row_lim);
+        t->launches += 6;
+    };
+    auto layout_radix = [&]() -> fmm_status {
+        const int64_t nmax = std::max<int64_t>({nm2l, np2p, 1});
+        FMM_TRY(ensure(t, t->b_lkeys, 8 * nmax));
+        FMM_TRY(ensure(t, t->b_lkeys2, 8 * nmax));
+        FMM_TRY(ensure(t, t->b_lval, 4 * nmax));
+        FMM_TRY(ensure(t, t->b_lval2, 4 * nmax));
+        FMM_TRY(ensure(t, t->b_hist, radix_hist_bytes(nmax)));
+        uint64_t *lk = (uint64_t *)t->b_lkeys.ptr, *lk2 = (uint64_t *)t->b_lkeys2.ptr;
+        uint32_t *lv = (uint32_t *)t->b_lval.ptr, *lv2 = (uint32_t *)t->b_lval2.ptr;
+        cudaMemsetAsync(cnt + 6, 0, 4 * 4, st);          // words 6 .. 9: flag, P2P count
+        k_pack_pairs<<<grid(np2p, 256), 256, 0, st>>>((const int2 *)t->b_p2p_raw.ptr, np2p, cbits, lk, lv);
+        radix_sort_pairs(lk, lv, lk2, lv2, np2p, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err, st,
+                         &t->launches);
+        k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, np2p, cbits, nc, p2p_off);
+        k_unpack_src<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, p2p_src);
+        k_p2p_interactions<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, c, inter_d);
+        t->launches += 4;
+        if (nm2l > 0) {
+            k_pack_pairs<<<grid(nm2l, 256), 256, 0, st>>>((const int2 *)t->b_m2l_raw.ptr, nm2l, cbits, lk, lv);
+            radix_sort_pairs(lk, lv, lk2, lv2, nm2l, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err,
+                             st, &t->launches);
+            k_unpack_src<<<grid(nm2l, 256), 256, 0, st>>>(lk, nm2l, cbits, m2l_src);
+            t->launches += 2;
+        }
+        k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, nm2l, cbits, nc, m2l_off);
+        ++t->launches;
+        return FMM_OK;
+    };
     cudaMemsetAsync(sort_err, 0, 4, st);
-    k_pack_pairs<<<grid(np2p, 256), 256, 0, st>>>((const int2 *)t->b_p2p_raw.ptr, np2p, cbits, lk, lv);
-    radix_sort_pairs(lk, lv, lk2, lv2, np2p, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err, st,
-                     &t->launches);
-    k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, np2p, cbits, nc, (int32_t *)t->b_p2p_off.ptr);
-    k_unpack_src<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, (int32_t *)t->b_p2p_src.ptr);
-    cudaMemsetAsync(cnt + 8, 0, 8, st);
-    k_p2p_interactions<<<grid(np2p, 256), 256, 0, st>>>(lk, np2p, cbits, c,
-                                                        (unsigned long long *)(cnt + 8));
-    t->launches += 4;
-    unsigned long long inter = 0;
-    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&inter, cnt + 8, 8, cudaMemcpyDeviceToHost, st), "p2p count"));
-
-    // M2L
-    if (nm2l > 0) {
-        k_pack_pairs<<<grid(nm2l, 256), 256, 0, st>>>((const int2 *)t->b_m2l_raw.ptr, nm2l, cbits, lk, lv);
-        radix_sort_pairs(lk, lv, lk2, lv2, nm2l, 2 * cbits, (uint32_t *)t->b_hist.ptr, sort_err,
-                         st, &t->launches);
-        k_unpack_src<<<grid(nm2l, 256), 256, 0, st>>>(lk, nm2l, cbits, (int32_t *)t->b_m2l_src.ptr);
-        t->launches += 2;
-    }
-    k_row_offsets<<<grid(nc + 1, 256), 256, 0, st>>>(lk, nm2l, cbits, nc, (int32_t *)t->b_m2l_off.ptr);
-    ++t->launches;
+    layout_rows();
 
     // ---- distinct M2L offsets (rows of the derivative table)
     int64_t ndoff = 0;
@@ -1064,14 +1271,19 @@ fmm_status build_lists(fmm_tree *t, double theta)
             FMM_TRY(ensure(t, t->b_scan, 4 * ((size_t)H + 1)));
             cudaMemsetAsync(t->b_hash.ptr, 0xff, 8 * (size_t)H, st);
             cudaMemsetAsync(t->b_err.ptr, 0, sizeof(int), st);
-            k_offset_keys<<<grid(nm2l, 256), 256, 0, st>>>(c, lk, nm2l, cbits,
-                                                            (unsigned long long *)t->b_hash.ptr,
-                                                            H - 1, (uint32_t *)t->b_m2l_didx.ptr,
-                                                            (int *)t->b_err.ptr, cnt + 12);
+            k_offset_keys<<<(unsigned)std::min<int64_t>((nc + 7) / 8, 8 * (int64_t)sm_count()), 256, 0, st>>>(
+                c, m2l_off, m2l_src, nc, (unsigned long long *)t->b_hash.ptr, H - 1,
+                (uint32_t *)t->b_m2l_didx.ptr, (int *)t->b_err.ptr, cnt + 12);
             ++t->launches;
-            int e = 0;
+            int e = 0, le = 0;
             FMM_TRY(cuda_check(t, cudaMemcpyAsync(&e, t->b_err.ptr, 4, cudaMemcpyDeviceToHost, st), "err"));
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&le, long_err, 4, cudaMemcpyDeviceToHost, st), "rows"));
             FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+            if (le) {
+                FMM_TRY(layout_radix());
+                cudaMemsetAsync(cnt + 12, 0, 4, st);
+                continue;
+            }
             if (e & kErrKeyRange) {
                 t->err = "an accepted M2L offset exceeds 2^16 finer half-cells (theta too small for the tree)";
                 return FMM_EINVAL;
@@ -1111,9 +1323,16 @@ fmm_status build_lists(fmm_tree *t, double theta)
         }
         k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense, rank_of);
     }
-    int serr = 0;
-    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&serr, sort_err, 4, cudaMemcpyDeviceToHost, st), "sort status"));
-    FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+    int serr = 0, le = 0;
+    unsigned long long inter = 0;
+    for (;;) {
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&serr, sort_err, 4, cudaMemcpyDeviceToHost, st), "sort status"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&le, long_err, 4, cudaMemcpyDeviceToHost, st), "rows"));
+        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&inter, inter_d, 8, cudaMemcpyDeviceToHost, st), "p2p count"));
+        FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+        if (!le) break;
+        FMM_TRY(layout_radix());        // a long P2P row with no M2L list to catch it earlier
+    }
     if (serr & kErrSortWait) {
         t->err = "a bounded wait of the radix sort gave up";
         return FMM_ETIMEOUT;

@@ -85,6 +85,27 @@ def test_tree_and_lists_bit_exact(orc, n, dist, ncrit, theta):
     _compare_trees(orc, pos, ncrit, theta)
 
 
+def test_lists_with_rows_longer_than_a_warp_sort(orc):
+    """theta 0.2 on 30,000 uniform points gives M2L rows of about 2,000
+    sources: those rows are sorted by a whole block, and the lists stay
+    bit-exact."""
+    pos = synth.make_system(30_000, 0, "uniform", 230_000)[0]
+    t = orc.Tree(pos, 8)
+    t.lists(0.2)
+    assert np.bincount(t.m2l[:, 0]).max() > 1024
+    _compare_trees(orc, pos, 8, 0.2)
+
+
+@pytest.mark.parametrize("limit", [2, 64])
+def test_lists_when_rows_exceed_the_row_sort(orc, monkeypatch, limit):
+    """Rows longer than the row sort takes send both lists through the radix
+    sort of (target, source) keys; FMM_ROW_SORT_LIMIT lowers that length so
+    that the path runs on ordinary trees.  Same lists either way."""
+    monkeypatch.setenv("FMM_ROW_SORT_LIMIT", str(limit))
+    _compare_trees(orc, synth.make_system(30_000, 0, "plummer", 230_030)[0], 16, 0.5)
+    _compare_trees(orc, synth.make_system(20_000, 0, "uniform", 220_000)[0], 32, 0.5)
+
+
 def test_tree_duplicates_and_tiny(orc):
     pos = np.concatenate([np.repeat([[0.1, 0.2, 0.3]], 300, axis=0), synth.uniform_cube(200, 9)])
     _compare_trees(orc, pos, 16, 0.5)
