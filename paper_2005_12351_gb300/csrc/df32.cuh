@@ -54,6 +54,13 @@ __device__ __forceinline__ df32 df_add(df32 a, df32 b)
 
 __device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df_neg(b)); }
 
+// a + b for a float b
+__device__ __forceinline__ df32 df_addf(df32 a, float b)
+{
+    const df32 s = df_two_sum(a.hi, b);
+    return df_fast2(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
 __device__ __forceinline__ df32 df_mul(df32 a, df32 b)
 {
     const float p = __fmul_rn(a.hi, b.hi);

@@ -56,12 +56,11 @@ __device__ __forceinline__ void axis_powers32(float w, int P, float *out)
 // their own size.  S32 = (float)S, and after the n rows of S32 the rows of
 // S32lo = (float)(S - S32), the moments' low halves for the close pairs that
 // the P2P evaluates in double-float.
-__global__ void k_prep32(const int32_t *leaves, const int32_t *begin, const int32_t *end,
-                         const double *centre, const double *px, const double *py,
-                         const double *pz, const double *S, int nS, int64_t n, float4 *o,
-                         float4 *olo, float *S32)
+__device__ __forceinline__ void prep32_leaf(int c, const int32_t *begin, const int32_t *end,
+                                            const double *centre, const double *px, const double *py,
+                                            const double *pz, const double *S, int nS, int64_t n,
+                                            float4 *o, float4 *olo, float *S32)
 {
-    const int c = leaves[blockIdx.x];
     const double z0 = centre[3 * c], z1 = centre[3 * c + 1], z2 = centre[3 * c + 2];
     const int nS32 = nS == 6 ? 7 : nS;
     float *S32lo = S32 + n * nS32;
@@ -135,11 +134,17 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
         for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
             Ssm[t] = S32[(int64_t)(j0 + t / nS) * nS32 + t % nS];
         __syncthreads();
-        for (int t = threadIdx.x; t < nj * nK1; t += blockDim.x) {
-            const int j = t / nK1, k = t % nK1;
-            const float *a = apow + j * 3 * P1;
-            const int v = mi_at(tb.mi, k < nK ? k : 0);
-            mono[t] = k < nK ? a[mi_nx(v)] * a[P1 + mi_ny(v)] * a[2 * P1 + mi_nz(v)] : 0.0f;
+        // each thread its monomials k (exponents decoded once) for every particle
+        for (int k = threadIdx.x; k < nK1; k += blockDim.x) {
+            int ox = 0, oy = 0, oz = 0;
+            if (k < nK) {
+                const int v = mi_at(tb.mi, k);
+                ox = mi_nx(v); oy = P1 + mi_ny(v); oz = 2 * P1 + mi_nz(v);
+            }
+            for (int j = 0; j < nj; ++j) {
+                const float *a = apow + j * 3 * P1;
+                mono[j * nK1 + k] = k < nK ? a[ox] * a[oy] * a[oz] : 0.0f;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -216,18 +221,22 @@ __device__ __forceinline__ void m2m32_cell(int c, const int32_t *child, const in
     }
 }
 
-// The upward pass of this form in one launch: P2M at leaf b, then the block
-// whose child arrives last at a parent forms the parent's multipole, up to the
-// root (the FP64 form's k_upward, same counters and ordering).
+// The upward pass of this form in one launch: the float offsets and moments
+// of leaf b's particles (prep32_leaf), its P2M, then the block whose child
+// arrives last at a parent forms the parent's multipole, up to the root (the
+// FP64 form's k_upward, same counters and ordering).
 __global__ void __launch_bounds__(128)
 k_upward32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *parent,
            const int32_t *child, const int32_t *nchild, const int32_t *cx, const int32_t *cy,
-           const int32_t *cz, const double *half, const float4 *o, const float *S32, DevTables tb,
-           float *M, unsigned *arrive)
+           const int32_t *cz, const double *half, const double *centre, const double *px,
+           const double *py, const double *pz, const double *S, int nS_in, int64_t n, float4 *o,
+           float *S32, DevTables tb, float *M, unsigned *arrive)
 {
     extern __shared__ float sf[];
     __shared__ int s_go;
     int c = leaves[blockIdx.x];
+    prep32_leaf(c, begin, end, centre, px, py, pz, S, nS_in, n, o, o + n, S32);
+    __syncthreads();
     p2m32_leaf(c, begin, end, half, o, S32, tb, M, sf);
     for (;;) {
         const int pa = parent[c];
@@ -405,45 +414,70 @@ k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t
 // ------------------------------------------------------------------ L2P
 constexpr int kL2PThreads = 128;
 
+// One block per leaf.  A leaf holds fewer particles than the block has
+// threads, so tp = a power of two of thread groups shares the particles (the
+// largest with tp x count <= the block): thread (slice sl, particle jl) sums
+// every tp-th term of particle jl.  The slices run across warps, so a warp's
+// lanes read the same term tables (constant-cache broadcast), and the tp
+// partial sums meet in shared memory in slice order.
 __global__ void __launch_bounds__(kL2PThreads)
 k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
         const float4 *o, const float *L, DevTables tb, int want_phi, int want_field,
         double *phi, double *E)
 {
     extern __shared__ float sf[];
+    __shared__ float part[4][kL2PThreads];
     const int P = tb.p, P1 = tb.p + 1;
     float *Lsm = sf;                                       // [nL]
-    float *a = Lsm + tb.nL + threadIdx.x * 3 * P1;         // this thread's [3][P1]
+    float *apow = Lsm + tb.nL;                             // [particles of a chunk][3][P1]
     const int c = leaves[blockIdx.x];
-    const int b = begin[c], e = end[c];
+    const int b = begin[c], e = end[c], nt = e - b;
     const double h = half[c];
     const float inv_h = (float)(1.0 / h);
     const int eh = ilogb(h);
     const double sphi = ldexp(1.0, -(tb.s + 1) * eh), sfield = ldexp(1.0, -(tb.s + 2) * eh);
+    int tp = 1;
+    while (tp < 32 && 2 * tp * nt <= kL2PThreads) tp *= 2;
+    const int npc = kL2PThreads / tp;
+    const int jl = threadIdx.x % npc, sl = threadIdx.x / npc;
     expand_local(L + (int64_t)c * tb.nLh, tb, Lsm);
-    for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const float4 v = o[j];
-        axis_powers32(v.x * inv_h, P, a);
-        axis_powers32(v.y * inv_h, P, a + P1);
-        axis_powers32(v.z * inv_h, P, a + 2 * P1);
-        if (want_phi) {
-            float f = 0.0f;
-            for (int k = 0; k < tb.nL; ++k)
+    for (int j0 = b; j0 < e; j0 += npc) {
+        const int j = j0 + jl;
+        const bool act = j < e;
+        float *a = apow + jl * 3 * P1;
+        if (act)
+            for (int ax = sl; ax < 3; ax += tp) {
+                const float4 v = o[j];
+                axis_powers32((ax == 0 ? v.x : (ax == 1 ? v.y : v.z)) * inv_h, P, a + ax * P1);
+            }
+        __syncthreads();
+        float f = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+        if (act && want_phi)
+            for (int k = sl; k < tb.nL; k += tp)
                 f = fmaf(a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]], Lsm[k], f);
-            phi[j] = (double)f * sphi;
-        }
-        if (want_field) {
-            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-            for (int k = 0; k < tb.nG; ++k) {
+        if (act && want_field)
+            for (int k = sl; k < tb.nG; k += tp) {
                 const float m = a[x_nx[k]] * a[P1 + x_ny[k]] * a[2 * P1 + x_nz[k]];
                 g0 = fmaf(m, Lsm[tb.l2p_grad[3 * k]], g0);
                 g1 = fmaf(m, Lsm[tb.l2p_grad[3 * k + 1]], g1);
                 g2 = fmaf(m, Lsm[tb.l2p_grad[3 * k + 2]], g2);
             }
-            E[3 * (int64_t)j] = -(double)g0 * sfield;
-            E[3 * (int64_t)j + 1] = -(double)g1 * sfield;
-            E[3 * (int64_t)j + 2] = -(double)g2 * sfield;
+        part[0][threadIdx.x] = f; part[1][threadIdx.x] = g0;
+        part[2][threadIdx.x] = g1; part[3][threadIdx.x] = g2;
+        __syncthreads();
+        if (act && sl == 0) {
+            for (int u = 1; u < tp; ++u) {
+                f += part[0][u * npc + jl]; g0 += part[1][u * npc + jl];
+                g1 += part[2][u * npc + jl]; g2 += part[3][u * npc + jl];
+            }
+            if (want_phi) phi[j] = (double)f * sphi;
+            if (want_field) {
+                E[3 * (int64_t)j] = -(double)g0 * sfield;
+                E[3 * (int64_t)j + 1] = -(double)g1 * sfield;
+                E[3 * (int64_t)j + 2] = -(double)g2 * sfield;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -516,6 +550,94 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     }
 }
 
+// Two FP32 lanes in one 64-bit register (low half = first): the f32x2
+// arithmetic of sm_100 and later, each half rounded as the scalar operation
+// would be, one issue slot for both.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_splat(float a) { return f2_pack(a, a); }
+
+// pair32 for two targets at once (one per half), the same operations in the
+// same order, so that each half's sums are those of pair32; y comes in as
+// the two seeds (0 where the pair is not kept).  Sj holds each source term
+// twice, as pairs.
+template <int S, bool PHI, bool FIELD>
+__device__ __forceinline__ void pair32x2(f2 dx, f2 dy, f2 dz, f2 r2, f2 y, const f2 *Sj, f2 &f, f2 &e0,
+                                         f2 &e1, f2 &e2)
+{
+    y = f2_mul(y, f2_fma(f2_mul(f2_mul(f2_splat(-0.5f), r2), y), y, f2_splat(1.5f)));
+    const f2 y2 = f2_mul(y, y);
+    if (S == 0) {
+        if (PHI) f = f2_fma(Sj[0], y, f);
+        if (FIELD) {
+            const f2 w = f2_mul(Sj[0], f2_mul(y, y2));
+            e0 = f2_fma(w, dx, e0); e1 = f2_fma(w, dy, e1); e2 = f2_fma(w, dz, e2);
+        }
+    } else if (S == 1) {
+        const f2 y3 = f2_mul(y, y2);
+        const f2 sr = f2_fma(Sj[0], dx, f2_fma(Sj[1], dy, f2_mul(Sj[2], dz)));
+        if (PHI) f = f2_fma(f2_mul(sr, f2_splat(-1.0f)), y3, f);
+        if (FIELD) {
+            const f2 nw = f2_mul(f2_mul(f2_splat(-3.0f), sr), f2_mul(y3, y2));   // -w exactly
+            e0 = f2_fma(Sj[0], y3, f2_fma(nw, dx, e0));
+            e1 = f2_fma(Sj[1], y3, f2_fma(nw, dy, e1));
+            e2 = f2_fma(Sj[2], y3, f2_fma(nw, dz, e2));
+        }
+    } else {
+        const f2 y3 = f2_mul(y, y2), y5 = f2_mul(y3, y2);
+        const f2 two = f2_splat(2.0f);
+        const f2 gq0 = f2_fma(f2_mul(two, Sj[0]), dx, f2_fma(Sj[1], dy, f2_mul(Sj[2], dz)));
+        const f2 gq1 = f2_fma(Sj[1], dx, f2_fma(f2_mul(two, Sj[3]), dy, f2_mul(Sj[4], dz)));
+        const f2 gq2 = f2_fma(Sj[2], dx, f2_fma(Sj[4], dy, f2_mul(f2_mul(two, Sj[5]), dz)));
+        const f2 q = f2_mul(f2_splat(0.5f), f2_fma(gq0, dx, f2_fma(gq1, dy, f2_mul(gq2, dz))));
+        const f2 tr = Sj[6];
+        if (PHI) f = f2_add(f, f2_fma(f2_mul(f2_splat(3.0f), q), y5, f2_mul(f2_mul(tr, y3), f2_splat(-1.0f))));
+        if (FIELD) {
+            const f2 na = f2_mul(f2_splat(-3.0f), y5);
+            const f2 w = f2_fma(f2_mul(f2_splat(15.0f), q), f2_mul(y5, y2),
+                                f2_mul(f2_mul(f2_splat(-3.0f), tr), y5));
+            e0 = f2_fma(w, dx, f2_fma(na, gq0, e0));
+            e1 = f2_fma(w, dy, f2_fma(na, gq1, e1));
+            e2 = f2_fma(w, dz, f2_fma(na, gq2, e2));
+        }
+    }
+}
+
 // the same separation as a double-float: (oi - a) by TwoSum, the low parts added
 __device__ __forceinline__ df32 sep_df(float oi, float li, float a, float b)
 {
@@ -524,7 +646,6 @@ __device__ __forceinline__ df32 sep_df(float oi, float li, float a, float b)
 }
 
 constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 768;
 constexpr int kGroups = 64;
 constexpr int kLaneQ = 8;                 // close pairs a thread queues per target
 constexpr double kCloseSpacings = 1.0;    // close: r < this many mean spacings of the target leaf
@@ -532,7 +653,7 @@ constexpr double kCloseSpacings = 1.0;    // close: r < this many mean spacings 
 // TT: targets per thread (1 or 2; the autotuner's tile choice): two share each
 // staged source read, one leaves more threads per target and fewer registers.
 template <int S, bool PHI, bool FIELD, int TT>
-__global__ void __launch_bounds__(kP2PThreads)
+__global__ void __launch_bounds__(kP2PThreads, S == 2 ? 4 : 6)
 k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *off,
         const int32_t *src, const int32_t *level, const int32_t *cx, const int32_t *cy,
         const int32_t *cz, const int32_t *sys, const double *sys_box, const double *half,
@@ -541,21 +662,21 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         double *E_out)
 {
     constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;     // + trace for quadrupoles
-    constexpr int nR = S == 2 ? 8 : (S == 1 ? 2 : 0);           // moments after the first, padded
-    constexpr int CH = S == 2 ? 704 : kP2PChunk;                // static smem stays < 48 KB
+    constexpr int nR2 = (nS - 1 + 1) / 2;                       // float4s of moments after the first
+    constexpr int CH = S == 2 ? 448 : (S == 1 ? 512 : 704);   // 6 blocks per SM for S < 2
     // a round stages at most CHU sources; the slots up to CH take the padding
     // that gives every thread the same number of steps
     constexpr int CHU = CH - kP2PThreads;
-    // staged sources of a round: (x, y, z, S_0) hi position in the target leaf's
-    // frame and first moment, the other moments, the positions' low parts; the
-    // per-thread totals of the final reduction reuse the same bytes once the
-    // last round is done
-    constexpr int kStageFloats = CH * (4 + nR + 3);
+    // staged sources of a round, every value twice (the f32x2 pairs of the
+    // two-target step): PD = (x, x, y, y), QD = (z, z, S_0, S_0) hi position in
+    // the target leaf's frame and first moment, RD = the other moments two to a
+    // float4, then the positions' low parts; the per-thread totals of the final
+    // reduction reuse the same bytes once the last round is done
+    constexpr int kStageFloats = CH * (8 + 4 * nR2 + 3);
     static_assert(kStageFloats >= 2 * 8 * kP2PThreads, "reduction area");
     __shared__ __align__(16) float stage[kStageFloats];
-    float4 *P4 = (float4 *)stage;
-    float *SR = stage + 4 * CH;
-    float *lx = SR + nR * CH, *ly = lx + CH, *lz = ly + CH;
+    float4 *PD = (float4 *)stage, *QD = PD + CH, *RD = QD + CH;
+    float *lx = (float *)(RD + nR2 * CH), *ly = lx + CH, *lz = ly + CH;
     double (*red)[kP2PThreads] = (double (*)[kP2PThreads])stage;
     __shared__ int gbeg[kGroups], gpre[kGroups + 1];
     __shared__ float gdx[kGroups], gdy[kGroups], gdz[kGroups];
@@ -584,7 +705,8 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 oi = act ? o[b + t0 + ti] : zero4;
         const float4 oj = two ? o[b + t0 + ti + h] : oi;
-        double F[2] = {0.0, 0.0}, A[2] = {0.0, 0.0}, B[2] = {0.0, 0.0}, C[2] = {0.0, 0.0};
+        // totals of the tile in double-float: the rounds' FP32 sums and the
+        // close pairs both go in
         df32 cF[2] = {{0.f, 0.f}, {0.f, 0.f}}, cA[2] = {{0.f, 0.f}, {0.f, 0.f}};
         df32 cB[2] = {{0.f, 0.f}, {0.f, 0.f}}, cC[2] = {{0.f, 0.f}, {0.f, 0.f}};
         int qa = 0, qb = 0;                          // close pairs queued for each target
@@ -609,10 +731,14 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                         }
                         const int64_t j = gbeg[lo] + (d - gpre[lo]);
                         float sl[nS], sh[nS];
-                        const float4 P = P4[d];
-                        sh[0] = P.w;
+                        const float4 pd = PD[d], qd = QD[d];
+                        const float4 P = make_float4(pd.x, pd.z, qd.x, qd.z);
+                        sh[0] = qd.z;
 #pragma unroll
-                        for (int a2 = 1; a2 < nS; ++a2) sh[a2] = SR[d * nR + a2 - 1];
+                        for (int a2 = 1; a2 < nS; ++a2) {
+                            const float4 r = RD[d * nR2 + (a2 - 1) / 2];
+                            sh[a2] = (a2 - 1) % 2 ? r.z : r.x;
+                        }
 #pragma unroll
                         for (int a2 = 0; a2 < nS; ++a2) sl[a2] = S32lo[j * nS + a2];
                         df32 &rf = cF[w], &r0 = cA[w], &r1 = cB[w], &r2 = cC[w];
@@ -672,9 +798,10 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             for (int d = tid; d < steps * k; d += kP2PThreads) {
                 if (d >= used) {
                     // padding: a far-away source with zero moments adds exactly 0
-                    P4[d] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+                    PD[d] = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
+                    QD[d] = make_float4(1e18f, 1e18f, 0.0f, 0.0f);
 #pragma unroll
-                    for (int a = 0; a < nR; ++a) SR[d * nR + a] = 0.0f;
+                    for (int a = 0; a < nR2; ++a) RD[d * nR2 + a] = make_float4(0.f, 0.f, 0.f, 0.f);
                     lx[d] = ly[d] = lz[d] = 0.0f;
                     continue;
                 }
@@ -690,74 +817,105 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                 two_sum_lo(v.x, gdx[lo], vl.x, hx, lx[d]);
                 two_sum_lo(v.y, gdy[lo], vl.y, hy, ly[d]);
                 two_sum_lo(v.z, gdz[lo], vl.z, hz, lz[d]);
-                P4[d] = make_float4(hx, hy, hz, S32[(int64_t)j * nS]);
+                const float s0 = S32[(int64_t)j * nS];
+                PD[d] = make_float4(hx, hx, hy, hy);
+                QD[d] = make_float4(hz, hz, s0, s0);
 #pragma unroll
-                for (int a = 0; a < nR; ++a) SR[d * nR + a] = a + 1 < nS ? S32[(int64_t)j * nS + a + 1] : 0.0f;
+                for (int a = 0; a < nR2; ++a) {
+                    const float u = S32[(int64_t)j * nS + 2 * a + 1];
+                    const float v = 2 * a + 2 < nS ? S32[(int64_t)j * nS + 2 * a + 2] : 0.0f;
+                    RD[d * nR2 + a] = make_float4(u, u, v, v);
+                }
             }
             __syncthreads();
             // The pair loop only queues close pairs; they are evaluated when a
             // queue of the warp is full and after the round.  Threads without a
             // target (and the second target of a thread that has one only) run
             // the loop on a copy with a zero close radius; their sums are never read.
-            float f = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, g = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
             const int spx = act ? sp : 0;
             const float c2a = act ? close2 : 0.0f, c2b = two ? close2 : 0.0f;
-            // one step: source slot spx + it k against the thread's two targets
+            // sums of the round: (target a, target b) pairs
+            f2 Fp = 0ull, E0p = 0ull, E1p = 0ull, E2p = 0ull;
+            const f2 OX = f2_pack(oi.x, oj.x), OY = f2_pack(oi.y, oj.y), OZ = f2_pack(oi.z, oj.z);
+            // one step: source slot spx + it k against the thread's targets
+            float f1 = 0.f, e10 = 0.f, e11 = 0.f, e12 = 0.f;    // one target per thread: scalar sums
             auto step = [&](int it2) {
                 const int jj = spx + it2 * k;
-                const float4 P = P4[jj];
-                float Sj[nS];
-                Sj[0] = P.w;
-                if constexpr (nR == 2) {
-                    const float2 r = *(const float2 *)(SR + jj * nR);
-                    Sj[1] = r.x; Sj[2] = r.y;
-                } else if constexpr (nR == 8) {
-                    const float4 r0 = *(const float4 *)(SR + jj * nR);
-                    const float4 r1 = *(const float4 *)(SR + jj * nR + 4);
-                    Sj[1] = r0.x; Sj[2] = r0.y; Sj[3] = r0.z; Sj[4] = r0.w;
-                    Sj[5] = r1.x; Sj[6] = r1.y;
+                if constexpr (TT == 1) {
+                    const float4 pd = PD[jj], qd = QD[jj];
+                    float Sj[nS];
+                    Sj[0] = qd.z;
+#pragma unroll
+                    for (int a = 0; a < nR2; ++a) {
+                        const float4 r = RD[jj * nR2 + a];
+                        Sj[2 * a + 1] = r.x;
+                        if (2 * a + 2 < nS) Sj[2 * a + 2] = r.z;
+                    }
+                    const float dx = oi.x - pd.x, dy = oi.y - pd.z, dz = oi.z - qd.x;
+                    const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    pair32<S, PHI, FIELD>(dx, dy, dz, r2a, r2a >= c2a, Sj, f1, e10, e11, e12);
+                    if (r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
+                    return;
+                }
+                const ulonglong2 pd = reinterpret_cast<const ulonglong2 *>(PD)[jj];
+                const ulonglong2 qd = reinterpret_cast<const ulonglong2 *>(QD)[jj];
+                f2 Sj[nS];
+                Sj[0] = qd.y;
+#pragma unroll
+                for (int a = 0; a < nR2; ++a) {
+                    const ulonglong2 r = reinterpret_cast<const ulonglong2 *>(RD)[jj * nR2 + a];
+                    Sj[2 * a + 1] = r.x;
+                    if (2 * a + 2 < nS) Sj[2 * a + 2] = r.y;
                 }
                 // separations from the rounded leaf-frame coordinates: the error is
                 // ~1 ulp of the leaf size, small next to r for every pair this
                 // loop keeps (the closer ones go to the double-float queue, which
                 // takes the low parts too)
-                const float dx = oi.x - P.x, dy = oi.y - P.y, dz = oi.z - P.z;
-                const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                pair32<S, PHI, FIELD>(dx, dy, dz, r2a, r2a >= c2a, Sj, f, e0, e1, e2);
-                if (r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
-                if constexpr (TT == 2) {
-                    const float ex = oj.x - P.x, ey = oj.y - P.y, ez = oj.z - P.z;
-                    const float r2b = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    pair32<S, PHI, FIELD>(ex, ey, ez, r2b, r2b >= c2b, Sj, g, g0, g1, g2);
-                    if (r2b < c2b && r2b > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
-                }
+                const f2 dx = f2_sub(OX, pd.x), dy = f2_sub(OY, pd.y), dz = f2_sub(OZ, qd.x);
+                const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                const float2 r2s = f2_unpack(r2);
+                const bool ka = r2s.x >= c2a, kb = r2s.y >= c2b;
+                const f2 y = f2_pack(ka ? rsqrt_mufu(r2s.x) : 0.0f, (TT == 2 && kb) ? rsqrt_mufu(r2s.y) : 0.0f);
+                pair32x2<S, PHI, FIELD>(dx, dy, dz, r2, y, Sj, Fp, E0p, E1p, E2p);
+                if (r2s.x < c2a && r2s.x > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
+                if (TT == 2 && r2s.y < c2b && r2s.y > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
             };
             int it = 0;
             while (it < steps) {
                 // two steps, then a look at the queues: they have room for two more
-                for (; it < steps; it += 2) {
+                bool full = false;
+                for (; it + 1 < steps; it += 2) {
                     step(it);
-                    if (it + 1 < steps) step(it + 1);
+                    step(it + 1);
                     if (__any_sync(0xffffffffu, qa > kLaneQ - 2 || qb > kLaneQ - 2)) {
                         it += 2;
+                        full = true;
                         break;
                     }
                 }
+                if (!full && it < steps) step(it++);                 // an odd last step
                 if (__any_sync(0xffffffffu, qa + qb > 0)) flush();   // staged sources change next round
             }
-            F[0] += f; A[0] += e0; B[0] += e1; C[0] += e2;
-            F[1] += g; A[1] += g0; B[1] += g1; C[1] += g2;
+            {
+                if constexpr (TT == 1) {
+                    cF[0] = df_addf(cF[0], f1); cA[0] = df_addf(cA[0], e10);
+                    cB[0] = df_addf(cB[0], e11); cC[0] = df_addf(cC[0], e12);
+                } else {
+                    const float2 f = f2_unpack(Fp), e0 = f2_unpack(E0p), e1 = f2_unpack(E1p), e2 = f2_unpack(E2p);
+                    cF[0] = df_addf(cF[0], f.x); cA[0] = df_addf(cA[0], e0.x);
+                    cB[0] = df_addf(cB[0], e1.x); cC[0] = df_addf(cC[0], e2.x);
+                    cF[1] = df_addf(cF[1], f.y); cA[1] = df_addf(cA[1], e0.y);
+                    cB[1] = df_addf(cB[1], e1.y); cC[1] = df_addf(cC[1], e2.y);
+                }
+            }
             q = s_next_q;
             j_in = s_next_j;
         }
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            F[w] += df_to_double(cF[w]); A[w] += df_to_double(cA[w]);
-            B[w] += df_to_double(cB[w]); C[w] += df_to_double(cC[w]);
-        }
         __syncthreads();
-        red[0][tid] = F[0]; red[1][tid] = A[0]; red[2][tid] = B[0]; red[3][tid] = C[0];
-        red[4][tid] = F[1]; red[5][tid] = A[1]; red[6][tid] = B[1]; red[7][tid] = C[1];
+        red[0][tid] = df_to_double(cF[0]); red[1][tid] = df_to_double(cA[0]);
+        red[2][tid] = df_to_double(cB[0]); red[3][tid] = df_to_double(cC[0]);
+        red[4][tid] = df_to_double(cF[1]); red[5][tid] = df_to_double(cA[1]);
+        red[6][tid] = df_to_double(cB[1]); red[7][tid] = df_to_double(cC[1]);
         __syncthreads();
         if (tid < h) {
 #pragma unroll
@@ -1261,14 +1419,8 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     float4 *o = (float4 *)t->b_o32.ptr;
     float *S32 = (float *)t->b_S32.ptr, *M = (float *)t->b_M32.ptr, *L = (float *)t->b_L32.ptr;
 
-    k_prep32<<<(unsigned)t->nleaves, 128, 0, st>>>(leaves, begin, end, (const double *)t->b_centre.ptr,
-                                                   (const double *)t->b_px.ptr,
-                                                   (const double *)t->b_py.ptr,
-                                                   (const double *)t->b_pz.ptr,
-                                                   (const double *)t->b_S.ptr, t->nS, n, o, o + n,
-                                                   S32);
     {
-        // P2M and M2M in one launch; the arrival counters start (and end) at zero
+        // prep, P2M and M2M in one launch; the arrival counters start (and end) at zero
         cudaMemsetAsync(t->b_ud.ptr, 0, 4 * (size_t)nc, st);
         size_t smem = 4 * std::max<size_t>((size_t)kChunk * 3 * P1 + (size_t)kChunk * (tb.nK + 1) +
                                                (size_t)kChunk * tb.nS,
@@ -1276,9 +1428,11 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         allow_max_dynamic_smem(k_upward32);
         k_upward32<<<(unsigned)t->nleaves, 128, smem, st>>>(
             leaves, begin, end, (const int32_t *)t->b_parent.ptr, (const int32_t *)t->b_child.ptr,
-            (const int32_t *)t->b_nchild.ptr, cx, cy, cz, half, o, S32, tb, M, (unsigned *)t->b_ud.ptr);
+            (const int32_t *)t->b_nchild.ptr, cx, cy, cz, half, (const double *)t->b_centre.ptr,
+            (const double *)t->b_px.ptr, (const double *)t->b_py.ptr, (const double *)t->b_pz.ptr,
+            (const double *)t->b_S.ptr, t->nS, n, o, S32, tb, M, (unsigned *)t->b_ud.ptr);
     }
-    t->launches += 2;
+    t->launches += 1;
     record(t, 7);
     cudaMemsetAsync(L, 0, 4 * (size_t)nc * tb.nLh, st);
     // harmonic M2L: the folded multipoles, for either M2L

@@ -186,45 +186,58 @@ __constant__ int8_t c_nx[kMaxTot], c_ny[kMaxTot], c_nz[kMaxTot];
 // i = first axis with n_i >= 1 (Leibniz' rule on r^2 d_i(1/r) = -R_i / r).
 // Rows are unit-free: D_k(v) at the integer offset v of the key; a pair with
 // finer half-cell u uses u^-(|k|+1) D_k(v), applied exactly as an exponent shift.
+// One warp per distinct offset: the row is built shell by shell in the warp's
+// shared memory (an entry of shell |n| reads shells |n| - 1 and |n| - 2 only,
+// so a shell's entries are independent and the lanes take them side by side),
+// then stored.  Each entry is the same arithmetic as a one-thread recurrence.
 __global__ void k_dtables(const uint64_t *dkeys, int64_t ndoff, int nD, const int32_t *lut,
                           double *D)
 {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    extern __shared__ double dsm[];
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= ndoff) return;
+    double *Dr = dsm + (threadIdx.x >> 5) * (int64_t)nD;
     const uint64_t key = dkeys[r];
     double R[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
         R[i] = (double)((long long)((key >> (34 - 17 * i)) & 0x1ffffull) - kKeyBias);
-    double *Dr = D + r * nD;
     const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
     const double inv_r2 = 1.0 / r2;
-    Dr[0] = rsqrt(r2);
+    if (lane == 0) Dr[0] = rsqrt(r2);
+    __syncwarp();
     const int L = kMaxOrder + 1;
-    for (int idx = 1; idx < nD; ++idx) {
-        const int n[3] = {c_nx[idx], c_ny[idx], c_nz[idx]};
-        const int i = n[0] ? 0 : (n[1] ? 1 : 2);
-        int m[3] = {n[0], n[1], n[2]};
-        m[i] -= 1;
-        double acc = -(2.0 * n[i] - 1.0) * R[i] * Dr[lut[(m[0] * L + m[1]) * L + m[2]]];
-        if (n[i] >= 2) {
-            int q[3] = {m[0], m[1], m[2]};
-            q[i] -= 1;
-            acc -= (double)((n[i] - 1) * (n[i] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j == i || n[j] == 0) continue;
-            int q[3] = {n[0], n[1], n[2]};
-            q[j] -= 1;
-            acc -= 2.0 * n[j] * R[j] * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
-            if (n[j] >= 2) {
-                q[j] -= 1;
-                acc -= (double)(n[j] * (n[j] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+    for (int sh = 1, s0 = 1; s0 < nD; ++sh) {
+        const int s1 = min(nD, (sh + 1) * (sh + 2) * (sh + 3) / 6);      // shell sh: [s0, s1)
+        for (int idx = s0 + lane; idx < s1; idx += 32) {
+            const int n[3] = {c_nx[idx], c_ny[idx], c_nz[idx]};
+            const int i = n[0] ? 0 : (n[1] ? 1 : 2);
+            int m[3] = {n[0], n[1], n[2]};
+            m[i] -= 1;
+            double acc = -(2.0 * n[i] - 1.0) * R[i] * Dr[lut[(m[0] * L + m[1]) * L + m[2]]];
+            if (n[i] >= 2) {
+                int q[3] = {m[0], m[1], m[2]};
+                q[i] -= 1;
+                acc -= (double)((n[i] - 1) * (n[i] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
             }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j == i || n[j] == 0) continue;
+                int q[3] = {n[0], n[1], n[2]};
+                q[j] -= 1;
+                acc -= 2.0 * n[j] * R[j] * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+                if (n[j] >= 2) {
+                    q[j] -= 1;
+                    acc -= (double)(n[j] * (n[j] - 1)) * Dr[lut[(q[0] * L + q[1]) * L + q[2]]];
+                }
+            }
+            Dr[idx] = acc * inv_r2;
         }
-        Dr[idx] = acc * inv_r2;
+        __syncwarp();
+        s0 = s1;
     }
+    for (int k = lane; k < nD; k += 32) D[r * nD + k] = Dr[k];
 }
 
 // per-axis scaled powers d^j / j!, j <= P, then monomials d^k / k! = ax[kx] ay[ky] az[kz]
@@ -285,11 +298,17 @@ __device__ __forceinline__ void p2m_leaf(int c, const int32_t *begin, const int3
         for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
             Ssm[t] = S[(int64_t)j0 * nS + t];
         __syncthreads();
-        for (int t = threadIdx.x; t < nj * nK1; t += blockDim.x) {
-            const int j = t / nK1, k = t % nK1;
-            const double *a = apow + j * 3 * P1;
-            const int v = mi_at(tb.mi, k < nK ? k : 0);
-            mono[t] = k < nK ? a[mi_nx(v)] * a[P1 + mi_ny(v)] * a[2 * P1 + mi_nz(v)] : 0.0;
+        // each thread its monomials k (exponents decoded once) for every particle
+        for (int k = threadIdx.x; k < nK1; k += blockDim.x) {
+            int ox = 0, oy = 0, oz = 0;
+            if (k < nK) {
+                const int v = mi_at(tb.mi, k);
+                ox = mi_nx(v); oy = P1 + mi_ny(v); oz = 2 * P1 + mi_nz(v);
+            }
+            for (int j = 0; j < nj; ++j) {
+                const double *a = apow + j * 3 * P1;
+                mono[j * nK1 + k] = k < nK ? a[ox] * a[oy] * a[oz] : 0.0;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -743,9 +762,11 @@ fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t 
 {
     if (t->d_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D, 8 * (size_t)t->n_doff * tb.nD));
-        k_dtables<<<grid(t->n_doff, 128), 128, 0, t->stream>>>((const uint64_t *)t->b_dkeys.ptr,
-                                                                t->n_doff, tb.nD, lut,
-                                                                (double *)t->b_D.ptr);
+        // warps per block: as many rows of nD doubles as fit in 48 KB, at most 8
+        const int wpb = (int)std::max<int64_t>(1, std::min<int64_t>(8, 49152 / (8 * (int64_t)tb.nD)));
+        k_dtables<<<(unsigned)((t->n_doff + wpb - 1) / wpb), 32 * wpb, 8 * (size_t)wpb * tb.nD,
+                    t->stream>>>((const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, lut,
+                                 (double *)t->b_D.ptr);
         ++t->launches;
         t->d_p = p;
         t->d32_p = -1;

@@ -64,12 +64,19 @@ __global__ void k_bbox(const double *pos, int64_t n, unsigned long long *box, in
             mx[d] = b > mx[d] ? b : mx[d];
         }
     }
-    if ((threadIdx.x & 31) == 0) {
+    // the block's warps through shared memory, then six atomics per block
+    __shared__ unsigned long long s_mm[6][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            atomicMin(&box[d], mn[d]);
-            atomicMax(&box[3 + d], mx[d]);
-        }
+        for (int d = 0; d < 3; ++d) { s_mm[d][warp] = mn[d]; s_mm[3 + d][warp] = mx[d]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int d = threadIdx.x;
+        unsigned long long v = s_mm[d][0];
+        for (int w = 1; w < nw; ++w) v = d < 3 ? (s_mm[d][w] < v ? s_mm[d][w] : v) : (s_mm[d][w] > v ? s_mm[d][w] : v);
+        if (d < 3) atomicMin(&box[d], v); else atomicMax(&box[d], v);
     }
     if (bad) atomicOr(err, kErrNonFinite);
 }
@@ -293,16 +300,69 @@ __device__ __forceinline__ int digit_at(uint64_t key, int level)
 // more room.
 constexpr int kCtlOverflow = 0, kCtlLevel = 1, kCtlWords = 32;
 constexpr int kLevelBatch = 8;                  // levels launched per host round trip
+constexpr int kLevelScanPer = 16;               // child counts per thread of the one-block scan
 
-// child ranges of every (cell of this level, octant), and each cell's child count
+// child ranges of every (cell of this level, octant), and each cell's child
+// count.  When the level has at most as many cells as the grid has warps
+// (the shallow levels, whose cells hold many particles) a warp takes a cell:
+// its seven groups of four lanes each find one octant boundary by a 5-way
+// search (four probes a step); otherwise a thread takes a (cell, octant) and
+// binary-searches both ends of its range.
+__device__ __forceinline__ int first_digit_ge(const uint64_t *keys, int L, int R, int level, int o)
+{
+    while (L < R) {
+        const int mid = (L + R) >> 1;
+        if (digit_at(keys[mid], level) < o) L = mid + 1; else R = mid;
+    }
+    return L;
+}
+
 __global__ void __launch_bounds__(256)
 k_level_ranges(CellArrays c, const unsigned *ctl, int level, int ncrit, const uint64_t *keys,
                int32_t *cb, int32_t *ce, uint32_t *cnt)
 {
     if (ctl[kCtlOverflow]) return;
     const int lb = (int)ctl[kCtlLevel + level];
-    const int64_t n8 = 8 * ((int64_t)ctl[kCtlLevel + level + 1] - lb);
+    const int ncl = (int)ctl[kCtlLevel + level + 1] - lb;
+    const int64_t n8 = 8 * (int64_t)ncl;
     const unsigned lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (ncl <= nwarps) {
+        const int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (wi >= ncl) return;
+        const int cell = lb + (int)wi;
+        const int b = c.begin[cell], e = c.end[cell];
+        if (!(e - b > ncrit && level < kLevels)) {
+            if (lane < 8) { cb[8 * wi + lane] = b; ce[8 * wi + lane] = b; }
+            if (lane == 0) cnt[wi] = 0u;
+            return;
+        }
+        const int g = (int)lane >> 2, q = (int)lane & 3;       // group g finds boundary g + 1
+        int bnd = b;
+        if (g < 7) {
+            const unsigned gm = 0xfu << (4 * g);
+            int L = b, R = e;
+            while (R - L > 4) {
+                const int len = R - L;
+                const bool lt = digit_at(keys[L + (int)(((int64_t)(q + 1) * len) / 5)], level + 1) < g + 1;
+                const int k = __popc(__ballot_sync(gm, lt) & gm);
+                const int nL = k > 0 ? L + (int)(((int64_t)k * len) / 5) + 1 : L;
+                const int nR = k < 4 ? L + (int)(((int64_t)(k + 1) * len) / 5) : R;
+                L = nL;
+                R = nR;
+            }
+            const bool lt = q < R - L && digit_at(keys[L + q], level + 1) < g + 1;
+            bnd = L + __popc(__ballot_sync(gm, lt) & gm);
+        }
+        const int o = (int)(lane & 7);
+        const int bl = __shfl_sync(0xffffffffu, bnd, (4 * (o - 1)) & 31);
+        const int bh = __shfl_sync(0xffffffffu, bnd, (4 * o) & 31);
+        const int lo_i = o == 0 ? b : bl, hi_i = o == 7 ? e : bh;
+        const unsigned m = __ballot_sync(0xffffffffu, lane < 8 && hi_i > lo_i);
+        if (lane < 8) { cb[8 * wi + lane] = lo_i; ce[8 * wi + lane] = hi_i; }
+        if (lane == 0) cnt[wi] = __popc(m);
+        return;
+    }
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n8; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = base + threadIdx.x;
         bool flag = false;
@@ -312,18 +372,8 @@ k_level_ranges(CellArrays c, const unsigned *ctl, int level, int ncrit, const ui
             int lo_i = b, hi_i = b;
             if (e - b > ncrit && level < kLevels) {
                 // first index in [b, e) whose child digit is >= o (resp. >= o + 1)
-                int L = b, R = e;
-                while (L < R) {
-                    const int mid = (L + R) >> 1;
-                    if (digit_at(keys[mid], level + 1) < o) L = mid + 1; else R = mid;
-                }
-                lo_i = L;
-                R = e;
-                while (L < R) {
-                    const int mid = (L + R) >> 1;
-                    if (digit_at(keys[mid], level + 1) <= o) L = mid + 1; else R = mid;
-                }
-                hi_i = L;
+                lo_i = first_digit_ge(keys, b, e, level + 1, o);
+                hi_i = first_digit_ge(keys, lo_i, e, level + 1, o + 1);
                 flag = hi_i > lo_i;
             }
             cb[t] = lo_i;
@@ -348,11 +398,11 @@ k_level_scan(unsigned *ctl, int level, const uint32_t *cnt, uint32_t *off, int64
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < ncl; base += 8 * (int)blockDim.x) {
-        const int i0 = base + 8 * (int)threadIdx.x;
-        uint32_t v[8], sum = 0;
+    for (int base = 0; base < ncl; base += kLevelScanPer * (int)blockDim.x) {
+        const int i0 = base + kLevelScanPer * (int)threadIdx.x;
+        uint32_t v[kLevelScanPer], sum = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kLevelScanPer; ++k) {
             v[k] = i0 + k < ncl ? cnt[i0 + k] : 0u;
             sum += v[k];
         }
@@ -376,7 +426,7 @@ k_level_scan(unsigned *ctl, int level, const uint32_t *cnt, uint32_t *off, int64
         __syncthreads();
         uint32_t ex = carry + (warp ? wsum[warp - 1] : 0u) + x - sum;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kLevelScanPer; ++k) {
             if (i0 + k < ncl) off[i0 + k] = ex;
             ex += v[k];
         }
@@ -473,24 +523,6 @@ __device__ __forceinline__ bool mac_accept(const int4 A, const int4 B, double th
     return lhs < __dmul_rn(theta2, (double)d2);
 }
 
-// Warp-aggregated reservation: every lane asks for `want` slots of one list;
-// one atomic per warp, lanes get consecutive ranges in lane order.
-__device__ __forceinline__ unsigned warp_reserve(unsigned *count, unsigned want)
-{
-    const int lane = threadIdx.x & 31;
-    unsigned incl = want;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned base = 0;
-    if (lane == 31 && total) base = atomicAdd(count, total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    return base + incl - want;
-}
-
 // Position of a pair inside its target's row: the lanes that emit a pair of
 // the same list for the same target share one atomic on that row's count.
 // All lanes of the warp call it; lanes with want == false get 0.
@@ -523,6 +555,7 @@ __device__ __forceinline__ unsigned row_slot(unsigned *rows, int a, bool want)
 constexpr int kTravOverflow = 16, kTravFront = 32, kTravMaxRounds = 960;
 // blocks of a traversal round: 8 resident blocks of 256 threads per SM
 constexpr int kTravBlocksPerSM = 8;
+constexpr int kTravWarps = 8;            // warps of a traversal block (256 threads)
 
 __global__ void __launch_bounds__(256)
 k_traverse_round(const int4 *__restrict__ tc, int round, double theta2, const int2 *front,
@@ -530,13 +563,25 @@ k_traverse_round(const int4 *__restrict__ tc, int round, double theta2, const in
                  int2 *p2p, uint32_t *slot_p2p, unsigned *rows_p2p, unsigned p2p_cap, int2 *next,
                  unsigned *counters)
 {
-    const unsigned nf = counters[kTravFront + round];
-    if (nf == 0 || counters[kTravOverflow]) return;
+    // the frontier size and the overflow flag, read once per block so that the
+    // whole block takes the same way (the loop below has block barriers)
+    __shared__ unsigned s_nf, s_stop;
+    if (threadIdx.x == 0) {
+        s_nf = counters[kTravFront + round];
+        s_stop = s_nf == 0 || counters[kTravOverflow] != 0u;
+    }
+    __syncthreads();
+    const unsigned nf = s_nf;
+    if (s_stop) return;
     if (nf > front_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&counters[kTravOverflow], 1u);
         return;
     }
     unsigned *next_count = &counters[kTravFront + round + 1];
+    // per-warp totals and block bases of the reservation, two sets used in turn
+    __shared__ unsigned s_wsum[2][3][kTravWarps], s_base[2][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int par = 0;
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned base = blockIdx.x * blockDim.x; base < nf; base += stride) {
         const unsigned t = base + threadIdx.x;
@@ -563,9 +608,40 @@ k_traverse_round(const int4 *__restrict__ tc, int round, double theta2, const in
         }
         const unsigned n_next = kind == 2 ? (a == b ? (unsigned)(na * na) : (unsigned)na)
                                           : (kind == 3 ? (unsigned)nb : 0u);
-        const unsigned o_m2l = warp_reserve(&counters[0], kind == 0);
-        const unsigned o_p2p = warp_reserve(&counters[1], kind == 1);
-        const unsigned o_next = warp_reserve(next_count, n_next);
+        // slots in the three outputs: one atomic per block and output (the
+        // counters are shared by the whole grid), lanes in thread order
+        const unsigned want[3] = {kind == 0 ? 1u : 0u, kind == 1 ? 1u : 0u, n_next};
+        unsigned incl[3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            incl[l] = want[l];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl[l], o);
+                if (lane >= o) incl[l] += y;
+            }
+        }
+        unsigned (*wsum)[kTravWarps] = s_wsum[par];
+        if (lane == 31) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) wsum[l][warp] = incl[l];
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int l = threadIdx.x;
+            unsigned run = 0;
+            for (int w = 0; w < kTravWarps; ++w) {
+                const unsigned v = wsum[l][w];
+                wsum[l][w] = run;
+                run += v;
+            }
+            s_base[par][l] = run ? atomicAdd(l == 0 ? &counters[0] : (l == 1 ? &counters[1] : next_count), run) : 0u;
+        }
+        __syncthreads();
+        const unsigned o_m2l = s_base[par][0] + wsum[0][warp] + incl[0] - want[0];
+        const unsigned o_p2p = s_base[par][1] + wsum[1][warp] + incl[1] - want[1];
+        const unsigned o_next = s_base[par][2] + wsum[2][warp] + incl[2] - want[2];
+        par ^= 1;
         const unsigned r_m2l = row_slot(rows_m2l, a, kind == 0);
         const unsigned r_p2p = row_slot(rows_p2p, a, kind == 1);
         if (kind == 0) {
@@ -915,7 +991,7 @@ static void morton_keys(cudaStream_t st, const double *pos, int64_t n, uint64_t 
                         int64_t *launches)
 {
     k_box_init<<<1, 32, 0, st>>>(box_scratch);
-    k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 8 * (int64_t)sm_count()), 256, 0, st>>>(pos, n, box_scratch, err);
+    k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 4 * (int64_t)sm_count()), 256, 0, st>>>(pos, n, box_scratch, err);
     k_box_final<<<1, 1, 0, st>>>(box_scratch, box_out);
     k_keys<<<grid(n, 256), 256, 0, st>>>(pos, n, box_out, keys, idx);
     *launches += 4;
