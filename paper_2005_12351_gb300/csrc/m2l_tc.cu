@@ -537,7 +537,32 @@ __global__ void k_tc_tiles(int T, int slots, const uint32_t *vals, int32_t *tile
     if (q < slots) tile_tgt[q] = q < T ? (int32_t)vals[q] : -1;
 }
 
-// one warp per target: mark the keys of its list in its tile's bitmap
+// The key set of each tile as a bitmap.  One block per tile: the set in
+// shared memory, then written out whole (no memset, no global atomics).
+constexpr int kTcBitsSmemMax = 96 * 1024;
+__global__ void __launch_bounds__(256) k_tc_bits_tile(int T, const int32_t *tile_tgt, const int32_t *m2l_off,
+                                                      const int32_t *didx, int W, uint32_t *bits)
+{
+    extern __shared__ uint32_t sb[];            // [W]
+    const int tile = blockIdx.x;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) sb[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < 128; r += blockDim.x >> 5) {
+        const int w = tile * 128 + r;
+        if (w >= T) break;
+        const int c = tile_tgt[w];
+        for (int e = m2l_off[c] + lane; e < m2l_off[c + 1]; e += 32) {
+            const int d = didx[e];
+            atomicOr(&sb[d >> 5], 1u << (d & 31));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bits[(size_t)tile * W + i] = sb[i];
+}
+
+// The same with global atomics (one warp per target marks the keys of its
+// list), for key sets too large for shared memory.
 __global__ void k_tc_bits(int T, const int32_t *tile_tgt, const int32_t *m2l_off, const int32_t *didx, int W,
                           uint32_t *bits)
 {
@@ -811,11 +836,18 @@ fmm_status build_plan(fmm_tree *t)
                                                          (int32_t *)t->b_tc_tgt.ptr);
     FMM_TRY(ensure(t, t->b_tc_bits, 4 * (size_t)tiles * W));
     FMM_TRY(ensure(t, t->b_tc_wpre, 4 * (size_t)tiles * W));
-    cudaMemsetAsync(t->b_tc_bits.ptr, 0, 4 * (size_t)tiles * W, st);
-    k_tc_bits<<<gridn((int64_t)T * 32, 256), 256, 0, st>>>((int)T, (const int32_t *)t->b_tc_tgt.ptr,
-                                                            (const int32_t *)t->b_m2l_off.ptr,
-                                                            (const int32_t *)t->b_m2l_didx.ptr, (int)W,
-                                                            (uint32_t *)t->b_tc_bits.ptr);
+    if (4 * W <= kTcBitsSmemMax) {
+        allow_max_dynamic_smem(k_tc_bits_tile);
+        k_tc_bits_tile<<<(unsigned)tiles, 256, 4 * (size_t)W, st>>>(
+            (int)T, (const int32_t *)t->b_tc_tgt.ptr, (const int32_t *)t->b_m2l_off.ptr,
+            (const int32_t *)t->b_m2l_didx.ptr, (int)W, (uint32_t *)t->b_tc_bits.ptr);
+    } else {
+        cudaMemsetAsync(t->b_tc_bits.ptr, 0, 4 * (size_t)tiles * W, st);
+        k_tc_bits<<<gridn((int64_t)T * 32, 256), 256, 0, st>>>((int)T, (const int32_t *)t->b_tc_tgt.ptr,
+                                                                (const int32_t *)t->b_m2l_off.ptr,
+                                                                (const int32_t *)t->b_m2l_didx.ptr, (int)W,
+                                                                (uint32_t *)t->b_tc_bits.ptr);
+    }
     for (DevBuf *b : {&t->b_tc_rcnt, &t->b_tc_ccnt, &t->b_tc_roff, &t->b_tc_coff}) {
         FMM_TRY(ensure(t, *b, 4 * (size_t)(tiles + 1)));
         cudaMemsetAsync(b->ptr, 0, 4 * (size_t)(tiles + 1), st);
