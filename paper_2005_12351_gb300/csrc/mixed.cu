@@ -97,9 +97,10 @@ constexpr int kChunk = 32;
 constexpr int kPer = 4;                   // up to 4 * 128 = 512 components per thread block
 constexpr int kMaxSrc = 6;
 
-// One block per leaf; each thread owns up to kPer components with their
-// source-term monomial indices in registers (absent terms hit a zero slot).
-// FP32 sums over groups of 8 particles, FP64 across groups.
+// One block per leaf; each thread owns up to kPer components, with the
+// monomial index of each of a component's source terms taken per chunk
+// (absent terms hit a zero slot).  FP32 sums over groups of 8 particles, FP64
+// across groups.
 __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const int32_t *end,
                                            const double *half, const float4 *o, const float *S32,
                                            const DevTables &tb, float *M, float *sf)
@@ -107,22 +108,14 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
     const int P = tb.p, P1 = tb.p + 1, nK = tb.nK, nK1 = tb.nK + 1, nS = tb.nS;
     float *apow = sf;                              // [chunk][3][P1]
     float *mono = apow + kChunk * 3 * P1;          // [chunk][nK + 1], last = 0
-    float *Ssm = mono + kChunk * nK1;              // [chunk][nS]
+    float *Ssm = mono + kChunk * nK1;              // [chunk][8], padded with zeros
+    Ssm = (float *)(((uintptr_t)Ssm + 15) & ~(uintptr_t)15);
     const int b = begin[c], e = end[c];
     const float inv_h = (float)(1.0 / half[c]);    // a power of two
     const int nS32 = nS == 6 ? 7 : nS;
-    int kt[kPer][kMaxSrc];
     double acc[kPer];
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        acc[u] = 0.0;
-        const int mi = threadIdx.x + u * 128;
-#pragma unroll
-        for (int a = 0; a < kMaxSrc; ++a) {
-            const int k = (mi < tb.nM && a < nS) ? tb.p2m_terms[mi * nS + a] : -1;
-            kt[u][a] = k >= 0 ? k : nK;
-        }
-    }
+    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
     for (int j0 = b; j0 < e; j0 += kChunk) {
         const int nj = min(kChunk, e - j0);
         for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
@@ -131,8 +124,8 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
             const float d = ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
             axis_powers32(-d * inv_h, P, apow + (j * 3 + ax) * P1);
         }
-        for (int t = threadIdx.x; t < nj * nS; t += blockDim.x)
-            Ssm[t] = S32[(int64_t)(j0 + t / nS) * nS32 + t % nS];
+        for (int t = threadIdx.x; t < nj * 8; t += blockDim.x)
+            Ssm[t] = (t & 7) < nS ? S32[(int64_t)(j0 + (t >> 3)) * nS32 + (t & 7)] : 0.0f;
         __syncthreads();
         // each thread its monomials k (exponents decoded once) for every particle
         for (int k = threadIdx.x; k < nK1; k += blockDim.x) {
@@ -149,15 +142,30 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
-            if (threadIdx.x + u * 128 >= tb.nM) break;
+            const int mi = threadIdx.x + u * 128;
+            if (mi >= tb.nM) break;
+            // the monomial index of each source term of component mi (absent: the zero slot)
+            int kt[kMaxSrc];
+#pragma unroll
+            for (int a = 0; a < kMaxSrc; ++a) {
+                const int k = a < nS ? tb.p2m_terms[mi * nS + a] : -1;
+                kt[a] = k >= 0 ? k : nK;
+            }
             for (int j8 = 0; j8 < nj; j8 += 8) {
                 float sum = 0.0f;
                 const int je = min(j8 + 8, nj);
                 for (int j = j8; j < je; ++j) {
-                    const float *mj = mono + j * nK1, *sj = Ssm + j * nS;
-#pragma unroll
-                    for (int a = 0; a < kMaxSrc; ++a)
-                        if (a < nS) sum = fmaf(mj[kt[u][a]], sj[a], sum);
+                    const float *mj = mono + j * nK1;
+                    const float4 s0 = *(const float4 *)(Ssm + 8 * j);
+                    sum = fmaf(mj[kt[0]], s0.x, sum);
+                    if (nS > 1) sum = fmaf(mj[kt[1]], s0.y, sum);
+                    if (nS > 2) sum = fmaf(mj[kt[2]], s0.z, sum);
+                    if (nS > 3) sum = fmaf(mj[kt[3]], s0.w, sum);
+                    if (nS > 4) {
+                        const float2 s1 = *(const float2 *)(Ssm + 8 * j + 4);
+                        sum = fmaf(mj[kt[4]], s1.x, sum);
+                        if (nS > 5) sum = fmaf(mj[kt[5]], s1.y, sum);
+                    }
                 }
                 acc[u] += (double)sum;
             }
@@ -183,41 +191,36 @@ __device__ __forceinline__ float sign_mono(const int *mi, int k, int nx_neg, int
 
 // ------------------------------------------------------------------ M2M
 // parent c from its children (the rows may have been written by other blocks
-// of the same launch: ldcg)
+// of the same launch: ldcg).  The children's sign-monomial tables and rows are
+// staged together, so the block meets once, not twice per child.
 __device__ __forceinline__ void m2m32_cell(int c, const int32_t *child, const int32_t *nchild,
                                            const int32_t *cx, const int32_t *cy, const int32_t *cz,
                                            const DevTables &tb, float *M, float *sf)
 {
-    float *mono = sf;               // [nK]
-    float *Mc = mono + tb.nK;       // [nM]
-    const int nch = nchild[c];
-    double acc[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+    const int nch = nchild[c], nK = tb.nK, nM = tb.nM;
+    float *mono = sf;               // [nch][nK]
+    float *Mc = mono + 8 * nK;      // [nch][nM]
     for (int i = 0; i < nch; ++i) {
         const int ch = child[c] + i;
         // z_p - z_c = (1 - 2 bit) h_c per axis: negative where the child's low bit is 1
         const int bx = cx[ch] & 1, by = cy[ch] & 1, bz = cz[ch] & 1;
-        for (int k = threadIdx.x; k < tb.nK; k += blockDim.x) mono[k] = sign_mono(tb.mi, k, bx, by, bz);
-        for (int t = threadIdx.x; t < tb.nM; t += blockDim.x) Mc[t] = __ldcg(M + (int64_t)ch * row4(tb.nM) + t);
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int ni = threadIdx.x + u * 128;
-            if (ni >= tb.nM) break;
-            float sum = 0.0f;
-            for (int q = tb.m2m_off[ni]; q < tb.m2m_off[ni + 1]; ++q)
-                sum = fmaf(mono[tb.m2m_k[q]], Mc[tb.m2m_q[q]], sum);
-            acc[u] += (double)sum;
-        }
-        __syncthreads();
+        for (int k = threadIdx.x; k < nK; k += blockDim.x) mono[i * nK + k] = sign_mono(tb.mi, k, bx, by, bz);
+        for (int t = threadIdx.x; t < nM; t += blockDim.x) Mc[i * nM + t] = __ldcg(M + (int64_t)ch * row4(nM) + t);
     }
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int ni = threadIdx.x + u * 128;
-        if (ni < tb.nM)
-            M[(int64_t)c * row4(tb.nM) + ni] =
-                (float)ldexp(acc[u], -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s));
+        if (ni >= nM) break;
+        const int q0 = tb.m2m_off[ni], q1 = tb.m2m_off[ni + 1];
+        double acc = 0.0;
+        for (int i = 0; i < nch; ++i) {
+            const float *mo = mono + i * nK, *mc = Mc + i * nM;
+            float sum = 0.0f;
+            for (int q = q0; q < q1; ++q) sum = fmaf(mo[tb.m2m_k[q]], mc[tb.m2m_q[q]], sum);
+            acc += (double)sum;
+        }
+        M[(int64_t)c * row4(nM) + ni] = (float)ldexp(acc, -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s));
     }
 }
 
@@ -225,7 +228,7 @@ __device__ __forceinline__ void m2m32_cell(int c, const int32_t *child, const in
 // of leaf b's particles (prep32_leaf), its P2M, then the block whose child
 // arrives last at a parent forms the parent's multipole, up to the root (the
 // FP64 form's k_upward, same counters and ordering).
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_upward32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const int32_t *parent,
            const int32_t *child, const int32_t *nchild, const int32_t *cx, const int32_t *cy,
            const int32_t *cz, const double *half, const double *centre, const double *px,
@@ -1423,8 +1426,8 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         // prep, P2M and M2M in one launch; the arrival counters start (and end) at zero
         cudaMemsetAsync(t->b_ud.ptr, 0, 4 * (size_t)nc, st);
         size_t smem = 4 * std::max<size_t>((size_t)kChunk * 3 * P1 + (size_t)kChunk * (tb.nK + 1) +
-                                               (size_t)kChunk * tb.nS,
-                                           (size_t)tb.nK + tb.nM);
+                                               (size_t)kChunk * 8 + 4,
+                                           8 * ((size_t)tb.nK + tb.nM));
         allow_max_dynamic_smem(k_upward32);
         k_upward32<<<(unsigned)t->nleaves, 128, smem, st>>>(
             leaves, begin, end, (const int32_t *)t->b_parent.ptr, (const int32_t *)t->b_child.ptr,
