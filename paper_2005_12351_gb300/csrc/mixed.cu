@@ -695,9 +695,15 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     const long long ccx = (2ll * cx[c] + 1) * rc, ccy = (2ll * cy[c] + 1) * rc,
                     ccz = (2ll * cz[c] + 1) * rc;
     const double unit = ldexp(sys_box[4 * sys[c] + 3], -(kLevels + 1));   // finest half-cell
-    // squared close-pair radius of this leaf's targets
-    const double sp_a = kCloseSpacings * 2.0 * half[c] / cbrt((double)max(nt, 1));
-    const float close2 = (float)(sp_a * sp_a);
+    // squared close-pair radius of this leaf's targets (FP64 cube root: formed
+    // once per block, not per thread)
+    __shared__ float s_close2;
+    if (tid == 0) {
+        const double sp_a = kCloseSpacings * 2.0 * half[c] / cbrt((double)max(nt, 1));
+        s_close2 = (float)(sp_a * sp_a);
+    }
+    __syncthreads();
+    const float close2 = s_close2;
     for (int t0 = 0; t0 < nt; t0 += TT * kP2PThreads) {
         const int cnt = min(TT * kP2PThreads, nt - t0);
         const int h = TT == 2 ? (cnt + 1) / 2 : cnt;
