@@ -401,11 +401,18 @@ k_level_scan(unsigned *ctl, int level, const uint32_t *cnt, uint32_t *off, int64
     for (int base = 0; base < ncl; base += kLevelScanPer * (int)blockDim.x) {
         const int i0 = base + kLevelScanPer * (int)threadIdx.x;
         uint32_t v[kLevelScanPer], sum = 0;
+        if (i0 + kLevelScanPer <= ncl) {             // whole: 16-byte loads (i0 is a multiple of 16)
 #pragma unroll
-        for (int k = 0; k < kLevelScanPer; ++k) {
-            v[k] = i0 + k < ncl ? cnt[i0 + k] : 0u;
-            sum += v[k];
+            for (int k = 0; k < kLevelScanPer; k += 4) {
+                const uint4 q = *(const uint4 *)(cnt + i0 + k);
+                v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kLevelScanPer; ++k) v[k] = i0 + k < ncl ? cnt[i0 + k] : 0u;
         }
+#pragma unroll
+        for (int k = 0; k < kLevelScanPer; ++k) sum += v[k];
         uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -425,10 +432,20 @@ k_level_scan(unsigned *ctl, int level, const uint32_t *cnt, uint32_t *off, int64
         }
         __syncthreads();
         uint32_t ex = carry + (warp ? wsum[warp - 1] : 0u) + x - sum;
+        uint32_t o[kLevelScanPer];
 #pragma unroll
         for (int k = 0; k < kLevelScanPer; ++k) {
-            if (i0 + k < ncl) off[i0 + k] = ex;
+            o[k] = ex;
             ex += v[k];
+        }
+        if (i0 + kLevelScanPer <= ncl) {
+#pragma unroll
+            for (int k = 0; k < kLevelScanPer; k += 4)
+                *(uint4 *)(off + i0 + k) = make_uint4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kLevelScanPer; ++k)
+                if (i0 + k < ncl) off[i0 + k] = o[k];
         }
         const uint32_t tot = wsum[nw - 1];
         __syncthreads();
@@ -1335,49 +1352,60 @@ fmm_status build_lists(fmm_tree *t, double theta)
     cudaMemsetAsync(sort_err, 0, 4, st);
     layout_rows();
 
-    // ---- distinct M2L offsets (rows of the derivative table)
+    // ---- distinct M2L offsets (rows of the derivative table).  One host sync
+    // reads everything at once: the hash status, the long-row flag, the
+    // distinct count, the largest level gap and the P2P interaction count;
+    // a full hash table or a long row (rare) redoes the part concerned.
     int64_t ndoff = 0;
+    int serr = 0, le = 0;
+    unsigned long long inter = 0;
+    bool dsort = false;                    // the distinct keys went through the radix sort
     if (nm2l > 0) {
         uint32_t H = 1u << 16;
         while (H < 4 * (uint32_t)std::min<int64_t>(nm2l, 1 << 22) && H < (1u << 20)) H <<= 1;
-        cudaMemsetAsync(cnt + 12, 0, 4, st);
+        uint32_t nd = 0;
         for (;;) {
             FMM_TRY(ensure(t, t->b_hash, 8 * (size_t)H));
             FMM_TRY(ensure(t, t->b_flags, 4 * ((size_t)H + 1)));
             FMM_TRY(ensure(t, t->b_scan, 4 * ((size_t)H + 1)));
+            FMM_TRY(ensure(t, t->b_scan_tmp, scan_scratch_bytes((int64_t)H + 1)));
             cudaMemsetAsync(t->b_hash.ptr, 0xff, 8 * (size_t)H, st);
             cudaMemsetAsync(t->b_err.ptr, 0, sizeof(int), st);
+            cudaMemsetAsync(cnt + 12, 0, 4, st);
             k_offset_keys<<<(unsigned)std::min<int64_t>((nc + 7) / 8, 8 * (int64_t)sm_count()), 256, 0, st>>>(
                 c, m2l_off, m2l_src, nc, (unsigned long long *)t->b_hash.ptr, H - 1,
                 (uint32_t *)t->b_m2l_didx.ptr, (int *)t->b_err.ptr, cnt + 12);
-            ++t->launches;
-            int e = 0, le = 0;
+            uint32_t *flag = (uint32_t *)t->b_flags.ptr, *dense = (uint32_t *)t->b_scan.ptr;
+            cudaMemsetAsync(flag + H, 0, 4, st);
+            k_slot_flags<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, flag);
+            exclusive_scan_u32(flag, dense, (int64_t)H + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
+            t->launches += 2;
+            int e = 0;
+            unsigned gmax = 0;
             FMM_TRY(cuda_check(t, cudaMemcpyAsync(&e, t->b_err.ptr, 4, cudaMemcpyDeviceToHost, st), "err"));
             FMM_TRY(cuda_check(t, cudaMemcpyAsync(&le, long_err, 4, cudaMemcpyDeviceToHost, st), "rows"));
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&gmax, cnt + 12, 4, cudaMemcpyDeviceToHost, st), "gap"));
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nd, dense + H, 4, cudaMemcpyDeviceToHost, st), "ndoff"));
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&inter, inter_d, 8, cudaMemcpyDeviceToHost, st), "p2p count"));
+            FMM_TRY(cuda_check(t, cudaMemcpyAsync(&serr, sort_err, 4, cudaMemcpyDeviceToHost, st), "sort status"));
             FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
             if (le) {
                 FMM_TRY(layout_radix());
-                cudaMemsetAsync(cnt + 12, 0, 4, st);
+                le = 0;
                 continue;
             }
             if (e & kErrKeyRange) {
                 t->err = "an accepted M2L offset exceeds 2^16 finer half-cells (theta too small for the tree)";
                 return FMM_EINVAL;
             }
-            if (!(e & kErrHashFull)) break;
+            if (!(e & kErrHashFull)) {
+                t->max_gap = (int)gmax;
+                break;
+            }
             H <<= 1;
         }
-        uint32_t *flag = (uint32_t *)t->b_flags.ptr, *dense = (uint32_t *)t->b_scan.ptr;
-        cudaMemsetAsync(flag + H, 0, 4, st);
-        k_slot_flags<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, flag);
-        exclusive_scan_u32(flag, dense, (int64_t)H + 1, (uint32_t *)t->b_scan_tmp.ptr, st, &t->launches);
-        uint32_t nd = 0;
-        unsigned gmax = 0;
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&gmax, cnt + 12, 4, cudaMemcpyDeviceToHost, st), "gap"));
-        FMM_TRY(cuda_check(t, cudaMemcpyAsync(&nd, dense + H, 4, cudaMemcpyDeviceToHost, st), "ndoff"));
-        FMM_TRY(cuda_check(t, cudaStreamSynchronize(st), "sync"));
+        uint32_t *dense = (uint32_t *)t->b_scan.ptr;
         ndoff = nd;
-        t->max_gap = (int)gmax;
         FMM_TRY(ensure(t, t->b_dkeys, 8 * std::max<int64_t>(ndoff, 1)));
         k_slot_compact<<<grid(H, 256), 256, 0, st>>>((unsigned long long *)t->b_hash.ptr, H, dense,
                                                        (uint64_t *)t->b_dkeys.ptr);
@@ -1396,12 +1424,13 @@ fmm_status build_lists(fmm_tree *t, double theta)
                              (uint32_t *)t->b_dsort_h.ptr, sort_err, st, &t->launches);
             k_rank_of<<<grid(ndoff, 256), 256, 0, st>>>(vals, ndoff, rank_of);
             t->launches += 3;
+            dsort = true;
         }
         k_slot_to_dense<<<grid(nm2l, 256), 256, 0, st>>>((int32_t *)t->b_m2l_didx.ptr, nm2l, dense, rank_of);
     }
-    int serr = 0, le = 0;
-    unsigned long long inter = 0;
-    for (;;) {
+    // the sort status once more when a radix sort ran after the read above; the
+    // long-row flag and the P2P count when there was no M2L list to read them with
+    while (nm2l == 0 || dsort) {
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(&serr, sort_err, 4, cudaMemcpyDeviceToHost, st), "sort status"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(&le, long_err, 4, cudaMemcpyDeviceToHost, st), "rows"));
         FMM_TRY(cuda_check(t, cudaMemcpyAsync(&inter, inter_d, 8, cudaMemcpyDeviceToHost, st), "p2p count"));
