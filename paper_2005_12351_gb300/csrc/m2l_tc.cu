@@ -861,8 +861,9 @@ fmm_status build_plan(fmm_tree *t)
                        (uint32_t *)t->b_tc_scan.ptr, st, &t->launches);
     t->launches += 4;
     uint32_t R = 0, C = 0;
-    FMM_TRY(d2h_u32(t, (const uint32_t *)t->b_tc_roff.ptr + tiles, &R, 1));
-    FMM_TRY(d2h_u32(t, (const uint32_t *)t->b_tc_coff.ptr + tiles, &C, 1));
+    FMM_TRY(cuda_check(t, cudaMemcpyAsync(&R, (const uint32_t *)t->b_tc_roff.ptr + tiles, 4,
+                                          cudaMemcpyDeviceToHost, st), "copy"));
+    FMM_TRY(d2h_u32(t, (const uint32_t *)t->b_tc_coff.ptr + tiles, &C, 1));      // one sync for both
     t->tc_rows = R;
     t->tc_chunks = C;
     FMM_TRY(ensure(t, t->b_tc_rowkey, 4 * (size_t)R));

@@ -665,22 +665,49 @@ k_traverse_round(const int4 *__restrict__ tc, int round, double theta2, const in
             if (o_m2l < m2l_cap) { m2l[o_m2l] = make_int2(a, b); slot_m2l[o_m2l] = r_m2l; }
         } else if (kind == 1) {
             if (o_p2p < p2p_cap) { p2p[o_p2p] = make_int2(a, b); slot_p2p[o_p2p] = r_p2p; }
-        } else if (kind == 2) {
-            const int f = A.w;
-            if (a == b) {
-                for (int i = 0; i < na; ++i)
-                    for (int j = 0; j < na; ++j) {
-                        const unsigned k = o_next + (unsigned)(i * na + j);
-                        if (k < front_cap) next[k] = make_int2(f + i, f + j);
-                    }
-            } else {
-                for (int i = 0; i < na; ++i)
-                    if (o_next + i < front_cap) next[o_next + i] = make_int2(f + i, b);
+        }
+        // the next frontier: a self pair opens into up to 64 child pairs, far
+        // more than other entries, so a warp holding one writes its lanes'
+        // children together (entry q of the warp's run goes to the lane whose
+        // range holds it); otherwise each lane writes its own
+        const int fc = kind == 2 ? A.w : B.w;
+        if (__any_sync(0xffffffffu, n_next > 16)) {
+            const unsigned wtot = __shfl_sync(0xffffffffu, incl[2], 31);
+            const unsigned wbase = o_next - (incl[2] - want[2]);
+            for (unsigned q0 = 0; q0 < wtot; q0 += 32) {
+                const unsigned q = q0 + lane;
+                // owner: the first lane whose inclusive end exceeds q
+                int lo = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const unsigned e = __shfl_sync(0xffffffffu, incl[2], lo + st - 1);
+                    if (e <= q) lo += st;
+                }
+                const unsigned ex = __shfl_sync(0xffffffffu, incl[2] - want[2], lo);
+                const int oa = __shfl_sync(0xffffffffu, a, lo), ob = __shfl_sync(0xffffffffu, b, lo);
+                const int of = __shfl_sync(0xffffffffu, fc, lo), ok = __shfl_sync(0xffffffffu, kind, lo);
+                const int on = __shfl_sync(0xffffffffu, na, lo);
+                if (q < wtot && wbase + q < front_cap) {
+                    const int k = (int)(q - ex);
+                    int2 v;
+                    if (ok == 3) v = make_int2(oa, of + k);
+                    else if (oa == ob) v = make_int2(of + k / on, of + k % on);
+                    else v = make_int2(of + k, ob);
+                    next[wbase + q] = v;
+                }
             }
+        } else if (kind == 2 && a == b) {
+            for (int i = 0; i < na; ++i)
+                for (int j = 0; j < na; ++j) {
+                    const unsigned k = o_next + (unsigned)(i * na + j);
+                    if (k < front_cap) next[k] = make_int2(fc + i, fc + j);
+                }
+        } else if (kind == 2) {
+            for (int i = 0; i < na; ++i)
+                if (o_next + i < front_cap) next[o_next + i] = make_int2(fc + i, b);
         } else if (kind == 3) {
-            const int f = B.w;
             for (int j = 0; j < nb; ++j)
-                if (o_next + j < front_cap) next[o_next + j] = make_int2(a, f + j);
+                if (o_next + j < front_cap) next[o_next + j] = make_int2(a, fc + j);
         }
     }
 }
