@@ -99,8 +99,8 @@ constexpr int kMaxSrc = 6;
 
 // One block per leaf; each thread owns up to kPer components, with the
 // monomial index of each of a component's source terms taken per chunk
-// (absent terms hit a zero slot).  FP32 sums over groups of 8 particles, FP64
-// across groups.
+// (absent terms hit a zero slot).  FP32 sums over groups of 8 particles,
+// double-float across groups.
 __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const int32_t *end,
                                            const double *half, const float4 *o, const float *S32,
                                            const DevTables &tb, float *M, float *sf)
@@ -113,9 +113,9 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
     const int b = begin[c], e = end[c];
     const float inv_h = (float)(1.0 / half[c]);    // a power of two
     const int nS32 = nS == 6 ? 7 : nS;
-    double acc[kPer];
+    df32 acc[kPer];                                // double-float: no FP64 in the pass
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+    for (int u = 0; u < kPer; ++u) acc[u] = {0.0f, 0.0f};
     for (int j0 = b; j0 < e; j0 += kChunk) {
         const int nj = min(kChunk, e - j0);
         for (int t = threadIdx.x; t < 3 * nj; t += blockDim.x) {
@@ -167,7 +167,7 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
                         if (nS > 5) sum = fmaf(mj[kt[5]], s1.y, sum);
                     }
                 }
-                acc[u] += (double)sum;
+                acc[u] = df_addf(acc[u], sum);
             }
         }
         __syncthreads();
@@ -175,7 +175,7 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int mi = threadIdx.x + u * 128;
-        if (mi < tb.nM) M[(int64_t)c * row4(tb.nM) + mi] = (float)acc[u];
+        if (mi < tb.nM) M[(int64_t)c * row4(tb.nM) + mi] = __fadd_rn(acc[u].hi, acc[u].lo);
     }
 }
 
@@ -213,14 +213,15 @@ __device__ __forceinline__ void m2m32_cell(int c, const int32_t *child, const in
         const int ni = threadIdx.x + u * 128;
         if (ni >= nM) break;
         const int q0 = tb.m2m_off[ni], q1 = tb.m2m_off[ni + 1];
-        double acc = 0.0;
+        df32 acc = {0.0f, 0.0f};
         for (int i = 0; i < nch; ++i) {
             const float *mo = mono + i * nK, *mc = Mc + i * nM;
             float sum = 0.0f;
             for (int q = q0; q < q1; ++q) sum = fmaf(mo[tb.m2m_k[q]], mc[tb.m2m_q[q]], sum);
-            acc += (double)sum;
+            acc = df_addf(acc, sum);
         }
-        M[(int64_t)c * row4(nM) + ni] = (float)ldexp(acc, -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s));
+        const int sc = -(mi_shell(mi_at(tb.mi, ni + tb.m0)) - tb.s);     // a power of two: exact
+        M[(int64_t)c * row4(nM) + ni] = ldexpf(__fadd_rn(acc.hi, acc.lo), sc);
     }
 }
 
@@ -380,60 +381,26 @@ __device__ __forceinline__ void l2l32_cell(int c, int pa, const int32_t *cx, con
     }
 }
 
-// All levels' L2L shifts of this form in one launch (the FP64 form's
-// k_downward: cells claimed in breadth-first order, bounded wait on the
-// parent's flag, NaN where a wait gave up).
-__global__ void __launch_bounds__(128)
-k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t *cy,
-             const int32_t *cz, DevTables tb, float *L, unsigned *ctl)
-{
-    extern __shared__ float sf[];
-    __shared__ int s_c, s_ok;
-    if (threadIdx.x == 0) s_c = (int)atomicAdd(&ctl[0], 1u);
-    __syncthreads();
-    const int c = s_c;
-    if (c >= nc) return;
-    const int pa = parent[c];
-    if (pa >= 0) {
-        if (threadIdx.x == 0) {
-            s_ok = wait_flag(ctl + 1 + pa);
-            __threadfence();
-        }
-        __syncthreads();
-        if (s_ok) {
-            l2l32_cell(c, pa, cx, cy, cz, tb, L, sf);
-        } else {
-            for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x)
-                L[(int64_t)c * tb.nLh + r] = __int_as_float(0x7fc00000);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(ctl + 1 + c, 1u);
-    }
-}
-
 // ------------------------------------------------------------------ L2P
 constexpr int kL2PThreads = 128;
 
-// One block per leaf.  A leaf holds fewer particles than the block has
-// threads, so tp = a power of two of thread groups shares the particles (the
-// largest with tp x count <= the block): thread (slice sl, particle jl) sums
-// every tp-th term of particle jl.  The slices run across warps, so a warp's
-// lanes read the same term tables (constant-cache broadcast), and the tp
-// partial sums meet in shared memory in slice order.
-__global__ void __launch_bounds__(kL2PThreads)
-k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
-        const float4 *o, const float *L, DevTables tb, int want_phi, int want_field,
-        double *phi, double *E)
+// L2P of leaf c by one block of kL2PThreads (shared memory sf: n_L +
+// kL2PThreads x 3 (p + 1) floats).  A leaf holds fewer particles than the
+// block has threads, so tp = a power of two of thread groups shares the
+// particles (the largest with tp x count <= the block): thread (slice sl,
+// particle jl) sums every tp-th term of particle jl.  The slices run across
+// warps, so a warp's lanes read the same term tables (constant-cache
+// broadcast), and the tp partial sums meet in shared memory in slice order.
+// CG: L was written earlier in the same launch (read through L2).
+template <bool CG>
+__device__ __forceinline__ void l2p32_leaf(int c, const int32_t *begin, const int32_t *end, const double *half,
+                                           const float4 *o, const float *L, const DevTables &tb, int want_phi,
+                                           int want_field, double *phi, double *E, float *sf)
 {
-    extern __shared__ float sf[];
     __shared__ float part[4][kL2PThreads];
     const int P = tb.p, P1 = tb.p + 1;
     float *Lsm = sf;                                       // [nL]
     float *apow = Lsm + tb.nL;                             // [particles of a chunk][3][P1]
-    const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c], nt = e - b;
     const double h = half[c];
     const float inv_h = (float)(1.0 / h);
@@ -443,7 +410,7 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
     while (tp < 32 && 2 * tp * nt <= kL2PThreads) tp *= 2;
     const int npc = kL2PThreads / tp;
     const int jl = threadIdx.x % npc, sl = threadIdx.x / npc;
-    expand_local(L + (int64_t)c * tb.nLh, tb, Lsm);
+    expand_local<float, CG>(L + (int64_t)c * tb.nLh, tb, Lsm);
     for (int j0 = b; j0 < e; j0 += npc) {
         const int j = j0 + jl;
         const bool act = j < e;
@@ -482,6 +449,55 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kL2PThreads)
+k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const double *half,
+        const float4 *o, const float *L, DevTables tb, int want_phi, int want_field,
+        double *phi, double *E)
+{
+    extern __shared__ float sf[];
+    l2p32_leaf<false>(leaves[blockIdx.x], begin, end, half, o, L, tb, want_phi, want_field, phi, E, sf);
+}
+
+// All levels' L2L shifts of this form in one launch (the FP64 form's
+// k_downward: cells claimed in breadth-first order, bounded wait on the
+// parent's flag, NaN where a wait gave up), each leaf's L2P right after its
+// shift.
+__global__ void __launch_bounds__(128)
+k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t *cy,
+             const int32_t *cz, DevTables tb, float *L, unsigned *ctl, const int32_t *nchild,
+             const int32_t *begin, const int32_t *end, const double *half, const float4 *o, int want_phi,
+             int want_field, double *phi, double *E)
+{
+    extern __shared__ float sf[];
+    __shared__ int s_c, s_ok;
+    if (threadIdx.x == 0) s_c = (int)atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nc) return;
+    const int pa = parent[c];
+    if (pa >= 0) {
+        if (threadIdx.x == 0) {
+            s_ok = wait_flag(ctl + 1 + pa);
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_ok) {
+            l2l32_cell(c, pa, cx, cy, cz, tb, L, sf);
+        } else {
+            for (int r = threadIdx.x; r < tb.nLh; r += blockDim.x)
+                L[(int64_t)c * tb.nLh + r] = __int_as_float(0x7fc00000);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(ctl + 1 + c, 1u);
+    }
+    // a leaf's expansion is final here: its L2P follows in the same block
+    if (nchild[c] == 0)
+        l2p32_leaf<true>(c, begin, end, half, o, L, tb, want_phi, want_field, phi, E, sf);
 }
 
 // ------------------------------------------------------------------ P2P
@@ -1467,18 +1483,22 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         ++t->launches;
     }
     record(t, 9);
-    // L2L downward, all levels in one launch (flags and claim counter start at zero)
+    // L2L downward, all levels in one launch (flags and claim counter start at
+    // zero), each leaf's L2P in the block that finishes its expansion; a
+    // one-level tree has no shifts and takes the L2P on its own
     if (t->nlevels > 1) {
         unsigned *ctl = (unsigned *)t->b_ud.ptr + nc + 1;
         cudaMemsetAsync(ctl, 0, 4 * (size_t)(nc + 1), st);
-        size_t smem = 4 * (size_t)(tb.nK + tb.nL);
-        k_downward32<<<(unsigned)nc, 128, smem, st>>>(nc, (const int32_t *)t->b_parent.ptr, cx, cy, cz,
-                                                      tb, L, ctl);
+        const size_t smem = 4 * std::max<size_t>((size_t)tb.nK + tb.nL, (size_t)tb.nL + kL2PThreads * 3 * P1);
+        allow_max_dynamic_smem(k_downward32);
+        k_downward32<<<(unsigned)nc, 128, smem, st>>>(
+            nc, (const int32_t *)t->b_parent.ptr, cx, cy, cz, tb, L, ctl, (const int32_t *)t->b_nchild.ptr,
+            begin, end, half, o, want_phi, want_field, (double *)t->b_phi.ptr, (double *)t->b_E.ptr);
         ++t->launches;
-    }
-    record(t, 10);
-    {
-        size_t smem = 4 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
+        record(t, 10);
+    } else {
+        record(t, 10);
+        const size_t smem = 4 * (size_t)(tb.nL + kL2PThreads * 3 * P1);
         allow_max_dynamic_smem(k_l2p32);
         k_l2p32<<<(unsigned)t->nleaves, kL2PThreads, smem, st>>>(
             leaves, begin, end, half, o, L, tb, want_phi, want_field, (double *)t->b_phi.ptr,
