@@ -161,6 +161,7 @@ constexpr int kTcMaxAcc = 4;          // row accumulator buffers in tensor memor
 constexpr int kTcThreads = 320;
 constexpr int kTcMaxKB = 64;          // n_M <= 512
 constexpr int kTcRawStage = 16384;    // 128 rows x 32 FP32
+constexpr int kTcDrainLag = 3;        // units between a row's last staging and its drain
 
 struct TcArgs {
     const int32_t *chunk_rb, *chunk_re;   // rows [rb, re) of each chunk
@@ -306,21 +307,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             cp_async_commit();
             ++ui;
         };
-        // Each key row accumulates in its own tensor-memory buffer (alternating
-        // between two when n_L <= 128); once its MMAs are done it is drained into
-        // FP32 registers (round to nearest), one row behind the staging.  A
-        // chunk's register sum is written to `partial` after its last row.
+        // Each key row accumulates in its own tensor-memory buffer; once its MMAs
+        // are done it is drained into FP32 registers (round to nearest), kTcDrainLag
+        // units behind the staging, so that the staging does not wait for the
+        // MMAs it has just enabled.  A chunk's register sum is written to
+        // `partial` after its last row.  The lag stays below four units (the MMA
+        // completion slots are four: a wait on a slot by parity must not see a
+        // later unit's phase) and below nas + nacc units (the MMAs of a row that
+        // waits for its accumulator must not hold up the staging that frees it).
         float acc[64];
 #pragma unroll
         for (int c = 0; c < 64; ++c) acc[c] = 0.0f;
-        int pend_j = -1, pend_b = 0, pend_end = 0, pend_g = 0;
-        int pend_L = 0, rows_seen = 0;
-        auto drain = [&]() -> bool {
-            const bool ok = mbar_wait(mma_done(pend_L & 3), (unsigned)((pend_L >> 2) & 1), abort);
+        int rows_seen = 0;
+        TcCursor cd = cu;                            // the unit kTcDrainLag behind
+        auto drain = [&](int w) -> bool {
+            const bool ok = mbar_wait(mma_done(w & 3), (unsigned)((w >> 2) & 1), abort);
             if (!__all_sync(0xffffffffu, ok)) return false;
             tc_fence_after();
-            const int W = a.g_width[pend_g], half = W >> 1;
-            const uint32_t col = tmem + lane_off + (uint32_t)(pend_b * a.acc_stride + h * half);
+            const int W = a.g_width[cd.g], half = W >> 1;
+            const int b = rows_seen & (a.nacc - 1);
+            const uint32_t col = tmem + lane_off + (uint32_t)(b * a.acc_stride + h * half);
 #pragma unroll
             for (int c = 0; c < 64; c += 32) {       // this thread's W / 2 columns, 4 loads per wait
                 if (c < half) {
@@ -337,9 +343,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
                 }
             }
             tc_fence_before();
-            mbar_arrive(acc_empty(pend_b));
-            if (pend_end) {
-                float *out = a.partial + ((size_t)pend_j * 128 + i) * a.Np + 128 * pend_g + h * half;
+            mbar_arrive(acc_empty(b));
+            ++rows_seen;
+            if (cd.r + 1 == cd.re) {
+                float *out = a.partial + ((size_t)cd.j * 128 + i) * a.Np + 128 * cd.g + h * half;
 #pragma unroll
                 for (int c = 0; c < 64; c += 4) {
                     if (c < half) {
@@ -348,10 +355,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
                     }
                 }
             }
-            pend_j = -1;
             return true;
         };
+        // drain unit w if it closed a key row, then move the lagging cursor on
+        auto drain_unit = [&](int w) -> bool {
+            if (cd.kc == cd.nkc - 1 && !drain(w)) return false;
+            cur_next(cd, a);
+            return true;
+        };
+        const int lag = a.nacc >= 4 && a.nas >= 2 ? kTcDrainLag : 1;
         int sa = 0;                                  // A stage of unit u
+        bool ok_all = true;
         for (int k = 0; k < RS - 1; ++k) issue();
         while (cu.ok) {
             issue();
@@ -374,7 +388,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             // A stage sa (of nas) is free once the MMAs of unit u - nas are done
             bool ok = u < a.nas ||
                       mbar_wait_backoff(mma_done((u - a.nas) & 3), (unsigned)(((u - a.nas) >> 2) & 1), abort);
-            if (!__all_sync(0xffffffffu, ok)) break;
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok_all = false;
+                break;
+            }
             tc_fence_after();
             const uint32_t acol = tmem + lane_off + (uint32_t)(a.a_col0 + 64 * sa + 16 * h);
             tmem_st16(acol, hi);
@@ -383,19 +400,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
             tc_fence_before();
             mbar_arrive(a_full(sa));
             if (++sa == a.nas) sa = 0;
-            if (pend_j >= 0 && !drain()) break;
-            if (cu.kc == cu.nkc - 1) {
-                pend_j = cu.j;
-                pend_g = cu.g;
-                pend_L = u;
-                pend_b = rows_seen & (a.nacc - 1);
-                pend_end = cu.r + 1 == cu.re;
-                ++rows_seen;
+            if (u - lag >= 0 && !drain_unit(u - lag)) {
+                ok_all = false;
+                break;
             }
             cur_next(cu, a);
             ++u;
         }
-        if (pend_j >= 0 && !*abort) drain();
+        // the units still to drain
+        for (int w = u - lag; ok_all && w < u && !*abort; ++w)
+            if (w >= 0 && !drain_unit(w)) break;
         cp_async_wait<0>();
     } else if (tid == 256) {
         // ------------------------------------------------ MMA issuer
