@@ -110,19 +110,31 @@ __device__ __forceinline__ uint64_t spread3(uint64_t x)
     return x;
 }
 
+// floor(d 2^k) for a double d >= 0 and 2^k a power of two, clamped to the
+// grid (the product is exact, so this is floor((x - lo) scale) of the
+// definition), from d's bits: one FP64 operation per coordinate, the rest
+// integer arithmetic.
+__device__ __forceinline__ uint64_t grid_coord(double d, int k)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    // d = m 2^(e - 1075), subnormals with e = 1 and no implicit bit
+    const uint64_t m = (b & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
+    const int sh = (ef ? ef : 1) - 1075 + k;        // d 2^k = m 2^sh
+    const uint64_t top = (uint64_t)((1 << kLevels) - 1);
+    if (sh >= 0) return sh > 11 ? top : ((m << sh) > top ? top : (m << sh));
+    return sh <= -64 ? 0 : ((m >> -sh) > top ? top : (m >> -sh));
+}
+
 __global__ void k_keys(const double *pos, int64_t n, const double *box, uint64_t *keys,
                        uint32_t *idx)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double scale = ldexp(1.0, kLevels) / box[3];      // a power of two
+    const int k = kLevels - ilogb(box[3]);          // scale = 2^kLevels / side = 2^k
     uint64_t q[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double u = floor(__dmul_rn(__dsub_rn(pos[3 * i + d], box[d]), scale));
-        uint64_t v = (uint64_t)u;
-        q[d] = v > (uint64_t)((1 << kLevels) - 1) ? (uint64_t)((1 << kLevels) - 1) : v;
-    }
+    for (int d = 0; d < 3; ++d) q[d] = grid_coord(__dsub_rn(pos[3 * i + d], box[d]), k);
     keys[i] = spread3(q[0]) << 2 | spread3(q[1]) << 1 | spread3(q[2]);
     idx[i] = (uint32_t)i;
 }
