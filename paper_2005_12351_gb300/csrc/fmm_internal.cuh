@@ -314,18 +314,24 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
 // passes and 16 tile counters (kRadixHead words), then two areas of 256
 // 64-bit status words per tile of 4096 keys.
 constexpr int kRadixMaxPasses = 8;
+constexpr int kRadixTile = 4096;       // keys per one-sweep tile
 constexpr int64_t kRadixHead = kRadixMaxPasses * 256 + 16;
 constexpr int64_t radix_hist_words(int64_t n)
 {
-    return kRadixHead + 4 * 256 * ((n + 4095) / 4096 > 0 ? (n + 4095) / 4096 : 1);
+    return kRadixHead + 4 * 256 * ((n + kRadixTile - 1) / kRadixTile > 0 ? (n + kRadixTile - 1) / kRadixTile : 1);
 }
 size_t radix_hist_bytes(int64_t n);
 // Stable LSD radix sort of (key, value) pairs on bits [0, end_bit), end_bit
 // <= 64, n < 2^32.  The result ends in (keys, vals); (keys2, vals2) are
 // scratch of the same size, hist holds radix_hist_bytes(n).  A bounded wait
 // of the one-sweep passes that gave up sets kErrSortWait in *err (device).
+// counted: the digit counts of every pass are already in hist and the first
+// status area is zero (the caller's key kernel formed them, after zeroing
+// the kRadixHead head words), so the sort skips its counting launch.
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
-                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches);
+                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches,
+                      bool counted = false);
+
 // Per-device set-up of the sort (its kernels loaded, the scatter's shared-
 // memory limit raised); radix_sort_pairs calls it, and callers that must not
 // trigger module loading later call it ahead of time.

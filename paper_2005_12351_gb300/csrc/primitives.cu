@@ -20,7 +20,7 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = kRadixTile / kSortThreads;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 
@@ -315,7 +315,8 @@ void radix_sort_prepare()
 }
 
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t *vals2, int64_t n,
-                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches)
+                      int end_bit, uint32_t *hist, int *err, cudaStream_t st, int64_t *launches,
+                      bool counted)
 {
     if (n <= 1) return;
     const int passes = std::min((end_bit + 7) / 8, kRadixMaxPasses);
@@ -326,11 +327,13 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys2, uint32_t 
     radix_sort_prepare();
     int max_polls = kOsWait;
     if (const char *env = getenv("FMM_SORT_POLLS")) max_polls = std::max(0, atoi(env));
-    cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
-    const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads,
-                                                       4 * (int64_t)sm_count());
-    k_os_hist<<<hgrid, kSortThreads, 0, st>>>(keys, n, passes, ghist, status[0], ntiles);
-    ++*launches;
+    if (!counted) {
+        cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
+        const unsigned hgrid = (unsigned)std::min<int64_t>((n + kSortThreads - 1) / kSortThreads,
+                                                           4 * (int64_t)sm_count());
+        k_os_hist<<<hgrid, kSortThreads, 0, st>>>(keys, n, passes, ghist, status[0], ntiles);
+        ++*launches;
+    }
     uint64_t *ka = keys, *kb = keys2;
     uint32_t *va = vals, *vb = vals2;
     for (int p = 0; p < passes; ++p) {

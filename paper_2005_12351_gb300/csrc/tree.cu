@@ -126,17 +126,36 @@ __device__ __forceinline__ uint64_t grid_coord(double d, int k)
     return sh <= -64 ? 0 : ((m >> -sh) > top ? top : (m >> -sh));
 }
 
-__global__ void k_keys(const double *pos, int64_t n, const double *box, uint64_t *keys,
-                       uint32_t *idx)
+// The keys, and for the radix sort that follows the counts of every 8-bit
+// digit of them (per block in shared memory, then one atomic per digit and
+// block) and the zeroed status words of its first pass.
+__global__ void __launch_bounds__(256)
+k_keys(const double *pos, int64_t n, const double *box, uint64_t *keys, uint32_t *idx,
+       uint32_t *ghist, uint64_t *status0, int64_t nstatus)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int k = kLevels - ilogb(box[3]);          // scale = 2^kLevels / side = 2^k
-    uint64_t q[3];
+    __shared__ uint32_t h[kRadixMaxPasses][256];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) q[d] = grid_coord(__dsub_rn(pos[3 * i + d], box[d]), k);
-    keys[i] = spread3(q[0]) << 2 | spread3(q[1]) << 1 | spread3(q[2]);
-    idx[i] = (uint32_t)i;
+    for (int p = 0; p < kRadixMaxPasses; ++p) h[p][threadIdx.x] = 0;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nstatus;
+         w += (int64_t)gridDim.x * blockDim.x)
+        status0[w] = 0ull;
+    __syncthreads();
+    const int k = kLevels - ilogb(box[3]);          // scale = 2^kLevels / side = 2^k
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t q[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) q[d] = grid_coord(__dsub_rn(pos[3 * i + d], box[d]), k);
+        const uint64_t key = spread3(q[0]) << 2 | spread3(q[1]) << 1 | spread3(q[2]);
+        keys[i] = key;
+        idx[i] = (uint32_t)i;
+#pragma unroll
+        for (int p = 0; p < kRadixMaxPasses; ++p) atomicAdd(&h[p][(unsigned)(key >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kRadixMaxPasses; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
 // ---- systems (a forest of independent octrees, one root per system)
@@ -1042,14 +1061,19 @@ void record(fmm_tree *t, int i)
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// keys of one system, with the digit counts of their radix sort (hist: the
+// sort's scratch, its head zeroed here)
 static void morton_keys(cudaStream_t st, const double *pos, int64_t n, uint64_t *keys,
                         uint32_t *idx, unsigned long long *box_scratch, double *box_out, int *err,
-                        int64_t *launches)
+                        uint32_t *hist, int64_t *launches)
 {
     k_box_init<<<1, 32, 0, st>>>(box_scratch);
     k_bbox<<<(unsigned)std::min<int64_t>(grid(n, 256), 4 * (int64_t)sm_count()), 256, 0, st>>>(pos, n, box_scratch, err);
     k_box_final<<<1, 1, 0, st>>>(box_scratch, box_out);
-    k_keys<<<grid(n, 256), 256, 0, st>>>(pos, n, box_out, keys, idx);
+    cudaMemsetAsync(hist, 0, 4 * (size_t)kRadixHead, st);
+    const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
+    k_keys<<<(unsigned)std::min<int64_t>(grid(n, 256), 4 * (int64_t)sm_count()), 256, 0, st>>>(
+        pos, n, box_out, keys, idx, hist, (uint64_t *)(hist + kRadixHead), ntiles * 256);
     *launches += 4;
 }
 
@@ -1068,8 +1092,8 @@ fmm_status morton_order_raw(cudaStream_t st, const double *pos, int64_t n, uint6
                             unsigned long long *box_scratch, double *box_out, int *err,
                             int64_t *launches)
 {
-    morton_keys(st, pos, n, keys, idx, box_scratch, box_out, err, launches);
-    radix_sort_pairs(keys, idx, keys2, idx2, n, 3 * kLevels, hist, err, st, launches);
+    morton_keys(st, pos, n, keys, idx, box_scratch, box_out, err, hist, launches);
+    radix_sort_pairs(keys, idx, keys2, idx2, n, 3 * kLevels, hist, err, st, launches, true);
     return FMM_OK;
 }
 
@@ -1108,7 +1132,8 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     FMM_TRY(cuda_check(t, cudaMemcpyAsync(off, t->sys_off.data(), 8 * (size_t)(nsys + 1),
                                           cudaMemcpyHostToDevice, st), "system offsets"));
     if (nsys == 1) {
-        morton_keys(st, pos, n, keys, idx, sbox_raw, sbox, (int *)t->b_err.ptr, &t->launches);
+        morton_keys(st, pos, n, keys, idx, sbox_raw, sbox, (int *)t->b_err.ptr, (uint32_t *)t->b_hist.ptr,
+                    &t->launches);
     } else {
         // particle -> system (kept in b_idx2 until the sort needs it)
         FMM_TRY(ensure(t, t->b_lval2, 4 * n));
@@ -1122,7 +1147,8 @@ fmm_status build_tree(fmm_tree *t, const double *pos, const double *mom)
     }
     record(t, 1);
     radix_sort_pairs(keys, idx, (uint64_t *)t->b_keys2.ptr, (uint32_t *)t->b_idx2.ptr, n,
-                     3 * kLevels, (uint32_t *)t->b_hist.ptr, (int *)t->b_err.ptr, st, &t->launches);
+                     3 * kLevels, (uint32_t *)t->b_hist.ptr, (int *)t->b_err.ptr, st, &t->launches,
+                     nsys == 1);                   // one system: k_keys counted the digits
     if (nsys > 1) {
         // stable second pass by system: order = (system, key, original index)
         FMM_TRY(ensure(t, t->b_lkeys, 8 * n));
