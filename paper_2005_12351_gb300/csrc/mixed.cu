@@ -504,7 +504,7 @@ k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t
 // FP32 pair terms on coordinates relative to the target leaf's centre:
 // target o_i, source o_j + (z_B - z_A), the centre offset formed exactly from
 // the integer cell coordinates.  Each thread sums a staged round in FP32 and
-// adds it to FP64 totals; the far field is added in FP64.
+// adds it to double-float totals; the far field is added in FP64.
 //
 // Close pairs.  A target's field error in FP32 pair arithmetic is set by its
 // nearest neighbours (the pair terms grow as r^-(s+2) and the rounding of
@@ -609,7 +609,13 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-__device__ __forceinline__ f2 f2_splat(float a) { return f2_pack(a, a); }
+// a constant in both halves, formed in plain integer arithmetic (foldable and
+// hoistable, unlike a pack through inline assembly)
+__device__ __forceinline__ f2 f2_splat(float a)
+{
+    const f2 u = (f2)__float_as_uint(a);
+    return u | (u << 32);
+}
 
 // pair32 for two targets at once (one per half), the same operations in the
 // same order, so that each half's sums are those of pair32; y comes in as
@@ -737,41 +743,83 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
         int qa = 0, qb = 0;                          // close pairs queued for each target
         // Evaluate this thread's queued close pairs in double-float into its own
         // sums, in queue order; the lanes of a warp work side by side.
+        // Evaluate the warp's queued close pairs in double-float: the queues of
+        // all lanes (each lane's target-0 entries, then its target-1 entries)
+        // are dealt to the lanes 32 at a time, each lane evaluating one pair
+        // into zeroed sums; then every owner adds its pairs' results to its own
+        // sums in queue order, so the result is that of evaluating them in turn.
         auto flush = [&]() {
-            const int ma = __reduce_max_sync(0xffffffffu, (unsigned)max(qa, qb));
+            const unsigned full = 0xffffffffu;
+            const int lane = tid & 31, wtid = tid - lane;
+            __syncwarp();
+            const int myn = qa + qb;
+            int incl = myn;
 #pragma unroll
-            for (int w = 0; w < TT; ++w) {
-                const int nq = w ? qb : qa;
-                const int ot = ti + w * h;                   // this thread's target in the tile
-                const float4 po = (act && (w == 0 || two)) ? o[b + t0 + ot] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 pl = (act && (w == 0 || two)) ? olo[b + t0 + ot] : make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int u = 0; u < ma; ++u) {
-                    if (u < nq) {
-                        const int d = closeq[w][u][tid];
-                        // the staged source's particle index: its group by the prefix of sizes
-                        int lo = 0, hi = s_ngroups - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const int y = __shfl_up_sync(full, incl, o2);
+                if (lane >= o2) incl += y;
+            }
+            const int tot = __shfl_sync(full, incl, 31), excl = incl - myn;
+            for (int c0 = 0; c0 < tot; c0 += 32) {
+                const int e = c0 + lane;
+                // the entry's owner: the first lane whose inclusive count exceeds e
+                int L = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int v = __shfl_sync(full, incl, L + st - 1);
+                    if (v <= e) L += st;
+                }
+                L = min(L, 31);
+                const int oqa = __shfl_sync(full, qa, L), oex = __shfl_sync(full, excl, L);
+                df32 rf = {0.f, 0.f}, r0 = {0.f, 0.f}, r1 = {0.f, 0.f}, r2 = {0.f, 0.f};
+                if (e < tot) {
+                    const int t = e - oex, w = t < oqa ? 0 : 1, u = w ? t - oqa : t;
+                    const int otid = wtid + L;
+                    const int d = closeq[w][u][otid];
+                    const int ot = otid % h + w * h;         // the owner's target in the tile
+                    const float4 po = o[b + t0 + ot], pl = olo[b + t0 + ot];
+                    // the staged source's particle index: its group by the prefix of sizes
+                    int lo = 0, hi = s_ngroups - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (gpre[mid] <= d) lo = mid; else hi = mid - 1;
+                    }
+                    const int64_t jsrc = gbeg[lo] + (d - gpre[lo]);
+                    float sl[nS], sh[nS];
+                    const float4 pd = PD[d], qd = QD[d];
+                    sh[0] = qd.z;
+#pragma unroll
+                    for (int a2 = 1; a2 < nS; ++a2) {
+                        const float4 r = RD[d * nR2 + (a2 - 1) / 2];
+                        sh[a2] = (a2 - 1) % 2 ? r.z : r.x;
+                    }
+#pragma unroll
+                    for (int a2 = 0; a2 < nS; ++a2) sl[a2] = S32lo[jsrc * nS + a2];
+                    pair_df<S, PHI, FIELD>(sep_df(po.x, pl.x, pd.x, lx[d]), sep_df(po.y, pl.y, pd.z, ly[d]),
+                                           sep_df(po.z, pl.z, qd.x, lz[d]), sh, sl, rf, r0, r1, r2);
+                }
+                // my own entries in this batch of 32: positions [s0, s1)
+                const int s0 = max(excl - c0, 0), s1 = min(incl - c0, 32);
+                const int cnt_max = (int)__reduce_max_sync(full, (unsigned)max(s1 - s0, 0));
+                for (int jj = 0; jj < cnt_max; ++jj) {
+                    const int srcl = min(s0 + jj, 31);
+                    const df32 vf = {__shfl_sync(full, rf.hi, srcl), __shfl_sync(full, rf.lo, srcl)};
+                    const df32 v0 = {__shfl_sync(full, r0.hi, srcl), __shfl_sync(full, r0.lo, srcl)};
+                    const df32 v1 = {__shfl_sync(full, r1.hi, srcl), __shfl_sync(full, r1.lo, srcl)};
+                    const df32 v2 = {__shfl_sync(full, r2.hi, srcl), __shfl_sync(full, r2.lo, srcl)};
+                    if (s0 + jj < s1) {
+                        const int te = c0 + s0 + jj - excl;      // my entry index
+                        if (te < qa) {
+                            if (PHI) cF[0] = df_add(cF[0], vf);
+                            if (FIELD) { cA[0] = df_add(cA[0], v0); cB[0] = df_add(cB[0], v1); cC[0] = df_add(cC[0], v2); }
+                        } else if constexpr (TT == 2) {
+                            if (PHI) cF[1] = df_add(cF[1], vf);
+                            if (FIELD) { cA[1] = df_add(cA[1], v0); cB[1] = df_add(cB[1], v1); cC[1] = df_add(cC[1], v2); }
                         }
-                        const int64_t j = gbeg[lo] + (d - gpre[lo]);
-                        float sl[nS], sh[nS];
-                        const float4 pd = PD[d], qd = QD[d];
-                        const float4 P = make_float4(pd.x, pd.z, qd.x, qd.z);
-                        sh[0] = qd.z;
-#pragma unroll
-                        for (int a2 = 1; a2 < nS; ++a2) {
-                            const float4 r = RD[d * nR2 + (a2 - 1) / 2];
-                            sh[a2] = (a2 - 1) % 2 ? r.z : r.x;
-                        }
-#pragma unroll
-                        for (int a2 = 0; a2 < nS; ++a2) sl[a2] = S32lo[j * nS + a2];
-                        df32 &rf = cF[w], &r0 = cA[w], &r1 = cB[w], &r2 = cC[w];
-                        pair_df<S, PHI, FIELD>(sep_df(po.x, pl.x, P.x, lx[d]), sep_df(po.y, pl.y, P.y, ly[d]),
-                                               sep_df(po.z, pl.z, P.z, lz[d]), sh, sl, rf, r0, r1, r2);
                     }
                 }
             }
+            __syncwarp();
             qa = qb = 0;
         };
         int q = q0, j_in = 0;
