@@ -504,7 +504,8 @@ k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t
 // FP32 pair terms on coordinates relative to the target leaf's centre:
 // target o_i, source o_j + (z_B - z_A), the centre offset formed exactly from
 // the integer cell coordinates.  Each thread sums a staged round in FP32 and
-// adds it to double-float totals; the far field is added in FP64.
+// adds it to double-float totals, the copies' totals meet in double-float,
+// and the far field is added in FP64.
 //
 // Close pairs.  A target's field error in FP32 pair arithmetic is set by its
 // nearest neighbours (the pair terms grow as r^-(s+2) and the rounding of
@@ -702,7 +703,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     __shared__ __align__(16) float stage[kStageFloats];
     float4 *PD = (float4 *)stage, *QD = PD + CH, *RD = QD + CH;
     float *lx = (float *)(RD + nR2 * CH), *ly = lx + CH, *lz = ly + CH;
-    double (*red)[kP2PThreads] = (double (*)[kP2PThreads])stage;
+    df32 (*red)[kP2PThreads] = (df32 (*)[kP2PThreads])stage;
     __shared__ int gbeg[kGroups], gpre[kGroups + 1];
     __shared__ float gdx[kGroups], gdy[kGroups], gdz[kGroups];
     __shared__ int s_next_q, s_next_j, s_ngroups;
@@ -985,30 +986,29 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             j_in = s_next_j;
         }
         __syncthreads();
-        red[0][tid] = df_to_double(cF[0]); red[1][tid] = df_to_double(cA[0]);
-        red[2][tid] = df_to_double(cB[0]); red[3][tid] = df_to_double(cC[0]);
-        red[4][tid] = df_to_double(cF[1]); red[5][tid] = df_to_double(cA[1]);
-        red[6][tid] = df_to_double(cB[1]); red[7][tid] = df_to_double(cC[1]);
+        // the k copies' totals meet in double-float (no FP64 until the far field joins)
+        red[0][tid] = cF[0]; red[1][tid] = cA[0]; red[2][tid] = cB[0]; red[3][tid] = cC[0];
+        red[4][tid] = cF[1]; red[5][tid] = cA[1]; red[6][tid] = cB[1]; red[7][tid] = cC[1];
         __syncthreads();
         if (tid < h) {
 #pragma unroll
             for (int half = 0; half < TT; ++half) {
                 if (half == 1 && tid + h >= cnt) break;
                 const int r = 4 * half;
-                double Fv = red[r][tid], Av = red[r + 1][tid], Bv = red[r + 2][tid], Cv = red[r + 3][tid];
+                df32 Fv = red[r][tid], Av = red[r + 1][tid], Bv = red[r + 2][tid], Cv = red[r + 3][tid];
                 for (int u = 1; u < k; ++u) {
-                    Fv += red[r][u * h + tid];
-                    Av += red[r + 1][u * h + tid];
-                    Bv += red[r + 2][u * h + tid];
-                    Cv += red[r + 3][u * h + tid];
+                    Fv = df_add(Fv, red[r][u * h + tid]);
+                    Av = df_add(Av, red[r + 1][u * h + tid]);
+                    Bv = df_add(Bv, red[r + 2][u * h + tid]);
+                    Cv = df_add(Cv, red[r + 3][u * h + tid]);
                 }
                 const int ii = b + t0 + tid + half * h;
                 const int64_t oo = perm[ii];
-                if (PHI) phi_out[oo] = phi_far[ii] + Fv;
+                if (PHI) phi_out[oo] = phi_far[ii] + df_to_double(Fv);
                 if (FIELD) {
-                    E_out[3 * oo] = E_far[3 * (int64_t)ii] + Av;
-                    E_out[3 * oo + 1] = E_far[3 * (int64_t)ii + 1] + Bv;
-                    E_out[3 * oo + 2] = E_far[3 * (int64_t)ii + 2] + Cv;
+                    E_out[3 * oo] = E_far[3 * (int64_t)ii] + df_to_double(Av);
+                    E_out[3 * oo + 1] = E_far[3 * (int64_t)ii + 1] + df_to_double(Bv);
+                    E_out[3 * oo + 2] = E_far[3 * (int64_t)ii + 2] + df_to_double(Cv);
                 }
             }
         }
