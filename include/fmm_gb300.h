@@ -411,16 +411,19 @@ fmm_status fmm_evaluate_graph(fmm_tree *t, int p, double theta, int want_potenti
  *   FMM_FP64    P2P with one or two targets per thread (p2p_variant 0, 1),
  *               or each mirrored leaf pair once for both directions (2)
  *   FMM_3XTF32  the tensor-core M2L with 8, 16 or 32 key rows per chunk, or
- *               the SIMT FP32 M2L (m2l_tensor 0); then, with the fastest of
- *               those, the P2P tile of the other shape (p2p_targets 1 or 2)
- *   FMM_FP32    the P2P tile: one or two targets per thread (p2p_targets)
+ *               the tiled SIMT FP32 M2L (m2l_tensor 0); then, with the fastest
+ *               of those, the P2P tile of the other shape (p2p_targets 1 or 2)
+ *   FMM_FP32    the tiled SIMT FP32 M2L with 8, 16 or 32 key rows per chunk,
+ *               or one block per target cell (m2l_tiled 0); then the P2P tile
+ *               of the other shape
  * The FP32 forms keep their P2P kernel: the one-way kernel (p2p_variant 1,
  * their default) evaluates the pairs closer than one mean particle spacing of
  * the target leaf in double-float arithmetic, which holds the near field's
  * rounding at the FP64 form's level; their symmetric kernel (2, selectable
  * with fmm_set_tuning) evaluates every pair in FP32 and is not a candidate.
  * Defaults before tuning: p2p_variant 2 (FP64) or 1 (FP32 forms), the
- * tensor-core M2L, 16 rows per chunk, harmonic M2L.
+ * tensor-core M2L (FMM_3XTF32), the tiled SIMT M2L (FMM_FP32), 16 rows per
+ * chunk, harmonic M2L.
  * The variants compute the same sums in another order: results agree to the
  * form's rounding, not bitwise.  Synchronises the stream.  out may be NULL.
  */
@@ -438,6 +441,11 @@ typedef struct {
     int p2p_targets;        /* FP32 forms' one-way P2P tile: targets per thread, */
                             /* 2 (default; both share each staged source read)   */
                             /* or 1 (more threads per target, fewer registers)   */
+    int m2l_tiled;          /* SIMT FP32 M2L (FMM_FP32; FMM_3XTF32 with          */
+                            /* m2l_tensor 0): 1 (default) over the tensor-core   */
+                            /* plan's target tiles and key rows (tc_chunk_rows   */
+                            /* rows summed per chunk), 0 one block per target    */
+                            /* cell                                              */
 } fmm_tuning;
 fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, int want_field,
                         double *potential, double *field, int reps, fmm_tuning *out);

@@ -34,7 +34,8 @@ void all_buffers(fmm_tree *t, std::vector<DevBuf *> &v)
                    &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist, &t->b_tc_scan, &t->b_tc_cnt,
                    &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rcnt, &t->b_tc_ccnt,
                    &t->b_tc_roff, &t->b_tc_coff, &t->b_tc_rowkey, &t->b_tc_crb, &t->b_tc_cre,
-                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_sym_mir,
+                   &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part, &t->b_m32_el, &t->b_m32_img,
+                   &t->b_sym_mir,
                    &t->b_sym_cnt, &t->b_sym_base, &t->b_sym_scan, &t->b_sym_tot, &t->b_sym_rev,
                    &t->b_sym_fwd, &t->b_Mh, &t->b_Mh32, &t->b_bh_mt, &t->b_bh_cnt, &t->b_ctl, &t->b_ud};
     v.assign(b, b + sizeof(b) / sizeof(b[0]));
@@ -57,6 +58,7 @@ static void forget_state(fmm_tree *t)
     t->have_lists = false;
     t->tc_plan = false;
     t->tc_img_p = -1;
+    t->m32_img_p = -1;
     t->sym_plan = false;
     t->bh_ran = false;
     t->bh_key_s = -1;

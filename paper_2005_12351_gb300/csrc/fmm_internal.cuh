@@ -106,6 +106,18 @@ struct TcLayout {
     std::vector<int> el_src, el_pos;
 };
 
+// Layout of the tiled SIMT FP32 M2L (m2l32_tile.cu): the kept locals n with
+// |n| >= n_lo in graded order as columns, in blocks of 8; block b takes the
+// first mb[b] kept multipoles m (a multiple of 4, graded order: those that
+// reach its lowest-order column, rounded up), and a key's operator image holds,
+// from float boff[b] on, T[8 b + j][m] at 8 m + j (zero outside the
+// truncation).  el_src: per image float, the D entry | order << 16 |
+// (|m| - s) << 24, or -1 for a zero.
+struct T32Layout {
+    int s = -1, p = -1, h = -1, n_lo = -1, nM = 0, ncol = 0, nb = 0, Np = 0, E = 0;
+    std::vector<int> col_n, mb, boff, el_src;
+};
+
 // threads of the M2L blocks (the per-thread term lists are built for it)
 constexpr int kM2LThreadsShared = 128;
 
@@ -270,6 +282,11 @@ struct fmm_tree {
     DevBuf b_tc_keys, b_tc_keys2, b_tc_vals, b_tc_vals2, b_tc_hist, b_tc_scan, b_tc_cnt;
     DevBuf b_tc_tgt, b_tc_bits, b_tc_wpre, b_tc_rcnt, b_tc_ccnt, b_tc_roff, b_tc_coff;
     DevBuf b_tc_rowkey, b_tc_crb, b_tc_cre, b_tc_slot, b_tc_el, b_tc_img, b_tc_part;
+    // tiled SIMT FP32 M2L on the same plan: its layout, FP32 operator images
+    // (m32_img_p: p they were built for, -1 none) and their element map
+    fmm::T32Layout m32_lay;
+    int m32_img_p = -1;
+    DevBuf b_m32_el, b_m32_img;
 
     // symmetric FP64 P2P (p2p_variant 2), derived from the lists: per list
     // entry its mirror entry (-1: none) and, for an entry (A, B) with B > A,
@@ -286,6 +303,7 @@ struct fmm_tree {
     int p2p_variant = 2;
     int p2p_tt = 2;                        // FP32 forms' one-way P2P: targets per thread (1 or 2)
     bool m2l_simt = false;
+    bool m2l_tiled = true;                 // SIMT FP32 M2L over the plan's tiles (else per target cell)
     bool m2l_harmonic = true;              // SIMT M2L over the traceless components
     bool tuned = false;
     // fmm_evaluate_graph: the evaluate of one parameter set captured as a CUDA graph
@@ -376,6 +394,19 @@ void tc_release(fmm_tree *t);
 // tb supplies the unfold of L)
 fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL,
                       const DevTables &tb, float *L);
+// the plan alone (target tiles, key rows, chunks, source slots; one host sync),
+// and the FP64 sum of the chunk partials [chunks][128][Np] into the stored
+// locals of the tiles' targets (NaN where err holds a tensor-core timeout)
+fmm_status tc_build_plan(fmm_tree *t);
+void launch_tc_reduce(fmm_tree *t, int Np, int ncol, const int32_t *col_n, int nL, const DevTables &tb,
+                      const unsigned *err, float *L);
+// m2l32_tile.cu: the SIMT FP32 M2L over the same plan, one thread per target
+// of a tile, the key's operator read by the whole block.  Usable when the
+// layout for (s, p, harmonic, n_lo) fits (fills t->m32_lay); prepare builds
+// the plan, images and partials (FMM_EBUDGET over the handle's budget)
+bool m32_usable(fmm_tree *t, int s, int p, int harmonic, int n_lo);
+fmm_status m32_prepare(fmm_tree *t, int p);
+fmm_status run_m2l32_tile(fmm_tree *t, int p, const float *M, int ldM, const DevTables &tb, float *L);
 // api.cu: the compute of an evaluate whose lists are current (no host sync)
 fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E);
 // graph.cu: drop a captured evaluate graph (the tree or the tuning changed)

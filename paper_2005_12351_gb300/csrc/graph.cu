@@ -147,6 +147,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     base.tc_chunk_rows = t->tc_G > 0 ? t->tc_G : 16;
     base.m2l_harmonic = t->m2l_harmonic ? 1 : 0;
     base.p2p_targets = t->p2p_tt;
+    base.m2l_tiled = t->m2l_tiled ? 1 : 0;
     if (t->prec == FMM_FP64) {
         for (int v : {0, 1, 2}) {
             fmm_tuning c = base;
@@ -162,9 +163,18 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
         }
         fmm_tuning c = base;
         c.m2l_tensor = 0;
+        c.m2l_tiled = 1;
         cand.push_back(c);
     } else {
-        cand.push_back(base);
+        for (int G : {8, 16, 32}) {
+            fmm_tuning c = base;
+            c.m2l_tiled = 1;
+            c.tc_chunk_rows = G;
+            cand.push_back(c);
+        }
+        fmm_tuning c = base;
+        c.m2l_tiled = 0;
+        cand.push_back(c);
     }
     // the FP32 forms' second stage: the winner with the other P2P tile shape
     const size_t stage1 = cand.size();
@@ -181,6 +191,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
         t->p2p_variant = c.p2p_variant;
         t->p2p_tt = c.p2p_targets;
         t->m2l_simt = !c.m2l_tensor;
+        t->m2l_tiled = c.m2l_tiled != 0;
         if (t->tc_G != c.tc_chunk_rows) {
             t->tc_G = c.tc_chunk_rows;
             t->tc_plan = false;
@@ -213,6 +224,7 @@ fmm_status fmm_autotune(fmm_tree *t, int p, double theta, int want_potential, in
     t->p2p_variant = c.p2p_variant;
     t->p2p_tt = c.p2p_targets;
     t->m2l_simt = !c.m2l_tensor;
+    t->m2l_tiled = c.m2l_tiled != 0;
     if (t->tc_G != c.tc_chunk_rows) {
         t->tc_G = c.tc_chunk_rows;
         t->tc_plan = false;
@@ -237,11 +249,13 @@ fmm_status fmm_set_tuning(fmm_tree *t, const fmm_tuning *tuning)
         return fail(t, FMM_EINVAL, "tc_chunk_rows must be in [1, 64]");
     if (c.m2l_harmonic > 1) return fail(t, FMM_EINVAL, "m2l_harmonic must be 0 or 1");
     if (c.p2p_targets > 2) return fail(t, FMM_EINVAL, "p2p_targets must be 1 or 2");
+    if (c.m2l_tiled > 1) return fail(t, FMM_EINVAL, "m2l_tiled must be 0 or 1");
     drop_graph(t);
     if (c.p2p_variant >= 0) t->p2p_variant = c.p2p_variant;
     if (c.m2l_tensor >= 0) t->m2l_simt = c.m2l_tensor == 0;
     if (c.m2l_harmonic >= 0) t->m2l_harmonic = c.m2l_harmonic == 1;
     if (c.p2p_targets > 0) t->p2p_tt = c.p2p_targets;
+    if (c.m2l_tiled >= 0) t->m2l_tiled = c.m2l_tiled == 1;
     if (c.tc_chunk_rows > 0 && t->tc_G != c.tc_chunk_rows) {
         t->tc_G = c.tc_chunk_rows;
         t->tc_plan = false;

@@ -902,6 +902,20 @@ fmm_status build_plan(fmm_tree *t)
 
 }  // namespace
 
+fmm_status tc_build_plan(fmm_tree *t)
+{
+    return build_plan(t);
+}
+
+void launch_tc_reduce(fmm_tree *t, int Np, int ncol, const int32_t *col_n, int nL, const DevTables &tb,
+                      const unsigned *err, float *L)
+{
+    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, t->stream>>>(
+        (int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr, (const uint32_t *)t->b_tc_coff.ptr,
+        (const float *)t->b_tc_part.ptr, Np, ncol, col_n, nL, tb.nLh, tb.h_rn, err, L);
+    ++t->launches;
+}
+
 bool tc_usable(fmm_tree *t, int s, int p)
 {
     const int h = t->m2l_harmonic ? 1 : 0;
@@ -917,10 +931,13 @@ void tc_release(fmm_tree *t)
 {
     for (DevBuf *b : {&t->b_tc_keys, &t->b_tc_keys2, &t->b_tc_vals, &t->b_tc_vals2, &t->b_tc_hist,
                       &t->b_tc_scan, &t->b_tc_tgt, &t->b_tc_bits, &t->b_tc_wpre, &t->b_tc_rowkey,
-                      &t->b_tc_crb, &t->b_tc_cre, &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part})
+                      &t->b_tc_crb, &t->b_tc_cre, &t->b_tc_slot, &t->b_tc_el, &t->b_tc_img, &t->b_tc_part,
+                      &t->b_m32_el, &t->b_m32_img})
         release(t, *b);
     t->tc_plan = false;
     t->tc_img_p = -1;
+    t->m32_img_p = -1;
+    t->tc_T = t->tc_tiles = t->tc_rows = t->tc_chunks = 0;
 }
 
 fmm_status tc_prepare(fmm_tree *t, int p)
@@ -1013,11 +1030,8 @@ fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int n
     case 4: go(k_m2l_tc<4>); break;
     default: go(k_m2l_tc<3>); break;
     }
-    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, st>>>(
-        (int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr, (const uint32_t *)t->b_tc_coff.ptr,
-        (const float *)t->b_tc_part.ptr, Ly.Np, Ly.ncol, (const int32_t *)t->b_tc_el.ptr + 2 * Ly.E, nL,
-        tb.nLh, tb.h_rn, err, L);
-    t->launches += 2;
+    ++t->launches;
+    launch_tc_reduce(t, Ly.Np, Ly.ncol, (const int32_t *)t->b_tc_el.ptr + 2 * Ly.E, nL, tb, err, L);
     return cuda_check(t, cudaGetLastError(), "tensor-core M2L");
 }
 

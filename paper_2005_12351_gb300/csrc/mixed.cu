@@ -1475,7 +1475,21 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
             FMM_TRY(pst);
         }
     }
-    if (!use_tc && t->d32_p != p && t->n_doff > 0) {
+    // otherwise the SIMT FP32 M2L: over the same plan's tiles where its layout
+    // fits and the budget allows, else one block per target cell
+    bool use_tile = !use_tc && t->m2l_tiled && t->n_m2l > 0 &&
+                    m32_usable(t, s, p, tb.harmonic, tb.n_lo);
+    if (use_tile) {
+        const fmm_status pst = m32_prepare(t, p);
+        if (pst == FMM_EBUDGET) {
+            tc_release(t);
+            t->err.clear();
+            use_tile = false;
+        } else {
+            FMM_TRY(pst);
+        }
+    }
+    if (!use_tc && !use_tile && t->d32_p != p && t->n_doff > 0) {
         FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
         k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
             (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr, tb.mi,
@@ -1519,6 +1533,8 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     record(t, 8);
     if (t->n_m2l > 0 && use_tc) {
         FMM_TRY(run_m2l_tc(t, p, Ms, row4(tb.nMh), tb.nMh, tb.nL, tb, L));
+    } else if (t->n_m2l > 0 && use_tile) {
+        FMM_TRY(run_m2l32_tile(t, p, Ms, row4(tb.nMh), tb, L));
     } else if (t->n_m2l > 0) {
         const int ldM = tb.nMh | 1, ldD = tb.nD | 1;
         size_t smem = 8 * (size_t)tb.m2l_slots * kM2LThreads +

@@ -771,6 +771,7 @@ fmm_status build_dtables(fmm_tree *t, int p, const DevTables &tb, const int32_t 
         t->d_p = p;
         t->d32_p = -1;
         t->tc_img_p = -1;
+        t->m32_img_p = -1;
     }
     return FMM_OK;
 }

@@ -52,7 +52,7 @@ class TreeInfo(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("p2p_variant", C.c_int), ("m2l_tensor", C.c_int), ("tc_chunk_rows", C.c_int),
                 ("candidates", C.c_int), ("ms_per_evaluate", C.c_float), ("m2l_harmonic", C.c_int),
-                ("p2p_targets", C.c_int)]
+                ("p2p_targets", C.c_int), ("m2l_tiled", C.c_int)]
 
 
 _lib = None
@@ -250,12 +250,13 @@ class FMMTree:
         return {k: getattr(out, k) for k, _ in out._fields_}
 
     def set_tuning(self, p2p_variant: int = -1, m2l_tensor: int = -1, tc_chunk_rows: int = -1,
-                   m2l_harmonic: int = -1, p2p_targets: int = -1):
+                   m2l_harmonic: int = -1, p2p_targets: int = -1, m2l_tiled: int = -1):
         """Applies a tuning without timing (-1 keeps the current setting)."""
         tu = Tuning()
         tu.p2p_variant, tu.m2l_tensor, tu.tc_chunk_rows = int(p2p_variant), int(m2l_tensor), int(tc_chunk_rows)
         tu.m2l_harmonic = int(m2l_harmonic)
         tu.p2p_targets = int(p2p_targets)
+        tu.m2l_tiled = int(m2l_tiled)
         fn = lib().fmm_set_tuning
         fn.argtypes = [C.c_void_p, C.POINTER(Tuning)]
         fn.restype = C.c_int

@@ -82,10 +82,11 @@ def test_batch_graph_replay():
     assert np.array_equal(E.cpu().numpy(), Eu.cpu().numpy())
 
 
-# candidates: the three FP64 P2P kernels; FP32: the P2P tile with two targets per
-# thread, then one; 3xTF32: 8/16/32 rows per chunk on the tensor cores or the
-# SIMT M2L, then the winner with the other P2P tile
-@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 2), ("3xtf32", 5)])
+# candidates: the three FP64 P2P kernels; FP32: 8/16/32 rows per chunk of the
+# tiled SIMT M2L or its per-cell kernel; 3xTF32: 8/16/32 rows per chunk on the
+# tensor cores or the tiled SIMT M2L; each FP32 form then the winner with the
+# other P2P tile
+@pytest.mark.parametrize("prec,ncand", [("fp64", 3), ("fp32", 5), ("3xtf32", 5)])
 def test_autotune(prec, ncand):
     import torch
     from gpu_util import rel_rms, to_dev
@@ -102,6 +103,8 @@ def test_autotune(prec, ncand):
     assert tune["p2p_targets"] in (1, 2)
     if prec == "3xtf32":
         assert tune["tc_chunk_rows"] in (8, 16, 32) and tune["m2l_tensor"] in (0, 1)
+    if prec == "fp32":
+        assert tune["tc_chunk_rows"] in (8, 16, 32) and tune["m2l_tiled"] in (0, 1)
     phi1, E1 = t.evaluate_graph(p, 0.5)
     torch.cuda.synchronize()
     tol = 1e-13 if prec == "fp64" else 1e-6

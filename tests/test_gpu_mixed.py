@@ -23,12 +23,12 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_eval(pos, S, s, p, theta, ncrit, precision, want_phi=True, want_field=True, harmonic=1,
-             p2p_variant=-1):
+             p2p_variant=-1, m2l_tiled=-1):
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
     tree = fmm.create_tree(max_leaf=ncrit, precision=precision)
-    tree.set_tuning(m2l_harmonic=harmonic, p2p_variant=p2p_variant)
+    tree.set_tuning(m2l_harmonic=harmonic, p2p_variant=p2p_variant, m2l_tiled=m2l_tiled)
     tree.set_sources(to_dev(pos), to_dev(S), s)
     phi, E = tree.evaluate(p, theta, want_phi, want_field)
     torch.cuda.synchronize()
@@ -213,41 +213,47 @@ def test_3xtf32_matches_fp32_form(s, p, dist, n, h):
     assert rel_rms(phi_b, phi_a) < 2e-6, rel_rms(phi_b, phi_a)
 
 
-def test_3xtf32_chunk_boundaries(monkeypatch):
+@pytest.mark.parametrize("precision", FORMS)
+def test_tile_chunk_boundaries(monkeypatch, precision):
     """Chunks of one key row each and chunks longer than any tile's rows give the
-    same result within FP32 rounding (the chunk partials are summed in FP64).
-    The chunk length is read when a handle builds its first plan."""
+    same result within FP32 rounding (the chunk partials are summed in FP64), on
+    the tensor cores (3xTF32) and in the tiled SIMT M2L (FP32).  The chunk length
+    is read when a handle builds its first plan."""
     from gpu_util import rel_rms
     pos, S = synth.make_system(20_000, 1, "plummer", 77)
     out = {}
     for g in ("1", "100000"):
         monkeypatch.setenv("FMM_TC_CHUNK", g)
-        (_, out[g]), tree = gpu_eval(pos, S, 1, 6, 0.5, 32, "3xtf32", want_phi=False)
+        (_, out[g]), tree = gpu_eval(pos, S, 1, 6, 0.5, 32, precision, want_phi=False)
         info = tree.info()
         assert info["tc_chunks"] == (info["tc_rows"] if g == "1" else info["tc_tiles"])
     assert rel_rms(out["1"], out["100000"]) < 1e-6
 
 
-def test_3xtf32_falls_back_to_simt_within_budget():
-    """When the tensor-core plan and operator images do not fit the handle's memory
-    budget, the 3xTF32 form takes the SIMT FP32 M2L: the evaluate succeeds and is
-    bitwise the FP32 form's result."""
+@pytest.mark.parametrize("precision", FORMS)
+def test_mixed_falls_back_to_per_cell_m2l_within_budget(precision):
+    """When the tile plan and operator images (of the tensor-core M2L, or of the
+    tiled SIMT M2L it falls back to first) do not fit the handle's memory budget,
+    a mixed form takes the SIMT FP32 M2L with one block per target cell: the
+    evaluate succeeds and is bitwise the FP32 form's result on that kernel."""
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
     pos, S = synth.make_system(40_000, 2, "plummer", 931)
     P, Sd = to_dev(pos), to_dev(S)
     f32 = fmm.create_tree(max_leaf=64, precision="fp32")
+    f32.set_tuning(m2l_tiled=0)
     f32.set_sources(P, Sd, 2)
     _, E32 = f32.evaluate(9, 0.5, False, True)
     torch.cuda.synchronize()
+    assert f32.info()["tc_rows"] == 0
     need32 = f32.info()["device_bytes"]
-    full = fmm.create_tree(max_leaf=64, precision="3xtf32")
+    full = fmm.create_tree(max_leaf=64, precision=precision)
     full.set_sources(P, Sd, 2)
     full.evaluate(9, 0.5, False, True)
     torch.cuda.synchronize()
     assert full.info()["tc_rows"] > 0 and full.info()["device_bytes"] > need32 * 1.05
-    t = fmm.create_tree(max_leaf=64, precision="3xtf32", mem_budget_bytes=int(need32 * 1.02))
+    t = fmm.create_tree(max_leaf=64, precision=precision, mem_budget_bytes=int(need32 * 1.02))
     t.set_sources(P, Sd, 2)
     _, E = t.evaluate(9, 0.5, False, True)
     torch.cuda.synchronize()
@@ -255,24 +261,71 @@ def test_3xtf32_falls_back_to_simt_within_budget():
     assert np.array_equal(E.cpu().numpy(), E32.cpu().numpy())
 
 
+@pytest.mark.parametrize("s,p,dist,n,h", [(1, 6, "uniform", 60_000, 1), (2, 5, "plummer", 40_000, 1),
+                                           (0, 10, "plummer", 30_000, 1), (1, 6, "uniform", 40_000, 0),
+                                           (1, 3, "plummer", 20_000, 0), (0, 12, "uniform", 10_000, 1)])
+@pytest.mark.parametrize("want_phi", [True, False])
+def test_fp32_tiled_m2l_matches_per_cell(orc, s, p, dist, n, h, want_phi):
+    """The FP32 form's two SIMT M2L kernels -- over the tile plan (a block per
+    chunk of key rows, a thread per target, the operator broadcast) and one block
+    per target cell -- sum the same FP32 products in another order: the stored
+    locals agree within 1e-5 column block by column block, the outputs within
+    FP32 rounding, and the tiled result is within 1e-6 of the FP64 oracle.
+    Column counts: 6 to 16 blocks of 8 (the register-held sums of one thread);
+    the harmonic p = 12 has 169 columns, more than the tiled kernel holds, and
+    takes the per-cell kernel (no plan).  Field only: the columns start at
+    order 1."""
+    import torch
+    from gpu_util import rel_rms, to_dev
+    from paper_2005_12351_gb300 import fmm
+    pos, S = synth.make_system(n, s, dist, 1200 + 10 * s + p)
+    out, Ls = {}, {}
+    nL = (p + 1) ** 2 if h else (p + 1) * (p + 2) * (p + 3) // 6
+    for tiled in (1, 0):
+        t = fmm.create_tree(max_leaf=64, precision="fp32")
+        t.set_tuning(m2l_harmonic=h, m2l_tiled=tiled)
+        t.set_sources(to_dev(pos), to_dev(S), s)
+        phi, E = t.evaluate(p, 0.5, want_phi, True)
+        torch.cuda.synchronize()
+        rows = t.info()["tc_rows"]
+        assert (rows > 0) == (tiled == 1 and nL - (0 if want_phi else 1) <= 128 and p < 12), rows
+        out[tiled] = (phi.cpu().numpy() if want_phi else None, E.cpu().numpy())
+        Ls[tiled] = t.copy_array("local", nL).numpy()
+        t.destroy()
+    c0 = 0 if want_phi else 1                   # the order-0 local is not formed for the field alone
+    for a in range(c0, nL, 64):
+        assert rel_rms(Ls[1][:, a:a + 64], Ls[0][:, a:a + 64]) < 1e-5, a
+    assert rel_rms(out[1][1], out[0][1]) < 1e-6
+    if want_phi:
+        assert rel_rms(out[1][0], out[0][0]) < 2e-6
+    if p <= 6:
+        ot = orc.Tree(pos, 64)
+        ot.lists(0.5)
+        phi_o, E_o = ot.fmm(S, s, p)
+        assert rel_rms(out[1][1], E_o) < 1e-6
+        if want_phi:
+            assert rel_rms(out[1][0], phi_o) < 1e-6
+
+
 @pytest.mark.parametrize("s", [1, 2])
 def test_fp32_symmetric_batch_matches_alone(s):
     """The FP32 symmetric P2P gives each system of a batch the bits it gets alone
-    (the FP32 form: its M2L is per target cell, where the tensor-core M2L's tiles
-    mix systems)."""
+    (with the FP32 form's per-cell M2L: the tiles of the tiled and tensor-core
+    M2L mix systems, and their chunks of key rows depend on the tile's other
+    targets)."""
     import torch
     from gpu_util import to_dev
     from paper_2005_12351_gb300 import fmm
     pos, S, off = synth.make_batch(24, 300, 5000, s, 1901 + s, dist="plummer")
     tb = fmm.create_tree(max_leaf=32, precision="fp32")
-    tb.set_tuning(p2p_variant=2)
+    tb.set_tuning(p2p_variant=2, m2l_tiled=0)
     tb.set_sources_batch(to_dev(pos), to_dev(S), off, s)
     phi_b, E_b = tb.evaluate(4, 0.5)
     torch.cuda.synchronize()
     phi_b, E_b = phi_b.cpu().numpy(), E_b.cpu().numpy()
     for k in (0, 11, 23):
         a, b = int(off[k]), int(off[k + 1])
-        (phi, E), t = gpu_eval(pos[a:b], S[a:b], s, 4, 0.5, 32, "fp32", p2p_variant=2)
+        (phi, E), t = gpu_eval(pos[a:b], S[a:b], s, 4, 0.5, 32, "fp32", p2p_variant=2, m2l_tiled=0)
         assert np.array_equal(phi, phi_b[a:b]) and np.array_equal(E, E_b[a:b]), k
         t.destroy()
     tb.destroy()
