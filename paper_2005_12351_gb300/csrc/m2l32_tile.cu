@@ -42,7 +42,7 @@ struct T32Args {
     const float *M;                      // scaled FP32 multipoles (folded when harmonic), stride ldM
     const float *img;                    // per key: E floats (layout T32Layout)
     float *partial;                      // [chunks][128][Np]
-    int ldM, nM, nq, E, Np;              // nq = float4 groups of a staged multipole row
+    int nchunks, ldM, nM, nq, E, Np;     // nq = float4 groups of a staged multipole row
     int mb[kT32MaxNB], boff[kT32MaxNB];
 };
 
@@ -58,55 +58,90 @@ __device__ __forceinline__ void fma8(float (&acc)[8], const float4 &t0, const fl
     acc[7] = fmaf(t1.w, m, acc[7]);
 }
 
+// What a stage holds: the row's chunk, whether it is the chunk's last row,
+// whether this thread's target has a pair in it; valid = false past the last.
+struct T32Row {
+    int chunk;
+    bool valid, last, has;
+};
+
 // NB >= the layout's blocks (those past it have mb = 0 and are not written).
 // Shared memory: two stages of [nq][128] float4 multipoles and two of E floats.
+// Persistent: block k takes the chunks k, k + grid, ... as one sequence of
+// rows, the next row (of this chunk or the next) staged while one is summed;
+// a row's source slot and key are loaded a row ahead of its staging, and the
+// next chunk's bounds a chunk ahead.
 template <int NB>
 __global__ void __launch_bounds__(kT32Threads) k_m2l32_tile(const T32Args a)
 {
     extern __shared__ float4 sm4[];
-    const int tid = threadIdx.x, j = blockIdx.x;
+    const int tid = threadIdx.x, G = gridDim.x, nch = a.nchunks;
     float4 *Mst = sm4;                                          // [2][nq][128]
     float *Tst = (float *)(sm4 + 2 * a.nq * kT32Threads);       // [2][E]
-    const int rb = a.chunk_rb[j], re = a.chunk_re[j];
     float acc[NB][8];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[b][k] = 0.0f;
-    // row r into stage buf: this thread's source row (zeros past nM, all zeros
-    // without a source) and a share of the key's image; true if it has a source
-    auto stage = [&](int r, int buf) {
-        const int src = a.slot[(size_t)r * kT32Threads + tid];
-        const float *g = a.M + (size_t)max(src, 0) * a.ldM;
-        const uint32_t d = smem_u32(Mst + (size_t)buf * a.nq * kT32Threads + tid);
-        for (int q = 0; q < a.nq; ++q) {
-            const int left = a.nM - 4 * q;
-            cp_async16(d + 16u * kT32Threads * q, g + 4 * q, src < 0 ? 0 : 4 * min(left, 4));
+    // staging cursor: row sr of chunk sj (rows up to sre); the bounds of chunk
+    // sj + G and the slot and key of row sr already in registers
+    int sj = blockIdx.x;
+    if (sj >= nch) return;
+    int sr = a.chunk_rb[sj], sre = a.chunk_re[sj];
+    int nrb = 0, nre = 0;
+    if (sj + G < nch) {
+        nrb = a.chunk_rb[sj + G];
+        nre = a.chunk_re[sj + G];
+    }
+    int src = a.slot[(size_t)sr * kT32Threads + tid], key = a.row_key[sr];
+    auto stage = [&](int buf) {
+        T32Row w;
+        w.valid = sj < nch;
+        w.chunk = sj;
+        w.last = sr + 1 == sre;
+        w.has = w.valid && src >= 0;
+        if (w.valid) {
+            const float *g = a.M + (size_t)max(src, 0) * a.ldM;
+            const uint32_t d = smem_u32(Mst + (size_t)buf * a.nq * kT32Threads + tid);
+            for (int q = 0; q < a.nq; ++q) {
+                const int left = a.nM - 4 * q;
+                cp_async16(d + 16u * kT32Threads * q, g + 4 * q, src < 0 ? 0 : 4 * min(left, 4));
+            }
+            const float *ti = a.img + (size_t)key * a.E;
+            const uint32_t td = smem_u32(Tst + (size_t)buf * a.E);
+            for (int e = 4 * tid; e < a.E; e += 4 * kT32Threads) cp_async16(td + 4u * e, ti + e, 16);
+            // advance the cursor and fetch what the next staging needs
+            if (++sr == sre) {
+                sj += G;
+                sr = nrb;
+                sre = nre;
+                if (sj + G < nch) {
+                    nrb = a.chunk_rb[sj + G];
+                    nre = a.chunk_re[sj + G];
+                }
+            }
+            if (sj < nch) {
+                src = a.slot[(size_t)sr * kT32Threads + tid];
+                key = a.row_key[sr];
+            }
         }
-        const float *ti = a.img + (size_t)a.row_key[r] * a.E;
-        const uint32_t td = smem_u32(Tst + (size_t)buf * a.E);
-        for (int e = 4 * tid; e < a.E; e += 4 * kT32Threads) cp_async16(td + 4u * e, ti + e, 16);
-        cp_async_commit();
-        return src >= 0;
+        cp_async_commit();                 // an empty group past the last row keeps the count
+        return w;
     };
-    bool cur = stage(rb, 0);
-    for (int r = rb; r < re; ++r) {
-        const int buf = (r - rb) & 1;
-        bool nxt = false;
-        if (r + 1 < re) {
-            nxt = stage(r + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+    T32Row cur = stage(0);
+    int buf = 0;
+    while (cur.valid) {
+        const T32Row nxt = stage(buf ^ 1);
+        cp_async_wait<1>();
         __syncthreads();
-        if (__any_sync(0xffffffffu, cur)) {      // a warp whose 32 targets have no pair here skips it
+        if (__any_sync(0xffffffffu, cur.has)) {   // a warp whose 32 targets have no pair here skips it
             const float4 *Mb = Mst + (size_t)buf * a.nq * kT32Threads + tid;
             const float4 *Tb = (const float4 *)(Tst + (size_t)buf * a.E);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const float4 *T4 = Tb + (a.boff[b] >> 2);
                 const int nqb = a.mb[b] >> 2;
+#pragma unroll 2
                 for (int q = 0; q < nqb; ++q) {
                     const float4 mv = Mb[q * kT32Threads];
                     fma8(acc[b], T4[8 * q + 0], T4[8 * q + 1], mv.x);
@@ -116,16 +151,23 @@ __global__ void __launch_bounds__(kT32Threads) k_m2l32_tile(const T32Args a)
                 }
             }
         }
-        __syncthreads();                         // the stage is refilled two rows on
-        cur = nxt;
-    }
-    float4 *P = (float4 *)(a.partial + ((size_t)j * kT32Threads + tid) * a.Np);
+        __syncthreads();                         // before the next row's staging refills the other stage
+        if (cur.last) {
+            float4 *P = (float4 *)(a.partial + ((size_t)cur.chunk * kT32Threads + tid) * a.Np);
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        if (8 * b >= a.Np) break;
-        P[2 * b] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
-        P[2 * b + 1] = make_float4(acc[b][4], acc[b][5], acc[b][6], acc[b][7]);
+            for (int b = 0; b < NB; ++b) {
+                if (8 * b < a.Np) {
+                    P[2 * b] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                    P[2 * b + 1] = make_float4(acc[b][4], acc[b][5], acc[b][6], acc[b][7]);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[b][k] = 0.0f;
+            }
+        }
+        cur = nxt;
+        buf ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // operator images: float e of key r's image is the D entry el_src[e] with the
@@ -260,15 +302,20 @@ fmm_status run_m2l32_tile(fmm_tree *t, int p, const float *M, int ldM, const Dev
     a.nq = (Ly.nM + 3) / 4;
     a.E = Ly.E;
     a.Np = Ly.Np;
+    a.nchunks = (int)t->tc_chunks;
     for (int b = 0; b < Ly.nb; ++b) {
         a.mb[b] = Ly.mb[b];
         a.boff[b] = Ly.boff[b];
     }
     const size_t smem = t32_smem(Ly);
-    const unsigned grid = (unsigned)t->tc_chunks;
     auto go = [&](auto kern) {
         allow_max_dynamic_smem(kern);
-        kern<<<grid, kT32Threads, smem, st>>>(a);
+        // persistent: as many blocks as are resident at once, at most one per chunk
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT32Threads, smem) != cudaSuccess)
+            per_sm = 1;
+        const int64_t grid = std::min<int64_t>(t->tc_chunks, (int64_t)std::max(per_sm, 1) * sm_count());
+        kern<<<(unsigned)grid, kT32Threads, smem, st>>>(a);
     };
     switch ((Ly.nb + 1) / 2) {
     case 1: go(k_m2l32_tile<2>); break;

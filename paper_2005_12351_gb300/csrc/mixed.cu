@@ -21,6 +21,8 @@
 #include <mutex>
 
 #include "df32.cuh"
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -689,7 +691,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
 {
     constexpr int nS = S == 2 ? 7 : (S + 1) * (S + 2) / 2;     // + trace for quadrupoles
     constexpr int nR2 = (nS - 1 + 1) / 2;                       // float4s of moments after the first
-    constexpr int CH = S == 2 ? 448 : (S == 1 ? 512 : 704);   // 6 blocks per SM for S < 2
+    constexpr int CH = S == 2 ? 448 : (S == 1 ? 512 : 688);   // 6 blocks per SM for S < 2
     // a round stages at most CHU sources; the slots up to CH take the padding
     // that gives every thread the same number of steps
     constexpr int CHU = CH - kP2PThreads;
@@ -709,6 +711,9 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     __shared__ int s_next_q, s_next_j, s_ngroups;
     // per thread and target: staged indices of its queued close pairs
     __shared__ uint16_t closeq[2][kLaneQ][kP2PThreads];
+    // a round's slots in pair-loop order: the sources near the target leaf first
+    __shared__ uint16_t order[CH];
+    __shared__ int s_wnear[kP2PThreads / 32];
     const int c = leaves[blockIdx.x];
     const int b = begin[c], e = end[c], nt = e - b;
     const int q0 = off[c], q1 = off[c + 1];
@@ -727,6 +732,11 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
     }
     __syncthreads();
     const float close2 = s_close2;
+    // a source is near when its squared distance to the leaf's box is under
+    // the close radius squared with a 2 % margin: only near sources can make a
+    // close pair (far ones are beyond the radius from every target, well past
+    // the FP32 rounding of the separations)
+    const float hw = (float)half[c], near2 = 1.02f * close2;
     for (int t0 = 0; t0 < nt; t0 += TT * kP2PThreads) {
         const int cnt = min(TT * kP2PThreads, nt - t0);
         const int h = TT == 2 ? (cnt + 1) / 2 : cnt;
@@ -869,7 +879,9 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             // every thread takes the same number of steps (the close-pair
             // evaluation between stretches of them is warp-collective)
             const int steps = (used + k - 1) / k;
-            for (int d = tid; d < steps * k; d += kP2PThreads) {
+            uint32_t nbits = 0;                // bit i: slot tid + 128 i is near
+            int nmine = 0;
+            for (int d = tid, i = 0; d < steps * k; d += kP2PThreads, ++i) {
                 if (d >= used) {
                     // padding: a far-away source with zero moments adds exactly 0
                     PD[d] = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
@@ -900,8 +912,41 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                     const float v = 2 * a + 2 < nS ? S32[(int64_t)j * nS + 2 * a + 2] : 0.0f;
                     RD[d * nR2 + a] = make_float4(u, u, v, v);
                 }
+                const float bx = fmaxf(fabsf(hx) - hw, 0.0f), by = fmaxf(fabsf(hy) - hw, 0.0f),
+                            bz = fmaxf(fabsf(hz) - hw, 0.0f);
+                if (bx * bx + by * by + bz * bz < near2) {
+                    nbits |= 1u << i;
+                    ++nmine;
+                }
+            }
+            // the loop order: near slots first (ranked by thread, then slot),
+            // then the far ones and the padding
+            int n_near;
+            {
+                const int lane = tid & 31, w = tid >> 5;
+                int incl = nmine;
+#pragma unroll
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o2);
+                    if (lane >= o2) incl += y;
+                }
+                if (lane == 31) s_wnear[w] = incl;
+                __syncthreads();
+                int base = 0;
+                n_near = 0;
+#pragma unroll
+                for (int u = 0; u < kP2PThreads / 32; ++u) {
+                    if (u < w) base += s_wnear[u];
+                    n_near += s_wnear[u];
+                }
+                const int S_ = steps * k, full = S_ / kP2PThreads, rem = S_ % kP2PThreads;
+                int rn = base + incl - nmine;                       // near slots of the threads before
+                int rf = n_near + tid * full + min(tid, rem) - rn;  // far slots of the threads before
+                for (int d = tid, i = 0; d < S_; d += kP2PThreads, ++i)
+                    order[(nbits >> i) & 1u ? rn++ : rf++] = (uint16_t)d;
             }
             __syncthreads();
+            const int steps_near = (n_near + k - 1) / k;
             // The pair loop only queues close pairs; they are evaluated when a
             // queue of the warp is full and after the round.  Threads without a
             // target (and the second target of a thread that has one only) run
@@ -913,8 +958,10 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
             const f2 OX = f2_pack(oi.x, oj.x), OY = f2_pack(oi.y, oj.y), OZ = f2_pack(oi.z, oj.z);
             // one step: source slot spx + it k against the thread's targets
             float f1 = 0.f, e10 = 0.f, e11 = 0.f, e12 = 0.f;    // one target per thread: scalar sums
-            auto step = [&](int it2) {
-                const int jj = spx + it2 * k;
+            // NEAR: the slot may hold a near source (close-pair test and queue)
+            auto step = [&](int it2, auto near_t) {
+                constexpr bool NEAR = decltype(near_t)::value;
+                const int jj = order[spx + it2 * k];
                 if constexpr (TT == 1) {
                     const float4 pd = PD[jj], qd = QD[jj];
                     float Sj[nS];
@@ -927,8 +974,8 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                     }
                     const float dx = oi.x - pd.x, dy = oi.y - pd.z, dz = oi.z - qd.x;
                     const float r2a = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    pair32<S, PHI, FIELD>(dx, dy, dz, r2a, r2a >= c2a, Sj, f1, e10, e11, e12);
-                    if (r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
+                    pair32<S, PHI, FIELD>(dx, dy, dz, r2a, !NEAR || r2a >= c2a, Sj, f1, e10, e11, e12);
+                    if (NEAR && r2a < c2a && r2a > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
                     return;
                 }
                 const ulonglong2 pd = reinterpret_cast<const ulonglong2 *>(PD)[jj];
@@ -948,28 +995,39 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                 const f2 dx = f2_sub(OX, pd.x), dy = f2_sub(OY, pd.y), dz = f2_sub(OZ, qd.x);
                 const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
                 const float2 r2s = f2_unpack(r2);
+                if constexpr (!NEAR) {
+                    // every pair is kept: beyond the close radius, r > 0
+                    pair32x2<S, PHI, FIELD>(dx, dy, dz, r2, f2_pack(rsqrt_mufu(r2s.x), rsqrt_mufu(r2s.y)), Sj,
+                                            Fp, E0p, E1p, E2p);
+                    return;
+                }
                 const bool ka = r2s.x >= c2a, kb = r2s.y >= c2b;
                 const f2 y = f2_pack(ka ? rsqrt_mufu(r2s.x) : 0.0f, (TT == 2 && kb) ? rsqrt_mufu(r2s.y) : 0.0f);
                 pair32x2<S, PHI, FIELD>(dx, dy, dz, r2, y, Sj, Fp, E0p, E1p, E2p);
                 if (r2s.x < c2a && r2s.x > 0.0f) closeq[0][qa++][tid] = (uint16_t)jj;
                 if (TT == 2 && r2s.y < c2b && r2s.y > 0.0f) closeq[1][qb++][tid] = (uint16_t)jj;
             };
+            const std::integral_constant<bool, true> near_s;
+            const std::integral_constant<bool, false> far_s;
             int it = 0;
-            while (it < steps) {
+            while (it < steps_near) {
                 // two steps, then a look at the queues: they have room for two more
                 bool full = false;
-                for (; it + 1 < steps; it += 2) {
-                    step(it);
-                    step(it + 1);
+                for (; it + 1 < steps_near; it += 2) {
+                    step(it, near_s);
+                    step(it + 1, near_s);
                     if (__any_sync(0xffffffffu, qa > kLaneQ - 2 || qb > kLaneQ - 2)) {
                         it += 2;
                         full = true;
                         break;
                     }
                 }
-                if (!full && it < steps) step(it++);                 // an odd last step
+                if (!full && it < steps_near) step(it++, near_s);    // an odd last step
                 if (__any_sync(0xffffffffu, qa + qb > 0)) flush();   // staged sources change next round
             }
+            // the far slots: no close pairs, nothing queued
+#pragma unroll 2
+            for (; it < steps; ++it) step(it, far_s);
             {
                 if constexpr (TT == 1) {
                     cF[0] = df_addf(cF[0], f1); cA[0] = df_addf(cA[0], e10);
