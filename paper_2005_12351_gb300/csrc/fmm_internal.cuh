@@ -395,7 +395,7 @@ void tc_release(fmm_tree *t);
 fmm_status run_m2l_tc(fmm_tree *t, int p, const float *M, int ldM, int nM, int nL,
                       const DevTables &tb, float *L);
 // the plan alone (target tiles, key rows, chunks, source slots; one host sync),
-// and the FP64 sum of the chunk partials [chunks][128][Np] into the stored
+// and the double-float sum of the chunk partials [chunks][128][Np] into the stored
 // locals of the tiles' targets (NaN where err holds a tensor-core timeout)
 fmm_status tc_build_plan(fmm_tree *t);
 void launch_tc_reduce(fmm_tree *t, int Np, int ncol, const int32_t *col_n, int nL, const DevTables &tb,

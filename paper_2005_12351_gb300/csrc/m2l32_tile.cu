@@ -16,7 +16,7 @@
 // the first mb[b] multipoles in graded order (those with |m| <= p + s - the
 // block's lowest order), so the triangle costs only the rounding of each
 // block.  A chunk's sums (at most G rows, in row order) are written as FP32
-// partials, summed over a tile's chunks in FP64 by the plan's reduction --
+// partials, summed over a tile's chunks in double-float by the plan's reduction --
 // the accumulation of the tensor-core form, with FP32 products in place of
 // 3xTF32.
 #include <algorithm>

@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "df32.cuh"
 #include "fmm_internal.cuh"
 #include "umma.cuh"
 
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(128) k_check_umma(const float *A, const float 
 // the block's MMA covers only N = (the number of n it reaches, rounded up to
 // 16) columns.  Each key row is accumulated in tensor memory on its own and
 // drained into FP32 registers (round to nearest); a chunk of at most G rows
-// of one tile is summed there, and the chunk partials are summed in FP64.
+// of one tile is summed there, and the chunk partials are summed in double-float
+// (TwoSum pairs of floats, about 44 bits) before the final rounding to FP32.
 //
 // Block roles (320 threads): warps 0-7 stage A (thread = tile row and half
 // of a 32-multipole K-chunk: cp.async gather into a shared ring, split,
@@ -500,30 +502,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs a)
 }
 
 // L~_t[col_n[col]] = sum of the tile's chunk partials of target t in column col,
-// in FP64, in chunk order; the stored components (slot r holds n = h_rn[r]:
-// for the harmonic M2L exactly its columns, the n with n_z <= 1) are written.
-// NaN everywhere if a wait of the M2L block gave up: the failure shows in the
-// output.
-__global__ void k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile_chunk_off,
-                            const float *partial, int Np, int ncol, const int32_t *col_n, int nL,
-                            int nLh, const int *h_rn, const unsigned *err, float *L)
+// in chunk order, in double-float (hi + lo FP32 pairs by TwoSum: some 44 bits,
+// then rounded once to the FP32 local), a warp per target (four to a block);
+// the stored components (slot r holds n = h_rn[r]: for the harmonic M2L
+// exactly its columns, the n with n_z <= 1) are written, the columns no
+// partial covers as zero.  NaN everywhere if a wait of the tensor-core M2L
+// gave up: the failure shows in the output.
+constexpr int kReduceWarps = 4;
+__global__ void __launch_bounds__(32 * kReduceWarps)
+k_tc_reduce(int T, const int32_t *tile_tgt, const uint32_t *tile_chunk_off, const float *partial, int Np,
+            int ncol, const int32_t *col_n, int nL, int nLh, const int *h_rn, const unsigned *err, float *L)
 {
-    __shared__ double Ls[kMaxTot];
-    const int q = blockIdx.x;
-    if (q >= T) return;
+    __shared__ float Ls[kReduceWarps][kMaxTot];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * kReduceWarps + w;
+    if (q >= T) return;                   // whole warps; no block barrier below
     const bool bad = (*err & kErrTcTimeout) != 0;
-    const int tile = q >> 7, lane = q & 127, c = tile_tgt[q];
+    const int tile = q >> 7, tl = q & 127, c = tile_tgt[q];
     const int j0 = (int)tile_chunk_off[tile], j1 = (int)tile_chunk_off[tile + 1];
-    for (int n = threadIdx.x; n < nL; n += blockDim.x) Ls[n] = 0.0;
-    __syncthreads();
-    for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
-        double v = 0.0;
-        for (int j = j0; j < j1; ++j) v += (double)partial[((size_t)j * 128 + lane) * Np + col];
-        Ls[col_n[col]] = v;
+    float *ls = Ls[w];
+    for (int n = lane; n < nL; n += 32) ls[n] = 0.0f;
+    __syncwarp();
+    for (int col = lane; col < ncol; col += 32) {
+        df32 v = {0.0f, 0.0f};
+        for (int j = j0; j < j1; ++j) v = df_addf(v, partial[((size_t)j * 128 + tl) * Np + col]);
+        ls[col_n[col]] = __fadd_rn(v.hi, v.lo);
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nLh; r += blockDim.x)
-        L[(size_t)c * nLh + r] = bad ? __int_as_float(0x7fc00000) : (float)Ls[h_rn[r]];
+    __syncwarp();
+    for (int r = lane; r < nLh; r += 32)
+        L[(size_t)c * nLh + r] = bad ? __int_as_float(0x7fc00000) : ls[h_rn[r]];
 }
 
 // ------------------------------------------------------------ the plan
@@ -910,7 +917,7 @@ fmm_status tc_build_plan(fmm_tree *t)
 void launch_tc_reduce(fmm_tree *t, int Np, int ncol, const int32_t *col_n, int nL, const DevTables &tb,
                       const unsigned *err, float *L)
 {
-    k_tc_reduce<<<(unsigned)t->tc_T, 128, 0, t->stream>>>(
+    k_tc_reduce<<<(unsigned)((t->tc_T + kReduceWarps - 1) / kReduceWarps), 32 * kReduceWarps, 0, t->stream>>>(
         (int)t->tc_T, (const int32_t *)t->b_tc_tgt.ptr, (const uint32_t *)t->b_tc_coff.ptr,
         (const float *)t->b_tc_part.ptr, Np, ncol, col_n, nL, tb.nLh, tb.h_rn, err, L);
     ++t->launches;

@@ -19,10 +19,9 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
-
-#include "df32.cuh"
 #include <type_traits>
 
+#include "df32.cuh"
 #include "fmm_internal.cuh"
 
 namespace fmm {

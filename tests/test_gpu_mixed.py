@@ -1,7 +1,7 @@
 """Mixed-precision forms: FMM_FP32 (scaled FP32 expansions and pair terms, FP64 D
 tables and outputs) and FMM_3XTF32 (the same with the M2L on the tcgen05 tensor
 cores in 3xTF32: FP32 operands split into two TF32 halves, FP32 accumulation in
-tensor memory over chunks of keys, FP64 across chunks).
+tensor memory over chunks of keys, double-float across chunks).
 
 Tolerances: the FP32 form is compared with the FP64 oracle FMM on the same tree
 (difference = FP32 rounding only: ~2e-7 measured, bounded here by 1e-6 relative
@@ -216,7 +216,7 @@ def test_3xtf32_matches_fp32_form(s, p, dist, n, h):
 @pytest.mark.parametrize("precision", FORMS)
 def test_tile_chunk_boundaries(monkeypatch, precision):
     """Chunks of one key row each and chunks longer than any tile's rows give the
-    same result within FP32 rounding (the chunk partials are summed in FP64), on
+    same result within FP32 rounding (the chunk partials are summed in double-float), on
     the tensor cores (3xTF32) and in the tiled SIMT M2L (FP32).  The chunk length
     is read when a handle builds its first plan."""
     from gpu_util import rel_rms
