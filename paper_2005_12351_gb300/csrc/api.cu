@@ -67,6 +67,17 @@ static void forget_state(fmm_tree *t)
     t->tab_key_s = t->tab_key_p = t->tab_key_nlo = t->tab_key_h = t->tab_key_shi = -1;
 }
 
+fmm_status side_stream(fmm_tree *t)
+{
+    if (!t->side_st)
+        FMM_TRY(cuda_check(t, cudaStreamCreateWithFlags(&t->side_st, cudaStreamNonBlocking), "stream"));
+    if (!t->ev_lists)
+        FMM_TRY(cuda_check(t, cudaEventCreateWithFlags(&t->ev_lists, cudaEventDisableTiming), "event"));
+    if (!t->ev_plan)
+        FMM_TRY(cuda_check(t, cudaEventCreateWithFlags(&t->ev_plan, cudaEventDisableTiming), "event"));
+    return FMM_OK;
+}
+
 fmm_status ensure(fmm_tree *t, DevBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
@@ -231,6 +242,12 @@ fmm_status fmm_destroy(fmm_tree *t)
     else cudaDeviceSynchronize();
     drop_graph(t);
     if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
+    if (t->side_st) {
+        cudaStreamSynchronize(t->side_st);
+        cudaStreamDestroy(t->side_st);
+    }
+    if (t->ev_lists) cudaEventDestroy(t->ev_lists);
+    if (t->ev_plan) cudaEventDestroy(t->ev_plan);
     std::vector<DevBuf *> v;
     all_buffers(t, v);
     for (DevBuf *b : v) release(t, *b);

@@ -310,6 +310,10 @@ struct fmm_tree {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // side stream of the mixed forms (the M2L plan is built on it while the
+    // upward pass runs) and the two events that join it to the handle's stream
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t ev_lists = nullptr, ev_plan = nullptr;
     int g_p = -1, g_phi = 0, g_field = 0;
     double g_theta = 0.0;
     double *g_pot = nullptr, *g_fld = nullptr;
@@ -407,6 +411,8 @@ void launch_tc_reduce(fmm_tree *t, int Np, int ncol, const int32_t *col_n, int n
 bool m32_usable(fmm_tree *t, int s, int p, int harmonic, int n_lo);
 fmm_status m32_prepare(fmm_tree *t, int p);
 fmm_status run_m2l32_tile(fmm_tree *t, int p, const float *M, int ldM, const DevTables &tb, float *L);
+// api.cu: the handle's side stream and join events, created on first use
+fmm_status side_stream(fmm_tree *t);
 // api.cu: the compute of an evaluate whose lists are current (no host sync)
 fmm_status evaluate_body(fmm_tree *t, int p, int want_phi, int want_field, double *phi, double *E);
 // graph.cu: drop a captured evaluate graph (the tree or the tuning changed)

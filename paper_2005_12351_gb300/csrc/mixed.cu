@@ -1518,41 +1518,51 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     FMM_TRY(ensure(t, t->b_ud, 8 * (size_t)(nc + 1)));      // upward counters, downward flags
     FMM_TRY(ensure(t, t->b_phi, 8 * (size_t)n));
     FMM_TRY(ensure(t, t->b_E, 24 * (size_t)n));
-    // FMM_3XTF32: the M2L runs on the tensor cores where its operator fits them
-    bool use_tc = t->prec == FMM_3XTF32 && !t->m2l_simt && tc_usable(t, s, p);
-    if (use_tc && t->n_m2l > 0) {
-        // the tensor-core plan and operator images must fit the handle's memory
-        // budget; otherwise this evaluate takes the SIMT FP32 M2L
-        const fmm_status pst = tc_prepare(t, p);
-        if (pst == FMM_EBUDGET) {
-            tc_release(t);
-            t->err.clear();
-            use_tc = false;
-        } else {
-            FMM_TRY(pst);
+    // The M2L this evaluate takes.  FMM_3XTF32: the tensor cores where the
+    // operator fits them; otherwise (and in FMM_FP32) the SIMT FP32 M2L over the
+    // same plan's tiles where its layout fits, else one block per target cell.
+    // The plan and operator images must also fit the handle's memory budget
+    // (decided when they are built, below).
+    bool use_tc = t->n_m2l > 0 && t->prec == FMM_3XTF32 && !t->m2l_simt && tc_usable(t, s, p);
+    const bool tile_ok = t->n_m2l > 0 && t->m2l_tiled && m32_usable(t, s, p, tb.harmonic, tb.n_lo);
+    bool use_tile = false;
+    auto prepare = [&]() -> fmm_status {
+        if (use_tc) {
+            const fmm_status pst = tc_prepare(t, p);
+            if (pst == FMM_EBUDGET) {
+                tc_release(t);
+                t->err.clear();
+                use_tc = false;
+            } else {
+                FMM_TRY(pst);
+            }
         }
-    }
-    // otherwise the SIMT FP32 M2L: over the same plan's tiles where its layout
-    // fits and the budget allows, else one block per target cell
-    bool use_tile = !use_tc && t->m2l_tiled && t->n_m2l > 0 &&
-                    m32_usable(t, s, p, tb.harmonic, tb.n_lo);
-    if (use_tile) {
-        const fmm_status pst = m32_prepare(t, p);
-        if (pst == FMM_EBUDGET) {
-            tc_release(t);
-            t->err.clear();
-            use_tile = false;
-        } else {
-            FMM_TRY(pst);
+        use_tile = !use_tc && tile_ok;
+        if (use_tile) {
+            const fmm_status pst = m32_prepare(t, p);
+            if (pst == FMM_EBUDGET) {
+                tc_release(t);
+                t->err.clear();
+                use_tile = false;
+            } else {
+                FMM_TRY(pst);
+            }
         }
-    }
-    if (!use_tc && !use_tile && t->d32_p != p && t->n_doff > 0) {
-        FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
-        k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
-            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr, tb.mi,
-            (float *)t->b_D32.ptr);
-        ++t->launches;
-        t->d32_p = p;
+        return FMM_OK;
+    };
+    // A plan that has to be built (new lists or p: its two host syncs) is
+    // built on the handle's side stream while the upward pass runs; it needs
+    // only the lists and the D table, both complete here.  Not while the
+    // stream is being captured (the graph's evaluate follows an ordinary one,
+    // which built the plan).
+    const bool plan_stale = (use_tc && (!t->tc_plan || t->tc_img_p != p)) ||
+                            (!use_tc && tile_ok && (!t->tc_plan || t->m32_img_p != p));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (plan_stale) FMM_TRY(cuda_check(t, cudaStreamIsCapturing(st, &cap), "capture status"));
+    const bool side = plan_stale && cap == cudaStreamCaptureStatusNone;
+    if (side) {
+        FMM_TRY(side_stream(t));
+        FMM_TRY(cuda_check(t, cudaEventRecord(t->ev_lists, st), "event"));
     }
     record(t, 6);
     const int32_t *leaves = (const int32_t *)t->b_leaves.ptr;
@@ -1588,6 +1598,25 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
         Ms = (const float *)t->b_Mh32.ptr;
     }
     record(t, 8);
+    if (side) {
+        cudaStreamWaitEvent(t->side_st, t->ev_lists, 0);
+        t->stream = t->side_st;
+        const fmm_status ps = prepare();
+        t->stream = st;
+        cudaEventRecord(t->ev_plan, t->side_st);
+        cudaStreamWaitEvent(st, t->ev_plan, 0);
+        FMM_TRY(ps);
+    } else {
+        FMM_TRY(prepare());
+    }
+    if (t->n_m2l > 0 && !use_tc && !use_tile && t->d32_p != p && t->n_doff > 0) {
+        FMM_TRY(ensure(t, t->b_D32, 4 * (size_t)t->n_doff * row4(tb.nD)));
+        k_dtables32<<<gridm(t->n_doff * tb.nD, 256), 256, 0, st>>>(
+            (const uint64_t *)t->b_dkeys.ptr, t->n_doff, tb.nD, (const double *)t->b_D.ptr, tb.mi,
+            (float *)t->b_D32.ptr);
+        ++t->launches;
+        t->d32_p = p;
+    }
     if (t->n_m2l > 0 && use_tc) {
         FMM_TRY(run_m2l_tc(t, p, Ms, row4(tb.nMh), tb.nMh, tb.nL, tb, L));
     } else if (t->n_m2l > 0 && use_tile) {
