@@ -271,7 +271,9 @@ fmm_status fmm_copy_array(const fmm_tree *t, fmm_array which, void *host_dst, si
  *   7 M2L, 8 L2L (all levels, one launch; in the FP32 forms each leaf's L2P
  *   too, when the tree has more than one level), 9 L2P (its own launch: the
  *   FP64 form, and one-level trees), 10 P2P (incl. un-permute)
- * Phases 0-2 belong to fmm_set_sources, 3-10 to fmm_evaluate. */
+ * Phases 0-2 belong to fmm_set_sources, 3-10 to fmm_evaluate.  In the FP32
+ * forms the M2L plan and operator images of new lists are built on a side
+ * stream while the upward pass runs; the M2L phase includes any wait for them. */
 #define FMM_NUM_PHASES 11
 fmm_status fmm_set_profiling(fmm_tree *t, int enable);
 fmm_status fmm_get_phase_times(const fmm_tree *t, float *ms_out /* FMM_NUM_PHASES */);
