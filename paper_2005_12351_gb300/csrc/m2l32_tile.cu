@@ -34,6 +34,7 @@ namespace {
 constexpr int kT32Threads = 128;     // one thread per target of a tile
 constexpr int kT32MaxNB = 16;        // blocks of 8 columns: n_L <= 128
 constexpr int kT32SmemMax = 232448;  // dynamic shared memory a block may opt into
+constexpr int kT32MaxSeg = 8;        // segments per warp pair of the two-target kernel
 
 struct T32Args {
     const int32_t *chunk_rb, *chunk_re;  // rows [rb, re) of each chunk
@@ -44,6 +45,12 @@ struct T32Args {
     float *partial;                      // [chunks][128][Np]
     int nchunks, ldM, nM, nq, E, Np;     // nq = float4 groups of a staged multipole row
     int mb[kT32MaxNB], boff[kT32MaxNB];
+    // two-target kernel: the column blocks dealt to the two warp pairs as
+    // segments (block, first and end float4 group of multipoles); second = the
+    // segment continues a block the other pair began (its sums are added to
+    // the other pair's at the chunk's end)
+    int nseg[2];
+    int seg_b[2][kT32MaxSeg], seg_q0[2][kT32MaxSeg], seg_q1[2][kT32MaxSeg], seg_second[2][kT32MaxSeg];
 };
 
 __device__ __forceinline__ void fma8(float (&acc)[8], const float4 &t0, const float4 &t1, float m)
@@ -163,6 +170,142 @@ __global__ void __launch_bounds__(kT32Threads) k_m2l32_tile(const T32Args a)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) acc[b][k] = 0.0f;
             }
+        }
+        cur = nxt;
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// The same sums with two targets per thread: warps 0-1 and 2-3 form two
+// pairs; thread u of a pair takes the tile's targets u and u + 64, and each
+// pair runs its share of the column blocks (segments of the blocks' multipole
+// ranges, about half of the float4 groups each), so every broadcast operator
+// value feeds two FMAs.  A block split between the pairs is summed at the
+// chunk's end: the first pair writes its part, then the second adds its own.
+template <int NS>
+__global__ void __launch_bounds__(kT32Threads, 3) k_m2l32_tile2(const T32Args a)
+{
+    extern __shared__ float4 sm4[];
+    __shared__ unsigned char s_has[2][kT32Threads];
+    const int tid = threadIdx.x, G = gridDim.x, nch = a.nchunks;
+    const int pr = tid >> 6, u = tid & 63;
+    float4 *Mst = sm4;                                          // [2][nq][128]
+    float *Tst = (float *)(sm4 + 2 * a.nq * kT32Threads);       // [2][E]
+    const int nseg = a.nseg[pr];
+    float acc[NS][2][8];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[i][0][k] = acc[i][1][k] = 0.0f;
+    int sj = blockIdx.x;
+    if (sj >= nch) return;
+    int sr = a.chunk_rb[sj], sre = a.chunk_re[sj];
+    int nrb = 0, nre = 0;
+    if (sj + G < nch) {
+        nrb = a.chunk_rb[sj + G];
+        nre = a.chunk_re[sj + G];
+    }
+    int src = a.slot[(size_t)sr * kT32Threads + tid], key = a.row_key[sr];
+    // staging as in k_m2l32_tile (each thread its own target's row), plus
+    // whether the thread's target has a pair in the row
+    auto stage = [&](int buf) {
+        T32Row w;
+        w.valid = sj < nch;
+        w.chunk = sj;
+        w.last = sr + 1 == sre;
+        w.has = false;
+        if (w.valid) {
+            s_has[buf][tid] = src >= 0;
+            const float *g = a.M + (size_t)max(src, 0) * a.ldM;
+            const uint32_t d = smem_u32(Mst + (size_t)buf * a.nq * kT32Threads + tid);
+            for (int q = 0; q < a.nq; ++q) {
+                const int left = a.nM - 4 * q;
+                cp_async16(d + 16u * kT32Threads * q, g + 4 * q, src < 0 ? 0 : 4 * min(left, 4));
+            }
+            const float *ti = a.img + (size_t)key * a.E;
+            const uint32_t td = smem_u32(Tst + (size_t)buf * a.E);
+            for (int e = 4 * tid; e < a.E; e += 4 * kT32Threads) cp_async16(td + 4u * e, ti + e, 16);
+            if (++sr == sre) {
+                sj += G;
+                sr = nrb;
+                sre = nre;
+                if (sj + G < nch) {
+                    nrb = a.chunk_rb[sj + G];
+                    nre = a.chunk_re[sj + G];
+                }
+            }
+            if (sj < nch) {
+                src = a.slot[(size_t)sr * kT32Threads + tid];
+                key = a.row_key[sr];
+            }
+        }
+        cp_async_commit();
+        return w;
+    };
+    T32Row cur = stage(0);
+    int buf = 0;
+    while (cur.valid) {
+        const T32Row nxt = stage(buf ^ 1);
+        cp_async_wait<1>();
+        __syncthreads();
+        if (__any_sync(0xffffffffu, s_has[buf][u] | s_has[buf][u + 64])) {
+            const float4 *Mb = Mst + (size_t)buf * a.nq * kT32Threads + u;
+            const float4 *Tb = (const float4 *)(Tst + (size_t)buf * a.E);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (i < nseg) {
+                    const float4 *T4 = Tb + (a.boff[a.seg_b[pr][i]] >> 2);
+                    const int q1 = a.seg_q1[pr][i];
+#pragma unroll 2
+                    for (int q = a.seg_q0[pr][i]; q < q1; ++q) {
+                        const float4 m0 = Mb[q * kT32Threads], m1 = Mb[q * kT32Threads + 64];
+                        float4 t0 = T4[8 * q + 0], t1 = T4[8 * q + 1];
+                        fma8(acc[i][0], t0, t1, m0.x);
+                        fma8(acc[i][1], t0, t1, m1.x);
+                        t0 = T4[8 * q + 2]; t1 = T4[8 * q + 3];
+                        fma8(acc[i][0], t0, t1, m0.y);
+                        fma8(acc[i][1], t0, t1, m1.y);
+                        t0 = T4[8 * q + 4]; t1 = T4[8 * q + 5];
+                        fma8(acc[i][0], t0, t1, m0.z);
+                        fma8(acc[i][1], t0, t1, m1.z);
+                        t0 = T4[8 * q + 6]; t1 = T4[8 * q + 7];
+                        fma8(acc[i][0], t0, t1, m0.w);
+                        fma8(acc[i][1], t0, t1, m1.w);
+                    }
+                }
+            }
+        }
+        __syncthreads();                         // before the next row's staging refills the other stage
+        if (cur.last) {
+            float *P = a.partial + (size_t)cur.chunk * kT32Threads * a.Np;
+            // first parts (and whole blocks), then the second parts added to them
+            for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    if (i < nseg && a.seg_second[pr][i] == pass) {
+                        const int c0 = 8 * a.seg_b[pr][i];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float4 *d = (float4 *)(P + (size_t)(u + 64 * h) * a.Np + c0);
+                            float4 v0 = make_float4(acc[i][h][0], acc[i][h][1], acc[i][h][2], acc[i][h][3]);
+                            float4 v1 = make_float4(acc[i][h][4], acc[i][h][5], acc[i][h][6], acc[i][h][7]);
+                            if (pass == 1) {
+                                const float4 w0 = d[0], w1 = d[1];
+                                v0 = make_float4(w0.x + v0.x, w0.y + v0.y, w0.z + v0.z, w0.w + v0.w);
+                                v1 = make_float4(w1.x + v1.x, w1.y + v1.y, w1.z + v1.z, w1.w + v1.w);
+                            }
+                            d[0] = v0;
+                            d[1] = v1;
+                        }
+                    }
+                }
+                __syncthreads();                 // the first parts are visible to the block
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[i][0][k] = acc[i][1][k] = 0.0f;
         }
         cur = nxt;
         buf ^= 1;
@@ -307,6 +450,42 @@ fmm_status run_m2l32_tile(fmm_tree *t, int p, const float *M, int ldM, const Dev
         a.mb[b] = Ly.mb[b];
         a.boff[b] = Ly.boff[b];
     }
+    // two targets per thread where the blocks' float4 groups split evenly into
+    // at most kT32MaxSeg segments per warp pair (in block order: the first
+    // pair takes the blocks up to half the groups, the block at the boundary
+    // split between the pairs)
+    int Q = 0;
+    for (int b = 0; b < Ly.nb; ++b) Q += Ly.mb[b] / 4;
+    const int halfQ = (Q + 1) / 2;
+    bool two = true;
+    auto add = [&](int pr, int b, int q0, int q1, int second) {
+        int &n = a.nseg[pr];
+        if (n >= kT32MaxSeg) {
+            two = false;
+            return;
+        }
+        a.seg_b[pr][n] = b;
+        a.seg_q0[pr][n] = q0;
+        a.seg_q1[pr][n] = q1;
+        a.seg_second[pr][n] = second;
+        ++n;
+    };
+    for (int b = 0, pr = 0, acc = 0; b < Ly.nb; ++b) {
+        const int qn = Ly.mb[b] / 4;
+        if (pr == 0 && acc + qn > halfQ) {
+            const int take = halfQ - acc;
+            if (take > 0) {
+                add(0, b, 0, take, 0);
+                add(1, b, take, qn, 1);
+            } else {
+                add(1, b, 0, qn, 0);
+            }
+            pr = 1;
+            continue;
+        }
+        add(pr, b, 0, qn, 0);
+        acc += qn;
+    }
     const size_t smem = t32_smem(Ly);
     auto go = [&](auto kern) {
         allow_max_dynamic_smem(kern);
@@ -317,7 +496,12 @@ fmm_status run_m2l32_tile(fmm_tree *t, int p, const float *M, int ldM, const Dev
         const int64_t grid = std::min<int64_t>(t->tc_chunks, (int64_t)std::max(per_sm, 1) * sm_count());
         kern<<<(unsigned)grid, kT32Threads, smem, st>>>(a);
     };
-    switch ((Ly.nb + 1) / 2) {
+    const int ns = std::max(a.nseg[0], a.nseg[1]);
+    if (two && ns <= 2) go(k_m2l32_tile2<2>);
+    else if (two && ns <= 4) go(k_m2l32_tile2<4>);
+    else if (two && ns <= 6) go(k_m2l32_tile2<6>);
+    else if (two) go(k_m2l32_tile2<8>);
+    else switch ((Ly.nb + 1) / 2) {
     case 1: go(k_m2l32_tile<2>); break;
     case 2: go(k_m2l32_tile<4>); break;
     case 3: go(k_m2l32_tile<6>); break;
