@@ -516,9 +516,11 @@ k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t
 // uniform set, ~0.2 % of the near field), which puts the near field's
 // rounding at the level of the FP64 form.  The FP32 loop zeroes such a pair
 // and queues it for its thread and target; when a queue of the warp is full,
-// and at the end of each staged round, every lane evaluates its own queue
-// into its own double-float sums, in queue order, so the result stays
-// deterministic.
+// and at the end of each staged round, the warp's queued pairs are dealt to
+// all its lanes, evaluated, and added by their owners to their double-float
+// sums in queue order, so the result stays deterministic.  Only the sources
+// staged near the target leaf (first in a round's order) can make close
+// pairs; the far ones run a step without the test.
 // the hardware reciprocal square root (PTX rsqrt.approx, relative error ~2^-23);
 // callers pass normal x > 0 only
 __device__ __forceinline__ float rsqrt_mufu(float x)

@@ -263,7 +263,8 @@ def test_mixed_falls_back_to_per_cell_m2l_within_budget(precision):
 
 @pytest.mark.parametrize("s,p,dist,n,h", [(1, 6, "uniform", 60_000, 1), (2, 5, "plummer", 40_000, 1),
                                            (0, 10, "plummer", 30_000, 1), (1, 6, "uniform", 40_000, 0),
-                                           (1, 3, "plummer", 20_000, 0), (0, 12, "uniform", 10_000, 1)])
+                                           (1, 3, "plummer", 20_000, 0), (0, 12, "uniform", 10_000, 1),
+                                           (0, 1, "uniform", 8_000, 1), (2, 2, "plummer", 8_000, 1)])
 @pytest.mark.parametrize("want_phi", [True, False])
 def test_fp32_tiled_m2l_matches_per_cell(orc, s, p, dist, n, h, want_phi):
     """The FP32 form's two SIMT M2L kernels -- over the tile plan (a block per
@@ -271,9 +272,11 @@ def test_fp32_tiled_m2l_matches_per_cell(orc, s, p, dist, n, h, want_phi):
     per target cell -- sum the same FP32 products in another order: the stored
     locals agree within 1e-5 column block by column block, the outputs within
     FP32 rounding, and the tiled result is within 1e-6 of the FP64 oracle.
-    Column counts: 6 to 16 blocks of 8 (the register-held sums of one thread);
-    the harmonic p = 12 has 169 columns, more than the tiled kernel holds, and
-    takes the per-cell kernel (no plan).  Field only: the columns start at
+    Column counts: 1 to 16 blocks of 8 (two targets per thread, the blocks
+    split between two warp pairs; from p = 10 one target per thread); the
+    harmonic p = 12 has 169 columns, more than the tiled kernel holds, and
+    takes the per-cell kernel (no plan).  p = 1 and 2: a single block whose
+    multipole groups are mostly padding.  Field only: the columns start at
     order 1."""
     import torch
     from gpu_util import rel_rms, to_dev
