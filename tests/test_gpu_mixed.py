@@ -74,7 +74,7 @@ def test_fp32_close_to_fp64_oracle(orc, precision, s, p, dist, n, ncrit, variant
                                        (1, 8, "plummer"), (2, 3, "plummer"), (2, 5, "plummer"),
                                        (2, 5, "uniform"), (2, 8, "uniform"), (1, 10, "uniform")])
 def test_fp32_error_within_1p1_of_fp64_truncation(orc, precision, s, p, dist):
-    """The benchmark spec's criterion, no additive term: the mixed form's error against the
+    """The precision criterion, with no additive term: the mixed form's error against the
     FP64 direct sum (oracle) is within 1.1x the FP64 FMM's, for the field and the
     potential.  Quadrupoles at p >= 5 and dipoles at p = 10 have field truncation
     errors of 1e-8..1e-7, at or below FP32 resolution."""
