@@ -461,22 +461,23 @@ k_l2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const d
     l2p32_leaf<false>(leaves[blockIdx.x], begin, end, half, o, L, tb, want_phi, want_field, phi, E, sf);
 }
 
-// All levels' L2L shifts of this form in one launch (the FP64 form's
-// k_downward: cells claimed in breadth-first order, bounded wait on the
-// parent's flag, NaN where a wait gave up), each leaf's L2P right after its
-// shift.
+// The L2L shifts of this form in two launches.  First the cells with
+// children, in breadth-first order (as the FP64 form's k_downward: a block
+// claims the next one through a counter, waits, bounded, for its parent's
+// flag, shifts, publishes; NaN where a wait gave up); inner = those cells in
+// index order.  Then the leaves, whose parents are final: each block shifts
+// its leaf and runs its L2P, with no claim and no wait (the leaves are most
+// of the cells, and one counter claimed by every block serialises them).
 __global__ void __launch_bounds__(128)
-k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t *cy,
-             const int32_t *cz, DevTables tb, float *L, unsigned *ctl, const int32_t *nchild,
-             const int32_t *begin, const int32_t *end, const double *half, const float4 *o, int want_phi,
-             int want_field, double *phi, double *E)
+k_downward32(int64_t nint, const int32_t *inner, const int32_t *parent, const int32_t *cx,
+             const int32_t *cy, const int32_t *cz, DevTables tb, float *L, unsigned *ctl)
 {
     extern __shared__ float sf[];
-    __shared__ int s_c, s_ok;
-    if (threadIdx.x == 0) s_c = (int)atomicAdd(&ctl[0], 1u);
+    __shared__ int s_k, s_ok;
+    if (threadIdx.x == 0) s_k = (int)atomicAdd(&ctl[0], 1u);
     __syncthreads();
-    const int c = s_c;
-    if (c >= nc) return;
+    if (s_k >= nint) return;
+    const int c = inner[s_k];
     const int pa = parent[c];
     if (pa >= 0) {
         if (threadIdx.x == 0) {
@@ -496,9 +497,20 @@ k_downward32(int64_t nc, const int32_t *parent, const int32_t *cx, const int32_t
         __threadfence();
         atomicExch(ctl + 1 + c, 1u);
     }
-    // a leaf's expansion is final here: its L2P follows in the same block
-    if (nchild[c] == 0)
-        l2p32_leaf<true>(c, begin, end, half, o, L, tb, want_phi, want_field, phi, E, sf);
+}
+
+__global__ void __launch_bounds__(128)
+k_downward32_leaf(const int32_t *leaves, const int32_t *parent, const int32_t *cx, const int32_t *cy,
+                  const int32_t *cz, DevTables tb, float *L, const int32_t *begin, const int32_t *end,
+                  const double *half, const float4 *o, int want_phi, int want_field, double *phi, double *E)
+{
+    extern __shared__ float sf[];
+    const int c = leaves[blockIdx.x], pa = parent[c];
+    if (pa >= 0) {
+        l2l32_cell(c, pa, cx, cy, cz, tb, L, sf);
+        __syncthreads();                 // the leaf's expansion is final: its L2P reads it back
+    }
+    l2p32_leaf<true>(c, begin, end, half, o, L, tb, want_phi, want_field, phi, E, sf);
 }
 
 // ------------------------------------------------------------------ P2P
@@ -1641,11 +1653,20 @@ fmm_status run_mixed(fmm_tree *t, int p, int want_phi, int want_field, double *p
     if (t->nlevels > 1) {
         unsigned *ctl = (unsigned *)t->b_ud.ptr + nc + 1;
         cudaMemsetAsync(ctl, 0, 4 * (size_t)(nc + 1), st);
+        const int64_t nint = nc - t->nleaves;        // cells with children: after the leaves in b_leaves
+        const int32_t *parent = (const int32_t *)t->b_parent.ptr;
+        if (nint > 0) {
+            const size_t smem_i = 4 * ((size_t)tb.nK + tb.nL);
+            allow_max_dynamic_smem(k_downward32);
+            k_downward32<<<(unsigned)nint, 128, smem_i, st>>>(nint, leaves + t->nleaves, parent, cx, cy, cz,
+                                                               tb, L, ctl);
+            ++t->launches;
+        }
         const size_t smem = 4 * std::max<size_t>((size_t)tb.nK + tb.nL, (size_t)tb.nL + kL2PThreads * 3 * P1);
-        allow_max_dynamic_smem(k_downward32);
-        k_downward32<<<(unsigned)nc, 128, smem, st>>>(
-            nc, (const int32_t *)t->b_parent.ptr, cx, cy, cz, tb, L, ctl, (const int32_t *)t->b_nchild.ptr,
-            begin, end, half, o, want_phi, want_field, (double *)t->b_phi.ptr, (double *)t->b_E.ptr);
+        allow_max_dynamic_smem(k_downward32_leaf);
+        k_downward32_leaf<<<(unsigned)t->nleaves, 128, smem, st>>>(
+            leaves, parent, cx, cy, cz, tb, L, begin, end, half, o, want_phi, want_field, (double *)t->b_phi.ptr,
+            (double *)t->b_E.ptr);
         ++t->launches;
         record(t, 10);
     } else {

@@ -547,11 +547,15 @@ __global__ void k_cell_geometry(CellArrays c, int64_t ncells, const double *box,
                          c.child[i]);
 }
 
+// leaves[0, nleaves): the leaves in index order; leaves[nleaves, ncells): the
+// cells with children in index (so breadth-first) order, for the downward pass
 __global__ void k_compact_leaves(const uint32_t *flag, const uint32_t *pos, int64_t ncells,
                                  int32_t *leaves)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < ncells && flag[i]) leaves[pos[i]] = (int32_t)i;
+    if (i >= ncells) return;
+    if (flag[i]) leaves[pos[i]] = (int32_t)i;
+    else leaves[pos[ncells] + (i - pos[i])] = (int32_t)i;
 }
 
 // ----------------------------------------------------------- traversal
