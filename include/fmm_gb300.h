@@ -268,8 +268,9 @@ fmm_status fmm_copy_array(const fmm_tree *t, fmm_array which, void *host_dst, si
  * the handle's stream) when profiling is on.  Phases, in order:
  *   0 keys+bbox, 1 sort, 2 cells, 3 lists, 4 D tables, 5 upward pass (P2M
  *   and M2M, one launch), 6 fold of the multipoles for the harmonic M2L,
- *   7 M2L, 8 L2L (all levels, one launch; in the FP32 forms each leaf's L2P
- *   too, when the tree has more than one level), 9 L2P (its own launch: the
+ *   7 M2L, 8 L2L (all levels, one launch; in the FP32 forms two: the cells
+ *   with children, then the leaves with each leaf's L2P, when the tree has
+ *   more than one level), 9 L2P (its own launch: the
  *   FP64 form, and one-level trees), 10 P2P (incl. un-permute)
  * Phases 0-2 belong to fmm_set_sources, 3-10 to fmm_evaluate.  In the FP32
  * forms the M2L plan and operator images of new lists are built on a side
