@@ -1039,7 +1039,7 @@ k_p2p32(const int32_t *leaves, const int32_t *begin, const int32_t *end, const i
                 if (__any_sync(0xffffffffu, qa + qb > 0)) flush();   // staged sources change next round
             }
             // the far slots: no close pairs, nothing queued
-#pragma unroll 2
+#pragma unroll 4
             for (; it < steps; ++it) step(it, far_s);
             {
                 if constexpr (TT == 1) {
