@@ -33,10 +33,10 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 
 # DRAM bytes (read + write) per particle of the dominant kernels, from full ncu captures of
 # the 125k-dipole case (same leaf occupancy; the kernels' traffic grows with the particles):
-# k_p2p_sym 7.546 MB + 0.183 MB, k_p2p32 11.207 MB + 0 MB per launch
+# k_p2p_sym 7.546 MB + 0.183 MB, k_p2p32 11.210 MB + 0 MB per launch
 # (profiles/fp64_pass_kernels_dipole_125k_p6.md, profiles/k_p2p32_k_m2l32_tile2_fp32_dipole_125k_p6.md)
-TRAFFIC_PER_PARTICLE = {("fp64", 1): 7.7291e6 / 125_000, ("fp32", 1): 11.2074e6 / 125_000,
-                        ("3xtf32", 1): 11.2074e6 / 125_000}
+TRAFFIC_PER_PARTICLE = {("fp64", 1): 7.7291e6 / 125_000, ("fp32", 1): 11.2097e6 / 125_000,
+                        ("3xtf32", 1): 11.2097e6 / 125_000}
 
 
 def flops_per_pair(s: int, want_phi: bool, want_field: bool) -> int:
