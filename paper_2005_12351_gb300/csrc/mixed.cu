@@ -112,7 +112,9 @@ __device__ __forceinline__ void p2m32_leaf(int c, const int32_t *begin, const in
     float *Ssm = mono + kChunk * nK1;              // [chunk][8], padded with zeros
     Ssm = (float *)(((uintptr_t)Ssm + 15) & ~(uintptr_t)15);
     const int b = begin[c], e = end[c];
-    const float inv_h = (float)(1.0 / half[c]);    // a power of two
+    // h is a power of two: 1/h from its exponent (exact, as the FP64 quotient
+    // rounded to float would be), no FP64 division in every thread
+    const float inv_h = ldexpf(1.0f, -ilogb(half[c]));
     const int nS32 = nS == 6 ? 7 : nS;
     df32 acc[kPer];                                // double-float: no FP64 in the pass
 #pragma unroll
@@ -404,8 +406,8 @@ __device__ __forceinline__ void l2p32_leaf(int c, const int32_t *begin, const in
     float *apow = Lsm + tb.nL;                             // [particles of a chunk][3][P1]
     const int b = begin[c], e = end[c], nt = e - b;
     const double h = half[c];
-    const float inv_h = (float)(1.0 / h);
     const int eh = ilogb(h);
+    const float inv_h = ldexpf(1.0f, -eh);                 // h = 2^eh: exact, no FP64 division
     const double sphi = ldexp(1.0, -(tb.s + 1) * eh), sfield = ldexp(1.0, -(tb.s + 2) * eh);
     int tp = 1;
     while (tp < 32 && 2 * tp * nt <= kL2PThreads) tp *= 2;
